@@ -1,0 +1,144 @@
+/*
+ * rpca.h -- C ABI of the GB300 AccAltProj library (robust PCA by accelerated alternating
+ * projections, Cai, Cai & Wei, arXiv 1711.05519).
+ *
+ * Problem (Eq. (1)): split an m x n matrix D into L + S with rank(L) <= r and S sparse.
+ * The library runs Algorithm 3 (initialisation) and Algorithm 1 (the iteration) on one
+ * GPU.  Every m x n step happens in one fused streaming pass over D per iteration; the
+ * O((m+n) r) steps (QR, 2r x 2r SVD, trim) run in small device kernels.
+ *
+ * Conventions for every call below:
+ *   - Matrices are row-major.  D has leading dimension ld >= n (in elements).
+ *   - Unless a name ends in _host, every pointer argument is a DEVICE pointer.
+ *   - All device work is enqueued on the CUDA stream given to rpca_create (NULL = the
+ *     legacy default stream).  Calls return after enqueueing, except where a host value
+ *     is needed (stated per call).
+ *   - No exception crosses the ABI.  A context is not thread-safe; separate contexts are.
+ *   - Return values are rpca_status codes; rpca_status_string() names them.
+ */
+#ifndef RPCA_H
+#define RPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RPCA_OK = 0,
+  RPCA_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unsupported rank or mode      */
+  RPCA_ERR_CUDA = 2,          /* a CUDA runtime call failed                             */
+  RPCA_ERR_NUMERICAL = 3,     /* NaN/Inf in D or in the factors                         */
+  RPCA_ERR_CAPACITY = 4,      /* output buffer too small; required size is returned     */
+  RPCA_ERR_NOT_CONVERGED = 5, /* max_iter reached; outputs are valid (last iterate)     */
+  RPCA_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                     */
+  RPCA_ERR_STATE = 7          /* call out of order (e.g. iterate before init)           */
+} rpca_status;
+
+typedef enum { RPCA_DTYPE_F64 = 0, RPCA_DTYPE_F32 = 1 } rpca_dtype;
+
+/* Arithmetic of the fused pass.  The O((m+n) r) steps always run in FP64. */
+typedef enum { RPCA_PREC_FP64 = 0, RPCA_PREC_FP32 = 1 } rpca_precision;
+
+/* Threshold rule.  PAPER: zeta_{k+1} = beta (sigma_{r+1} + gamma^{k+1} sigma_1) of
+ * P_T(D - S_k) (Algorithm 1).  SIMPLE: zeta_{k+1} = beta gamma^{k+1} sigma_1.
+ * EXTERNAL: the caller sets zeta before each iteration with rpca_set_zeta. */
+typedef enum { RPCA_ZETA_PAPER = 0, RPCA_ZETA_SIMPLE = 1, RPCA_ZETA_EXTERNAL = 2 } rpca_zeta_mode;
+
+typedef struct {
+  double beta;       /* threshold parameter of Algorithm 1                               */
+  double gamma;      /* convergence-rate parameter, 0 <= gamma < 1                        */
+  double tol;        /* stop when err_k < tol (Eq. (11))                                  */
+  double beta_init;  /* Algorithm 3 threshold parameter; 0 selects 2 beta (Section 3)     */
+  double mu_trim;    /* incoherence level for Trim; 0 selects 2 beta sqrt(mn) / r         */
+  int max_iter;      /* iteration cap; Section 3 uses 100                                 */
+  int trim;          /* 1: Trim (Algorithm 2) before each projection; 0: skip it          */
+  int precision;     /* rpca_precision                                                   */
+  int zeta_mode;     /* rpca_zeta_mode                                                   */
+  int init_max_passes; /* cap on D passes of each subspace iteration in rpca_init; 0=40   */
+  double init_tol;   /* relative change of the top singular values that ends a subspace
+                        iteration; 0 selects 1e-13 (FP64) / 1e-6 (FP32)                  */
+} rpca_params;
+
+typedef struct {
+  int k;               /* iteration index of L_k, S_k                                     */
+  double err;          /* err_k = ||D - L_k - S_k||_F / ||D||_F                           */
+  double zeta;         /* zeta_k used for S_k                                            */
+  double sigma1;       /* sigma_1 of P_T(D - S_k) (0 if the iteration stopped at k)       */
+  double sigma_r1;     /* sigma_{r+1} of P_T(D - S_k)                                    */
+  int64_t nnz;         /* |supp(S_k)|                                                    */
+} rpca_iter_stats;
+
+typedef struct rpca_ctx rpca_ctx;
+
+const char* rpca_status_string(int status);
+
+/* Fills *p with the defaults above (beta = gamma = tol = 0 must still be set). */
+int rpca_params_default(rpca_params* p);
+
+/* Creates a context.  `stream` is a cudaStream_t (may be NULL).  The context owns its
+ * device workspace; rpca_destroy frees it. */
+int rpca_create(rpca_ctx** ctx, const rpca_params* params, void* stream);
+void rpca_destroy(rpca_ctx* ctx);
+
+/* Algorithm 3 (initialisation by two steps of AltProj).
+ *   D: device, m x n, row-major with leading dimension ld, element type `dtype`.
+ *   The context BORROWS D when dtype matches the precision (FP64/F64, FP32/F32): the
+ *   caller keeps D alive and unchanged until rpca_destroy or the next rpca_init.  With
+ *   an F64 input and FP32 precision the context keeps its own FP32 copy.
+ *   r: target rank, 1 <= r <= 16, 2r <= min(m, n).
+ * sigma_1(D) and the top-r SVD of D - S_{-1} are computed by block subspace iteration
+ * with one fused pass over D per step.  Synchronises the stream once per pass. */
+int rpca_init(rpca_ctx* ctx, const void* D, int64_t m, int64_t n, int64_t ld, int dtype, int r);
+
+/* Runs up to n_iters iterations of Algorithm 1 (each: Trim, one fused pass giving S_k
+ * and err_k, then the QR + 2r x 2r SVD route to L_{k+1} and zeta_{k+1}).  Stops early
+ * when err_k < tol or k reaches max_iter.  `stats` (host, may be NULL) receives one
+ * entry per pass run; *n_done (host, may be NULL) their number.  Returns RPCA_OK when
+ * converged, RPCA_ERR_NOT_CONVERGED when n_iters passes ran without convergence (call
+ * again to continue) or max_iter was hit.  Synchronises the stream at its end. */
+int rpca_iterate(rpca_ctx* ctx, int n_iters, rpca_iter_stats* stats, int* n_done);
+
+/* Sets zeta_k for the next pass (zeta_mode EXTERNAL). */
+int rpca_set_zeta(rpca_ctx* ctx, double zeta);
+
+/* Copies the current low-rank factors L_k = U diag(sigma) V^T into caller-owned device
+ * buffers: U (m x r), sigma (r), V (n x r), all double, row-major. */
+int rpca_get_lowrank(rpca_ctx* ctx, double* U, double* sigma, double* V);
+
+/* Writes supp(S_k) = {(i,j) : |D_ij - L_k,ij| > zeta_k} (Eq. (10)) as linear indices
+ * i*n + j in ascending order with the values S_ij = D_ij - L_k,ij, into caller-owned
+ * device buffers idx (int64) and val (double).  If cap < nnz returns RPCA_ERR_CAPACITY
+ * and writes only *nnz (host).  Takes three passes over D; synchronises the stream. */
+int rpca_get_sparse(rpca_ctx* ctx, int64_t* idx, double* val, int64_t cap, int64_t* nnz);
+
+/* One call: init + iterate to tolerance + outputs.  D, U, sigma, V, s_idx, s_val are
+ * device pointers; D is float32, m x n, leading dimension n; FP32 precision.  *nnz,
+ * *iters, *err are host.  If s_cap < nnz the sparse part is not written and
+ * RPCA_ERR_CAPACITY is returned with the other outputs valid. */
+int rpca_solve(const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol,
+               double* U, double* sigma, double* V, int64_t* s_idx, double* s_val, int64_t s_cap,
+               int64_t* nnz, int* iters, double* err);
+
+/* As rpca_solve, with every array in HOST memory (D float32; outputs double/int64).  The
+ * host-to-device copy of D and the device-to-host copies of the outputs are part of the
+ * call. */
+int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, double gamma,
+                    double tol, double* U, double* sigma, double* V, int64_t* s_idx,
+                    double* s_val, int64_t s_cap, int64_t* nnz, int* iters, double* err);
+
+/* Diagnostics.  With profiling on, the context records a CUDA event pair around every
+ * kernel it launches on its stream.  rpca_get_profile (host outputs, any may be NULL)
+ * returns, since profiling was switched on, the summed device time and the number of
+ * fused-pass launches that did work (passes skipped after convergence are not counted),
+ * and the same for all other kernels of the library.  Synchronises the stream. */
+int rpca_set_profiling(rpca_ctx* ctx, int on);
+int rpca_get_profile(rpca_ctx* ctx, double* pass_ms, int64_t* pass_launches, double* other_ms,
+                     int64_t* other_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPCA_H */

@@ -1,0 +1,604 @@
+// C ABI of the AccAltProj library (include/rpca.h): context, workspace and the host loop
+// that enqueues the fused pass and the tall-skinny kernel.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/rpca.h"
+#include "common.cuh"
+
+namespace rpca {
+cudaError_t launch_pass_f32(int R, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_f64(int R, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_extract_count_f32(int R, const ExtractArgs& a, cudaStream_t s);
+cudaError_t launch_extract_count_f64(int R, const ExtractArgs& a, cudaStream_t s);
+cudaError_t launch_extract_write_f32(int R, const ExtractArgs& a, cudaStream_t s);
+cudaError_t launch_extract_write_f64(int R, const ExtractArgs& a, cudaStream_t s);
+PassGeom pass_geometry_f32(int R);
+PassGeom pass_geometry_f64(int R);
+
+PassGeom pass_geometry(int prec, int R) { return prec == PREC_F32 ? pass_geometry_f32(R) : pass_geometry_f64(R); }
+cudaError_t launch_fused_pass(int prec, int R, const PassArgs& a, cudaStream_t s) {
+  return prec == PREC_F32 ? launch_pass_f32(R, a, s) : launch_pass_f64(R, a, s);
+}
+cudaError_t launch_extract_count(int prec, int R, const ExtractArgs& a, cudaStream_t s) {
+  return prec == PREC_F32 ? launch_extract_count_f32(R, a, s) : launch_extract_count_f64(R, a, s);
+}
+cudaError_t launch_extract_write(int prec, int R, const ExtractArgs& a, cudaStream_t s) {
+  return prec == PREC_F32 ? launch_extract_write_f32(R, a, s) : launch_extract_write_f64(R, a, s);
+}
+}  // namespace rpca
+
+using namespace rpca;
+
+struct rpca_ctx {
+  rpca_params p;
+  cudaStream_t stream = nullptr;
+  int device = 0, small_grid = 0;
+  int prec = PREC_F32;
+  size_t tsize = 4;
+  int64_t m = 0, n = 0, ld = 0;
+  int r = 0, Rr = 0, b = 0, Rb = 0;
+  const void* D = nullptr;
+  void* Down = nullptr;
+  int vec = 0;
+  // workspace
+  double *U = nullptr, *sig = nullptr, *V = nullptr, *Ut = nullptr, *Vt = nullptr, *Y1 = nullptr,
+         *Y2 = nullptr, *part = nullptr;
+  void *Wc = nullptr, *Vc = nullptr, *Utc = nullptr, *Vtc = nullptr, *P1 = nullptr, *P2 = nullptr;
+  double* resP = nullptr;
+  unsigned long long* nnzP = nullptr;
+  DevState* st = nullptr;
+  DevStats* stats = nullptr;
+  int* h_flags = nullptr;  // pinned: done, k, status, conv
+  unsigned long long *rowcnt = nullptr, *rowoff = nullptr;
+  bool ready = false;
+  // allocation signature of the current workspace
+  int64_t ws_m = -1, ws_n = -1;
+  int ws_r = -1;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pass, ev_other;
+  double pass_ms = 0, other_ms = 0;
+  int64_t pass_n = 0, other_n = 0;
+};
+
+namespace {
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return RPCA_ERR_CUDA; \
+  } while (0)
+
+void free_workspace(rpca_ctx* c) {
+  void** ptrs[] = {(void**)&c->U,   (void**)&c->sig,  (void**)&c->V,    (void**)&c->Ut,   (void**)&c->Vt,
+                   (void**)&c->Y1,  (void**)&c->Y2,   (void**)&c->part, &c->Wc,           &c->Vc,
+                   &c->Utc,         &c->Vtc,          &c->P1,           &c->P2,           (void**)&c->resP,
+                   (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
+                   &c->Down};
+  for (void** p : ptrs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  c->ready = false;
+}
+
+cudaEvent_t take_event(rpca_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Event pair around one launch: call with begin=true before and begin=false after.
+void prof_mark(rpca_ctx* c, bool pass, bool begin) {
+  if (!c->prof) return;
+  auto& v = pass ? c->ev_pass : c->ev_other;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->stream);
+  if (begin)
+    v.push_back({e, nullptr});
+  else
+    v.back().second = e;
+}
+
+// Accumulates the recorded pairs (the stream must be synchronised); only the first
+// `effective_pass` pass pairs count (later ones were skipped on the device).
+void prof_collect(rpca_ctx* c, int64_t effective_pass) {
+  auto drain = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, double& ms, int64_t& n, int64_t lim) {
+    int64_t i = 0;
+    for (auto& pr : v) {
+      if (pr.second && (lim < 0 || i < lim)) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, pr.first, pr.second);
+        ms += t;
+        ++n;
+      }
+      ++i;
+      c->ev_free.push_back(pr.first);
+      if (pr.second) c->ev_free.push_back(pr.second);
+    }
+    v.clear();
+  };
+  drain(c->ev_pass, c->pass_ms, c->pass_n, effective_pass);
+  drain(c->ev_other, c->other_ms, c->other_n, -1);
+}
+
+struct Grid {
+  int n_p1, n_p2, n_cta;
+};
+Grid pass_grid(const rpca_ctx* c, int R) {
+  const PassGeom g = pass_geometry(c->prec, R);
+  const int gx = (int)((c->n + g.BW - 1) / g.BW), gy = (int)((c->m + g.BH - 1) / g.BH);
+  return Grid{gx, gy, gx * gy};
+}
+
+int run_pass(rpca_ctx* c, int R) {
+  PassArgs a;
+  a.D = c->D;
+  a.ld = c->ld;
+  a.m = (int)c->m;
+  a.n = (int)c->n;
+  a.W = c->Wc;
+  a.V = c->Vc;
+  a.Ut = c->Utc;
+  a.Vt = c->Vtc;
+  a.st = c->st;
+  a.P1 = c->P1;
+  a.P2 = c->P2;
+  a.resP = c->resP;
+  a.nnzP = c->nnzP;
+  a.vec = c->vec;
+  prof_mark(c, true, true);
+  CK(launch_fused_pass(c->prec, R, a, c->stream));
+  prof_mark(c, true, false);
+  return RPCA_OK;
+}
+
+int run_small(rpca_ctx* c, const SmallArgs& a) {
+  prof_mark(c, false, true);
+  CK(launch_small(a, c->small_grid, c->stream));
+  prof_mark(c, false, false);
+  return RPCA_OK;
+}
+
+SmallArgs small_args(rpca_ctx* c, int mode, int R) {
+  SmallArgs a;
+  memset(&a, 0, sizeof(a));
+  const Grid g = pass_grid(c, R);
+  a.mode = mode;
+  a.m = (int)c->m;
+  a.n = (int)c->n;
+  a.r = c->r;
+  a.R = R;
+  a.b = c->b;
+  a.prec = c->prec;
+  a.n_p1 = g.n_p1;
+  a.n_p2 = g.n_p2;
+  a.n_cta = g.n_cta;
+  a.P1 = c->P1;
+  a.P2 = c->P2;
+  a.resP = c->resP;
+  a.nnzP = c->nnzP;
+  a.U = c->U;
+  a.sig = c->sig;
+  a.V = c->V;
+  a.Ut = c->Ut;
+  a.Vt = c->Vt;
+  a.Y1 = c->Y1;
+  a.Y2 = c->Y2;
+  a.part = c->part;
+  a.Wc = c->Wc;
+  a.Vc = c->Vc;
+  a.Utc = c->Utc;
+  a.Vtc = c->Vtc;
+  a.Rc = c->Rb;
+  a.Rit = c->Rr;
+  a.st = c->st;
+  a.stats = c->stats;
+  a.init_tol = c->p.init_tol;
+  a.seed = 0x243f6a8885a308d3ull;
+  return a;
+}
+
+int read_flags(rpca_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_flags, &c->st->k, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPCA_OK;
+}
+// DevState layout: k, done, status, conv are consecutive ints.
+inline int flag_k(const rpca_ctx* c) { return c->h_flags[0]; }
+inline int flag_done(const rpca_ctx* c) { return c->h_flags[1]; }
+inline int flag_status(const rpca_ctx* c) { return c->h_flags[2]; }
+inline int flag_conv(const rpca_ctx* c) { return c->h_flags[3]; }
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  return RPCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rpca_status_string(int s) {
+  switch (s) {
+    case RPCA_OK: return "RPCA_OK";
+    case RPCA_ERR_INVALID_ARG: return "RPCA_ERR_INVALID_ARG";
+    case RPCA_ERR_CUDA: return "RPCA_ERR_CUDA";
+    case RPCA_ERR_NUMERICAL: return "RPCA_ERR_NUMERICAL";
+    case RPCA_ERR_CAPACITY: return "RPCA_ERR_CAPACITY";
+    case RPCA_ERR_NOT_CONVERGED: return "RPCA_ERR_NOT_CONVERGED";
+    case RPCA_ERR_TIMEOUT: return "RPCA_ERR_TIMEOUT";
+    case RPCA_ERR_STATE: return "RPCA_ERR_STATE";
+  }
+  return "RPCA_UNKNOWN_STATUS";
+}
+
+int rpca_params_default(rpca_params* p) {
+  if (!p) return RPCA_ERR_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  p->max_iter = 100;
+  p->trim = 1;
+  p->precision = RPCA_PREC_FP32;
+  p->zeta_mode = RPCA_ZETA_PAPER;
+  return RPCA_OK;
+}
+
+int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
+  if (!out || !params) return RPCA_ERR_INVALID_ARG;
+  *out = nullptr;
+  const rpca_params& p = *params;
+  if (!(p.beta > 0) || !(p.gamma >= 0 && p.gamma < 1) || !(p.tol >= 0) || p.max_iter < 0 ||
+      (p.precision != RPCA_PREC_FP32 && p.precision != RPCA_PREC_FP64) || p.zeta_mode < 0 || p.zeta_mode > 2 ||
+      p.beta_init < 0 || p.mu_trim < 0)
+    return RPCA_ERR_INVALID_ARG;
+  rpca_ctx* c = new (std::nothrow) rpca_ctx();
+  if (!c) return RPCA_ERR_CUDA;
+  c->p = p;
+  if (c->p.init_max_passes <= 0) c->p.init_max_passes = 40;
+  c->prec = (p.precision == RPCA_PREC_FP32) ? PREC_F32 : PREC_F64;
+  c->tsize = (c->prec == PREC_F32) ? 4 : 8;
+  if (c->p.init_tol <= 0) c->p.init_tol = (c->prec == PREC_F32) ? 1e-6 : 1e-13;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess || cudaMallocHost((void**)&c->h_flags, 8 * sizeof(int)) != cudaSuccess) {
+    delete c;
+    return RPCA_ERR_CUDA;
+  }
+  c->small_grid = small_grid_size(c->device);
+  *out = c;
+  return RPCA_OK;
+}
+
+void rpca_destroy(rpca_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  prof_collect(c, 0);
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  free_workspace(c);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  delete c;
+}
+
+int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int dtype, int r) {
+  if (!c || !D || m < 1 || n < 1 || ld < n || r < 1 || r > kMaxR || 2 * (int64_t)r > (m < n ? m : n) ||
+      (dtype != RPCA_DTYPE_F32 && dtype != RPCA_DTYPE_F64) || m > (1ll << 30) || n > (1ll << 30) ||
+      m * n > (1ll << 40))
+    return RPCA_ERR_INVALID_ARG;
+  const bool reuse = c->U && c->ws_m == m && c->ws_n == n && c->ws_r == r;
+  if (!reuse) free_workspace(c);
+  c->ready = false;
+  c->m = m;
+  c->n = n;
+  c->r = r;
+  c->Rr = padded_rank(r);
+  int b = (2 * r <= 16) ? 2 * r : 16;
+  const int64_t mn_min = m < n ? m : n;
+  if (b > mn_min) b = (int)(mn_min & ~1ll);
+  if (b < r) b = r + (r & 1);
+  c->b = b;
+  c->Rb = padded_rank(b);
+  if (c->Rr < 0 || c->Rb < 0) return RPCA_ERR_INVALID_ARG;
+  const int want = (c->prec == PREC_F32) ? RPCA_DTYPE_F32 : RPCA_DTYPE_F64;
+  if (dtype == want) {
+    c->D = D;
+    c->ld = ld;
+  } else {
+    if (!c->Down) CK(cudaMalloc(&c->Down, (size_t)m * n * c->tsize));
+    if (dtype == RPCA_DTYPE_F64)
+      CK(launch_convert_f64_to_f32((const double*)D, ld, (float*)c->Down, (int)m, (int)n, c->stream));
+    else
+      CK(launch_convert_f32_to_f64((const float*)D, ld, (double*)c->Down, (int)m, (int)n, c->stream));
+    c->D = c->Down;
+    c->ld = n;
+  }
+  c->vec = ((reinterpret_cast<uintptr_t>(c->D) & 15) == 0 && ((c->ld * (int64_t)c->tsize) & 15) == 0) ? 1 : 0;
+
+  const int w = c->b > c->r ? c->b : c->r;
+  const int Rmax = c->Rb > c->Rr ? c->Rb : c->Rr;
+  size_t p1 = 0, p2 = 0, ncta = 0;
+  for (int R : {c->Rr, c->Rb}) {
+    const Grid g = pass_grid(c, R);
+    p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
+    p2 = p2 > (size_t)g.n_p2 * n * R ? p2 : (size_t)g.n_p2 * n * R;
+    ncta = ncta > (size_t)g.n_cta ? ncta : (size_t)g.n_cta;
+  }
+  int st = RPCA_OK;
+  if (!reuse) {
+  if ((st = dalloc(&c->U, (size_t)m * r)) || (st = dalloc(&c->sig, 16)) || (st = dalloc(&c->V, (size_t)n * r)) ||
+      (st = dalloc(&c->Ut, (size_t)m * w)) || (st = dalloc(&c->Vt, (size_t)n * w)) ||
+      (st = dalloc(&c->Y1, (size_t)m * w)) || (st = dalloc(&c->Y2, (size_t)n * w)) ||
+      (st = dalloc(&c->part, (size_t)c->small_grid * 4 * 256)) || (st = dalloc(&c->resP, ncta)) ||
+      (st = dalloc(&c->nnzP, ncta)) || (st = dalloc(&c->st, 1)) || (st = dalloc(&c->stats, (size_t)c->p.max_iter + 2)))
+    return st;
+  CK(cudaMalloc(&c->Wc, (size_t)m * Rmax * c->tsize));
+  CK(cudaMalloc(&c->Utc, (size_t)m * Rmax * c->tsize));
+  CK(cudaMalloc(&c->Vc, (size_t)n * Rmax * c->tsize));
+  CK(cudaMalloc(&c->Vtc, (size_t)n * Rmax * c->tsize));
+  CK(cudaMalloc(&c->P1, p1 * c->tsize));
+  CK(cudaMalloc(&c->P2, p2 * c->tsize));
+  c->ws_m = m;
+  c->ws_n = n;
+  c->ws_r = r;
+  }
+  CK(cudaMemsetAsync(c->stats, 0, sizeof(DevStats) * ((size_t)c->p.max_iter + 2), c->stream));
+  CK(cudaMemsetAsync(c->sig, 0, 16 * sizeof(double), c->stream));
+
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  const double root = sqrt((double)m * (double)n);
+  h.beta = c->p.beta;
+  h.gamma = c->p.gamma;
+  h.tol = c->p.tol;
+  h.beta_init = c->p.beta_init > 0 ? c->p.beta_init : 2.0 * c->p.beta;
+  h.mu_trim = c->p.mu_trim > 0 ? c->p.mu_trim : 2.0 * c->p.beta * root / r;
+  h.max_iter = c->p.max_iter;
+  h.zeta_mode = c->p.zeta_mode;
+  h.trim = c->p.trim;
+  h.zeta = INFINITY;
+  CK(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+
+  // Algorithm 3.  Phase A: sigma_1(D) with L = 0 and no threshold; phase B: top-r SVD of
+  // D - S_{-1} (the pass with L = 0 and zeta_{-1} keeps exactly D_ij where |D_ij| <= zeta).
+  SmallArgs ra = small_args(c, SM_RAND, c->Rb);
+  if ((st = run_small(c, ra))) return st;
+  for (int phase = 0; phase < 2; ++phase) {
+    bool conv = false;
+    for (int q = 0; q < c->p.init_max_passes && !conv; ++q) {
+      if ((st = run_pass(c, c->Rb))) return st;
+      SmallArgs a = small_args(c, SM_RR, c->Rb);
+      a.init_phase = phase;
+      a.rr_first = (q == 0);
+      a.rr_force = (q == c->p.init_max_passes - 1);
+      if ((st = run_small(c, a))) return st;
+      if ((st = read_flags(c))) return st;
+      prof_collect(c, -1);
+      if (flag_status(c)) return flag_status(c);
+      conv = flag_conv(c) != 0;
+    }
+  }
+  c->ready = true;
+  return RPCA_OK;
+}
+
+int rpca_set_zeta(rpca_ctx* c, double zeta) {
+  if (!c || !c->ready || !(zeta >= 0)) return RPCA_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(&c->st->zeta, &zeta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  return RPCA_OK;
+}
+
+int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
+  if (n_done) *n_done = 0;
+  if (!c || n_iters < 0) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  int st;
+  if ((st = read_flags(c))) return st;
+  const int k0 = flag_k(c);
+  int done = flag_done(c);
+  int launched = 0;
+  while (!done && launched < n_iters) {
+    const int chunk = (n_iters - launched) < 8 ? (n_iters - launched) : 8;
+    for (int i = 0; i < chunk; ++i) {
+      if ((st = run_pass(c, c->Rr))) return st;
+      if ((st = run_small(c, small_args(c, SM_UPDATE, c->Rr)))) return st;
+    }
+    launched += chunk;
+    if ((st = read_flags(c))) return st;
+    if (flag_status(c)) return flag_status(c);
+    done = flag_done(c);
+  }
+  if ((st = read_flags(c))) return st;
+  const int k1 = flag_k(c);
+  int count = k1 - k0 + (flag_done(c) ? 1 : 0);
+  if (count > n_iters) count = n_iters;
+  if (count < 0) count = 0;
+  prof_collect(c, count);
+  std::vector<DevStats> hs((size_t)(count > 0 ? count : 1));
+  if (count > 0) {
+    CK(cudaMemcpyAsync(hs.data(), c->stats + k0, sizeof(DevStats) * count, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (out)
+    for (int i = 0; i < count; ++i) {
+      out[i].k = hs[i].k;
+      out[i].err = hs[i].err;
+      out[i].zeta = hs[i].zeta;
+      out[i].sigma1 = hs[i].sigma1;
+      out[i].sigma_r1 = hs[i].sigma_r1;
+      out[i].nnz = hs[i].nnz;
+    }
+  if (n_done) *n_done = count;
+  if (flag_done(c)) {
+    DevStats last;
+    CK(cudaMemcpyAsync(&last, c->stats + k1, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return (last.err < c->p.tol) ? RPCA_OK : RPCA_ERR_NOT_CONVERGED;
+  }
+  return RPCA_ERR_NOT_CONVERGED;
+}
+
+int rpca_get_lowrank(rpca_ctx* c, double* U, double* sigma, double* V) {
+  if (!c || !U || !sigma || !V) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(sigma, c->sig, sizeof(double) * c->r, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(V, c->V, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToDevice, c->stream));
+  return RPCA_OK;
+}
+
+int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t* nnz) {
+  if (!c || !nnz || cap < 0 || (cap > 0 && (!idx || !val))) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  if (!c->rowcnt) {
+    CK(cudaMalloc((void**)&c->rowcnt, sizeof(unsigned long long) * c->m));
+    CK(cudaMalloc((void**)&c->rowoff, sizeof(unsigned long long) * (c->m + 1)));
+  }
+  ExtractArgs a;
+  a.D = c->D;
+  a.ld = c->ld;
+  a.m = (int)c->m;
+  a.n = (int)c->n;
+  a.W = c->Wc;
+  a.V = c->Vc;
+  a.st = c->st;
+  a.rowcnt = c->rowcnt;
+  a.rowoff = c->rowoff;
+  a.idx = (long long*)idx;
+  a.val = val;
+  a.vec = c->vec;
+  prof_mark(c, false, true);
+  CK(launch_extract_count(c->prec, c->Rr, a, c->stream));
+  prof_mark(c, false, false);
+  prof_mark(c, false, true);
+  CK(launch_scan_rows(c->rowcnt, c->rowoff, (int)c->m, c->stream));
+  prof_mark(c, false, false);
+  unsigned long long total = 0;
+  CK(cudaMemcpyAsync(&total, c->rowoff + c->m, sizeof(total), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *nnz = (int64_t)total;
+  if ((int64_t)total > cap) {
+    prof_collect(c, 0);
+    return RPCA_ERR_CAPACITY;
+  }
+  prof_mark(c, false, true);
+  CK(launch_extract_write(c->prec, c->Rr, a, c->stream));
+  prof_mark(c, false, false);
+  CK(cudaStreamSynchronize(c->stream));
+  prof_collect(c, 0);
+  return RPCA_OK;
+}
+
+int rpca_set_profiling(rpca_ctx* c, int on) {
+  if (!c) return RPCA_ERR_INVALID_ARG;
+  CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+  prof_collect(c, 0);
+  c->prof = on != 0;
+  c->pass_ms = c->other_ms = 0;
+  c->pass_n = c->other_n = 0;
+  return RPCA_OK;
+}
+
+int rpca_get_profile(rpca_ctx* c, double* pass_ms, int64_t* pass_launches, double* other_ms,
+                     int64_t* other_launches) {
+  if (!c) return RPCA_ERR_INVALID_ARG;
+  CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+  prof_collect(c, 0);
+  if (pass_ms) *pass_ms = c->pass_ms;
+  if (pass_launches) *pass_launches = c->pass_n;
+  if (other_ms) *other_ms = c->other_ms;
+  if (other_launches) *other_launches = c->other_n;
+  return RPCA_OK;
+}
+
+static int solve_device(const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol,
+                        double* U, double* sigma, double* V, int64_t* s_idx, double* s_val, int64_t s_cap,
+                        int64_t* nnz, int* iters, double* err, cudaStream_t stream) {
+  rpca_params p;
+  rpca_params_default(&p);
+  p.beta = beta;
+  p.gamma = gamma;
+  p.tol = tol;
+  rpca_ctx* c = nullptr;
+  int st = rpca_create(&c, &p, stream);
+  if (st) return st;
+  int result = rpca_init(c, D, m, n, n, RPCA_DTYPE_F32, r);
+  if (!result) {
+    std::vector<rpca_iter_stats> hs((size_t)p.max_iter + 1);
+    int done = 0;
+    result = rpca_iterate(c, p.max_iter + 1, hs.data(), &done);
+    if (iters) *iters = done > 0 ? hs[done - 1].k : 0;
+    if (err) *err = done > 0 ? hs[done - 1].err : NAN;
+    if (result == RPCA_OK || result == RPCA_ERR_NOT_CONVERGED) {
+      int s2 = rpca_get_lowrank(c, U, sigma, V);
+      if (!s2) s2 = rpca_get_sparse(c, s_idx, s_val, s_cap, nnz);
+      if (s2) result = s2;
+    }
+  }
+  rpca_destroy(c);
+  return result;
+}
+
+int rpca_solve(const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol, double* U,
+               double* sigma, double* V, int64_t* s_idx, double* s_val, int64_t s_cap, int64_t* nnz, int* iters,
+               double* err) {
+  if (!D || !U || !sigma || !V || !nnz) return RPCA_ERR_INVALID_ARG;
+  return solve_device(D, m, n, r, beta, gamma, tol, U, sigma, V, s_idx, s_val, s_cap, nnz, iters, err, nullptr);
+}
+
+int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol, double* U,
+                    double* sigma, double* V, int64_t* s_idx, double* s_val, int64_t s_cap, int64_t* nnz, int* iters,
+                    double* err) {
+  if (!D || !U || !sigma || !V || !nnz || m < 1 || n < 1 || r < 1 || r > kMaxR || s_cap < 0 ||
+      (s_cap > 0 && (!s_idx || !s_val)))
+    return RPCA_ERR_INVALID_ARG;
+  float* dD = nullptr;
+  double *dU = nullptr, *dS = nullptr, *dV = nullptr, *dval = nullptr;
+  int64_t* didx = nullptr;
+  cudaStream_t s = nullptr;
+  int result = RPCA_OK;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RPCA_ERR_CUDA;
+  const size_t cap = s_cap > 0 ? (size_t)s_cap : 1;
+  if (cudaMalloc(&dD, sizeof(float) * m * n) || cudaMalloc(&dU, sizeof(double) * m * r) ||
+      cudaMalloc(&dS, sizeof(double) * r) || cudaMalloc(&dV, sizeof(double) * n * r) ||
+      cudaMalloc(&didx, sizeof(int64_t) * cap) || cudaMalloc(&dval, sizeof(double) * cap)) {
+    result = RPCA_ERR_CUDA;
+  } else if (cudaMemcpyAsync(dD, D, sizeof(float) * m * n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    result = RPCA_ERR_CUDA;
+  } else {
+    result = solve_device(dD, m, n, r, beta, gamma, tol, dU, dS, dV, s_cap > 0 ? didx : nullptr,
+                          s_cap > 0 ? dval : nullptr, s_cap, nnz, iters, err, s);
+    if (result == RPCA_OK || result == RPCA_ERR_NOT_CONVERGED) {
+      const int64_t nz = (*nnz < s_cap) ? *nnz : s_cap;
+      if (cudaMemcpyAsync(U, dU, sizeof(double) * m * r, cudaMemcpyDeviceToHost, s) ||
+          cudaMemcpyAsync(sigma, dS, sizeof(double) * r, cudaMemcpyDeviceToHost, s) ||
+          cudaMemcpyAsync(V, dV, sizeof(double) * n * r, cudaMemcpyDeviceToHost, s) ||
+          (nz > 0 && cudaMemcpyAsync(s_idx, didx, sizeof(int64_t) * nz, cudaMemcpyDeviceToHost, s)) ||
+          (nz > 0 && cudaMemcpyAsync(s_val, dval, sizeof(double) * nz, cudaMemcpyDeviceToHost, s)) ||
+          cudaStreamSynchronize(s))
+        result = RPCA_ERR_CUDA;
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(dD);
+  cudaFree(dU);
+  cudaFree(dS);
+  cudaFree(dV);
+  cudaFree(didx);
+  cudaFree(dval);
+  cudaStreamDestroy(s);
+  return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal declarations shared by the CUDA translation units of the AccAltProj library.
+// Nothing here is part of the C ABI (include/rpca.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rpca {
+
+// Ranks with a compiled fused pass.  A rank r is run with the smallest entry >= r and
+// zero-padded factors.
+#define RPCA_FOR_EACH_R(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14) X(16)
+constexpr int kMaxR = 16;
+inline int padded_rank(int r) {
+  const int table[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 10, 12, 12, 14, 14, 16, 16};
+  return (r >= 1 && r <= kMaxR) ? table[r - 1] : -1;
+}
+
+// Device-side state of one solve.  Lives in device memory; only `done`, `k` and `status`
+// are read back by the host while iterating.
+struct DevState {
+  double zeta;           // threshold used by the next fused pass
+  double normD2;         // ||D||_F^2
+  double beta, gamma, tol, beta_init, mu_trim;
+  double sigma[64];      // spectrum of the last small SVD (2r for M_k, b for init)
+  double sigma_prev[64]; // previous spectrum (init convergence test)
+  int k;                 // iteration index of the factors currently held
+  int done;              // 1: converged or capped; passes and updates return at once
+  int status;            // 0 or an rpca_status code raised on the device
+  int conv;              // init subspace iteration converged
+  int max_iter;
+  int zeta_mode;
+  int trim;
+  int pad0;
+  unsigned bar_count;    // grid barrier
+  unsigned bar_gen;
+};
+
+// One record per fused pass of Algorithm 1.
+struct DevStats {
+  double err, zeta, sigma1, sigma_r1, res2;
+  long long nnz;
+  int k, pad;
+};
+
+// Precision of the fused pass (what D is read as and what the m x n arithmetic uses).
+enum PassPrec { PREC_F64 = 0, PREC_F32 = 1 };
+
+// Geometry of one fused-pass work unit (a BH x BW block of D handled by one CTA).
+struct PassGeom {
+  int BH, BW;   // unit rows, unit columns
+  int TM;       // rows per warp per row block
+  int VW;       // columns per lane (one 16-byte vector of D)
+  size_t smem;  // dynamic shared memory bytes
+};
+PassGeom pass_geometry(int prec, int R);
+
+struct PassArgs {
+  const void* D;
+  long long ld;
+  int m, n;
+  const void* W;    // m x R, W = U_k Sigma_k (pass precision), row stride R
+  const void* V;    // n x R, V_k
+  const void* Ut;   // m x R, trimmed orthonormal U~_k
+  const void* Vt;   // n x R, trimmed orthonormal V~_k
+  const DevState* st;
+  void* P1;         // [ceil(n/BW)][m][R] partial Z V~
+  void* P2;         // [ceil(m/BH)][n][R] partial Z^T U~
+  double* resP;     // per CTA: sum of R_ij^2 over the unthresholded entries
+  unsigned long long* nnzP;  // per CTA: |supp(S)|
+  int vec;          // 16-byte vector loads of D allowed
+};
+
+// Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
+cudaError_t launch_fused_pass(int prec, int R, const PassArgs& a, cudaStream_t s);
+
+// Sparse extraction (three kernels): per-row counts, exclusive scan, ordered write.
+struct ExtractArgs {
+  const void* D;
+  long long ld;
+  int m, n;
+  const void* W;
+  const void* V;
+  const DevState* st;
+  unsigned long long* rowcnt;  // m counts, then m+1 offsets (in place scan into rowoff)
+  unsigned long long* rowoff;  // m+1
+  long long* idx;
+  double* val;
+  int vec;
+};
+cudaError_t launch_extract_count(int prec, int R, const ExtractArgs& a, cudaStream_t s);
+cudaError_t launch_extract_write(int prec, int R, const ExtractArgs& a, cudaStream_t s);
+
+// The FP64 tall-skinny kernel (cooperative launch): reductions of the pass partials,
+// CholeskyQR, the small SVD, the factor update, Trim and the pass-precision copies.
+enum SmallMode { SM_UPDATE = 0, SM_PREPARE = 1, SM_RR = 2, SM_RAND = 3 };
+
+struct SmallArgs {
+  int mode;
+  int m, n;
+  int r;        // rank of the iteration (columns of U, V)
+  int R;        // width of the pass arrays (compiled rank of the pass that ran)
+  int b;        // width of the subspace-iteration bases in init (RR / RAND modes)
+  int prec;
+  int n_p1, n_p2, n_cta;  // partial slices and CTA count of the pass that ran
+  const void* P1;
+  const void* P2;
+  const double* resP;
+  const unsigned long long* nnzP;
+  double* U; double* sig; double* V;   // master factors (m x r, r, n x r)
+  double* Ut; double* Vt;              // FP64 bases (m x w, n x w), w = r or b
+  double* Y1; double* Y2;              // m x w, n x w
+  double* part;                        // [grid][2][32*32] Gram partials
+  void* Wc; void* Vc; void* Utc; void* Vtc;  // pass-precision copies, width Rc
+  int Rc;                              // width of the copies written for an init pass
+  int Rit;                             // width of the copies written for an iteration pass
+  DevState* st;
+  DevStats* stats;
+  int init_phase;     // RR: 0 = sigma_1(D) (phase A), 1 = top-r of D - S_{-1} (phase B)
+  double init_tol;
+  unsigned long long seed;
+  int rr_first;       // RR: first pass of a phase (no convergence test)
+  int rr_force;       // RR: accept this step as converged (pass cap reached)
+};
+cudaError_t launch_small(const SmallArgs& a, int grid, cudaStream_t s);
+int small_grid_size(int device);
+
+cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s);
+cudaError_t launch_convert_f64_to_f32(const double* src, long long ld_src, float* dst, int m, int n,
+                                      cudaStream_t s);
+cudaError_t launch_convert_f32_to_f64(const float* src, long long ld_src, double* dst, int m, int n,
+                                      cudaStream_t s);
+
+}  // namespace rpca

@@ -1,0 +1,71 @@
+// Small helper kernels: precision conversion of D and the row-offset scan of the sparse
+// extraction.
+#include "common.cuh"
+
+namespace rpca {
+
+namespace {
+
+__global__ void convert_f64_f32(const double* __restrict__ src, long long ld, float* __restrict__ dst, int m,
+                                int n) {
+  const long long total = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    dst[e] = static_cast<float>(src[i * ld + j]);
+  }
+}
+
+__global__ void convert_f32_f64(const float* __restrict__ src, long long ld, double* __restrict__ dst, int m,
+                                int n) {
+  const long long total = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    dst[e] = static_cast<double>(src[i * ld + j]);
+  }
+}
+
+// Exclusive scan of m row counts into m+1 offsets, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_rows(const unsigned long long* __restrict__ cnt,
+                                                  unsigned long long* __restrict__ off, int m) {
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x;
+  const int chunk = (m + 1023) / 1024;
+  const int lo = min(m, t * chunk), hi = min(m, lo + chunk);
+  unsigned long long s = 0;
+  for (int i = lo; i < hi; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+    const unsigned long long v = (t >= o) ? part[t - o] : 0ull;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = (t == 0) ? 0ull : part[t - 1];
+  for (int i = lo; i < hi; ++i) {
+    off[i] = run;
+    run += cnt[i];
+  }
+  if (t == 1023) off[m] = part[1023];
+}
+
+}  // namespace
+
+cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s) {
+  scan_rows<<<1, 1024, 0, s>>>(cnt, off, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f64_to_f32(const double* src, long long ld, float* dst, int m, int n, cudaStream_t s) {
+  convert_f64_f32<<<1024, 256, 0, s>>>(src, ld, dst, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32_to_f64(const float* src, long long ld, double* dst, int m, int n, cudaStream_t s) {
+  convert_f32_f64<<<1024, 256, 0, s>>>(src, ld, dst, m, n);
+  return cudaGetLastError();
+}
+
+}  // namespace rpca

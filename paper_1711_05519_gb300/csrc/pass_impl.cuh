@@ -1,0 +1,315 @@
+// Fused streaming pass of one AccAltProj iteration (SIMT form), templated on the
+// arithmetic type T (float or double) and the compiled rank R.
+//
+// For every entry of D (one read of D from HBM per iteration) the pass
+//   rebuilds L_ij = sum_k W_ik V_jk                  (L_k = U_k Sigma_k V_k^T, W = U_k Sigma_k)
+//   forms R_ij = D_ij - L_ij and the hard threshold S_ij = R_ij if |R_ij| > zeta_k
+//                                                   (Eq. (10), strict inequality)
+//   accumulates sum R_ij^2 over unthresholded entries (the numerator of err_k, Eq. (11))
+//   forms Z_ij = D_ij - S_ij (= L_ij on the support, D_ij elsewhere)
+//   accumulates Y1 = Z V~_k and Y2 = Z^T U~_k          (the two tall-skinny products of
+//                                                   Section 2.1 feeding the QR route)
+// so S_k, err_k and the products for L_{k+1} all come from the same read.
+//
+// Work decomposition: a CTA owns a BH x BW unit of D.  Its 8 warps sweep the unit in row
+// blocks of 8*TM rows; within a row block each lane owns VW consecutive columns of a
+// 32*VW-column sub-chunk (one 16-byte vector load per row).  Y1 for the warp's TM rows
+// stays in registers across the whole unit width and is reduced across lanes once per
+// row block; Y2 for the lane's columns is summed over the TM rows in registers and added
+// into a per-warp shared-memory slot.  At the end of the unit the 8 slots are summed in
+// a fixed order and written as the unit's partial.  Partials are reduced in FP64 by the
+// tall-skinny kernel, so results do not depend on scheduling.
+#pragma once
+
+#include "common.cuh"
+
+namespace rpca {
+
+template <typename T, int R>
+struct PassCfg;
+
+template <int R>
+struct PassCfg<float, R> {
+  static constexpr int VW = 4;
+  static constexpr int TM = (R <= 6) ? 8 : 4;
+  static constexpr int BH = (R <= 8) ? 512 : 256;
+  static constexpr int BW = (R <= 6) ? 512 : 256;
+};
+
+template <int R>
+struct PassCfg<double, R> {
+  static constexpr int VW = 2;
+  static constexpr int TM = (R <= 6) ? 4 : 2;
+  static constexpr int BH = (R <= 8) ? 256 : 128;
+  static constexpr int BW = (R <= 6) ? 256 : 128;
+};
+
+template <typename T, int R>
+struct PassLayout {
+  using C = PassCfg<T, R>;
+  static constexpr int WARPS = 8;
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr int SCW = 32 * C::VW;          // sub-chunk width
+  static constexpr int NSC = C::BW / SCW;          // sub-chunks per unit
+  static constexpr int NRB = C::BH / (WARPS * C::TM);  // row blocks per unit
+  // shared memory: W, U~ rows [BH][R]; V, V~ columns [R][BW]; Y2 slots [WARPS][R][BW]
+  static constexpr size_t SMEM = sizeof(T) * (size_t)R * (2 * C::BH + 2 * C::BW + WARPS * C::BW);
+  static_assert(C::BH % (WARPS * C::TM) == 0, "row blocks");
+  static_assert(C::BW % SCW == 0, "sub-chunks");
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// L_ij for one entry: fixed summation order k = 0..R-1 (the extraction kernels use the
+// same order so that their threshold decisions agree with the pass).
+template <typename T, int R>
+__device__ __forceinline__ T rebuild(const T* w, const T* v) {
+  T l = T(0);
+#pragma unroll
+  for (int k = 0; k < R; ++k) l = fma(w[k], v[k], l);
+  return l;
+}
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
+// Loads D[i][c .. c+VW) with zero fill past the matrix edge.
+template <typename T, int VW>
+__device__ __forceinline__ void load_row_vec(const T* __restrict__ D, long long ld, int m, int n, int i,
+                                             int c, bool vec, T (&out)[VW]) {
+  if (i < m && vec && c + VW <= n) {
+    static_assert(sizeof(typename Vec16<T>::type) == VW * sizeof(T), "one 16-byte vector per lane");
+    const typename Vec16<T>::type x =
+        __ldcs(reinterpret_cast<const typename Vec16<T>::type*>(D + (long long)i * ld + c));
+    const T* xs = reinterpret_cast<const T*>(&x);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) out[e] = xs[e];
+  } else {
+#pragma unroll
+    for (int e = 0; e < VW; ++e)
+      out[e] = (i < m && c + e < n) ? __ldcs(D + (long long)i * ld + c + e) : T(0);
+  }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
+  using C = PassCfg<T, R>;
+  using Lay = PassLayout<T, R>;
+  constexpr int VW = C::VW, TM = C::TM, BH = C::BH, BW = C::BW;
+  constexpr int WARPS = Lay::WARPS, SCW = Lay::SCW, NSC = Lay::NSC, NRB = Lay::NRB;
+  if (a.st->done) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sW = reinterpret_cast<T*>(smem_raw);   // [BH][R]
+  T* sUt = sW + BH * R;                     // [BH][R]
+  T* sV = sUt + BH * R;                     // [R][BW]
+  T* sVt = sV + R * BW;                     // [R][BW]
+  T* sY2 = sVt + R * BW;                    // [WARPS][R][BW]
+
+  const T* __restrict__ D = static_cast<const T*>(a.D);
+  const T* __restrict__ W = static_cast<const T*>(a.W);
+  const T* __restrict__ V = static_cast<const T*>(a.V);
+  const T* __restrict__ Ut = static_cast<const T*>(a.Ut);
+  const T* __restrict__ Vt = static_cast<const T*>(a.Vt);
+  const int m = a.m, n = a.n;
+  const int row0 = blockIdx.y * BH, col0 = blockIdx.x * BW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int e = tid; e < BH * R; e += Lay::THREADS) {
+    const int i = row0 + e / R;
+    sW[e] = (i < m) ? W[(long long)row0 * R + e] : T(0);
+    sUt[e] = (i < m) ? Ut[(long long)row0 * R + e] : T(0);
+  }
+  for (int e = tid; e < BW * R; e += Lay::THREADS) {
+    const int cl = e / R, k = e % R, j = col0 + cl;
+    sV[k * BW + cl] = (j < n) ? V[(long long)j * R + k] : T(0);
+    sVt[k * BW + cl] = (j < n) ? Vt[(long long)j * R + k] : T(0);
+  }
+  for (int e = tid; e < WARPS * R * BW; e += Lay::THREADS) sY2[e] = T(0);
+  __syncthreads();
+
+  const T zeta = static_cast<T>(a.st->zeta);
+  const bool vec = a.vec != 0;
+  T res = T(0);
+  unsigned nnz = 0;
+  T* mySlot = sY2 + warp * R * BW;
+
+  for (int rb = 0; rb < NRB; ++rb) {
+    const int rl0 = rb * WARPS * TM + warp * TM;  // local row of this warp's first row
+    T y1[TM][R];
+#pragma unroll
+    for (int t = 0; t < TM; ++t)
+#pragma unroll
+      for (int k = 0; k < R; ++k) y1[t][k] = T(0);
+
+#pragma unroll 1
+    for (int sc = 0; sc < NSC; ++sc) {
+      const int cl = sc * SCW + lane * VW;  // local column of this lane's first column
+      T d[TM][VW];
+#pragma unroll
+      for (int t = 0; t < TM; ++t) load_row_vec<T, VW>(D, a.ld, m, n, row0 + rl0 + t, col0 + cl, vec, d[t]);
+      T v[VW][R], vt[VW][R], y2[VW][R];
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+          v[c][k] = sV[k * BW + cl + c];
+          vt[c][k] = sVt[k * BW + cl + c];
+          y2[c][k] = T(0);
+        }
+#pragma unroll
+      for (int t = 0; t < TM; ++t) {
+        T w[R], ut[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+          w[k] = sW[(rl0 + t) * R + k];
+          ut[k] = sUt[(rl0 + t) * R + k];
+        }
+#pragma unroll
+        for (int c = 0; c < VW; ++c) {
+          const T l = rebuild<T, R>(w, v[c]);
+          const T rr = d[t][c] - l;
+          const bool s = fabs(rr) > zeta;
+          res = s ? res : fma(rr, rr, res);
+          nnz += s ? 1u : 0u;
+          const T z = s ? l : d[t][c];
+#pragma unroll
+          for (int k = 0; k < R; ++k) {
+            y1[t][k] = fma(z, vt[c][k], y1[t][k]);
+            y2[c][k] = fma(z, ut[k], y2[c][k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+#pragma unroll
+        for (int c = 0; c < VW; ++c) mySlot[k * BW + cl + c] += y2[c][k];
+    }
+    // Y1 partial of the warp's TM rows over the unit width.
+#pragma unroll
+    for (int t = 0; t < TM; ++t) {
+      const int i = row0 + rl0 + t;
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const T s = warp_sum(y1[t][k]);
+        if (lane == 0 && i < m) static_cast<T*>(a.P1)[((long long)blockIdx.x * m + i) * R + k] = s;
+      }
+    }
+  }
+  __syncthreads();
+  // Y2 partial of the unit: fixed-order sum of the per-warp slots.
+  for (int e = tid; e < BW * R; e += Lay::THREADS) {
+    const int cl = e / R, k = e % R, j = col0 + cl;
+    T s = T(0);
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) s += sY2[(w * R + k) * BW + cl];
+    if (j < n) static_cast<T*>(a.P2)[((long long)blockIdx.y * n + j) * R + k] = s;
+  }
+  // CTA totals of the residual and the support size.
+  __shared__ double sres[8];
+  __shared__ unsigned long long snnz[8];
+  double rd = warp_sum(static_cast<double>(res));
+  unsigned long long nz = nnz;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+  if (lane == 0) {
+    sres[warp] = rd;
+    snnz[warp] = nz;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    unsigned long long z = 0;
+    for (int w = 0; w < WARPS; ++w) {
+      t += sres[w];
+      z += snnz[w];
+    }
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    a.resP[cta] = t;
+    a.nnzP[cta] = z;
+  }
+}
+
+template <typename T, int R>
+cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t s) {
+  using C = PassCfg<T, R>;
+  using Lay = PassLayout<T, R>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Lay::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((a.n + C::BW - 1) / C::BW, (a.m + C::BH - 1) / C::BH);
+  fused_pass_kernel<T, R><<<grid, Lay::THREADS, Lay::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Sparse extraction: supp(S_k) and its values, in ascending linear index order.
+// One warp per row, 32 columns per step; the decision uses rebuild<T,R> and the same
+// comparison as the pass, so the support agrees with the pass's nnz.
+// ---------------------------------------------------------------------------------------
+template <typename T, int R, bool WRITE>
+__global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= a.m) return;
+  const T* __restrict__ D = static_cast<const T*>(a.D);
+  const T* __restrict__ W = static_cast<const T*>(a.W);
+  const T* __restrict__ V = static_cast<const T*>(a.V);
+  const T zeta = static_cast<T>(a.st->zeta);
+  T w[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) w[k] = W[(long long)row * R + k];
+  unsigned long long base = WRITE ? a.rowoff[row] : 0ull;
+  unsigned long long cnt = 0;
+  for (int j0 = 0; j0 < a.n; j0 += 32) {
+    const int j = j0 + lane;
+    bool s = false;
+    T rr = T(0);
+    if (j < a.n) {
+      T v[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = V[(long long)j * R + k];
+      const T l = rebuild<T, R>(w, v);
+      rr = D[(long long)row * a.ld + j] - l;
+      s = fabs(rr) > zeta;
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, s);
+    if (WRITE && s) {
+      const unsigned long long pos = base + cnt + __popc(ballot & ((1u << lane) - 1u));
+      a.idx[pos] = (long long)row * a.n + j;
+      a.val[pos] = static_cast<double>(rr);
+    }
+    cnt += __popc(ballot);
+  }
+  if (!WRITE && lane == 0) a.rowcnt[row] = cnt;
+}
+
+template <typename T, int R>
+cudaError_t launch_extract_count_t(const ExtractArgs& a, cudaStream_t s) {
+  extract_kernel<T, R, false><<<(a.m + 7) / 8, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int R>
+cudaError_t launch_extract_write_t(const ExtractArgs& a, cudaStream_t s) {
+  extract_kernel<T, R, true><<<(a.m + 7) / 8, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rpca

@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in include/rpca.h (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA library ``librpca.so``; this module only passes
+device pointers, sizes and the current torch CUDA stream across the ABI.  There is no
+CPU path: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librpca.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "rpca.h")
+
+OK, INVALID_ARG, CUDA_ERR, NUMERICAL, CAPACITY, NOT_CONVERGED, TIMEOUT, STATE = range(8)
+DTYPE_F64, DTYPE_F32 = 0, 1
+PREC = {"fp64": 0, "fp32": 1}
+ZETA = {"paper": 0, "simple": 1, "external": 2}
+
+
+class RpcaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("beta", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("beta_init", ctypes.c_double),
+        ("mu_trim", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("trim", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("zeta_mode", ctypes.c_int),
+        ("init_max_passes", ctypes.c_int),
+        ("init_tol", ctypes.c_double),
+    ]
+
+
+class IterStats(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int),
+        ("err", ctypes.c_double),
+        ("zeta", ctypes.c_double),
+        ("sigma1", ctypes.c_double),
+        ("sigma_r1", ctypes.c_double),
+        ("nnz", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads librpca.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1711_05519_gb300.build.build()")
+    import torch.cuda  # noqa: F401  (loads the CUDA runtime the library links against)
+
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    pi64, pint, pdbl = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    L.rpca_status_string.restype = ctypes.c_char_p
+    L.rpca_status_string.argtypes = [i32]
+    L.rpca_params_default.argtypes = [ctypes.POINTER(Params)]
+    L.rpca_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), vp]
+    L.rpca_destroy.argtypes = [vp]
+    L.rpca_destroy.restype = None
+    L.rpca_init.argtypes = [vp, vp, i64, i64, i64, i32, i32]
+    L.rpca_iterate.argtypes = [vp, i32, ctypes.POINTER(IterStats), pint]
+    L.rpca_set_zeta.argtypes = [vp, dbl]
+    L.rpca_get_lowrank.argtypes = [vp, vp, vp, vp]
+    L.rpca_get_sparse.argtypes = [vp, vp, vp, i64, pi64]
+    solve_args = [vp, i64, i64, i32, dbl, dbl, dbl, vp, vp, vp, vp, vp, i64, pi64, pint, pdbl]
+    L.rpca_solve.argtypes = solve_args
+    L.rpca_solve_host.argtypes = solve_args
+    for name in ("rpca_params_default", "rpca_create", "rpca_init", "rpca_iterate", "rpca_set_zeta",
+                 "rpca_get_lowrank", "rpca_get_sparse", "rpca_solve", "rpca_solve_host"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().rpca_status_string(code).decode()
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/rpca.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rpca_[a-z_]+)\s*\(", text)))
+
+
+def _check(code: int, where: str, allow=(OK,)) -> int:
+    if code not in allow:
+        raise RpcaError(code, where)
+    return code
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """One AccAltProj solve on the current CUDA device (a context of the C ABI)."""
+
+    def __init__(self, beta: float, gamma: float, tol: float, precision: str = "fp32", trim: bool = True,
+                 zeta_mode: str = "paper", max_iter: int = 100, beta_init: float = 0.0, mu_trim: float = 0.0,
+                 init_max_passes: int = 0, init_tol: float = 0.0, stream=None):
+        L = lib()
+        p = Params()
+        L.rpca_params_default(ctypes.byref(p))
+        p.beta, p.gamma, p.tol = beta, gamma, tol
+        p.beta_init, p.mu_trim = beta_init, mu_trim
+        p.max_iter, p.trim = max_iter, int(bool(trim))
+        p.precision, p.zeta_mode = PREC[precision], ZETA[zeta_mode]
+        p.init_max_passes, p.init_tol = init_max_passes, init_tol
+        self.params = p
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = ctypes.c_void_p()
+        _check(L.rpca_create(ctypes.byref(self._ctx), ctypes.byref(p), _stream_ptr(self.stream)), "rpca_create")
+        self._D = None
+        self.m = self.n = self.r = 0
+
+    def close(self):
+        if self._ctx:
+            lib().rpca_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, D: torch.Tensor, r: int) -> None:
+        """Algorithm 3 on D (2-D CUDA tensor, float32 or float64, unit column stride)."""
+        if not (D.is_cuda and D.dim() == 2 and D.stride(1) == 1):
+            raise ValueError("D must be a 2-D CUDA tensor with unit column stride")
+        dt = {torch.float32: DTYPE_F32, torch.float64: DTYPE_F64}.get(D.dtype)
+        if dt is None:
+            raise ValueError("D must be float32 or float64")
+        self._D = D  # the context borrows D
+        self.m, self.n = D.shape
+        self.r = r
+        _check(lib().rpca_init(self._ctx, ctypes.c_void_p(D.data_ptr()), self.m, self.n, D.stride(0), dt, r),
+               "rpca_init")
+
+    def iterate(self, n_iters: int) -> tuple[int, list[dict]]:
+        buf = (IterStats * max(n_iters, 1))()
+        done = ctypes.c_int(0)
+        code = lib().rpca_iterate(self._ctx, n_iters, buf, ctypes.byref(done))
+        _check(code, "rpca_iterate", allow=(OK, NOT_CONVERGED))
+        stats = [{"k": s.k, "err": s.err, "zeta": s.zeta, "sigma1": s.sigma1, "sigma_r1": s.sigma_r1,
+                  "nnz": s.nnz} for s in buf[: done.value]]
+        return code, stats
+
+    def run(self, max_passes: int | None = None) -> tuple[int, list[dict]]:
+        """Iterates until err_k < tol or the iteration cap."""
+        return self.iterate(max_passes if max_passes is not None else self.params.max_iter + 1)
+
+    def set_zeta(self, zeta: float) -> None:
+        _check(lib().rpca_set_zeta(self._ctx, zeta), "rpca_set_zeta")
+
+    def lowrank(self):
+        dev = self._D.device
+        U = torch.empty(self.m, self.r, dtype=torch.float64, device=dev)
+        s = torch.empty(self.r, dtype=torch.float64, device=dev)
+        V = torch.empty(self.n, self.r, dtype=torch.float64, device=dev)
+        _check(lib().rpca_get_lowrank(self._ctx, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                                      ctypes.c_void_p(V.data_ptr())), "rpca_get_lowrank")
+        return U, s, V
+
+    def sparse(self):
+        """supp(S_k) as ascending linear indices i*n + j, and the values S_ij."""
+        nnz = ctypes.c_int64(0)
+        code = lib().rpca_get_sparse(self._ctx, None, None, 0, ctypes.byref(nnz))
+        _check(code, "rpca_get_sparse", allow=(OK, CAPACITY))
+        dev = self._D.device
+        idx = torch.empty(max(nnz.value, 1), dtype=torch.int64, device=dev)
+        val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
+        _check(lib().rpca_get_sparse(self._ctx, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                     nnz.value, ctypes.byref(nnz)), "rpca_get_sparse")
+        return idx[: nnz.value], val[: nnz.value]
+
+
+def solve(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s_cap: int | None = None) -> dict:
+    """rpca_solve on a float32 CUDA tensor (contiguous)."""
+    if not (D.is_cuda and D.dtype == torch.float32 and D.is_contiguous()):
+        raise ValueError("D must be a contiguous float32 CUDA tensor")
+    m, n = D.shape
+    dev = D.device
+    cap = m * n if s_cap is None else s_cap
+    U = torch.empty(m, r, dtype=torch.float64, device=dev)
+    s = torch.empty(r, dtype=torch.float64, device=dev)
+    V = torch.empty(n, r, dtype=torch.float64, device=dev)
+    idx = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+    val = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+    nnz, iters, err = ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_double(0)
+    code = lib().rpca_solve(ctypes.c_void_p(D.data_ptr()), m, n, r, beta, gamma, tol,
+                            ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                            ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(idx.data_ptr()),
+                            ctypes.c_void_p(val.data_ptr()), cap, ctypes.byref(nnz), ctypes.byref(iters),
+                            ctypes.byref(err))
+    _check(code, "rpca_solve", allow=(OK, NOT_CONVERGED))
+    return {"status": code, "U": U, "sigma": s, "V": V, "idx": idx[: nnz.value], "val": val[: nnz.value],
+            "iters": iters.value, "err": err.value}
+
+
+def solve_host(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s_cap: int,
+               out: dict | None = None) -> dict:
+    """rpca_solve_host on a float32 CPU tensor (ideally pinned); outputs are CPU tensors
+    (pass ``out`` from a previous call to reuse them)."""
+    if D.is_cuda or D.dtype != torch.float32 or not D.is_contiguous():
+        raise ValueError("D must be a contiguous float32 CPU tensor")
+    m, n = D.shape
+    if out is None:
+        out = {"U": torch.empty(m, r, dtype=torch.float64, pin_memory=True),
+               "sigma": torch.empty(r, dtype=torch.float64, pin_memory=True),
+               "V": torch.empty(n, r, dtype=torch.float64, pin_memory=True),
+               "idx": torch.empty(max(s_cap, 1), dtype=torch.int64, pin_memory=True),
+               "val": torch.empty(max(s_cap, 1), dtype=torch.float64, pin_memory=True)}
+    nnz, iters, err = ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_double(0)
+    code = lib().rpca_solve_host(ctypes.c_void_p(D.data_ptr()), m, n, r, beta, gamma, tol,
+                                 ctypes.c_void_p(out["U"].data_ptr()), ctypes.c_void_p(out["sigma"].data_ptr()),
+                                 ctypes.c_void_p(out["V"].data_ptr()), ctypes.c_void_p(out["idx"].data_ptr()),
+                                 ctypes.c_void_p(out["val"].data_ptr()), s_cap, ctypes.byref(nnz),
+                                 ctypes.byref(iters), ctypes.byref(err))
+    _check(code, "rpca_solve_host", allow=(OK, NOT_CONVERGED))
+    out.update(status=code, nnz=nnz.value, iters=iters.value, err=err.value)
+    return out

@@ -1,0 +1,188 @@
+"""GPU versus FP64-oracle parity through the C ABI (needs a GB300 and the built library).
+
+Tolerances (relative Frobenius error of L against the oracle at the same iteration count):
+1e-10 in FP64 mode and 1e-5 in FP32 mode.  Supports must agree exactly except for entries
+whose residual lies within the tie band around the threshold (1e-6 zeta_k, plus the FP32
+rounding of R_ij, 1e-6 max(|D_ij|, |L_ij|), in FP32 mode).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import accaltproj as O
+from parity_helpers import rel_fro, support_mismatch
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_1711_05519_gb300")
+
+
+def _solver(p, prec, tol, **kw):
+    return P.Solver(p["beta"], p["gamma"], tol, precision=prec, beta_init=p["beta_init"], mu_trim=p["mu"], **kw)
+
+
+def _gpu_run(inst, prec, tol, r=None, **kw):
+    p = inst.params()
+    r = r or inst.r
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    D = torch.from_numpy(inst.D).to("cuda", dt)
+    with _solver(p, prec, tol, **kw) as s:
+        s.init(D, r)
+        code, stats = s.run()
+        U, sig, V = (t.cpu().numpy() for t in s.lowrank())
+        idx, val = (t.cpu().numpy() for t in s.sparse())
+    Dh = D.double().cpu().numpy()
+    return {"code": code, "stats": stats, "L": (U * sig) @ V.T, "U": U, "sig": sig, "V": V, "idx": idx,
+            "val": val, "D": Dh}
+
+
+def _oracle_same_k(D, inst, k, r=None, **kw):
+    p = inst.params()
+    return O.accaltproj(D, r or inst.r, p["beta"], p["gamma"], 0.0, p["mu"], beta_init=p["beta_init"], max_iter=k,
+                        **kw)
+
+
+def test_fp64_config1_end_to_end():
+    """500 x 500, r = 5, alpha = 0.1, c = 1, seed 0, stop at 1e-10."""
+    inst = synth.planted_instance(500, 500, 5, 0.1, 1.0, 0)
+    g = _gpu_run(inst, "fp64", 1e-10)
+    assert g["code"] == P.OK
+    k = g["stats"][-1]["k"]
+    assert g["stats"][-1]["err"] < 1e-10
+    full = O.accaltproj(inst.D, 5, inst.params()["beta"], inst.params()["gamma"], 1e-10, inst.params()["mu"],
+                        beta_init=inst.params()["beta_init"])
+    assert abs(full["iters"] - k) <= 1
+    ref = _oracle_same_k(inst.D, inst, k)
+    assert rel_fro(g["L"], ref["L"]) < 1e-10
+    diff, ok = support_mismatch(g["idx"], inst.D, ref["L"], ref["zeta"])
+    assert ok, diff
+    assert rel_fro(g["L"], inst.L) < 1e-9
+    # per-iteration error history agrees
+    errs = np.array([s["err"] for s in g["stats"]])
+    assert np.allclose(errs, ref["history"]["err"], rtol=1e-6, atol=1e-14)
+
+
+def test_fp64_init_matches_algorithm3():
+    inst = synth.planted_instance(300, 260, 4, 0.1, 1.0, 3)
+    p = inst.params()
+    D = torch.from_numpy(inst.D).cuda()
+    with _solver(p, "fp64", 1e-10) as s:
+        s.init(D, 4)
+        U, sig, V = (t.cpu().numpy() for t in s.lowrank())
+        idx, _ = (t.cpu().numpy() for t in s.sparse())
+        _, st = s.iterate(1)
+    ref = O.initialize(inst.D, 4, p["beta_init"], p["beta"])
+    L0 = (ref["U"] * ref["sigma"]) @ ref["V"].T
+    assert rel_fro((U * sig) @ V.T, L0) < 1e-10
+    assert st[0]["zeta"] == pytest.approx(ref["zeta"], rel=1e-12)
+    diff, ok = support_mismatch(idx, inst.D, L0, ref["zeta"])
+    assert ok, diff
+
+
+def test_fp64_one_step_from_gpu_state():
+    """The oracle takes the GPU's own state after k passes and performs pass k; the GPU's
+    S_k, err_k, L_{k+1} and spectrum of M_k must match it."""
+    inst = synth.planted_instance(400, 350, 5, 0.15, 1.0, 5)
+    p = inst.params()
+    D = torch.from_numpy(inst.D).cuda()
+    with _solver(p, "fp64", 0.0) as s:
+        s.init(D, 5)
+        for k in range(0, 12):
+            U, sig, V = (t.cpu().numpy() for t in s.lowrank())
+            idx, val = (t.cpu().numpy() for t in s.sparse())
+            _, st = s.iterate(1)
+            U1, sig1, V1 = (t.cpu().numpy() for t in s.lowrank())
+            o = O.step(inst.D, U, sig, V, st[0]["zeta"], k, 5, p["beta"], p["gamma"], p["mu"])
+            assert st[0]["k"] == k
+            assert st[0]["err"] == pytest.approx(o["err"], rel=1e-9)
+            diff, ok = support_mismatch(idx, inst.D, (U * sig) @ V.T, st[0]["zeta"])
+            assert ok, (k, diff)
+            assert st[0]["nnz"] == len(idx)
+            assert st[0]["sigma1"] == pytest.approx(o["sigma_M"][0], rel=1e-11)
+            assert st[0]["sigma_r1"] == pytest.approx(o["sigma_M"][5], rel=1e-9, abs=1e-12 * o["sigma_M"][0])
+            assert rel_fro((U1 * sig1) @ V1.T, (o["U"] * o["sigma"]) @ o["V"].T) < 1e-11
+
+
+def test_fp32_config1_matches_oracle():
+    inst = synth.planted_instance(500, 500, 5, 0.1, 1.0, 0)
+    g = _gpu_run(inst, "fp32", 1e-5)
+    k = g["stats"][-1]["k"]
+    assert g["stats"][-1]["err"] < 1e-5
+    ref = _oracle_same_k(g["D"], inst, k)
+    assert rel_fro(g["L"], ref["L"]) < 1e-5
+    diff, ok = support_mismatch(g["idx"], g["D"], ref["L"], ref["zeta"], band_abs_rel_D=1e-6)
+    assert ok, diff
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("m,n,r", [(333, 217, 3), (129, 515, 2), (600, 97, 1), (257, 263, 7)])
+def test_ragged_shapes(prec, m, n, r):
+    inst = synth.planted_instance(m, n, r, 0.08, 1.0, m + n)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    g = _gpu_run(inst, prec, tol)
+    k = g["stats"][-1]["k"]
+    assert g["stats"][-1]["err"] < tol
+    ref = _oracle_same_k(g["D"], inst, k)
+    assert rel_fro(g["L"], ref["L"]) < (1e-10 if prec == "fp64" else 1e-5)
+    diff, ok = support_mismatch(g["idx"], g["D"], ref["L"], ref["zeta"],
+                                band_abs_rel_D=0.0 if prec == "fp64" else 1e-6)
+    assert ok, diff
+
+
+def test_large_rank_no_trim_and_simple_threshold():
+    inst = synth.planted_instance(220, 200, 16, 0.05, 1.0, 2)
+    for kw in ({"trim": False}, {"zeta_mode": "simple"}):
+        g = _gpu_run(inst, "fp64", 1e-9, **kw)
+        k = g["stats"][-1]["k"]
+        okw = {"do_trim": kw.get("trim", True), "zeta_mode": kw.get("zeta_mode", "paper")}
+        ref = _oracle_same_k(inst.D, inst, k, **okw)
+        assert rel_fro(g["L"], ref["L"]) < 1e-9
+        assert g["stats"][-1]["err"] < 1e-9
+
+
+def test_invalid_arguments_and_capacity():
+    inst = synth.planted_instance(64, 64, 2, 0.1, 1.0, 1)
+    p = inst.params()
+    D = torch.from_numpy(inst.D).cuda()
+    with _solver(p, "fp64", 1e-8) as s:
+        for r in (0, 17, 33):
+            with pytest.raises(P.RpcaError) as e:
+                s.init(D, r)
+            assert e.value.code == P.INVALID_ARG
+        with pytest.raises(P.RpcaError) as e:
+            s.iterate(1)
+        assert e.value.code == P.STATE
+        s.init(D, 2)
+        s.run()
+        import ctypes
+        nnz = ctypes.c_int64(0)
+        code = P.lib().rpca_get_sparse(s._ctx, None, None, 0, ctypes.byref(nnz))
+        assert code == P.CAPACITY and nnz.value > 0
+
+
+def test_nan_in_D_is_reported():
+    inst = synth.planted_instance(64, 80, 2, 0.1, 1.0, 1)
+    Dn = inst.D.copy()
+    Dn[3, 7] = np.nan
+    p = inst.params()
+    with _solver(p, "fp32", 1e-6, init_max_passes=3) as s:
+        with pytest.raises(P.RpcaError) as e:
+            s.init(torch.from_numpy(Dn).float().cuda(), 2)
+            s.run()
+        assert e.value.code == P.NUMERICAL
+
+
+def test_solve_device_and_host_entry_points():
+    inst = synth.planted_instance(300, 280, 3, 0.1, 1.0, 8)
+    p = inst.params()
+    D = torch.from_numpy(inst.D).float()
+    out_d = P.solve(D.cuda(), 3, p["beta"], p["gamma"], 1e-5)
+    out_h = P.solve_host(D.pin_memory(), 3, p["beta"], p["gamma"], 1e-5, s_cap=300 * 280)
+    assert out_d["status"] == P.OK and out_h["status"] == P.OK
+    assert out_d["iters"] == out_h["iters"] and out_d["err"] < 1e-5
+    Ld = (out_d["U"].cpu().numpy() * out_d["sigma"].cpu().numpy()) @ out_d["V"].cpu().numpy().T
+    Lh = (out_h["U"].numpy() * out_h["sigma"].numpy()) @ out_h["V"].numpy().T
+    assert np.array_equal(Ld, Lh)
+    assert np.array_equal(out_d["idx"].cpu().numpy(), out_h["idx"][: out_h["nnz"]].numpy())
+    assert rel_fro(Ld, inst.L) < 1e-4
