@@ -131,9 +131,10 @@ int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, do
 
 /* Diagnostics.  With profiling on, the context records a CUDA event pair around every
  * kernel it launches on its stream.  rpca_get_profile (host outputs, any may be NULL)
- * returns, since profiling was switched on, the summed device time and the number of
- * fused-pass launches that did work (passes skipped after convergence are not counted),
- * and the same for all other kernels of the library.  Synchronises the stream. */
+ * returns, since profiling was last switched on: the summed device time and the number
+ * of fused-pass launches that did work, and the same for every other launch of the
+ * library (including passes that returned at once because the solve had already
+ * converged).  Synchronises the stream. */
 int rpca_set_profiling(rpca_ctx* ctx, int on);
 int rpca_get_profile(rpca_ctx* ctx, double* pass_ms, int64_t* pass_launches, double* other_ms,
                      int64_t* other_launches);

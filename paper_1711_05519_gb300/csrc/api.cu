@@ -129,7 +129,26 @@ void prof_collect(rpca_ctx* c, int64_t effective_pass) {
     }
     v.clear();
   };
-  drain(c->ev_pass, c->pass_ms, c->pass_n, effective_pass);
+  // pass launches past the effective count returned at once on the device: they are
+  // counted with the other kernels so the pass average covers only passes that did work
+  int64_t i = 0;
+  for (auto& pr : c->ev_pass) {
+    if (pr.second) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, pr.first, pr.second);
+      if (effective_pass < 0 || i < effective_pass) {
+        c->pass_ms += t;
+        ++c->pass_n;
+      } else {
+        c->other_ms += t;
+        ++c->other_n;
+      }
+    }
+    ++i;
+    c->ev_free.push_back(pr.first);
+    if (pr.second) c->ev_free.push_back(pr.second);
+  }
+  c->ev_pass.clear();
   drain(c->ev_other, c->other_ms, c->other_n, -1);
 }
 

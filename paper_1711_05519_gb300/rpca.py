@@ -81,11 +81,14 @@ def lib() -> ctypes.CDLL:
     L.rpca_set_zeta.argtypes = [vp, dbl]
     L.rpca_get_lowrank.argtypes = [vp, vp, vp, vp]
     L.rpca_get_sparse.argtypes = [vp, vp, vp, i64, pi64]
+    L.rpca_set_profiling.argtypes = [vp, i32]
+    L.rpca_get_profile.argtypes = [vp, pdbl, pi64, pdbl, pi64]
     solve_args = [vp, i64, i64, i32, dbl, dbl, dbl, vp, vp, vp, vp, vp, i64, pi64, pint, pdbl]
     L.rpca_solve.argtypes = solve_args
     L.rpca_solve_host.argtypes = solve_args
     for name in ("rpca_params_default", "rpca_create", "rpca_init", "rpca_iterate", "rpca_set_zeta",
-                 "rpca_get_lowrank", "rpca_get_sparse", "rpca_solve", "rpca_solve_host"):
+                 "rpca_get_lowrank", "rpca_get_sparse", "rpca_solve", "rpca_solve_host", "rpca_set_profiling",
+                 "rpca_get_profile"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -177,6 +180,16 @@ class Solver:
     def run(self, max_passes: int | None = None) -> tuple[int, list[dict]]:
         """Iterates until err_k < tol or the iteration cap."""
         return self.iterate(max_passes if max_passes is not None else self.params.max_iter + 1)
+
+    def set_profiling(self, on: bool) -> None:
+        _check(lib().rpca_set_profiling(self._ctx, int(bool(on))), "rpca_set_profiling")
+
+    def profile(self) -> dict:
+        pm, om = ctypes.c_double(0), ctypes.c_double(0)
+        pn, on = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().rpca_get_profile(self._ctx, ctypes.byref(pm), ctypes.byref(pn), ctypes.byref(om),
+                                      ctypes.byref(on)), "rpca_get_profile")
+        return {"pass_ms": pm.value, "pass_launches": pn.value, "other_ms": om.value, "other_launches": on.value}
 
     def set_zeta(self, zeta: float) -> None:
         _check(lib().rpca_set_zeta(self._ctx, zeta), "rpca_set_zeta")
