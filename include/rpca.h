@@ -129,6 +129,32 @@ int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, do
                     double tol, double* U, double* sigma, double* V, int64_t* s_idx,
                     double* s_val, int64_t s_cap, int64_t* nnz, int* iters, double* err);
 
+/* Largest m accepted by rpca_get_sparse_noalloc. */
+#define RPCA_NOALLOC_MAX_ROWS 65536
+
+/* rpca_get_sparse without any device allocation (the paper has no counterpart; this is a
+ * service of the library).  Some callers cannot call cudaMalloc: code that runs inside a
+ * framework owning all device memory through its own pool, code with a fixed device-memory
+ * budget set at start-up, or latency-critical loops that must not take the implicit
+ * synchronisation of an allocation.  This entry point writes the same support list as
+ * rpca_get_sparse for the low-rank estimate L = U diag(sigma) V^T and threshold zeta:
+ * linear indices i*n + j in ascending order of every entry with |D_ij - L_ij| > zeta, and
+ * the values D_ij - L_ij, computed in FP32 as the FP32 pass does.
+ *   D: device, float32, m x n, leading dimension ld.  U (m x r), sigma (r), V (n x r):
+ *   device, double, row-major (as returned by rpca_get_lowrank).  idx, val: caller-owned
+ *   device buffers of cap entries.  nnz: host.  stream: cudaStream_t (NULL allowed).
+ * It allocates nothing: its per-row scratch lives in a static device array of
+ * 2 * RPCA_NOALLOC_MAX_ROWS + 1 64-bit words (1 MiB) that every GPU loading the library
+ * holds until the process exits.  m above RPCA_NOALLOC_MAX_ROWS returns
+ * RPCA_ERR_INVALID_ARG; cap < nnz returns RPCA_ERR_CAPACITY with *nnz set.  The first call
+ * on a device looks up the scratch address on that device (make that first call before
+ * any stream capture).  All calls share the scratch and each call rewrites what it reads,
+ * so calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Synchronises the stream. */
+int rpca_get_sparse_noalloc(const float* D, int64_t m, int64_t n, int64_t ld, int r, const double* U,
+                            const double* sigma, const double* V, double zeta, int64_t* idx,
+                            double* val, int64_t cap, int64_t* nnz, void* stream);
+
 /* Diagnostics.  With profiling on, the context records a CUDA event pair around every
  * kernel it launches on its stream.  rpca_get_profile (host outputs, any may be NULL)
  * returns, since profiling was last switched on: the summed device time and the number

@@ -83,12 +83,13 @@ def lib() -> ctypes.CDLL:
     L.rpca_get_sparse.argtypes = [vp, vp, vp, i64, pi64]
     L.rpca_set_profiling.argtypes = [vp, i32]
     L.rpca_get_profile.argtypes = [vp, pdbl, pi64, pdbl, pi64]
+    L.rpca_get_sparse_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp, dbl, vp, vp, i64, pi64, vp]
     solve_args = [vp, i64, i64, i32, dbl, dbl, dbl, vp, vp, vp, vp, vp, i64, pi64, pint, pdbl]
     L.rpca_solve.argtypes = solve_args
     L.rpca_solve_host.argtypes = solve_args
     for name in ("rpca_params_default", "rpca_create", "rpca_init", "rpca_iterate", "rpca_set_zeta",
                  "rpca_get_lowrank", "rpca_get_sparse", "rpca_solve", "rpca_solve_host", "rpca_set_profiling",
-                 "rpca_get_profile"):
+                 "rpca_get_profile", "rpca_get_sparse_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
