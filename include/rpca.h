@@ -58,9 +58,16 @@ typedef struct {
   int precision;     /* rpca_precision                                                   */
   int zeta_mode;     /* rpca_zeta_mode                                                   */
   int init_max_passes; /* cap on D passes of each subspace iteration in rpca_init; 0=40   */
-  double init_tol;   /* relative change of the top singular values that ends a subspace
-                        iteration; 0 selects 1e-13 (FP64) / 1e-6 (FP32)                  */
+  double init_tol;   /* residual of the top Ritz triplets that ends a subspace iteration;
+                        0 selects 1e-13 (FP64) / 1e-6 (FP32)                             */
+  int pass_kind;     /* rpca_pass_kind: kernel of the fused pass                          */
 } rpca_params;
+
+/* Kernel of the fused pass.  AUTO takes the tensor-core (tcgen05 + TMA) pass where it
+ * applies (FP32, compiled rank <= 8, ld a multiple of 4, D 16-byte aligned) and the SIMT
+ * pass otherwise; SIMT and TENSOR force one (TENSOR falls back to SIMT where it does not
+ * apply). */
+typedef enum { RPCA_PASS_AUTO = 0, RPCA_PASS_SIMT = 1, RPCA_PASS_TENSOR = 2 } rpca_pass_kind;
 
 typedef struct {
   int k;               /* iteration index of L_k, S_k                                     */
@@ -101,6 +108,11 @@ int rpca_init(rpca_ctx* ctx, const void* D, int64_t m, int64_t n, int64_t ld, in
  * again to continue) or max_iter was hit.  Synchronises the stream at its end. */
 int rpca_iterate(rpca_ctx* ctx, int n_iters, rpca_iter_stats* stats, int* n_done);
 
+/* Reports the fused-pass kernel in use after rpca_init (host outputs): for the iterations
+ * of Algorithm 1 and for the passes of the initialisation, RPCA_PASS_SIMT or
+ * RPCA_PASS_TENSOR. */
+int rpca_get_pass_kind(rpca_ctx* ctx, int* iteration_kind, int* init_kind);
+
 /* Sets zeta_k for the next pass (zeta_mode EXTERNAL). */
 int rpca_set_zeta(rpca_ctx* ctx, double zeta);
 
@@ -128,6 +140,37 @@ int rpca_solve(const float* D, int64_t m, int64_t n, int r, double beta, double 
 int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, double gamma,
                     double tol, double* U, double* sigma, double* V, int64_t* s_idx,
                     double* s_val, int64_t s_cap, int64_t* nnz, int* iters, double* err);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned threshold schedule: stateless pass and adjoint pass.
+ *
+ * Training a schedule zeta_k = f(statistics) through an unrolled AccAltProj needs the
+ * derivative of one pass in zeta, which the hard threshold of Eq. (10) does not have.
+ * These calls evaluate the pass with the soft gate g(R; zeta) = sigmoid((|R| - zeta) /
+ * (tau zeta)), S = R g, Z = D - S (tau = 0 gives the hard threshold of Eq. (10)), and its
+ * exact adjoint.  They allocate nothing and touch no context.
+ *   D: device, m x n, leading dimension ld, dtype F32 or F64.  W = U Sigma (m x r),
+ *   V (n x r), U~ (m x r), V~ (n x r): device, the same dtype, row-major.  r must be one
+ *   of 1..8, 10, 12, 14, 16 (pad the factors with zero columns otherwise).
+ *   zeta: device pointer to one double.
+ * rpca_learn_pass writes Y1 = Z V~ (m x r), Y2 = Z^T U~ (n x r) and stats[0..2] (device
+ * doubles): sum of (R - S)^2 over all entries, the hard support size |{|R| > zeta}|, and,
+ * when mask_old is given, the number of entries whose hard support membership differs
+ * from mask_old.  mask_new (optional) receives the hard support as a bitmask of
+ * m * ceil(n/32) words (bit j%32 of word i*ceil(n/32) + j/32).
+ * rpca_learn_pass_adjoint takes the cotangents Y1b (m x r), Y2b (n x r), resb of (Y1, Y2,
+ * stats[0]) and writes the cotangents of U~ (Utb), V~ (Vtb), W (Wb), V (Vb) and of zeta
+ * (*zetab, device).  Outputs are cleared by the call; sums use atomics, so results vary at
+ * rounding level between runs.  Both calls enqueue on `stream` and return. */
+int rpca_learn_pass(const void* D, int64_t m, int64_t n, int64_t ld, int dtype, int r, const void* W,
+                    const void* V, const void* Ut, const void* Vt, const double* zeta, double tau,
+                    void* Y1, void* Y2, double* stats, const uint32_t* mask_old, uint32_t* mask_new,
+                    void* stream);
+int rpca_learn_pass_adjoint(const void* D, int64_t m, int64_t n, int64_t ld, int dtype, int r,
+                            const void* W, const void* V, const void* Ut, const void* Vt,
+                            const double* zeta, double tau, const void* Y1b, const void* Y2b,
+                            double resb, void* Utb, void* Vtb, void* Wb, void* Vb, double* zetab,
+                            void* stream);
 
 /* Largest m accepted by rpca_get_sparse_noalloc. */
 #define RPCA_NOALLOC_MAX_ROWS 65536

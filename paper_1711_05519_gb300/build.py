@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librpca.so")
-SOURCES = ["api.cu", "small.cu", "misc.cu", "pass_f32.cu", "pass_f64.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "small.cu", "misc.cu", "pass_f32.cu", "pass_f64.cu", "noalloc.cu", "pass_tc.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 

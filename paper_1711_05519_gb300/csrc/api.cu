@@ -1,5 +1,7 @@
 // C ABI of the AccAltProj library (include/rpca.h): context, workspace and the host loop
 // that enqueues the fused pass and the tall-skinny kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -46,8 +48,10 @@ struct rpca_ctx {
   void* Down = nullptr;
   int vec = 0;
   // workspace
-  double *U = nullptr, *sig = nullptr, *V = nullptr, *Ut = nullptr, *Vt = nullptr, *Y1 = nullptr,
-         *Y2 = nullptr, *part = nullptr;
+  // tall-skinny arrays in the working precision (tsize bytes per entry)
+  void *U = nullptr, *sig = nullptr, *V = nullptr, *Ut = nullptr, *Vt = nullptr, *Y1 = nullptr, *Y2 = nullptr,
+       *part = nullptr;
+  double* lowrank_tmp = nullptr;  // unused
   void *Wc = nullptr, *Vc = nullptr, *Utc = nullptr, *Vtc = nullptr, *P1 = nullptr, *P2 = nullptr;
   double* resP = nullptr;
   unsigned long long* nnzP = nullptr;
@@ -56,6 +60,11 @@ struct rpca_ctx {
   int* h_flags = nullptr;  // pinned: done, k, status, conv
   unsigned long long *rowcnt = nullptr, *rowoff = nullptr;
   bool ready = false;
+  // tensor-core pass
+  bool tc_iter = false, tc_init = false;
+  CUtensorMap dmap;
+  int tcA = 0, tcB = 0, TR = 0, TC = 0;
+  uint8_t *wop = nullptr, *vop = nullptr, *vtop = nullptr, *utop = nullptr;
   // allocation signature of the current workspace
   int64_t ws_m = -1, ws_n = -1;
   int ws_r = -1;
@@ -76,11 +85,11 @@ namespace {
   } while (0)
 
 void free_workspace(rpca_ctx* c) {
-  void** ptrs[] = {(void**)&c->U,   (void**)&c->sig,  (void**)&c->V,    (void**)&c->Ut,   (void**)&c->Vt,
-                   (void**)&c->Y1,  (void**)&c->Y2,   (void**)&c->part, &c->Wc,           &c->Vc,
+  void** ptrs[] = {&c->U,   &c->sig,  &c->V,    &c->Ut,   &c->Vt,
+                   &c->Y1,  &c->Y2,   &c->part, &c->Wc,           &c->Vc,
                    &c->Utc,         &c->Vtc,          &c->P1,           &c->P2,           (void**)&c->resP,
                    (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
-                   &c->Down};
+                   &c->Down, (void**)&c->wop, (void**)&c->vop, (void**)&c->vtop, (void**)&c->utop};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -155,7 +164,10 @@ void prof_collect(rpca_ctx* c, int64_t effective_pass) {
 struct Grid {
   int n_p1, n_p2, n_cta;
 };
+bool use_tc(const rpca_ctx* c, int R) { return (R == c->Rr) ? c->tc_iter : (R == c->Rb ? c->tc_init : false); }
+
 Grid pass_grid(const rpca_ctx* c, int R) {
+  if (use_tc(c, R)) return Grid{c->tcB, c->tcA, c->tcA * c->tcB};
   const PassGeom g = pass_geometry(c->prec, R);
   const int gx = (int)((c->n + g.BW - 1) / g.BW), gy = (int)((c->m + g.BH - 1) / g.BH);
   return Grid{gx, gy, gx * gy};
@@ -178,7 +190,29 @@ int run_pass(rpca_ctx* c, int R) {
   a.nnzP = c->nnzP;
   a.vec = c->vec;
   prof_mark(c, true, true);
-  CK(launch_fused_pass(c->prec, R, a, c->stream));
+  if (use_tc(c, R)) {
+    TcPassArgs t;
+    t.m = (int)c->m;
+    t.n = (int)c->n;
+    t.R = R;
+    t.A = c->tcA;
+    t.B = c->tcB;
+    t.TR = c->TR;
+    t.TC = c->TC;
+    t.wop = c->wop;
+    t.vop = c->vop;
+    t.vtop = c->vtop;
+    t.utop = c->utop;
+    t.st = c->st;
+    t.status = &c->st->status;
+    t.P1 = static_cast<float*>(c->P1);
+    t.P2 = static_cast<float*>(c->P2);
+    t.resP = c->resP;
+    t.nnzP = c->nnzP;
+    CK(launch_fused_pass_tc(&c->dmap, t, c->stream));
+  } else {
+    CK(launch_fused_pass(c->prec, R, a, c->stream));
+  }
   prof_mark(c, true, false);
   return RPCA_OK;
 }
@@ -188,6 +222,58 @@ int run_small(rpca_ctx* c, const SmallArgs& a) {
   CK(launch_small(a, c->small_grid, c->stream));
   prof_mark(c, false, false);
   return RPCA_OK;
+}
+
+// Operand images for the tensor-core pass from the pass-precision copies of width R.
+int pack_images(rpca_ctx* c, int R) {
+  if (!use_tc(c, R)) return RPCA_OK;
+  prof_mark(c, false, true);
+  CK(launch_pack_tc_images(static_cast<const float*>(c->Wc), static_cast<const float*>(c->Vc),
+                           static_cast<const float*>(c->Utc), static_cast<const float*>(c->Vtc), (int)c->m, (int)c->n, R,
+                           c->wop, c->vop, c->vtop, c->utop, c->st, c->stream));
+  prof_mark(c, false, false);
+  return RPCA_OK;
+}
+
+// A x B CTA grid of the tensor-core pass: every CTA gets at least one 128-row and one
+// 64-column tile and at most 20 column tiles (tensor-memory budget); minimises the
+// largest block of tiles.
+bool tc_partition(int TR, int TC, int nsm, int* A, int* B) {
+  long best = -1;
+  int bA = 0, bB = 0;
+  for (int a = 1; a <= TR && a <= nsm; ++a) {
+    int b = nsm / a;
+    if (b > TC) b = TC;
+    if (b < 1) continue;
+    if ((TC + b - 1) / b > 20) continue;
+    const long mx = (long)((TR + a - 1) / a) * ((TC + b - 1) / b);
+    if (best < 0 || mx < best || (mx == best && a * b > bA * bB)) {
+      best = mx;
+      bA = a;
+      bB = b;
+    }
+  }
+  if (best < 0) return false;
+  *A = bA;
+  *B = bB;
+  return true;
+}
+
+bool encode_dmap(rpca_ctx* c) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&enc, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        !enc)
+      return false;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)c->n, (cuuint64_t)c->m};
+  cuuint64_t gstr[1] = {(cuuint64_t)c->ld * 4};
+  cuuint32_t box[2] = {32, 128}, es[2] = {1, 1};
+  return enc(&c->dmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(c->D), gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 SmallArgs small_args(rpca_ctx* c, int mode, int R) {
@@ -281,7 +367,7 @@ int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
   const rpca_params& p = *params;
   if (!(p.beta > 0) || !(p.gamma >= 0 && p.gamma < 1) || !(p.tol >= 0) || p.max_iter < 0 ||
       (p.precision != RPCA_PREC_FP32 && p.precision != RPCA_PREC_FP64) || p.zeta_mode < 0 || p.zeta_mode > 2 ||
-      p.beta_init < 0 || p.mu_trim < 0)
+      p.beta_init < 0 || p.mu_trim < 0 || p.pass_kind < 0 || p.pass_kind > 2)
     return RPCA_ERR_INVALID_ARG;
   rpca_ctx* c = new (std::nothrow) rpca_ctx();
   if (!c) return RPCA_ERR_CUDA;
@@ -323,7 +409,9 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   c->n = n;
   c->r = r;
   c->Rr = padded_rank(r);
-  int b = (2 * r <= 16) ? 2 * r : 16;
+  // block size of the initial subspace iteration: oversample to 8 columns for r <= 6 (so
+  // the tensor-core pass, compiled for ranks up to 8, runs the initialisation as well)
+  int b = (r <= 6) ? 8 : ((2 * r <= 16) ? 2 * r : 16);
   const int64_t mn_min = m < n ? m : n;
   if (b > mn_min) b = (int)(mn_min & ~1ll);
   if (b < r) b = r + (r & 1);
@@ -344,22 +432,44 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     c->ld = n;
   }
   c->vec = ((reinterpret_cast<uintptr_t>(c->D) & 15) == 0 && ((c->ld * (int64_t)c->tsize) & 15) == 0) ? 1 : 0;
+  c->tc_iter = c->tc_init = false;
+  if (c->prec == PREC_F32 && c->vec && c->p.pass_kind != RPCA_PASS_SIMT) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    c->TR = (int)((m + 127) / 128);
+    c->TC = (int)((n + 63) / 64);
+    if (nsm > 0 && tc_partition(c->TR, c->TC, nsm, &c->tcA, &c->tcB) && encode_dmap(c)) {
+      c->tc_iter = tc_pass_supported(c->Rr);
+      c->tc_init = tc_pass_supported(c->Rb);
+    }
+  }
 
   const int w = c->b > c->r ? c->b : c->r;
   const int Rmax = c->Rb > c->Rr ? c->Rb : c->Rr;
   size_t p1 = 0, p2 = 0, ncta = 0;
   for (int R : {c->Rr, c->Rb}) {
-    const Grid g = pass_grid(c, R);
-    p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
-    p2 = p2 > (size_t)g.n_p2 * n * R ? p2 : (size_t)g.n_p2 * n * R;
-    ncta = ncta > (size_t)g.n_cta ? ncta : (size_t)g.n_cta;
+    const PassGeom pg = pass_geometry(c->prec, R);
+    const Grid gs{(int)((n + pg.BW - 1) / pg.BW), (int)((m + pg.BH - 1) / pg.BH), 0};
+    const Grid gt{c->tcB, c->tcA, c->tcA * c->tcB};
+    for (const Grid& g : {gs, gt}) {
+      p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
+      p2 = p2 > (size_t)g.n_p2 * n * R ? p2 : (size_t)g.n_p2 * n * R;
+    }
+    ncta = ncta > (size_t)gs.n_p1 * gs.n_p2 ? ncta : (size_t)gs.n_p1 * gs.n_p2;
+    ncta = ncta > (size_t)gt.n_cta ? ncta : (size_t)gt.n_cta;
   }
   int st = RPCA_OK;
   if (!reuse) {
-  if ((st = dalloc(&c->U, (size_t)m * r)) || (st = dalloc(&c->sig, 16)) || (st = dalloc(&c->V, (size_t)n * r)) ||
-      (st = dalloc(&c->Ut, (size_t)m * w)) || (st = dalloc(&c->Vt, (size_t)n * w)) ||
-      (st = dalloc(&c->Y1, (size_t)m * w)) || (st = dalloc(&c->Y2, (size_t)n * w)) ||
-      (st = dalloc(&c->part, (size_t)c->small_grid * 4 * 256)) || (st = dalloc(&c->resP, ncta)) ||
+  const size_t ts = c->tsize;
+  CK(cudaMalloc(&c->U, (size_t)m * r * ts));
+  CK(cudaMalloc(&c->sig, 16 * ts));
+  CK(cudaMalloc(&c->V, (size_t)n * r * ts));
+  CK(cudaMalloc(&c->Ut, (size_t)m * w * ts));
+  CK(cudaMalloc(&c->Vt, (size_t)n * w * ts));
+  CK(cudaMalloc(&c->Y1, (size_t)m * w * ts));
+  CK(cudaMalloc(&c->Y2, (size_t)n * w * ts));
+  CK(cudaMalloc(&c->part, (size_t)c->small_grid * 4 * 256 * ts));
+  if ((st = dalloc(&c->resP, ncta)) ||
       (st = dalloc(&c->nnzP, ncta)) || (st = dalloc(&c->st, 1)) || (st = dalloc(&c->stats, (size_t)c->p.max_iter + 2)))
     return st;
   CK(cudaMalloc(&c->Wc, (size_t)m * Rmax * c->tsize));
@@ -368,12 +478,22 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   CK(cudaMalloc(&c->Vtc, (size_t)n * Rmax * c->tsize));
   CK(cudaMalloc(&c->P1, p1 * c->tsize));
   CK(cudaMalloc(&c->P2, p2 * c->tsize));
+  if (c->TR > 0) {
+    CK(cudaMalloc((void**)&c->wop, (size_t)c->TR * 16384));
+    CK(cudaMalloc((void**)&c->utop, (size_t)c->TR * 4096));
+    CK(cudaMalloc((void**)&c->vop, (size_t)c->TC * 8192));
+    CK(cudaMalloc((void**)&c->vtop, (size_t)c->TC * 2048));
+    CK(cudaMemsetAsync(c->wop, 0, (size_t)c->TR * 16384, c->stream));
+    CK(cudaMemsetAsync(c->utop, 0, (size_t)c->TR * 4096, c->stream));
+    CK(cudaMemsetAsync(c->vop, 0, (size_t)c->TC * 8192, c->stream));
+    CK(cudaMemsetAsync(c->vtop, 0, (size_t)c->TC * 2048, c->stream));
+  }
   c->ws_m = m;
   c->ws_n = n;
   c->ws_r = r;
   }
   CK(cudaMemsetAsync(c->stats, 0, sizeof(DevStats) * ((size_t)c->p.max_iter + 2), c->stream));
-  CK(cudaMemsetAsync(c->sig, 0, 16 * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(c->sig, 0, 16 * c->tsize, c->stream));
 
   DevState h;
   memset(&h, 0, sizeof(h));
@@ -393,6 +513,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   // D - S_{-1} (the pass with L = 0 and zeta_{-1} keeps exactly D_ij where |D_ij| <= zeta).
   SmallArgs ra = small_args(c, SM_RAND, c->Rb);
   if ((st = run_small(c, ra))) return st;
+  if ((st = pack_images(c, c->Rb))) return st;
   for (int phase = 0; phase < 2; ++phase) {
     bool conv = false;
     for (int q = 0; q < c->p.init_max_passes && !conv; ++q) {
@@ -406,9 +527,19 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       prof_collect(c, -1);
       if (flag_status(c)) return flag_status(c);
       conv = flag_conv(c) != 0;
+      // images for the next pass: init width, or the iteration width once phase B is done
+      if ((st = pack_images(c, (conv && phase == 1) ? c->Rr : c->Rb))) return st;
     }
   }
   c->ready = true;
+  return RPCA_OK;
+}
+
+int rpca_get_pass_kind(rpca_ctx* c, int* iteration_kind, int* init_kind) {
+  if (!c) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  if (iteration_kind) *iteration_kind = c->tc_iter ? RPCA_PASS_TENSOR : RPCA_PASS_SIMT;
+  if (init_kind) *init_kind = c->tc_init ? RPCA_PASS_TENSOR : RPCA_PASS_SIMT;
   return RPCA_OK;
 }
 
@@ -432,6 +563,7 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     for (int i = 0; i < chunk; ++i) {
       if ((st = run_pass(c, c->Rr))) return st;
       if ((st = run_small(c, small_args(c, SM_UPDATE, c->Rr)))) return st;
+      if ((st = pack_images(c, c->Rr))) return st;
     }
     launched += chunk;
     if ((st = read_flags(c))) return st;
@@ -471,9 +603,15 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
 int rpca_get_lowrank(rpca_ctx* c, double* U, double* sigma, double* V) {
   if (!c || !U || !sigma || !V) return RPCA_ERR_INVALID_ARG;
   if (!c->ready) return RPCA_ERR_STATE;
-  CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(sigma, c->sig, sizeof(double) * c->r, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(V, c->V, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->prec == PREC_F64) {
+    CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(sigma, c->sig, sizeof(double) * c->r, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(V, c->V, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(launch_convert_f32_to_f64(static_cast<const float*>(c->U), c->r, U, (int)c->m, c->r, c->stream));
+    CK(launch_convert_f32_to_f64(static_cast<const float*>(c->sig), c->r, sigma, 1, c->r, c->stream));
+    CK(launch_convert_f32_to_f64(static_cast<const float*>(c->V), c->r, V, (int)c->n, c->r, c->stream));
+  }
   return RPCA_OK;
 }
 

@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/rpca.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,6 +75,30 @@ struct PassArgs {
 // Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
 cudaError_t launch_fused_pass(int prec, int R, const PassArgs& a, cudaStream_t s);
 
+// Tensor-core fused pass (FP32 D, compiled rank R <= 8); see pass_tc.cu.
+struct TcPassArgs {
+  int m, n, R;
+  int A, B;      // CTA grid: A row groups x B column groups
+  int TR, TC;    // 128-row and 64-column tile counts
+  const uint8_t* wop;   // [TR] 16 KB images of [W_hi W_hi W_lo 0] (tf32, 128B-swizzled)
+  const uint8_t* vop;   // [TC] 8 KB images of [V_hi V_lo V_hi 0]
+  const uint8_t* vtop;  // [TC] 2 KB images of [V~_hi | V~_lo]^T (bf16)
+  const uint8_t* utop;  // [TR] 4 KB images of [U~_hi | U~_lo]^T (bf16)
+  const DevState* st;
+  int* status;
+  float* P1;     // [B][m][R]
+  float* P2;     // [A][n][R]
+  double* resP;  // [A*B]
+  unsigned long long* nnzP;
+};
+bool tc_pass_supported(int R);
+size_t tc_pass_smem();
+cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, cudaStream_t s);
+// Rewrites the operand images from the FP32 pass copies W, V, U~, V~ (width R <= 8).
+cudaError_t launch_pack_tc_images(const float* Wc, const float* Vc, const float* Utc, const float* Vtc, int m, int n,
+                                  int R, uint8_t* wop, uint8_t* vop, uint8_t* vtop, uint8_t* utop, const DevState* st,
+                                  cudaStream_t s);
+
 // Sparse extraction (three kernels): per-row counts, exclusive scan, ordered write.
 struct ExtractArgs {
   const void* D;
@@ -107,10 +132,12 @@ struct SmallArgs {
   const void* P2;
   const double* resP;
   const unsigned long long* nnzP;
-  double* U; double* sig; double* V;   // master factors (m x r, r, n x r)
-  double* Ut; double* Vt;              // FP64 bases (m x w, n x w), w = r or b
-  double* Y1; double* Y2;              // m x w, n x w
-  double* part;                        // [grid][2][32*32] Gram partials
+  // Arrays below hold the kernel's working precision (double in FP64 mode, float in
+  // FP32 mode).
+  void* U; void* sig; void* V;         // factors of L_k (m x r, r, n x r)
+  void* Ut; void* Vt;                  // bases (m x w, n x w), w = r or b
+  void* Y1; void* Y2;                  // m x w, n x w
+  void* part;                          // [grid][4][16*16] Gram partials
   void* Wc; void* Vc; void* Utc; void* Vtc;  // pass-precision copies, width Rc
   int Rc;                              // width of the copies written for an init pass
   int Rit;                             // width of the copies written for an iteration pass

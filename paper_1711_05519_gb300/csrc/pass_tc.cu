@@ -1,0 +1,491 @@
+// Tensor-core fused pass (tcgen05 + TMA) for FP32 D and compiled rank R <= 8.
+//
+// Same quantities as the SIMT pass (pass_impl.cuh): per entry of D, rebuild L_ij, take
+// R_ij = D_ij - L_ij, the strict threshold S_ij = R_ij if |R_ij| > zeta_k (Eq. (10)),
+// the residual sum over unthresholded entries (Eq. (11)) and Z = D - S_k; accumulate
+// Y1 = Z V~ and Y2 = Z^T U~ (Section 2.1).  D is read once from HBM.
+//
+// Work decomposition.  D is cut into 128 x 64 tiles.  The CTA grid is A x B (one CTA per
+// SM); CTA (a, b) owns a contiguous block of row tiles and column tiles and walks it row
+// tile by row tile.  Y1 for the current row tile and Y2 for every column tile of the CTA
+// stay in tensor memory, so each CTA writes one Y1 partial per row (slice b) and one Y2
+// partial per column (slice a).
+//
+// Per tile:
+//   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, 128-byte swizzle) plus the operand
+//                      images of V (tf32 hi/lo), V~ and U~ (bf16 hi/lo) -> stage s (3 stages)
+//   MMA (warp 1)     : L = [W_hi W_hi W_lo 0] [V_hi V_lo V_hi 0]^T, kind::tf32, M128 N64 K32
+//                      (three-term split product: FP32-level accuracy of the K = r rebuild)
+//   epilogue (8 warps): L from TMEM, D from shared memory, threshold, residual, support
+//                      count, Z split into bf16 hi + lo, written K-major 128B-swizzled
+//   MMA (warp 1)     : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N16 K64 (x2)
+//                      Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N16 K128
+// The column halves of the N16 accumulators (hi and lo parts of V~, U~) and the two M
+// halves of the Y2 accumulator (Z_hi, Z_lo) are added when the accumulators are drained.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc_util.cuh"
+
+namespace rpca {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128, BN = 64;
+constexpr int NSTAGE = 3;
+constexpr int D_BYTES = BM * BN * 4;          // 32 KB
+constexpr int VOP_BYTES = BN * 32 * 4;        // 8 KB  [64 x 32] tf32
+constexpr int VTOP_BYTES = 16 * 64 * 2;       // 2 KB  [16 x 64] bf16
+constexpr int UTOP_BYTES = 2 * 16 * 64 * 2;   // 4 KB  2 x [16 x 64] bf16
+constexpr int WOP_BYTES = BM * 32 * 4;        // 16 KB [128 x 32] tf32
+constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES + UTOP_BYTES;  // 46 KB
+constexpr int Z_BYTES = 2 * BM * BN * 2;      // hi + lo, 32 KB
+constexpr int OFF_STAGE = 0;
+constexpr int OFF_Z = NSTAGE * STAGE_BYTES;
+constexpr int OFF_W = OFF_Z + Z_BYTES;
+constexpr int OFF_BAR = OFF_W + 2 * WOP_BYTES;
+constexpr int NBAR = 32;
+constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 256 + 1024;  // + alignment slack
+constexpr int THREADS = 320;                  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int EPI_THREADS = 256;
+constexpr int TMEM_COLS = 512;
+constexpr int TM_Y1 = 128, TM_Y2 = 160;
+static_assert(STAGE_BYTES % 1024 == 0 && OFF_Z % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned operands");
+static_assert(SMEM_BYTES <= 232448, "shared memory");
+
+// barrier slots
+enum {
+  B_FULL = 0,      // [3]
+  B_EMPTY = 3,     // [3]
+  B_LFULL = 6,     // [2]
+  B_LEMPTY = 8,    // [2]
+  B_ZFULL = 10,
+  B_ZEMPTY = 11,
+  B_WFULL = 12,    // [2]
+  B_WEMPTY = 14,   // [2]
+  B_Y1FULL = 16,   // [2]
+  B_Y1EMPTY = 18,  // [2]
+  B_YFIN = 20,
+  B_DRAIN = 21
+};
+
+constexpr uint32_t kErrTimeout = 6;
+
+struct TcArgs {
+  int m, n, R;
+  int A, B, TR, TC;
+  const uint8_t* wop;
+  const uint8_t* vop;
+  const uint8_t* vtop;
+  const uint8_t* utop;
+  const DevState* st;
+  int* status;
+  float* P1;
+  float* P2;
+  double* resP;
+  unsigned long long* nnzP;
+};
+
+__device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) {
+  atomicCAS(a.status, 0, (int)kErrTimeout);
+  *abort_flag = 1;
+}
+
+__global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap, TcArgs a) {
+  if (a.st->done) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  __shared__ double red_res[8];
+  __shared__ unsigned long long red_nnz[8];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cta = blockIdx.x;
+  const int ai = cta / a.B, bi = cta % a.B;
+  const int rt0 = (int)((long long)ai * a.TR / a.A), rt1 = (int)((long long)(ai + 1) * a.TR / a.A);
+  const int ct0 = (int)((long long)bi * a.TC / a.B), ct1 = (int)((long long)(bi + 1) * a.TC / a.B);
+  const int nrt = rt1 - rt0, nct = ct1 - ct0;
+  const int ntiles = nrt * nct;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&bar[B_FULL + s], 1);
+      mbar_init(&bar[B_EMPTY + s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar[B_LFULL + i], 1);
+      mbar_init(&bar[B_LEMPTY + i], 8);
+      mbar_init(&bar[B_WFULL + i], 1);
+      mbar_init(&bar[B_WEMPTY + i], 1);
+      mbar_init(&bar[B_Y1FULL + i], 1);
+      mbar_init(&bar[B_Y1EMPTY + i], 4);
+    }
+    mbar_init(&bar[B_ZFULL], 8);
+    mbar_init(&bar[B_ZEMPTY], 1);
+    mbar_init(&bar[B_YFIN], 1);
+    mbar_init(&bar[B_DRAIN], 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (ntiles > 0 && warp == 0 && lane == 0) {
+    // ------------------------------------------------------------------ producer
+    int issued = 0;
+    for (int t = 0; t < ntiles && !abort_flag; ++t) {
+      const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE;
+      const int rt = rt0 + rtl, ct = ct0 + ctl;
+      if (ctl == 0) {
+        const int wb = rtl & 1;
+        if (rtl >= 2 && !mbar_wait(&bar[B_WEMPTY + wb], ((rtl - 2) >> 1) & 1)) {
+          fail(a, &abort_flag);
+          break;
+        }
+        mbar_arrive_expect_tx(&bar[B_WFULL + wb], WOP_BYTES);
+        bulk_load(sm + OFF_W + wb * WOP_BYTES, a.wop + (size_t)rt * WOP_BYTES, WOP_BYTES, &bar[B_WFULL + wb]);
+      }
+      if (t >= NSTAGE && !mbar_wait(&bar[B_EMPTY + s], ((t - NSTAGE) / NSTAGE) & 1)) {
+        fail(a, &abort_flag);
+        break;
+      }
+      uint8_t* st = sm + OFF_STAGE + s * STAGE_BYTES;
+      mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES);
+      tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
+      tma_load_2d(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s]);
+      bulk_load(st + D_BYTES, a.vop + (size_t)ct * VOP_BYTES, VOP_BYTES, &bar[B_FULL + s]);
+      bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
+      bulk_load(st + D_BYTES + VOP_BYTES + VTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES,
+                &bar[B_FULL + s]);
+      issued = t + 1;
+    }
+    // wait (bounded) for this thread's copies still in flight before the CTA may exit
+    for (int t = (issued > NSTAGE ? issued - NSTAGE : 0); t < issued; ++t)
+      mbar_wait(&bar[B_FULL + (t % NSTAGE)], (t / NSTAGE) & 1, 100000000ull);
+  } else if (ntiles > 0 && warp == 1 && lane == 0) {
+    // ------------------------------------------------------------------ MMA issuer
+    const uint32_t base = smem_u32(sm);
+    const uint32_t idL = instr_desc(128, 64, 2, 2, false, false);
+    const uint32_t idY1 = instr_desc(128, 16, 1, 1, false, false);
+    const uint32_t idY2 = instr_desc(128, 16, 1, 1, true, false);
+    for (int t = 0; t <= ntiles && !abort_flag; ++t) {
+      if (t < ntiles) {
+        const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, wb = rtl & 1;
+        bool ok = true;
+        if (ctl == 0) ok = ok && mbar_wait(&bar[B_WFULL + wb], (rtl >> 1) & 1);
+        ok = ok && mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1);
+        if (t >= 2) ok = ok && mbar_wait(&bar[B_LEMPTY + lb], ((t - 2) >> 1) & 1);
+        if (!ok) {
+          fail(a, &abort_flag);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t wop = base + OFF_W + wb * WOP_BYTES;
+        const uint32_t vop = base + OFF_STAGE + s * STAGE_BYTES + D_BYTES;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_tf32(tmem + lb * BN, smem_desc(wop + 32 * k, 16, 1024), smem_desc(vop + 32 * k, 16, 1024), idL, k > 0);
+        mma_commit(&bar[B_LFULL + lb]);
+        if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
+      }
+      if (t >= 1) {
+        const int tp = t - 1;
+        const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE, yb = rtl & 1;
+        bool ok = mbar_wait(&bar[B_ZFULL], tp & 1);
+        if (ok && ctl == 0 && rtl >= 2) ok = mbar_wait(&bar[B_Y1EMPTY + yb], ((rtl - 2) >> 1) & 1);
+        if (!ok) {
+          fail(a, &abort_flag);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t zhi = base + OFF_Z, zlo = base + OFF_Z + Z_BYTES / 2;
+        const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
+        const uint32_t vtop = stg + D_BYTES + VOP_BYTES, utop = stg + D_BYTES + VOP_BYTES + VTOP_BYTES;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_f16(tmem + TM_Y1 + yb * 16, smem_desc((h ? zlo : zhi) + 32 * k, 16, 1024),
+                    smem_desc(vtop + 32 * k, 16, 1024), idY1, !(ctl == 0 && h == 0 && k == 0));
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          mma_f16(tmem + TM_Y2 + ctl * 16, smem_desc(zhi + 2048 * k, Z_BYTES / 2, 1024),
+                  smem_desc(utop + (k >= 4 ? 2048 : 0) + 32 * (k & 3), 16, 1024), idY2, !(rtl == 0 && k == 0));
+        mma_commit(&bar[B_ZEMPTY]);
+        mma_commit(&bar[B_EMPTY + s]);
+        if (ctl == nct - 1) mma_commit(&bar[B_Y1FULL + yb]);
+      }
+    }
+    mma_commit(&bar[B_YFIN]);
+    mma_commit(&bar[B_DRAIN]);
+    mbar_wait(&bar[B_DRAIN], 0, 100000000ull);  // all issued MMAs complete before TMEM is freed
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int rowl = 32 * q + lane;
+    const float zeta = static_cast<float>(a.st->zeta);
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    float res = 0.f;
+    unsigned nnz = 0;
+    uint8_t* zhi = sm + OFF_Z;
+    uint8_t* zlo = sm + OFF_Z + Z_BYTES / 2;
+    for (int t = 0; t < ntiles && !abort_flag; ++t) {
+      const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
+      if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
+        fail(a, &abort_flag);
+        break;
+      }
+      tc_fence_after();
+      uint32_t lv[32];
+      tmem_ld32(tmem + lane_base + lb * BN + 32 * h, lv);
+      const uint8_t* drow = sm + OFF_STAGE + s * STAGE_BYTES + h * (D_BYTES / 2) + rowl * 128;
+      float z[32];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
+        const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z[4 * c + e] = dv[e];
+      }
+      tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float l = __uint_as_float(lv[c]);
+        const float rr = z[c] - l;
+        const bool sflag = fabsf(rr) > zeta;
+        res = sflag ? res : fmaf(rr, rr, res);
+        nnz += sflag ? 1u : 0u;
+        z[c] = sflag ? l : z[c];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
+      if (t >= 1 && !mbar_wait(&bar[B_ZEMPTY], (t - 1) & 1)) {
+        fail(a, &abort_flag);
+        break;
+      }
+      // Z -> bf16 hi/lo, row rowl, columns 32h .. 32h+31 = 16-byte chunks 4h .. 4h+3
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float z0 = z[8 * c + 2 * e], z1 = z[8 * c + 2 * e + 1];
+          const __nv_bfloat162 hi = __floats2bfloat162_rn(z0, z1);
+          const float2 hf = __bfloat1622float2(hi);
+          const __nv_bfloat162 lo = __floats2bfloat162_rn(z0 - hf.x, z1 - hf.y);
+          hw[e] = *reinterpret_cast<const uint32_t*>(&hi);
+          lw[e] = *reinterpret_cast<const uint32_t*>(&lo);
+        }
+        const int off = rowl * 128 + ((((4 * h + c) ^ (rowl & 7)) & 7) << 4);
+        *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[B_ZFULL]);
+      if (ctl == nct - 1 && h == 0) {
+        // drain Y1 of this row tile
+        if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {
+          fail(a, &abort_flag);
+          break;
+        }
+        tc_fence_after();
+        uint32_t yv[16];
+        tmem_ld16(tmem + lane_base + TM_Y1 + yb * 16, yv);
+        tmem_wait_ld();
+        const int row = (rt0 + rtl) * BM + rowl;
+        if (row < a.m)
+          for (int k = 0; k < a.R; ++k)
+            a.P1[((size_t)bi * a.m + row) * a.R + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[8 + k]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[B_Y1EMPTY + yb]);
+      }
+    }
+    // drain Y2: each warp takes the column tiles ctl = h, h + 2, ...; lane quarter q holds
+    // accumulator rows 32q .. 32q+31 (rows 0..63: Z_hi part, 64..127: Z_lo part)
+    if (ntiles > 0 && !abort_flag) {
+      if (!mbar_wait(&bar[B_YFIN], 0)) {
+        fail(a, &abort_flag);
+      } else {
+        tc_fence_after();
+        float* scratch = reinterpret_cast<float*>(sm + OFF_STAGE);  // [nct][128][8], stages are idle now
+        for (int ctl = h; ctl < nct; ctl += 2) {
+          uint32_t yv[16];
+          tmem_ld16(tmem + lane_base + TM_Y2 + ctl * 16, yv);
+          tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            scratch[((size_t)ctl * BM + rowl) * 8 + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[8 + k]);
+        }
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
+    if (ntiles > 0 && !abort_flag) {
+      const float* scratch = reinterpret_cast<const float*>(sm + OFF_STAGE);
+      const int et = tid - 64;
+      for (int e = et; e < nct * 64; e += EPI_THREADS) {
+        const int ctl = e / 64, jl = e % 64;
+        const int col = (ct0 + ctl) * BN + jl;
+        if (col < a.n)
+          for (int k = 0; k < a.R; ++k)
+            a.P2[((size_t)ai * a.n + col) * a.R + k] =
+                scratch[((size_t)ctl * BM + jl) * 8 + k] + scratch[((size_t)ctl * BM + 64 + jl) * 8 + k];
+      }
+    }
+    // CTA totals of the residual and the support size
+    double rd = (double)res;
+    unsigned long long nz = nnz;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rd += __shfl_xor_sync(0xffffffffu, rd, o);
+      nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    }
+    if (lane == 0) {
+      red_res[warp - 2] = rd;
+      red_nnz[warp - 2] = nz;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
+    if (tid == 64) {
+      double tr = 0.0;
+      unsigned long long tz = 0;
+      for (int w = 0; w < 8; ++w) {
+        tr += red_res[w];
+        tz += red_nnz[w];
+      }
+      a.resP[cta] = tr;
+      a.nnzP[cta] = tz;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace
+
+bool tc_pass_supported(int R) { return R <= 8; }
+
+size_t tc_pass_smem() { return SMEM_BYTES; }
+
+namespace {
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ int sw128(int row, int byte_in_row) {
+  return row * 128 + ((((byte_in_row >> 4) ^ (row & 7)) & 7) << 4) + (byte_in_row & 15);
+}
+
+// One thread per row of W / U~ (i < m) and per row of V / V~ (j < n).
+__global__ void pack_tc_images(const float* __restrict__ Wc, const float* __restrict__ Vc,
+                               const float* __restrict__ Utc, const float* __restrict__ Vtc, int m, int n, int R,
+                               uint8_t* __restrict__ wop, uint8_t* __restrict__ vop, uint8_t* __restrict__ vtop,
+                               uint8_t* __restrict__ utop, const DevState* st) {
+  if (st->done) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < m) {
+    const int i = idx, rt = i / BM, il = i % BM;
+    float hi[8], lo[8];
+    __nv_bfloat16 uh[8], ul[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float w = k < R ? Wc[(size_t)i * R + k] : 0.f;
+      hi[k] = tf32_rna(w);
+      lo[k] = w - hi[k];
+      const float u = k < R ? Utc[(size_t)i * R + k] : 0.f;
+      uh[k] = __float2bfloat16_rn(u);
+      ul[k] = __float2bfloat16_rn(u - __bfloat162float(uh[k]));
+    }
+    float* wt = reinterpret_cast<float*>(wop + (size_t)rt * WOP_BYTES);
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+      const float v = kk < 8 ? hi[kk] : kk < 16 ? hi[kk - 8] : kk < 24 ? lo[kk - 16] : 0.f;
+      wt[sw128(il, 4 * kk) >> 2] = v;
+    }
+    __nv_bfloat16* ut = reinterpret_cast<__nv_bfloat16*>(utop + (size_t)rt * UTOP_BYTES);
+    const int sub = il / 64, kl = il % 64;
+#pragma unroll
+    for (int nn = 0; nn < 16; ++nn) ut[(sub * 2048 + sw128(nn, 2 * kl)) >> 1] = nn < 8 ? uh[nn] : ul[nn - 8];
+  }
+  if (idx < n) {
+    const int j = idx, ct = j / BN, jl = j % BN;
+    float hi[8], lo[8];
+    __nv_bfloat16 vh[8], vl[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float v = k < R ? Vc[(size_t)j * R + k] : 0.f;
+      hi[k] = tf32_rna(v);
+      lo[k] = v - hi[k];
+      const float u = k < R ? Vtc[(size_t)j * R + k] : 0.f;
+      vh[k] = __float2bfloat16_rn(u);
+      vl[k] = __float2bfloat16_rn(u - __bfloat162float(vh[k]));
+    }
+    float* vt = reinterpret_cast<float*>(vop + (size_t)ct * VOP_BYTES);
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+      const float v = kk < 8 ? hi[kk] : kk < 16 ? lo[kk - 8] : kk < 24 ? hi[kk - 16] : 0.f;
+      vt[sw128(jl, 4 * kk) >> 2] = v;
+    }
+    __nv_bfloat16* tt = reinterpret_cast<__nv_bfloat16*>(vtop + (size_t)ct * VTOP_BYTES);
+#pragma unroll
+    for (int nn = 0; nn < 16; ++nn) tt[sw128(nn, 2 * jl) >> 1] = nn < 8 ? vh[nn] : vl[nn - 8];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_tc_images(const float* Wc, const float* Vc, const float* Utc, const float* Vtc, int m, int n,
+                                  int R, uint8_t* wop, uint8_t* vop, uint8_t* vtop, uint8_t* utop, const DevState* st,
+                                  cudaStream_t s) {
+  const int rows = m > n ? m : n;
+  pack_tc_images<<<(rows + 255) / 256, 256, 0, s>>>(Wc, Vc, Utc, Vtc, m, n, R, wop, vop, vtop, utop, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(fused_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  TcArgs a;
+  a.m = p.m;
+  a.n = p.n;
+  a.R = p.R;
+  a.A = p.A;
+  a.B = p.B;
+  a.TR = p.TR;
+  a.TC = p.TC;
+  a.wop = p.wop;
+  a.vop = p.vop;
+  a.vtop = p.vtop;
+  a.utop = p.utop;
+  a.st = p.st;
+  a.status = p.status;
+  a.P1 = p.P1;
+  a.P2 = p.P2;
+  a.resP = p.resP;
+  a.nnzP = p.nnzP;
+  fused_pass_tc<<<p.A * p.B, THREADS, SMEM_BYTES, s>>>(*dmap, a);
+  return cudaGetLastError();
+}
+
+}  // namespace rpca

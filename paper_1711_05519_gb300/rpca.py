@@ -20,6 +20,7 @@ OK, INVALID_ARG, CUDA_ERR, NUMERICAL, CAPACITY, NOT_CONVERGED, TIMEOUT, STATE = 
 DTYPE_F64, DTYPE_F32 = 0, 1
 PREC = {"fp64": 0, "fp32": 1}
 ZETA = {"paper": 0, "simple": 1, "external": 2}
+PASS_KIND = {"auto": 0, "simt": 1, "tensor": 2}
 
 
 class RpcaError(RuntimeError):
@@ -41,6 +42,7 @@ class Params(ctypes.Structure):
         ("zeta_mode", ctypes.c_int),
         ("init_max_passes", ctypes.c_int),
         ("init_tol", ctypes.c_double),
+        ("pass_kind", ctypes.c_int),
     ]
 
 
@@ -83,13 +85,14 @@ def lib() -> ctypes.CDLL:
     L.rpca_get_sparse.argtypes = [vp, vp, vp, i64, pi64]
     L.rpca_set_profiling.argtypes = [vp, i32]
     L.rpca_get_profile.argtypes = [vp, pdbl, pi64, pdbl, pi64]
+    L.rpca_get_pass_kind.argtypes = [vp, pint, pint]
     L.rpca_get_sparse_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp, dbl, vp, vp, i64, pi64, vp]
     solve_args = [vp, i64, i64, i32, dbl, dbl, dbl, vp, vp, vp, vp, vp, i64, pi64, pint, pdbl]
     L.rpca_solve.argtypes = solve_args
     L.rpca_solve_host.argtypes = solve_args
     for name in ("rpca_params_default", "rpca_create", "rpca_init", "rpca_iterate", "rpca_set_zeta",
                  "rpca_get_lowrank", "rpca_get_sparse", "rpca_solve", "rpca_solve_host", "rpca_set_profiling",
-                 "rpca_get_profile", "rpca_get_sparse_noalloc"):
+                 "rpca_get_profile", "rpca_get_sparse_noalloc", "rpca_get_pass_kind"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -123,7 +126,7 @@ class Solver:
 
     def __init__(self, beta: float, gamma: float, tol: float, precision: str = "fp32", trim: bool = True,
                  zeta_mode: str = "paper", max_iter: int = 100, beta_init: float = 0.0, mu_trim: float = 0.0,
-                 init_max_passes: int = 0, init_tol: float = 0.0, stream=None):
+                 init_max_passes: int = 0, init_tol: float = 0.0, pass_kind: str = "auto", stream=None):
         L = lib()
         p = Params()
         L.rpca_params_default(ctypes.byref(p))
@@ -132,6 +135,7 @@ class Solver:
         p.max_iter, p.trim = max_iter, int(bool(trim))
         p.precision, p.zeta_mode = PREC[precision], ZETA[zeta_mode]
         p.init_max_passes, p.init_tol = init_max_passes, init_tol
+        p.pass_kind = PASS_KIND[pass_kind]
         self.params = p
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._ctx = ctypes.c_void_p()
@@ -181,6 +185,12 @@ class Solver:
     def run(self, max_passes: int | None = None) -> tuple[int, list[dict]]:
         """Iterates until err_k < tol or the iteration cap."""
         return self.iterate(max_passes if max_passes is not None else self.params.max_iter + 1)
+
+    def pass_kind(self) -> tuple[str, str]:
+        it, ini = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().rpca_get_pass_kind(self._ctx, ctypes.byref(it), ctypes.byref(ini)), "rpca_get_pass_kind")
+        names = {1: "simt", 2: "tensor"}
+        return names[it.value], names[ini.value]
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().rpca_set_profiling(self._ctx, int(bool(on))), "rpca_set_profiling")
