@@ -46,7 +46,7 @@ CMAG = 1.0
 SEED = 0
 TOL = 1e-5
 PROFILE_JSON = os.path.join(ROOT, "profiles", "fused_pass_traffic.json")
-KERNEL_SOURCES = ["paper_1711_05519_gb300/csrc/pass_impl.cuh", "paper_1711_05519_gb300/csrc/pass_f32.cu"]
+KERNEL_SOURCES = ["paper_1711_05519_gb300/csrc/pass_tc.cu", "paper_1711_05519_gb300/csrc/tc_util.cuh"]
 
 
 def config(extra=None):
@@ -266,6 +266,60 @@ def profile_case(n: int) -> int:
     return 0 if code == P.OK else 1
 
 
+def unfused_iteration_ms(D, inst_params, solver, reps=5):
+    """Same iteration with every m x n intermediate (L, R, S, Z) materialised in HBM by
+    plain torch ops: the unfused comparison point for the fused pass."""
+    U, s, V = solver.lowrank()
+    Ut, _ = torch.linalg.qr(U)
+    Vt, _ = torch.linalg.qr(V)
+    W = (U * s).float()
+    Vf, Utf, Vtf = V.float(), Ut.float(), Vt.float()
+    zeta = float(inst_params["beta"] * float(s[0]))
+    times = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L = W @ Vf.T
+        R = D - L
+        S = torch.where(R.abs() > zeta, R, torch.zeros_like(R))
+        Z = D - S
+        Y1 = Z @ Vtf
+        Y2 = Z.T @ Utf
+        res = torch.linalg.norm(R - S)
+        e1.record()
+        torch.cuda.synchronize()
+        if i:
+            times.append(e0.elapsed_time(e1))
+        del L, R, S, Z, Y1, Y2, res
+    return statistics.median(times)
+
+
+def learned_section(dev):
+    """Time to 1e-5 of the unrolled method with the plain and the learned threshold schedule
+    on the evaluation instance m = n = 10^4, r = 5, alpha = 0.2 (same runner for both)."""
+    path = os.path.join(ROOT, "paper_1711_05519_gb300", "schedule_mlp.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weights (paper_1711_05519_gb300/schedule_mlp.npz)"}
+    from paper_1711_05519_gb300 import learned as PL
+
+    inst = synth.planted_instance(M, N, RANK, 0.2, CMAG, SEED)
+    p = inst.params()
+    D = torch.from_numpy(inst.D.astype(np.float32)).to(dev)
+    Pm, Qm = torch.from_numpy(inst.P).to(dev), torch.from_numpy(inst.Q).to(dev)
+    mlp = PL.load_mlp(path, device=dev)
+    out = {"workload": "planted m=n=10^4 r=5 alpha=0.2 c=1 seed 0, FP32, tol 1e-5", "runner": "unrolled (hard gate)"}
+    for name, net in (("plain", None), ("learned", mlp)):
+        run = PL.Unrolled(D, RANK, p["beta"], p["gamma"], p["mu"], K=12)
+        run.run(mlp=net, hard=True, tol=TOL, max_iter=60)  # warm-up
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        _, err, f = run.run(mlp=net, hard=True, tol=TOL, max_iter=60)
+        torch.cuda.synchronize(dev)
+        out[name] = {"passes": run.passes, "ms": round((time.perf_counter() - t) * 1e3, 2), "err": err,
+                     "L_rel_err": PL.final_error(f, Pm, Qm)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,6 +328,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the unfused and learned-schedule comparisons")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run 3 solves of a planted n x n instance (same recipe) and exit; for ncu captures")
     args = ap.parse_args()
@@ -343,6 +398,8 @@ def main():
     gpu_launches = int(prof["pass_launches"] + prof["other_launches"])
 
     # roofline of the dominant kernel: the fused pass of Algorithm 1 (r = 5, FP32)
+    it_kind, _ = solver.pass_kind()
+    kernel_name = "fused_pass_tc (tcgen05 + TMA)" if it_kind == "tensor" else "fused_pass_kernel<float,5> (SIMT)"
     pass_ms = iter_pass_ms / max(iter_pass_n, 1)
     alg_bytes = M * N * 4  # D read once per pass
     achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
@@ -350,7 +407,7 @@ def main():
     traffic = dram_traffic_per_pass()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "fused_pass_kernel<float,5>", "avg_launch_ms": round(pass_ms, 4),
+                "kernel": kernel_name, "avg_launch_ms": round(pass_ms, 4),
                 "launches": iter_pass_n, "algorithmic_bytes_per_launch": alg_bytes,
                 "other_kernels_ms_per_step": round(prof["other_ms"] / args.steps, 4)}
 
@@ -371,6 +428,11 @@ def main():
         e2e = {"value": round(e2e_ms, 2), "unit": "ms", "h2d_bytes_per_step": M * N * 4,
                "d2h_bytes_per_step": 8 * (M + N) * RANK + 8 * RANK + 16 * nnz}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["unfused_iteration_ms"] = round(unfused_iteration_ms(D, p, solver), 3)
+        extras["learned_schedule"] = learned_section(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle_sample(inst, iters)
@@ -384,7 +446,7 @@ def main():
                                   "iteration_ms": round(statistics.median(run_ms) / (iters + 1), 4),
                                   "init_ms": round(ms_per_step - statistics.median(run_ms), 3)}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-                "clocks": clocks}
+                "clocks": clocks, **extras}
         print(json.dumps(line))
     solver.close()
     if world > 1:

@@ -175,31 +175,37 @@ __device__ void gram_reduce(const T* part, int slot, int P, T* G, Smem<T>& sh) {
   __syncthreads();
 }
 
-// Upper Cholesky factor R (R^T R = G + shift I) of a w x w symmetric matrix, by warp 0.
+// Upper Cholesky factor R (R^T R = G + shift I) of a w x w symmetric matrix, by one warp.
 // A pivot that is not positive (rank deficiency) gives a zero row of R.
 template <typename T>
-__device__ void cholesky_upper(const T* G, int w, T shift, T* R) {
-  if (threadIdx.x < 32) {
-    const int l = threadIdx.x;
-    for (int j = 0; j < w; ++j)
-      if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] + ((l == j) ? shift : T(0)) : T(0);
+__device__ void cholesky_warp(const T* G, int w, T shift, T* R) {
+  const int l = threadIdx.x & 31;
+  for (int j = 0; j < w; ++j)
+    if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] + ((l == j) ? shift : T(0)) : T(0);
+  __syncwarp();
+  T scale = T(0);
+  for (int j = 0; j < w; ++j) scale = fmax(scale, fabs(G[j * w + j]) + shift);
+  const T tiny = sizeof(T) == 8 ? T(1e-30) : T(1e-12);
+  for (int j = 0; j < w; ++j) {
+    const T d = R[j * w + j];
+    const bool good = d > T(0) && d > tiny * scale;
+    const T rjj = good ? sqrt(d) : T(0);
+    const T inv = good ? T(1) / rjj : T(0);
     __syncwarp();
-    T scale = T(0);
-    for (int j = 0; j < w; ++j) scale = fmax(scale, fabs(G[j * w + j]) + shift);
-    const T tiny = sizeof(T) == 8 ? T(1e-30) : T(1e-12);
-    for (int j = 0; j < w; ++j) {
-      const T d = R[j * w + j];
-      const bool good = d > T(0) && d > tiny * scale;
-      const T rjj = good ? sqrt(d) : T(0);
-      const T inv = good ? T(1) / rjj : T(0);
-      __syncwarp();
-      if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : T(0);
-      __syncwarp();
-      if (l > j && l < w)
-        for (int k = j + 1; k <= l; ++k) R[k * w + l] -= R[j * w + k] * R[j * w + l];
-      __syncwarp();
-    }
+    if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : T(0);
+    __syncwarp();
+    if (l > j && l < w)
+      for (int k = j + 1; k <= l; ++k) R[k * w + l] -= R[j * w + k] * R[j * w + l];
+    __syncwarp();
   }
+}
+
+// Both sides at once: warp 0 factors G1, warp 1 factors G2 (if given).
+template <typename T>
+__device__ void cholesky_pair(const T* G1, int w1, T s1, T* R1, const T* G2, int w2, T s2, T* R2) {
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) cholesky_warp(G1, w1, s1, R1);
+  if (warp == 1 && G2) cholesky_warp(G2, w2, s2, R2);
   __syncthreads();
 }
 
@@ -261,8 +267,7 @@ __device__ bool cholqr(T* X1, int rows1, int w1, T* X2, int rows2, int w2, int p
       sh1 = T(11) * (T(rows1) * w1 + T(w1) * (w1 + 1)) * u * tr1;
       sh2 = T(11) * (T(rows2) * w2 + T(w2) * (w2 + 1)) * u * tr2;
     }
-    cholesky_upper(sh.G[0], w1, sh1, sh.Rstep[0]);
-    if (X2) cholesky_upper(sh.G[1], w2, sh2, sh.Rstep[1]);
+    cholesky_pair(sh.G[0], w1, sh1, sh.Rstep[0], X2 ? sh.G[1] : nullptr, w2, sh2, sh.Rstep[1]);
     if (t < w1) sh.rinv[0][t] = sh.Rstep[0][t * w1 + t] != T(0) ? T(1) / sh.Rstep[0][t * w1 + t] : T(0);
     if (X2 && t >= 32 && t - 32 < w2) {
       const int j = t - 32;
@@ -652,7 +657,8 @@ __device__ void mode_update(const SmallArgs& a, Smem<T>& sh) {
   __syncthreads();
   if (blockIdx.x == 0 && t == 0) {
     const int k1 = k + 1;
-    const double g = pow(st->gamma, (double)k1);
+    double g = 1.0;  // gamma^(k+1) by repeated multiplication (k is small)
+    for (int i = 0; i < k1; ++i) g *= st->gamma;
     if (st->zeta_mode == 0)
       st->zeta = st->beta * (sr1 + g * s1);
     else if (st->zeta_mode == 1)
