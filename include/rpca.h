@@ -59,7 +59,7 @@ typedef struct {
   int zeta_mode;     /* rpca_zeta_mode                                                   */
   int init_max_passes; /* cap on D passes of each subspace iteration in rpca_init; 0=40   */
   double init_tol;   /* residual of the top Ritz triplets that ends a subspace iteration;
-                        0 selects 1e-13 (FP64) / 1e-6 (FP32)                             */
+                        0 selects 1e-13 (FP64) / 1e-5 (FP32)                             */
   int pass_kind;     /* rpca_pass_kind: kernel of the fused pass                          */
 } rpca_params;
 

@@ -375,7 +375,7 @@ int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
   if (c->p.init_max_passes <= 0) c->p.init_max_passes = 40;
   c->prec = (p.precision == RPCA_PREC_FP32) ? PREC_F32 : PREC_F64;
   c->tsize = (c->prec == PREC_F32) ? 4 : 8;
-  if (c->p.init_tol <= 0) c->p.init_tol = (c->prec == PREC_F32) ? 1e-6 : 1e-13;
+  if (c->p.init_tol <= 0) c->p.init_tol = (c->prec == PREC_F32) ? 1e-5 : 1e-13;
   c->stream = static_cast<cudaStream_t>(stream);
   if (cudaGetDevice(&c->device) != cudaSuccess || cudaMallocHost((void**)&c->h_flags, 8 * sizeof(int)) != cudaSuccess) {
     delete c;
@@ -468,7 +468,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   CK(cudaMalloc(&c->Vt, (size_t)n * w * ts));
   CK(cudaMalloc(&c->Y1, (size_t)m * w * ts));
   CK(cudaMalloc(&c->Y2, (size_t)n * w * ts));
-  CK(cudaMalloc(&c->part, (size_t)c->small_grid * 4 * 256 * ts));
+  CK(cudaMalloc(&c->part, (size_t)c->small_grid * kSmallSlots * 256 * sizeof(double)));
   if ((st = dalloc(&c->resP, ncta)) ||
       (st = dalloc(&c->nnzP, ncta)) || (st = dalloc(&c->st, 1)) || (st = dalloc(&c->stats, (size_t)c->p.max_iter + 2)))
     return st;

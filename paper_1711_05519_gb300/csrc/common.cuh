@@ -116,8 +116,10 @@ struct ExtractArgs {
 cudaError_t launch_extract_count(int prec, int R, const ExtractArgs& a, cudaStream_t s);
 cudaError_t launch_extract_write(int prec, int R, const ExtractArgs& a, cudaStream_t s);
 
-// The FP64 tall-skinny kernel (cooperative launch): reductions of the pass partials,
+// The tall-skinny kernel (cooperative launch): reductions of the pass partials,
 // CholeskyQR, the small SVD, the factor update, Trim and the pass-precision copies.
+// Gram partials: kSmallSlots slots of 16 x 16 doubles per block.
+constexpr int kSmallSlots = 8;
 enum SmallMode { SM_UPDATE = 0, SM_PREPARE = 1, SM_RR = 2, SM_RAND = 3 };
 
 struct SmallArgs {
@@ -137,7 +139,7 @@ struct SmallArgs {
   void* U; void* sig; void* V;         // factors of L_k (m x r, r, n x r)
   void* Ut; void* Vt;                  // bases (m x w, n x w), w = r or b
   void* Y1; void* Y2;                  // m x w, n x w
-  void* part;                          // [grid][4][16*16] Gram partials
+  void* part;                          // [kSmallSlots][grid][16*16] Gram partials (double)
   void* Wc; void* Vc; void* Utc; void* Vtc;  // pass-precision copies, width Rc
   int Rc;                              // width of the copies written for an init pass
   int Rit;                             // width of the copies written for an iteration pass

@@ -1,31 +1,38 @@
 // Tall-skinny kernel of the AccAltProj iteration and of the initialisation.
 //
-// One cooperative launch per call (one block per SM, all co-resident).  Phases are
-// separated by a bounded grid barrier.  Rows of the m x w and n x w arrays are split
-// into contiguous block ranges; small matrices (w x w Gram and Cholesky factors, the
-// 2r x 2r core M_k and its SVD) are computed redundantly by every block in shared memory,
-// so the only cross-block traffic is the per-block Gram partials.
+// One cooperative launch per call (one block per SM, all co-resident).  Rows of the m x w
+// and n x w arrays are split into contiguous block ranges and every per-row step runs on
+// the rows a block owns; phases that need a sum over all rows are separated by a bounded
+// grid barrier.  Small matrices (w x w Gram matrices, their Cholesky factors, the
+// 2r x 2r core M_k and its SVD) are computed redundantly, in the same order, by every
+// block, so the only cross-block traffic is the per-block Gram partials.
 //
-// The kernel is templated on the arithmetic of the per-row work: double in FP64 mode,
-// float in FP32 mode.  GB300 runs FP64 at a small fraction of its FP32 rate, so the
-// FP32 mode keeps FP64 for what needs it: the residual / support totals, the threshold,
-// and the singular values of M_k (an FP32 Jacobi SVD refined in FP64: the columns of
-// M_k V are formed in double and their norms taken as the singular values).
+// Gram matrices are accumulated in double from the working-precision rows (a product of two
+// floats is exact in double), so one Cholesky factorisation gives the R factor of a QR to
+// double accuracy.  The Q factor of the projected products is never formed: with
+// (I - U~U~^T) Z V~ = W1 = Q1 R1 and Q1 = W1 T1 (T1 upper, T1 = R1^{-1} on the non-zero
+// pivots), Eq. (9) becomes U_{k+1} = U~ U_M[:r, :r] + W1 (T1 U_M[r:, :r]).
 //
 // Modes:
-//   SM_UPDATE : after a fused pass of Algorithm 1.  Reduce the pass partials to
-//               Y1 = Z V~ and Y2 = Z^T U~ and err_k (Eq. (11)); stop if err_k < tol;
-//               otherwise C = U~^T Y1, QR of (I - U~U~^T) Z V~ = Y1 - U~ C and of
-//               (I - V~V~^T) Z^T U~ = Y2 - V~ C^T (shifted CholeskyQR3), the 2r x 2r
-//               M = [[C, R2^T], [R1, 0]] and its SVD (one-sided Jacobi), the new
-//               factors by Eq. (9), zeta_{k+1} (Algorithm 1), then PREPARE.
-//   SM_PREPARE: Trim (Algorithm 2) of U_k, V_k, orthonormal bases U~_k, V~_k of the
-//               trimmed factors (CholeskyQR2; the footnote to Eq. (5) asks for a QR),
-//               and the pass-precision copies W = U_k Sigma_k, V_k, U~_k, V~_k.
-//   SM_RR     : one step of block subspace iteration for Algorithm 3 (sigma_1(D), then
-//               the top-r SVD of D - S_{-1}): Rayleigh-Ritz B = U~^T (Z V~), SVD(B),
-//               convergence test, new bases orth(Z V~), orth(Z^T U~).
+//   SM_UPDATE : after a fused pass of Algorithm 1.  err_k (Eq. (11)) from the per-CTA
+//               totals; stop if err_k < tol.  Otherwise
+//                 A: Y1 = Z V~, Y2 = Z^T U~ (sums of the pass partials); C = U~^T Y1
+//                 B: W1 = Y1 - U~ C, W2 = Y2 - V~ C^T and their Gram matrices
+//                 C: R1, R2 (Cholesky), M = [[C, R2^T], [R1, 0]] and its SVD, zeta_{k+1}
+//                    (Algorithm 1), the new factors (Eq. (9)), Trim (Algorithm 2) and the
+//                    Gram matrices of the trimmed factors
+//                 D: orthonormal bases U~, V~ of the trimmed factors (the footnote to
+//                    Eq. (5) asks for a QR) and the copies read by the next pass.
+//   SM_PREPARE: Trim + D from the factors held (U, sigma, V).
+//   SM_RR     : one step of block subspace iteration for Algorithm 3 (sigma_1(D), then the
+//               top-r SVD of D - S_{-1}): Rayleigh-Ritz B = U~^T (Z V~), SVD(B), the Ritz
+//               residuals, and the next bases orth(Z V~), orth(Z^T U~) by CholeskyQR2.
 //   SM_RAND   : random orthonormal starting bases for SM_RR.
+//
+// The SVD is a one-sided Jacobi run by one warp with a column per lane, in single
+// precision; the singular values are then taken as the norms of the columns of M V formed
+// in double.  In FP64 mode V is first re-orthonormalised in double and double-precision
+// sweeps polish the result.
 #include <math.h>
 
 #include "common.cuh"
@@ -34,47 +41,33 @@ namespace rpca {
 
 namespace {
 
-constexpr int ST = 512;     // threads per block
-constexpr int MW = 16;      // max width of the tall-skinny arrays
-constexpr int MN = 32;      // max order of the small SVD (2r)
-constexpr int LD = MN + 1;  // leading dimension of the column-major SVD work arrays
-constexpr int GSLOT = MW * MW;
-constexpr int NSLOT = 4;    // Gram partial slots per block
+constexpr int ST = 256;             // threads per block
+constexpr int MW = 16;              // max width of the tall-skinny arrays
+constexpr int GSLOT = MW * MW;      // doubles per Gram partial
 constexpr int kErrTimeout = 6;
 constexpr int kErrNumerical = 3;
+constexpr unsigned FULL = 0xffffffffu;
 
-template <typename T>
+template <typename T, int WM>
 struct Smem {
+  static constexpr int NM = 2 * WM;  // max order of the small SVD
   double red[ST];
-  T G[2][GSLOT];       // reduced Gram matrices
-  T Racc[2][GSLOT];    // accumulated R factors (upper)
-  T Rstep[2][GSLOT];   // R factor of the current CholeskyQR pass
-  T C[GSLOT];          // U~^T Y1
-  T rinv[2][MW];       // reciprocals of the diagonal of Rstep
-  T um[2][MN * MW];    // ordered top columns of U_M, V_M in the working precision
-  T ub[MN * MW];       // Rayleigh-Ritz: U_B, V_B top columns, sigma, 1/sigma
-  T vb[MN * MW];
-  T sgs[MW];
-  T invs[MW];
-  double A[MN * LD];   // SVD: the matrix, then its rotated columns (U Sigma), column-major
-  double Vm[MN * LD];  // SVD: right singular vectors
-  float Af[MN * LD];   // FP32 Jacobi work
-  float Vf[MN * LD];
-  double UMs[MN * LD];  // scratch / ordered top columns of U_M, V_M in double
-  double VMs[MN * MW];
-  double sig[MN];
-  int order[MN];
-  int flag;
+  double G[3][GSLOT];      // reduced Gram matrices (row-major, leading dimension w)
+  double Rf[2][GSLOT];     // Cholesky factors (upper)
+  double Tf[2][GSLOT];     // T factors: X T has orthonormal columns (upper)
+  double C[GSLOT];         // U~^T Y1 (leading dimension r)
+  double cmd[WM * WM];     // C zero-padded to WM x WM
+  double M[NM * NM];       // small SVD input (row-major, leading dimension NM, zero-padded)
+  double UM[NM * NM];      // left singular vectors, column c at UM[c * NM + i], descending
+  double VM[NM * NM];      // right singular vectors
+  double sig[NM];          // singular values, descending
+  double scal[4];
+  double stage[2][ST * WM];  // rows staged for the Gram sums (row stride WM)
+  T mat[2][2 * WM * WM];   // per side: rows 0..w-1 act on the basis, rows w..2w-1 on W
+  T tm[2][WM * WM];        // T factors in the working precision (zero-padded WM x WM)
+  T sv[2][MW];             // sigma_c, 1/sigma_c
   int ok;
-  double scal[8];
 };
-
-template <typename T>
-__device__ __forceinline__ T wsum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -84,8 +77,8 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 
 // Grid-wide barrier with a bounded wait.  Returns false (and leaves a TIMEOUT status) if
 // another block failed to arrive within one second, so no block can spin forever.
-template <typename T>
-__device__ bool grid_barrier(DevState* st, Smem<T>& sh) {
+template <typename S>
+__device__ bool grid_barrier(DevState* st, S& sh) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = &st->bar_gen;
@@ -113,86 +106,112 @@ __device__ bool grid_barrier(DevState* st, Smem<T>& sh) {
   return sh.ok != 0;
 }
 
-__device__ void block_range(int rows, int& lo, int& hi) {
+__device__ __forceinline__ void block_range(int rows, int& lo, int& hi) {
   const int chunk = (rows + gridDim.x - 1) / gridDim.x;
   lo = min(rows, (int)blockIdx.x * chunk);
   hi = min(rows, lo + chunk);
 }
 
-// This block's part of X^T Y over its rows (X: rows x wx, Y: rows x wy, row-major with
-// leading dimensions ldx, ldy) into part[blockIdx][slot][wx*wy].
-template <typename T>
-__device__ void gram_partial(const T* X, int ldx, int wx, const T* Y, int ldy, int wy, int rows, T* part, int slot,
-                             Smem<T>& sh) {
-  int lo, hi;
-  block_range(rows, lo, hi);
-  const int P = wx * wy;
+__device__ __forceinline__ double* slot_ptr(void* part, int slot, int block) {
+  return static_cast<double*>(part) + ((size_t)slot * gridDim.x + block) * GSLOT;
+}
+
+// Sum of v over the block, the same fixed order in every block; the result in all threads.
+template <typename S>
+__device__ double block_sum(double v, S& sh) {
   const int t = threadIdx.x;
-  T* out = part + ((size_t)blockIdx.x * NSLOT + slot) * GSLOT;
-  const int nl = ST / P;  // P <= 256
-  const int p = t % P, l = t / P;
-  T acc = T(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  __syncthreads();
+  if ((t & 31) == 0) sh.red[t >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < ST / 32; ++q) s += sh.red[q];
+  __syncthreads();
+  return s;
+}
+
+// Per-thread share of X^T Y over the staged rows (row stride WM): thread t takes entry
+// p = t % P and rows l, l + nl, ... with l = t / P, nl = ST / P (P = wx * wy <= 256).
+template <int WM>
+__device__ __forceinline__ double gram_acc(const double* X, int wx, const double* Y, int wy, int nrows, double acc) {
+  const int P = wx * wy, t = threadIdx.x, nl = ST / P, l = t / P;
   if (l < nl) {
-    const int a = p / wy, b = p % wy;
-    for (int i = lo + l; i < hi; i += nl) acc = fma(X[(size_t)i * ldx + a], Y[(size_t)i * ldy + b], acc);
+    const int p = t % P, a = p / wy, b = p % wy;
+    for (int i = l; i < nrows; i += nl) acc = fma(X[i * WM + a], Y[i * WM + b], acc);
   }
-  sh.red[t] = (double)acc;
+  return acc;
+}
+
+// Combines the per-thread shares of a P-entry Gram matrix into this block's partial.
+template <typename S>
+__device__ void gram_store(double acc, int P, void* part, int slot, S& sh) {
+  const int t = threadIdx.x;
+  sh.red[t] = acc;
   __syncthreads();
   if (t < P) {
-    T s = T(0);
-    for (int q = 0; q < nl; ++q) s += (T)sh.red[t + q * P];
-    out[t] = s;
+    const int nl = ST / P;
+    double s = 0.0;
+    for (int q = 0; q < nl; ++q) s += sh.red[t + q * P];
+    slot_ptr(part, slot, blockIdx.x)[t] = s;
   }
   __syncthreads();
 }
 
-// Fixed-order sum over blocks of a partial slot into shared G (P <= 256).  Threads are
-// split into (pair, block-chunk) groups with eight independent loads in flight.
-template <typename T>
-__device__ void gram_reduce(const T* part, int slot, int P, T* G, Smem<T>& sh) {
-  const int t = threadIdx.x, nb = gridDim.x;
-  const int nch = ST / P;
-  const int p = t % P, c = t / P;
-  T s = T(0);
-  if (c < nch) {
-    int b = c;
-    for (; b + 7 * nch < nb; b += 8 * nch) {
-      T v[8];
+// G + s * GSLOT <- sum over blocks of slot (slot0 + s), entries 0..P-1, for s < ns.  The
+// summation order depends only on the grid size, so every block gets the same bits.
+template <typename S>
+__device__ void reduce_slots(const void* part, int slot0, int ns, int P, double* G, S& sh) {
+  const int t = threadIdx.x, nb = gridDim.x, total = ns * P;
+  const double* pb = static_cast<const double*>(part);
+  for (int j0 = 0; j0 < total; j0 += ST) {
+    const int cnt = min(ST, total - j0);
+    const int nch = min(32, ST / cnt);
+    const int c = t / cnt;
+    double s = 0.0;
+    if (c < nch) {
+      const int j = j0 + t % cnt;
+      const double* base = pb + (size_t)(slot0 + j / P) * nb * GSLOT + (j % P);
+      for (int b0 = c; b0 < nb; b0 += 16 * nch) {
+        double v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = part[((size_t)(b + u * nch) * NSLOT + slot) * GSLOT + p];
+        for (int u = 0; u < 16; ++u) {
+          const int b = b0 + u * nch;
+          v[u] = (b < nb) ? base[(size_t)b * GSLOT] : 0.0;
+        }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
+        for (int u = 0; u < 16; ++u) s += v[u];
+      }
     }
-    for (; b < nb; b += nch) s += part[((size_t)b * NSLOT + slot) * GSLOT + p];
+    sh.red[t] = s;
+    __syncthreads();
+    if (t < cnt) {
+      double acc = 0.0;
+      for (int q = 0; q < nch; ++q) acc += sh.red[t + q * cnt];
+      const int j = j0 + t;
+      G[(j / P) * GSLOT + (j % P)] = acc;
+    }
+    __syncthreads();
   }
-  sh.red[t] = (double)s;
-  __syncthreads();
-  if (t < P) {
-    T acc = T(0);
-    for (int q = 0; q < nch; ++q) acc += (T)sh.red[t + q * P];
-    G[t] = acc;
-  }
-  __syncthreads();
 }
 
-// Upper Cholesky factor R (R^T R = G + shift I) of a w x w symmetric matrix, by one warp.
-// A pivot that is not positive (rank deficiency) gives a zero row of R.
-template <typename T>
-__device__ void cholesky_warp(const T* G, int w, T shift, T* R) {
+// Upper Cholesky factor R (R^T R = G) of a w x w symmetric matrix, by one warp, in double.
+// A pivot below 1e-14 of the largest diagonal entry (a direction lost to rounding) gives
+// a zero row of R.
+__device__ void cholesky_warp(const double* G, int w, double* R) {
   const int l = threadIdx.x & 31;
   for (int j = 0; j < w; ++j)
-    if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] + ((l == j) ? shift : T(0)) : T(0);
+    if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] : 0.0;
   __syncwarp();
-  T scale = T(0);
-  for (int j = 0; j < w; ++j) scale = fmax(scale, fabs(G[j * w + j]) + shift);
-  const T tiny = sizeof(T) == 8 ? T(1e-30) : T(1e-12);
+  double scale = 0.0;
+  for (int j = 0; j < w; ++j) scale = fmax(scale, G[j * w + j]);
   for (int j = 0; j < w; ++j) {
-    const T d = R[j * w + j];
-    const bool good = d > T(0) && d > tiny * scale;
-    const T rjj = good ? sqrt(d) : T(0);
-    const T inv = good ? T(1) / rjj : T(0);
+    const double d = R[j * w + j];
+    const bool good = d > 1e-14 * scale && d > 0.0;
+    const double rjj = good ? sqrt(d) : 0.0;
+    const double inv = good ? 1.0 / rjj : 0.0;
     __syncwarp();
-    if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : T(0);
+    if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : 0.0;
     __syncwarp();
     if (l > j && l < w)
       for (int k = j + 1; k <= l; ++k) R[k * w + l] -= R[j * w + k] * R[j * w + l];
@@ -200,322 +219,222 @@ __device__ void cholesky_warp(const T* G, int w, T shift, T* R) {
   }
 }
 
-// Both sides at once: warp 0 factors G1, warp 1 factors G2 (if given).
-template <typename T>
-__device__ void cholesky_pair(const T* G1, int w1, T s1, T* R1, const T* G2, int w2, T s2, T* R2) {
-  const int warp = threadIdx.x >> 5;
-  if (warp == 0) cholesky_warp(G1, w1, s1, R1);
-  if (warp == 1 && G2) cholesky_warp(G2, w2, s2, R2);
-  __syncthreads();
-}
-
-// y (1 x w) <- y R^{-1} for upper R given the reciprocals of its diagonal (0 where the
-// diagonal is 0, which gives a zero entry).
-template <typename T>
-__device__ __forceinline__ void trsv_row(T* y, const T* R, const T* rinv, int w) {
+// T (upper, w x w) with X T = Q for X = Q R: column j of T is (e_j - sum_{k<j} T e_k R_kj)
+// / R_jj, or zero where R_jj is zero.  One full warp, lane = row of T.
+__device__ void tri_inverse_warp(const double* R, int w, double* Tm) {
+  const int l = threadIdx.x & 31;
+  const double rinv = (l < w && R[l * w + l] != 0.0) ? 1.0 / R[l * w + l] : 0.0;
   for (int j = 0; j < w; ++j) {
-    T s = y[j];
-    for (int k = 0; k < j; ++k) s -= y[k] * R[k * w + j];
-    y[j] = s * rinv[j];
+    const double rj = __shfl_sync(FULL, rinv, j);
+    if (l < w) {
+      double s = (l == j) ? 1.0 : 0.0;
+      for (int k = l; k < j; ++k) s -= Tm[l * w + k] * R[k * w + j];
+      Tm[l * w + j] = (j >= l) ? s * rj : 0.0;
+    }
   }
+  __syncwarp();
 }
 
-// Racc <- Rstep * Racc (both upper w x w), by the block.
-template <typename T>
-__device__ void upper_mul_acc(T* Racc, const T* Rstep, int w) {
-  const int t = threadIdx.x;
-  T v = T(0);
-  if (t < w * w) {
-    const int i = t / w, j = t % w;
-    for (int k = i; k <= j; ++k) v += Rstep[i * w + k] * Racc[k * w + j];
+// Both factors at once: warp 0 factors G[ga] into Rf[0]/Tf[0], warp 1 G[gb] into
+// Rf[1]/Tf[1]; then the T factors are copied to sh.tm in the working precision.
+template <typename T, int WM>
+__device__ void factor_pair(int w, int ga, int gb, Smem<T, WM>& sh) {
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    cholesky_warp(sh.G[ga], w, sh.Rf[0]);
+    tri_inverse_warp(sh.Rf[0], w, sh.Tf[0]);
+  }
+  if (warp == 1) {
+    cholesky_warp(sh.G[gb], w, sh.Rf[1]);
+    tri_inverse_warp(sh.Rf[1], w, sh.Tf[1]);
   }
   __syncthreads();
-  if (t < w * w) Racc[t] = v;
-  __syncthreads();
-}
-
-// In-place QR of X1 (rows1 x w1) and X2 (rows2 x w2, may be null) by CholeskyQR, `passes`
-// passes, the first with the shift of shifted CholeskyQR (Fukaya et al. 2020) when
-// `shifted`.  Leaves the R factors in sh.Racc[0], sh.Racc[1].  When `first_reduced` the
-// Gram matrices of the first pass are already in sh.G.  Returns false on a barrier
-// failure.  `copy1`/`copy2` (may be null) receive a copy of the final Q.
-template <typename T>
-__device__ bool cholqr(T* X1, int rows1, int w1, T* X2, int rows2, int w2, int passes, bool shifted, T* part,
-                       DevState* st, Smem<T>& sh, T* copy1, T* copy2, bool first_reduced = false) {
-  const int t = threadIdx.x;
-  for (int e = t; e < GSLOT; e += ST) {
-    sh.Racc[0][e] = ((e / w1) == (e % w1) && e < w1 * w1) ? T(1) : T(0);
-    sh.Racc[1][e] = (X2 && (e / w2) == (e % w2) && e < w2 * w2) ? T(1) : T(0);
-  }
-  if (!first_reduced) {
-    gram_partial((const T*)X1, w1, w1, (const T*)X1, w1, w1, rows1, part, 0, sh);
-    if (X2) gram_partial((const T*)X2, w2, w2, (const T*)X2, w2, w2, rows2, part, 1, sh);
-  }
-  __syncthreads();
-  for (int ps = 0; ps < passes; ++ps) {
-    if (!(first_reduced && ps == 0)) {
-      if (!grid_barrier(st, sh)) return false;
-      gram_reduce((const T*)part, 0, w1 * w1, sh.G[0], sh);
-      if (X2) gram_reduce((const T*)part, 1, w2 * w2, sh.G[1], sh);
-    }
-    T sh1 = T(0), sh2 = T(0);
-    if (shifted && ps == 0) {
-      const T u = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08);
-      T tr1 = T(0), tr2 = T(0);
-      for (int j = 0; j < w1; ++j) tr1 += sh.G[0][j * w1 + j];
-      for (int j = 0; X2 && j < w2; ++j) tr2 += sh.G[1][j * w2 + j];
-      sh1 = T(11) * (T(rows1) * w1 + T(w1) * (w1 + 1)) * u * tr1;
-      sh2 = T(11) * (T(rows2) * w2 + T(w2) * (w2 + 1)) * u * tr2;
-    }
-    cholesky_pair(sh.G[0], w1, sh1, sh.Rstep[0], X2 ? sh.G[1] : nullptr, w2, sh2, sh.Rstep[1]);
-    if (t < w1) sh.rinv[0][t] = sh.Rstep[0][t * w1 + t] != T(0) ? T(1) / sh.Rstep[0][t * w1 + t] : T(0);
-    if (X2 && t >= 32 && t - 32 < w2) {
-      const int j = t - 32;
-      sh.rinv[1][j] = sh.Rstep[1][j * w2 + j] != T(0) ? T(1) / sh.Rstep[1][j * w2 + j] : T(0);
-    }
-    upper_mul_acc(sh.Racc[0], sh.Rstep[0], w1);
-    if (X2) upper_mul_acc(sh.Racc[1], sh.Rstep[1], w2);
-    const bool last = (ps == passes - 1);
-    for (int side = 0; side < (X2 ? 2 : 1); ++side) {
-      T* X = side ? X2 : X1;
-      const int rows = side ? rows2 : rows1, w = side ? w2 : w1;
-      T* cp = side ? copy2 : copy1;
-      int lo, hi;
-      block_range(rows, lo, hi);
-      for (int i = lo + t; i < hi; i += ST) {
-        T y[MW];
-        for (int j = 0; j < w; ++j) y[j] = X[(size_t)i * w + j];
-        trsv_row(y, sh.Rstep[side], sh.rinv[side], w);
-        for (int j = 0; j < w; ++j) X[(size_t)i * w + j] = y[j];
-        if (last && cp)
-          for (int j = 0; j < w; ++j) cp[(size_t)i * w + j] = y[j];
-      }
-    }
-    __syncthreads();
-    if (!last) {
-      gram_partial((const T*)X1, w1, w1, (const T*)X1, w1, w1, rows1, part, 0, sh);
-      if (X2) gram_partial((const T*)X2, w2, w2, (const T*)X2, w2, w2, rows2, part, 1, sh);
-    }
-  }
-  return true;
-}
-
-// One-sided Jacobi on the N x N column-major matrix X (leading dimension LD), with the
-// right rotations accumulated in Vr (set to I here); N even, N <= 32; the warps that own
-// a rotation pair synchronise on a named barrier.  The rotation angle is computed in
-// single precision; c and s follow from it in the working precision, so each rotation is
-// orthogonal to working precision.
-template <typename U>
-__device__ void jacobi_sweeps(int N, U* X, U* Vr, U tol2, int max_sweeps, int* flag) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int e = t; e < N * N; e += ST) {
-    const int c = e / N, rw = e % N;
-    Vr[c * LD + rw] = (c == rw) ? U(1) : U(0);
-  }
-  __syncthreads();
-  const int half = N / 2;
-  if (warp < half) {
-    const int nthr = half * 32;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-      if (t == 0) *flag = 0;
-      asm volatile("bar.sync 1, %0;" ::"r"(nthr));
-      for (int round = 0; round < N - 1; ++round) {
-        // round-robin pairing: position 0 fixed, positions 1..N-1 rotated by `round`
-        int p = (warp == 0) ? 0 : 1 + (warp - 1 + round) % (N - 1);
-        int q = 1 + (N - 2 - warp + round) % (N - 1);
-        if (p > q) {
-          const int x = p;
-          p = q;
-          q = x;
-        }
-        const U ap = (lane < N) ? X[p * LD + lane] : U(0);
-        const U aq = (lane < N) ? X[q * LD + lane] : U(0);
-        const U alpha = wsum(ap * ap), beta = wsum(aq * aq), gam = wsum(ap * aq);
-        if (gam != U(0) && gam * gam > tol2 * alpha * beta) {
-          const float zf = (float)((beta - alpha) / (U(2) * gam));
-          const float tf = (zf >= 0.f ? 1.f : -1.f) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f)));
-          const U tt = (U)tf;
-          const U c = U(1) / sqrt(tt * tt + U(1)), s = c * tt;
-          if (lane < N) {
-            X[p * LD + lane] = c * ap - s * aq;
-            X[q * LD + lane] = s * ap + c * aq;
-            const U vp = Vr[p * LD + lane], vq = Vr[q * LD + lane];
-            Vr[p * LD + lane] = c * vp - s * vq;
-            Vr[q * LD + lane] = s * vp + c * vq;
-          }
-          if (lane == 0) *flag = 1;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(nthr));
-      }
-      const int f = *flag;
-      asm volatile("bar.sync 1, %0;" ::"r"(nthr));
-      if (!f) break;
-    }
+  for (int e = threadIdx.x; e < 2 * WM * WM; e += ST) {
+    const int s = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
+    sh.tm[s][q * WM + c] = (q < w && c < w) ? (T)sh.Tf[s][q * w + c] : T(0);
   }
   __syncthreads();
 }
 
-// SVD of the N x N matrix held column-major (double) in sh.A.  On return sh.sig holds the
-// singular values, sh.order their descending order, sh.A the columns M V (= U Sigma) and
-// sh.Vm the right singular vectors, all in double.
-template <typename T>
-__device__ void small_svd(int N, Smem<T>& sh) {
-  const int t = threadIdx.x;
-  if (sizeof(T) == 8) {
-    jacobi_sweeps<double>(N, sh.A, sh.Vm, 1e-30, 40, &sh.flag);
-  } else {
-    // FP32 Jacobi, then the columns M V are formed in double and their norms taken as
-    // the singular values (exact up to the square of the FP32 orthogonality error).
-    for (int e = t; e < N * N; e += ST) {
-      const int c = e / N, rw = e % N;
-      sh.Af[c * LD + rw] = (float)sh.A[c * LD + rw];
-    }
-    __syncthreads();
-    jacobi_sweeps<float>(N, sh.Af, sh.Vf, 1e-13f, 30, &sh.flag);
-    for (int e = t; e < N * N; e += ST) {
-      const int c = e / N, rw = e % N;
-      double s = 0.0;
-      for (int q = 0; q < N; ++q) s += sh.A[q * LD + rw] * (double)sh.Vf[c * LD + q];
-      sh.UMs[c * LD + rw] = s;  // scratch: column c of M V
-    }
-    __syncthreads();
-    for (int e = t; e < N * N; e += ST) {
-      const int c = e / N, rw = e % N;
-      sh.A[c * LD + rw] = sh.UMs[c * LD + rw];
-      sh.Vm[c * LD + rw] = (double)sh.Vf[c * LD + rw];
-    }
-    __syncthreads();
-  }
-  if (t < N) {
-    double s = 0.0;
-    for (int rw = 0; rw < N; ++rw) s += sh.A[t * LD + rw] * sh.A[t * LD + rw];
-    sh.sig[t] = sqrt(s);
-  }
-  __syncthreads();
-  if (t == 0) {
-    for (int i = 0; i < N; ++i) sh.order[i] = i;
-    for (int i = 1; i < N; ++i) {  // insertion sort, descending, stable
-      const int x = sh.order[i];
-      int j = i - 1;
-      while (j >= 0 && sh.sig[sh.order[j]] < sh.sig[x]) {
-        sh.order[j + 1] = sh.order[j];
-        --j;
-      }
-      sh.order[j + 1] = x;
-    }
-  }
-  __syncthreads();
+template <typename T, int WM>
+__device__ __forceinline__ void zero_row(T (&x)[WM]) {
+#pragma unroll
+  for (int j = 0; j < WM; ++j) x[j] = T(0);
 }
 
-// Trim (Algorithm 2) + orthonormal bases + pass-precision copies, from the master
-// factors U (m x r), sig, V (n x r).
-template <typename T>
-__device__ bool prepare(const SmallArgs& a, Smem<T>& sh) {
-  const int m = a.m, n = a.n, r = a.r, t = threadIdx.x;
-  T* U = static_cast<T*>(a.U);
-  T* V = static_cast<T*>(a.V);
-  T* Ut = static_cast<T*>(a.Ut);
-  T* Vt = static_cast<T*>(a.Vt);
-  const T* sig = static_cast<const T*>(a.sig);
-  T* part = static_cast<T*>(a.part);
-  const double mu = a.st->mu_trim;
-  const T cu = (T)sqrt(mu * r / m), cv = (T)sqrt(mu * r / n);
-  int scaled = 0;
-  for (int side = 0; side < 2; ++side) {
-    const T* F = side ? V : U;
-    T* Tt = side ? Vt : Ut;
-    const int rows = side ? n : m;
-    const T cap = side ? cv : cu;
-    int lo, hi;
-    block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
-      T nrm = T(0);
-      for (int j = 0; j < r; ++j) nrm += F[(size_t)i * r + j] * F[(size_t)i * r + j];
-      nrm = sqrt(nrm);
-      const bool cut = a.st->trim && nrm > cap;
-      scaled += cut ? 1 : 0;
-      const T sc = cut ? cap / nrm : T(1);
-      for (int j = 0; j < r; ++j) Tt[(size_t)i * r + j] = sc * F[(size_t)i * r + j];
-    }
-  }
-  __syncthreads();
-  if (a.st->trim) {
-    // Orthonormal bases of the trimmed factors by CholeskyQR2.  When no row was scaled the
-    // trimmed factors are U_k, V_k themselves and the QR is skipped.
-    gram_partial((const T*)Ut, r, r, (const T*)Ut, r, r, m, part, 0, sh);
-    gram_partial((const T*)Vt, r, r, (const T*)Vt, r, r, n, part, 1, sh);
-    sh.red[t] = (double)scaled;
-    __syncthreads();
-    for (int h = ST / 2; h > 0; h >>= 1) {
-      if (t < h) sh.red[t] += sh.red[t + h];
-      __syncthreads();
-    }
-    if (t == 0) part[((size_t)blockIdx.x * NSLOT + 3) * GSLOT] = (T)sh.red[0];
-    if (!grid_barrier(a.st, sh)) return false;
-    double tot = 0.0;
-    for (int b = t; b < (int)gridDim.x; b += ST) tot += (double)part[((size_t)b * NSLOT + 3) * GSLOT];
-    __syncthreads();
-    sh.red[t] = tot;
-    __syncthreads();
-    for (int h = ST / 2; h > 0; h >>= 1) {
-      if (t < h) sh.red[t] += sh.red[t + h];
-      __syncthreads();
-    }
-    const double any = sh.red[0];
-    __syncthreads();
-    if (any > 0.0) {
-      gram_reduce((const T*)part, 0, r * r, sh.G[0], sh);
-      gram_reduce((const T*)part, 1, r * r, sh.G[1], sh);
-      if (!cholqr(Ut, m, r, Vt, n, r, 2, false, part, a.st, sh, (T*)nullptr, (T*)nullptr, true)) return false;
-    }
-  }
-  // pass-precision copies, zero-padded to the compiled width of the iteration's pass
-  const int Rc = a.Rit;
-  for (int side = 0; side < 2; ++side) {
-    const int rows = side ? n : m;
-    int lo, hi;
-    block_range(rows, lo, hi);
-    T* dst0 = static_cast<T*>(side ? a.Vc : a.Wc);
-    T* dst1 = static_cast<T*>(side ? a.Vtc : a.Utc);
-    const T* F = side ? V : U;
-    const T* Tt = side ? Vt : Ut;
-    for (int i = lo + t; i < hi; i += ST)
-      for (int j = 0; j < Rc; ++j) {
-        const size_t o = (size_t)i * Rc + j;
-        dst0[o] = j < r ? (side ? F[(size_t)i * r + j] : F[(size_t)i * r + j] * sig[j]) : T(0);
-        dst1[o] = j < r ? Tt[(size_t)i * r + j] : T(0);
-      }
-  }
-  return true;
+template <typename T, int WM>
+__device__ __forceinline__ void load_row(const T* X, size_t i, int w, T (&x)[WM]) {
+#pragma unroll
+  for (int j = 0; j < WM; ++j) x[j] = (j < w) ? X[i * w + j] : T(0);
 }
 
-// Y1 (m x w), Y2 (n x w) <- fixed-order sums of the pass partials (width R), each block
-// taking its own rows (block_range) so it can use them without a grid barrier.
-template <typename T>
-__device__ void reduce_side(const T* __restrict__ Pp, int nsl, int rows, int R, int w, T* __restrict__ Y) {
-  int lo, hi;
-  block_range(rows, lo, hi);
-  const size_t stride = (size_t)rows * R;
-  for (int e = threadIdx.x; e < (hi - lo) * w; e += ST) {
-    const int i = lo + e / w, c = e % w;
-    const T* p = Pp + (size_t)i * R + c;
+template <typename T, int WM>
+__device__ __forceinline__ void store_row(T* X, size_t i, int w, const T (&x)[WM]) {
+#pragma unroll
+  for (int j = 0; j < WM; ++j)
+    if (j < w) X[i * w + j] = x[j];
+}
+
+// Row i of a pass copy of width Rc <= WM: x zero-padded.
+template <typename T, int WM>
+__device__ __forceinline__ void store_copy(T* X, size_t i, int Rc, const T (&x)[WM]) {
+#pragma unroll
+  for (int j = 0; j < WM; ++j)
+    if (j < Rc) X[i * Rc + j] = x[j];
+}
+
+template <typename T, int WM>
+__device__ __forceinline__ void stage_row(double* S, int li, const T (&x)[WM]) {
+#pragma unroll
+  for (int j = 0; j < WM; ++j) S[li * WM + j] = (double)x[j];
+}
+
+// y = x A for a WM x WM matrix A in shared memory (row-major, leading dimension WM).
+template <typename T, int WM>
+__device__ __forceinline__ void row_times(const T (&x)[WM], const T* A, T (&y)[WM]) {
+#pragma unroll
+  for (int c = 0; c < WM; ++c) {
     T s = T(0);
-#pragma unroll 8
-    for (int q = 0; q < nsl; ++q) s += p[q * stride];
-    Y[(size_t)i * w + c] = s;
+#pragma unroll
+    for (int q = 0; q < WM; ++q) s = fma(x[q], A[q * WM + c], s);
+    y[c] = s;
   }
 }
 
-template <typename T>
-__device__ void reduce_partials(const SmallArgs& a, int w) {
-  reduce_side(static_cast<const T*>(a.P1), a.n_p1, a.m, a.R, w, static_cast<T*>(a.Y1));
-  reduce_side(static_cast<const T*>(a.P2), a.n_p2, a.n, a.R, w, static_cast<T*>(a.Y2));
-  __syncthreads();
+// One-sided Jacobi by one warp: lane j < N holds column j of X in x[] and of V in v[]
+// (entries >= N zero).  Columns are paired round-robin (lane 0 fixed, the others rotated);
+// both lanes of a pair compute the same rotation from the same numbers.  A pair rotates
+// while gamma^2 > tol2 * alpha * beta; the sweeps stop when no pair rotated.
+template <typename U, int NM>
+__device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_sweeps) {
+  const int lane = threadIdx.x & 31;
+  const int Np = N + (N & 1), L = Np - 1;
+  const U big = sizeof(U) == 4 ? U(1e18) : U(1e150);
+  for (int sweep = 0; sweep < max_sweeps && L > 0; ++sweep) {
+    bool rot = false;
+    for (int rd = 0; rd < L; ++rd) {
+      int q = lane;
+      if (lane < Np) {
+        const int pos = (lane == 0) ? 0 : 1 + (lane - 1 + rd) % L;
+        const int pp = Np - 1 - pos;
+        q = (pp == 0) ? 0 : 1 + ((pp - 1 - rd) % L + L) % L;
+      }
+      const bool low = lane < q;
+      U xq[NM];
+      U sa = U(0), sb = U(0), sg = U(0);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        xq[i] = __shfl_sync(FULL, x[i], q);
+        const U a = low ? x[i] : xq[i], b = low ? xq[i] : x[i];
+        sa = fma(a, a, sa);
+        sb = fma(b, b, sb);
+        sg = fma(a, b, sg);
+      }
+      bool doit = (q != lane) && sg != U(0) && sg * sg > tol2 * sa * sb;
+      U c = U(1), s = U(0);
+      if (doit) {
+        const U z = (sb - sa) / (U(2) * sg);
+        const U az = fabs(z);
+        U tt = (az > big) ? U(0.5) / az : U(1) / (az + sqrt(fma(z, z, U(1))));
+        tt = (z < U(0)) ? -tt : tt;
+        c = U(1) / sqrt(fma(tt, tt, U(1)));
+        s = c * tt;
+        doit = tt != U(0);
+      }
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        const U vq = __shfl_sync(FULL, v[i], q);
+        if (doit) {
+          v[i] = low ? (c * v[i] - s * vq) : (s * vq + c * v[i]);
+          x[i] = low ? (c * x[i] - s * xq[i]) : (s * xq[i] + c * x[i]);
+        }
+      }
+      rot = rot || doit;
+    }
+    if (!__any_sync(FULL, rot)) break;
+  }
 }
 
-template <typename T>
-__device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long& nnz, Smem<T>& sh) {
-  // every block sums the per-CTA totals with the same fixed-shape tree
+// SVD of the N x N matrix in sh.M (N <= NM), by warp 0 (other threads return at once).
+// On return sh.sig holds the singular values in descending order and sh.UM / sh.VM the
+// matching left / right singular vectors (a zero singular value gives a zero left vector).
+template <typename T, int WM>
+__device__ void small_svd(int N, Smem<T, WM>& sh) {
+  constexpr int NM = Smem<T, WM>::NM;
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double mx = 0.0;
+  for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.M[(e / N) * NM + (e % N)]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+  const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+  float xf[NM], vf[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    xf[i] = (lane < N && i < N) ? (float)(sh.M[i * NM + lane] * sc) : 0.f;
+    vf[i] = (lane < N && i == lane) ? 1.f : 0.f;
+  }
+  // single precision: rotate until every pair of columns is orthogonal to ~3e-6
+  jacobi_lanes<float, NM>(N, xf, vf, 1e-11f, 12);
+  double y[NM], vd[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) vd[i] = (double)vf[i];
+  if (sizeof(T) == 8) {
+    // V is orthogonal to single precision only: orthonormalise it in double (modified
+    // Gram-Schmidt over the lanes) before the double-precision sweeps
+    for (int j = 0; j < N; ++j) {
+      double s2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) s2 = fma(vd[i], vd[i], s2);
+      if (lane == j) {
+        const double inv = 1.0 / sqrt(s2);
+#pragma unroll
+        for (int i = 0; i < NM; ++i) vd[i] *= inv;
+      }
+      double vj[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) vj[i] = __shfl_sync(FULL, vd[i], j);
+      if (lane > j && lane < N) {
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < NM; ++i) d = fma(vd[i], vj[i], d);
+#pragma unroll
+        for (int i = 0; i < NM; ++i) vd[i] = fma(-d, vj[i], vd[i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) s = fma(sh.M[i * NM + k], vd[k], s);
+    y[i] = (lane < N) ? s : 0.0;
+  }
+  if (sizeof(T) == 8) jacobi_lanes<double, NM>(N, y, vd, 1e-28, 8);
+  double s2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NM; ++i) s2 = fma(y[i], y[i], s2);
+  const double sg = (lane < N) ? sqrt(s2) : -1.0;
+  int rank = 0;
+  for (int i = 0; i < N; ++i) {
+    const double si = __shfl_sync(FULL, sg, i);
+    rank += (si > sg || (si == sg && i < lane)) ? 1 : 0;
+  }
+  if (lane < N) {
+    const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
+    sh.sig[rank] = sg;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      sh.UM[rank * NM + i] = y[i] * inv;
+      sh.VM[rank * NM + i] = vd[i];
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, int WM>
+__device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long& nnz, Smem<T, WM>& sh) {
+  // every block sums the per-CTA totals in the same order
   const int t = threadIdx.x;
   double s = 0.0;
   unsigned long long z = 0;
@@ -523,36 +442,116 @@ __device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long&
     s += a.resP[c];
     z += a.nnzP[c];
   }
-  sh.red[t] = s;
-  __syncthreads();
-  for (int h = ST / 2; h > 0; h >>= 1) {
-    if (t < h) sh.red[t] += sh.red[t + h];
-    __syncthreads();
-  }
-  res2 = sh.red[0];
-  __syncthreads();
-  sh.red[t] = __longlong_as_double((long long)z);
-  __syncthreads();
-  for (int h = ST / 2; h > 0; h >>= 1) {
-    if (t < h)
-      sh.red[t] = __longlong_as_double(__double_as_longlong(sh.red[t]) + __double_as_longlong(sh.red[t + h]));
-    __syncthreads();
-  }
-  nnz = (unsigned long long)__double_as_longlong(sh.red[0]);
-  __syncthreads();
+  res2 = block_sum(s, sh);
+  nnz = (unsigned long long)block_sum((double)z, sh);
 }
 
-template <typename T>
-__device__ void mode_update(const SmallArgs& a, Smem<T>& sh) {
+// Row i of Y (width w) <- fixed-order sum of the nsl pass partial slices (width R,
+// slice stride `stride`).
+template <typename T, int WM>
+__device__ __forceinline__ void reduce_row(const T* __restrict__ Pp, int nsl, size_t stride, size_t i, int R, int w,
+                                           T (&y)[WM]) {
+  zero_row<T, WM>(y);
+  const T* p = Pp + i * R;
+  int q = 0;
+  for (; q + 4 <= nsl; q += 4) {
+    T v[4][WM];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < WM; ++j) v[u][j] = (j < w) ? p[(size_t)(q + u) * stride + j] : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < WM; ++j) y[j] += v[u][j];
+  }
+  for (; q < nsl; ++q)
+#pragma unroll
+    for (int j = 0; j < WM; ++j) y[j] += (j < w) ? p[(size_t)q * stride + j] : T(0);
+}
+
+// ---------------------------------------------------------------------------------------
+// Trim of the factors held (Algorithm 2) and the Gram matrices of the trimmed factors
+// (slots 3, 4).  The trimmed rows go to U~, V~ (orthonormalised by finish_bases).
+template <typename T, int WM>
+__device__ void trim_and_gram(const SmallArgs& a, Smem<T, WM>& sh) {
+  const int r = a.r, t = threadIdx.x;
+  const double mu = a.st->mu_trim;
+  const bool do_trim = a.st->trim != 0;
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? a.n : a.m;
+    const T cap = (T)sqrt(mu * r / rows);
+    const T* F = static_cast<const T*>(side ? a.V : a.U);
+    T* Tt = static_cast<T*>(side ? a.Vt : a.Ut);
+    int lo, hi;
+    block_range(rows, lo, hi);
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T x[WM];
+      zero_row<T, WM>(x);
+      if (i < hi) {
+        load_row<T, WM>(F, i, r, x);
+        T nrm = T(0);
+#pragma unroll
+        for (int j = 0; j < WM; ++j) nrm = fma(x[j], x[j], nrm);
+        nrm = sqrt(nrm);
+        const T sc = (do_trim && nrm > cap) ? cap / nrm : T(1);
+#pragma unroll
+        for (int j = 0; j < WM; ++j) x[j] *= sc;
+        store_row<T, WM>(Tt, i, r, x);
+      }
+      stage_row<T, WM>(sh.stage[0], t, x);
+      __syncthreads();
+      acc = gram_acc<WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      __syncthreads();
+    }
+    gram_store(acc, r * r, a.part, 3 + side, sh);
+  }
+}
+
+// After a barrier: U~ <- trimmed U T_u, V~ <- trimmed V T_v (one CholeskyQR with double
+// Gram matrices), and the copies read by the next pass: W = U Sigma, V, U~, V~ zero-padded
+// to width Rit.  sh.sv[0] holds sigma.
+template <typename T, int WM>
+__device__ void finish_bases(const SmallArgs& a, Smem<T, WM>& sh) {
+  const int r = a.r, t = threadIdx.x, Rc = a.Rit;
+  reduce_slots(a.part, 3, 2, r * r, &sh.G[0][0], sh);
+  factor_pair<T, WM>(r, 0, 1, sh);
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? a.n : a.m;
+    const T* F = static_cast<const T*>(side ? a.V : a.U);
+    T* Tt = static_cast<T*>(side ? a.Vt : a.Ut);
+    T* d0 = static_cast<T*>(side ? a.Vc : a.Wc);
+    T* d1 = static_cast<T*>(side ? a.Vtc : a.Utc);
+    int lo, hi;
+    block_range(rows, lo, hi);
+    for (int i = lo + t; i < hi; i += ST) {
+      T x[WM], q[WM], f[WM];
+      load_row<T, WM>(Tt, i, r, x);
+      load_row<T, WM>(F, i, r, f);
+      row_times<T, WM>(x, sh.tm[side], q);
+      store_row<T, WM>(Tt, i, r, q);
+      if (!side) {
+#pragma unroll
+        for (int j = 0; j < WM; ++j) f[j] *= sh.sv[0][j];
+      }
+      store_copy<T, WM>(d0, i, Rc, f);
+      store_copy<T, WM>(d1, i, Rc, q);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+template <typename T, int WM>
+__device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
+  constexpr int NM = Smem<T, WM>::NM;
   DevState* st = a.st;
   const int m = a.m, n = a.n, r = a.r, t = threadIdx.x;
-  T* U = static_cast<T*>(a.U);
-  T* V = static_cast<T*>(a.V);
   T* Ut = static_cast<T*>(a.Ut);
   T* Vt = static_cast<T*>(a.Vt);
   T* Y1 = static_cast<T*>(a.Y1);
   T* Y2 = static_cast<T*>(a.Y2);
-  T* part = static_cast<T*>(a.part);
   double res2;
   unsigned long long nnz;
   cta_totals(a, res2, nnz, sh);
@@ -579,96 +578,167 @@ __device__ void mode_update(const SmallArgs& a, Smem<T>& sh) {
     if (blockIdx.x == 0 && t == 0) st->done = 1;
     return;
   }
-  reduce_partials<T>(a, r);  // this block's rows of Y1, Y2
-  // C = U~^T Y1
-  gram_partial((const T*)Ut, r, r, (const T*)Y1, r, r, m, part, 2, sh);
+
+  // A: own rows of Y1 = Z V~ and Y2 = Z^T U~; partial of C = U~^T Y1 (slot 0)
+  {
+    int lo, hi;
+    block_range(m, lo, hi);
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T y[WM], u[WM];
+      zero_row<T, WM>(y);
+      zero_row<T, WM>(u);
+      if (i < hi) {
+        reduce_row<T, WM>(static_cast<const T*>(a.P1), a.n_p1, (size_t)m * a.R, i, a.R, r, y);
+        load_row<T, WM>(Ut, i, r, u);
+        store_row<T, WM>(Y1, i, r, y);
+      }
+      stage_row<T, WM>(sh.stage[0], t, u);
+      stage_row<T, WM>(sh.stage[1], t, y);
+      __syncthreads();
+      acc = gram_acc<WM>(sh.stage[0], r, sh.stage[1], r, min(ST, hi - c0), acc);
+      __syncthreads();
+    }
+    gram_store(acc, r * r, a.part, 0, sh);
+    block_range(n, lo, hi);
+    for (int i = lo + t; i < hi; i += ST) {
+      T y[WM];
+      reduce_row<T, WM>(static_cast<const T*>(a.P2), a.n_p2, (size_t)n * a.R, i, a.R, r, y);
+      store_row<T, WM>(Y2, i, r, y);
+    }
+  }
   if (!grid_barrier(st, sh)) return;
-  gram_reduce((const T*)part, 2, r * r, sh.C, sh);
-  // Y1 <- Y1 - U~ C ; Y2 <- Y2 - V~ C^T
+
+  // B: W1 = Y1 - U~ C, W2 = Y2 - V~ C^T (in place) and their Gram matrices (slots 1, 2)
+  reduce_slots(a.part, 0, 1, r * r, sh.C, sh);
+  for (int e = t; e < WM * WM; e += ST) {
+    const int q = e / WM, c = e % WM;
+    sh.cmd[e] = (q < r && c < r) ? sh.C[q * r + c] : 0.0;
+  }
+  __syncthreads();
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     T* Y = side ? Y2 : Y1;
     const T* B = side ? Vt : Ut;
     int lo, hi;
     block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
-      T bq[MW], y[MW];
-      for (int q = 0; q < r; ++q) {
-        bq[q] = B[(size_t)i * r + q];
-        y[q] = Y[(size_t)i * r + q];
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T y[WM];
+      zero_row<T, WM>(y);
+      if (i < hi) {
+        T b[WM];
+        load_row<T, WM>(Y, i, r, y);
+        load_row<T, WM>(B, i, r, b);
+#pragma unroll
+        for (int c = 0; c < WM; ++c) {
+          double s = (double)y[c];
+#pragma unroll
+          for (int q = 0; q < WM; ++q) s -= (double)b[q] * (side ? sh.cmd[c * WM + q] : sh.cmd[q * WM + c]);
+          y[c] = (T)s;
+        }
+        store_row<T, WM>(Y, i, r, y);
       }
-      for (int c = 0; c < r; ++c) {
-        T s = y[c];
-        for (int q = 0; q < r; ++q) s -= bq[q] * (side ? sh.C[c * r + q] : sh.C[q * r + c]);
-        Y[(size_t)i * r + c] = s;
-      }
+      stage_row<T, WM>(sh.stage[0], t, y);
+      __syncthreads();
+      acc = gram_acc<WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      __syncthreads();
     }
+    gram_store(acc, r * r, a.part, 1 + side, sh);
   }
-  __syncthreads();
-  if (!cholqr(Y1, m, r, Y2, n, r, 3, true, part, st, sh, (T*)nullptr, (T*)nullptr)) return;
-  // M = [[C, R2^T], [R1, 0]], column-major in sh.A (double)
+  if (!grid_barrier(st, sh)) return;
+
+  // C: R1, R2; M = [[C, R2^T], [R1, 0]]; SVD; new factors (Eq. (9)); Trim
+  reduce_slots(a.part, 1, 2, r * r, &sh.G[0][0], sh);
+  factor_pair<T, WM>(r, 0, 1, sh);
   const int N = 2 * r;
-  for (int e = t; e < N * N; e += ST) {
-    const int row = e / N, col = e % N;
-    T v = T(0);
+  for (int e = t; e < NM * NM; e += ST) {
+    const int row = e / NM, col = e % NM;
+    double v = 0.0;
     if (row < r && col < r)
       v = sh.C[row * r + col];
-    else if (row < r && col >= r)
-      v = sh.Racc[1][(col - r) * r + row];  // R2^T
-    else if (row >= r && col < r)
-      v = sh.Racc[0][(row - r) * r + col];  // R1
-    sh.A[col * LD + row] = (double)v;
+    else if (row < r && col >= r && col < N)
+      v = sh.Rf[1][(col - r) * r + row];  // R2^T
+    else if (row >= r && row < N && col < r)
+      v = sh.Rf[0][(row - r) * r + col];  // R1
+    sh.M[e] = v;
   }
   __syncthreads();
-  small_svd(N, sh);
-  const double s1 = sh.sig[sh.order[0]];
-  const double sr1 = sh.sig[sh.order[r]];
-  // new factors by Eq. (9): U <- [U~ Q1] U_M[:, :r], V <- [V~ Q2] V_M[:, :r]; the needed
-  // columns of U_M and V_M (ordered by singular value) go to shared memory first
-  for (int e = t; e < N * r; e += ST) {
-    const int q = e / r, c = e % r, oc = sh.order[c];
-    const double sg = sh.sig[oc];
-    sh.um[0][e] = (T)(sg > 0.0 ? sh.A[oc * LD + q] / sg : 0.0);
-    sh.um[1][e] = (T)sh.Vm[oc * LD + q];
-  }
+  small_svd<T, WM>(N, sh);
   __syncthreads();
+  // update matrices: side 0 acts on [U~ W1], side 1 on [V~ W2]; rows q < r take the top
+  // block of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2)
+  for (int e = t; e < 2 * 2 * WM * WM; e += ST) {
+    const int side = e / (2 * WM * WM), rem = e % (2 * WM * WM), row = rem / WM, c = rem % WM;
+    const double* Y = side ? sh.VM : sh.UM;
+    double v = 0.0;
+    if (c < r) {
+      if (row < r) {
+        v = Y[c * NM + row];
+      } else if (row < 2 * r) {
+        const int q = row - r;
+        for (int kk = q; kk < r; ++kk) v += sh.Tf[side][q * r + kk] * Y[c * NM + r + kk];
+      }
+    }
+    sh.mat[side][rem] = (T)v;
+  }
+  if (t < MW) sh.sv[0][t] = (t < r) ? (T)sh.sig[t] : T(0);
+  __syncthreads();
+  const double s1 = sh.sig[0], sr1 = sh.sig[r];
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
-    const T* Q = side ? Y2 : Y1;
-    T* F = side ? V : U;
-    const T* MM = sh.um[side];
+    const T* W = side ? Y2 : Y1;
+    T* F = static_cast<T*>(side ? a.V : a.U);
+    const T* A = sh.mat[side];
     int lo, hi;
     block_range(rows, lo, hi);
     for (int i = lo + t; i < hi; i += ST) {
-      T bq[MW], qq[MW];
-      for (int q = 0; q < r; ++q) {
-        bq[q] = B[(size_t)i * r + q];
-        qq[q] = Q[(size_t)i * r + q];
-      }
-      for (int c = 0; c < r; ++c) {
+      T b[WM], w[WM], f[WM];
+      load_row<T, WM>(B, i, r, b);
+      load_row<T, WM>(W, i, r, w);
+#pragma unroll
+      for (int c = 0; c < WM; ++c) {
         T s = T(0);
-        for (int q = 0; q < r; ++q) s += bq[q] * MM[q * r + c] + qq[q] * MM[(r + q) * r + c];
-        F[(size_t)i * r + c] = s;
+#pragma unroll
+        for (int q = 0; q < WM; ++q) s = fma(b[q], A[q * WM + c], fma(w[q], A[(r + q) * WM + c], s));
+        f[c] = s;
       }
+      store_row<T, WM>(F, i, r, f);
     }
   }
-  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[sh.order[t]];
-  __syncthreads();
-  if (blockIdx.x == 0 && t == 0) {
+  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[t];
+  if (blockIdx.x == 0 && t == ST - 32) {  // a warp with no rows when m, n <= 224 * grid
     const int k1 = k + 1;
+    const double gamma = st->gamma, beta = st->beta;
+    const int zmode = st->zeta_mode;
     double g = 1.0;  // gamma^(k+1) by repeated multiplication (k is small)
-    for (int i = 0; i < k1; ++i) g *= st->gamma;
-    if (st->zeta_mode == 0)
-      st->zeta = st->beta * (sr1 + g * s1);
-    else if (st->zeta_mode == 1)
-      st->zeta = st->beta * g * s1;
-    for (int i = 0; i < N; ++i) st->sigma[i] = sh.sig[sh.order[i]];
+    for (int i = 0; i < k1; ++i) g *= gamma;
+    if (zmode == 0)
+      st->zeta = beta * (sr1 + g * s1);
+    else if (zmode == 1)
+      st->zeta = beta * g * s1;
+    for (int i = 0; i < N; ++i) st->sigma[i] = sh.sig[i];
     a.stats[k].sigma1 = s1;
     a.stats[k].sigma_r1 = sr1;
     st->k = k1;
   }
-  prepare(a, sh);
+  __syncthreads();
+  trim_and_gram<T, WM>(a, sh);
+  if (!grid_barrier(st, sh)) return;
+  // D: orthonormal bases of the trimmed factors and the pass copies
+  finish_bases<T, WM>(a, sh);
+}
+
+template <typename T, int WM>
+__device__ void mode_prepare(const SmallArgs& a, Smem<T, WM>& sh) {
+  if (threadIdx.x < MW) sh.sv[0][threadIdx.x] = (threadIdx.x < a.r) ? static_cast<const T*>(a.sig)[threadIdx.x] : T(0);
+  __syncthreads();
+  trim_and_gram<T, WM>(a, sh);
+  if (!grid_barrier(a.st, sh)) return;
+  finish_bases<T, WM>(a, sh);
 }
 
 __device__ float gauss(unsigned long long seed, unsigned long long i) {
@@ -685,164 +755,280 @@ __device__ float gauss(unsigned long long seed, unsigned long long i) {
   return sqrtf(-2.0f * logf(u1)) * cosf(6.2831853f * u2);
 }
 
-template <typename T>
-__device__ void write_basis_copies(const SmallArgs& a, int w) {
-  // U~, V~ (width w) -> pass copies of width Rc; W = 0, V = 0 (init passes use L = 0)
-  const int t = threadIdx.x, Rc = a.Rc;
+// Y1 <- Y1 T1, Y2 <- Y2 T2 on the own rows (T factors in sh.tm) and the Gram matrices of
+// the results into slots s1, s1 + 1: the first pass of CholeskyQR2.
+template <typename T, int WM>
+__device__ void orth_first_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>& sh) {
+  const int t = threadIdx.x;
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? a.n : a.m;
-    const T* B = static_cast<const T*>(side ? a.Vt : a.Ut);
+    T* Y = static_cast<T*>(side ? a.Y2 : a.Y1);
+    int lo, hi;
+    block_range(rows, lo, hi);
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T q[WM];
+      zero_row<T, WM>(q);
+      if (i < hi) {
+        T y[WM];
+        load_row<T, WM>(Y, i, w, y);
+        row_times<T, WM>(y, sh.tm[side], q);
+        store_row<T, WM>(Y, i, w, q);
+      }
+      stage_row<T, WM>(sh.stage[0], t, q);
+      __syncthreads();
+      acc = gram_acc<WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
+      __syncthreads();
+    }
+    gram_store(acc, w * w, a.part, s1 + side, sh);
+  }
+}
+
+// After a barrier: the second CholeskyQR pass from slots s1, s1 + 1, the new bases U~, V~
+// (width w) and their pass copies (width Rc; W = V = 0 for the initialisation passes).
+template <typename T, int WM>
+__device__ void orth_second_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>& sh) {
+  const int t = threadIdx.x, Rc = a.Rc;
+  reduce_slots(a.part, s1, 2, w * w, &sh.G[0][0], sh);
+  factor_pair<T, WM>(w, 0, 1, sh);
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? a.n : a.m;
+    const T* Y = static_cast<const T*>(side ? a.Y2 : a.Y1);
+    T* B = static_cast<T*>(side ? a.Vt : a.Ut);
     T* d0 = static_cast<T*>(side ? a.Vtc : a.Utc);
     T* d1 = static_cast<T*>(side ? a.Vc : a.Wc);
     int lo, hi;
     block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST)
-      for (int j = 0; j < Rc; ++j) {
-        const size_t o = (size_t)i * Rc + j;
-        d0[o] = j < w ? B[(size_t)i * w + j] : T(0);
-        d1[o] = T(0);
-      }
+    for (int i = lo + t; i < hi; i += ST) {
+      T y[WM], q[WM], z[WM];
+      load_row<T, WM>(Y, i, w, y);
+      row_times<T, WM>(y, sh.tm[side], q);
+      store_row<T, WM>(B, i, w, q);
+      zero_row<T, WM>(z);
+      store_copy<T, WM>(d0, i, Rc, q);
+      store_copy<T, WM>(d1, i, Rc, z);
+    }
   }
 }
 
-template <typename T>
-__device__ void mode_rand(const SmallArgs& a, Smem<T>& sh) {
-  const int w = a.b;
-  T* Y1 = static_cast<T*>(a.Y1);
-  T* Y2 = static_cast<T*>(a.Y2);
-  const size_t gt = (size_t)blockIdx.x * ST + threadIdx.x, gs = (size_t)gridDim.x * ST;
-  for (size_t e = gt; e < (size_t)a.m * w; e += gs) Y1[e] = (T)gauss(a.seed, e);
-  for (size_t e = gt; e < (size_t)a.n * w; e += gs) Y2[e] = (T)gauss(a.seed ^ 0x5bd1e995ull, e);
+template <typename T, int WM>
+__device__ void mode_rand(const SmallArgs& a, Smem<T, WM>& sh) {
+  const int w = a.b, t = threadIdx.x;
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? a.n : a.m;
+    T* Y = static_cast<T*>(side ? a.Y2 : a.Y1);
+    const unsigned long long seed = side ? (a.seed ^ 0x5bd1e995ull) : a.seed;
+    int lo, hi;
+    block_range(rows, lo, hi);
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T y[WM];
+#pragma unroll
+      for (int j = 0; j < WM; ++j) y[j] = (i < hi && j < w) ? (T)gauss(seed, (unsigned long long)i * w + j) : T(0);
+      if (i < hi) store_row<T, WM>(Y, i, w, y);
+      stage_row<T, WM>(sh.stage[0], t, y);
+      __syncthreads();
+      acc = gram_acc<WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
+      __syncthreads();
+    }
+    gram_store(acc, w * w, a.part, 1 + side, sh);
+  }
   if (!grid_barrier(a.st, sh)) return;
-  if (!cholqr(Y1, a.m, w, Y2, a.n, w, 3, true, static_cast<T*>(a.part), a.st, sh, static_cast<T*>(a.Ut),
-              static_cast<T*>(a.Vt)))
-    return;
-  write_basis_copies<T>(a, w);
+  reduce_slots(a.part, 1, 2, w * w, &sh.G[0][0], sh);
+  factor_pair<T, WM>(w, 0, 1, sh);
+  orth_first_pass<T, WM>(a, w, 3, sh);
+  if (!grid_barrier(a.st, sh)) return;
+  orth_second_pass<T, WM>(a, w, 3, sh);
 }
 
-template <typename T>
-__device__ void mode_rr(const SmallArgs& a, Smem<T>& sh) {
+template <typename T, int WM>
+__device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
+  constexpr int NM = Smem<T, WM>::NM;
   DevState* st = a.st;
   const int m = a.m, n = a.n, w = a.b, r = a.r, t = threadIdx.x;
-  T* Ut = static_cast<T*>(a.Ut);
-  T* Vt = static_cast<T*>(a.Vt);
+  const T* Ut = static_cast<const T*>(a.Ut);
+  const T* Vt = static_cast<const T*>(a.Vt);
   T* Y1 = static_cast<T*>(a.Y1);
   T* Y2 = static_cast<T*>(a.Y2);
-  T* part = static_cast<T*>(a.part);
   double res2;
   unsigned long long nnz;
   cta_totals(a, res2, nnz, sh);
   if (a.init_phase == 0 && a.rr_first && blockIdx.x == 0 && t == 0) st->normD2 = res2;
-  reduce_partials<T>(a, w);  // this block's rows of Y1, Y2
-  gram_partial((const T*)Ut, w, w, (const T*)Y1, w, w, m, part, 2, sh);  // B = U~^T (Z V~)
+
+  // A: own rows of Y1 = Z V~, Y2 = Z^T U~; partials of B = U~^T Y1 (slot 0), Y1^T Y1
+  // (slot 1) and Y2^T Y2 (slot 2)
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? n : m;
+    int lo, hi;
+    block_range(rows, lo, hi);
+    double accB = 0.0, accG = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T y[WM], u[WM];
+      zero_row<T, WM>(y);
+      zero_row<T, WM>(u);
+      if (i < hi) {
+        reduce_row<T, WM>(static_cast<const T*>(side ? a.P2 : a.P1), side ? a.n_p2 : a.n_p1, (size_t)rows * a.R, i,
+                          a.R, w, y);
+        store_row<T, WM>(side ? Y2 : Y1, i, w, y);
+        if (!side) load_row<T, WM>(Ut, i, w, u);
+      }
+      stage_row<T, WM>(sh.stage[1], t, y);
+      if (!side) stage_row<T, WM>(sh.stage[0], t, u);
+      __syncthreads();
+      const int nr = min(ST, hi - c0);
+      if (!side) accB = gram_acc<WM>(sh.stage[0], w, sh.stage[1], w, nr, accB);
+      accG = gram_acc<WM>(sh.stage[1], w, sh.stage[1], w, nr, accG);
+      __syncthreads();
+    }
+    if (!side) gram_store(accB, w * w, a.part, 0, sh);
+    gram_store(accG, w * w, a.part, 1 + side, sh);
+  }
   if (!grid_barrier(st, sh)) return;
-  gram_reduce((const T*)part, 2, w * w, sh.C, sh);
-  for (int e = t; e < w * w; e += ST) {
-    const int row = e / w, col = e % w;
-    sh.A[col * LD + row] = (double)sh.C[row * w + col];
+
+  // B: SVD of B (warp 0) while warps 1, 2 factor Y1^T Y1 and Y2^T Y2; Ritz vectors,
+  // residuals, first CholeskyQR pass of Y1, Y2
+  reduce_slots(a.part, 0, 3, w * w, &sh.G[0][0], sh);  // G[0] = B, G[1], G[2] = Grams
+  for (int e = t; e < NM * NM; e += ST) {
+    const int row = e / NM, col = e % NM;
+    sh.M[e] = (row < w && col < w) ? sh.G[0][row * w + col] : 0.0;
   }
   __syncthreads();
-  small_svd(w, sh);
+  {
+    const int warp = t >> 5;
+    if (warp == 0) small_svd<T, WM>(w, sh);
+    if (warp == 1) {
+      cholesky_warp(sh.G[1], w, sh.Rf[0]);
+      tri_inverse_warp(sh.Rf[0], w, sh.Tf[0]);
+    }
+    if (warp == 2) {
+      cholesky_warp(sh.G[2], w, sh.Rf[1]);
+      tri_inverse_warp(sh.Rf[1], w, sh.Tf[1]);
+    }
+  }
+  __syncthreads();
+  // mat[0] rows 0..w-1: U_B[:, :r]; mat[1]: V_B[:, :r]; tm: T1, T2
+  for (int e = t; e < 2 * WM * WM; e += ST) {
+    const int s = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
+    const double* Y = s ? sh.VM : sh.UM;
+    sh.mat[s][q * WM + c] = (q < w && c < r) ? (T)Y[c * NM + q] : T(0);
+    sh.tm[s][q * WM + c] = (q < w && c < w) ? (T)sh.Tf[s][q * w + c] : T(0);
+  }
+  if (t < MW) {
+    const double sg = (t < r) ? sh.sig[t] : 0.0;
+    sh.sv[0][t] = (T)sg;
+    sh.sv[1][t] = (T)(sg > 0.0 ? 1.0 / sg : 0.0);
+  }
+  __syncthreads();
   // Top Ritz triplets: u_c = U~ U_B[:, c], v_c = V~ V_B[:, c], sigma_c.  Their residuals
   // Z v_c - sigma_c u_c = Y1 V_B[:, c] - sigma_c u_c and Z^T u_c - sigma_c v_c =
   // Y2 U_B[:, c] - sigma_c v_c need no further pass over D; the sum of their squared
   // norms, each divided by sigma_c^2, decides convergence.
-  for (int e = t; e < w * r; e += ST) {
-    const int q = e / r, c = e % r, oc = sh.order[c];
-    const double sg = sh.sig[oc];
-    sh.ub[e] = (T)(sg > 0.0 ? sh.A[oc * LD + q] / sg : 0.0);
-    sh.vb[e] = (T)sh.Vm[oc * LD + q];
-    if (q == 0) {
-      sh.sgs[c] = (T)sg;
-      sh.invs[c] = (T)(sg > 0.0 ? 1.0 / sg : 0.0);
-    }
-  }
-  __syncthreads();
   const int nr = (a.init_phase == 0) ? 1 : r;
-  T acc = T(0);
+  double res = 0.0;
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
-    const T* Y = side ? Y2 : Y1;
+    T* Y = side ? Y2 : Y1;
     T* F = static_cast<T*>(side ? a.V : a.U);
+    const T* Mb = sh.mat[side];      // basis coefficients
+    const T* My = sh.mat[1 - side];  // product coefficients
     int lo, hi;
     block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
-      for (int c = 0; c < r; ++c) {
-        T f = T(0), zy = T(0);
-        for (int q = 0; q < w; ++q) {
-          f += B[(size_t)i * w + q] * (side ? sh.vb[q * r + c] : sh.ub[q * r + c]);
-          zy += Y[(size_t)i * w + q] * (side ? sh.ub[q * r + c] : sh.vb[q * r + c]);
-        }
-        F[(size_t)i * r + c] = f;
-        if (c < nr) {
-          const T d = (zy - sh.sgs[c] * f) * sh.invs[c];
-          acc += d * d;
-        }
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T q[WM];
+      zero_row<T, WM>(q);
+      if (i < hi) {
+        T b[WM], y[WM], f[WM], zy[WM];
+        load_row<T, WM>(B, i, w, b);
+        load_row<T, WM>(Y, i, w, y);
+        row_times<T, WM>(b, Mb, f);
+        row_times<T, WM>(y, My, zy);
+        store_row<T, WM>(F, i, r, f);
+#pragma unroll
+        for (int c = 0; c < WM; ++c)
+          if (c < nr) {
+            const double d = ((double)zy[c] - (double)sh.sv[0][c] * (double)f[c]) * (double)sh.sv[1][c];
+            res = fma(d, d, res);
+          }
+        row_times<T, WM>(y, sh.tm[side], q);
+        store_row<T, WM>(Y, i, w, q);
       }
+      stage_row<T, WM>(sh.stage[0], t, q);
+      __syncthreads();
+      acc = gram_acc<WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
+      __syncthreads();
     }
+    gram_store(acc, w * w, a.part, 3 + side, sh);
   }
-  sh.red[t] = (double)acc;
-  __syncthreads();
-  for (int h = ST / 2; h > 0; h >>= 1) {
-    if (t < h) sh.red[t] += sh.red[t + h];
-    __syncthreads();
-  }
-  if (t == 0) part[((size_t)blockIdx.x * NSLOT + 3) * GSLOT] = (T)sh.red[0];
-  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[sh.order[t]];
+  const double rs = block_sum(res, sh);
+  if (t == 0) slot_ptr(a.part, 5, blockIdx.x)[0] = rs;
+  if (blockIdx.x == 0 && t < w) st->sigma[t] = sh.sig[t];
+  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[t];
   if (!grid_barrier(st, sh)) return;
-  if (t == 0) {
-    double tot = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) tot += (double)part[((size_t)b * NSLOT + 3) * GSLOT];
-    const double crit = sqrt(tot);
-    if (!(crit == crit) && blockIdx.x == 0) atomicCAS(&st->status, 0, kErrNumerical);
-    const double tol = (a.init_phase == 0) ? sqrt(a.init_tol) : a.init_tol;
-    sh.flag = (a.rr_force || (!a.rr_first && crit <= tol)) ? 1 : 0;
-    sh.scal[2] = crit;
-  }
-  __syncthreads();
-  const int conv = sh.flag;
+
+  // C: convergence; then either the bases for the next step or (top-r converged) Trim
+  reduce_slots(a.part, 5, 1, 1, sh.scal, sh);
+  const double crit = sqrt(sh.scal[0]);
+  const double tol = (a.init_phase == 0) ? sqrt(a.init_tol) : a.init_tol;
+  const int conv = (a.rr_force || (!a.rr_first && crit <= tol)) ? 1 : 0;
   if (blockIdx.x == 0 && t == 0) {
-    for (int c = 0; c < w; ++c) st->sigma[c] = sh.sig[sh.order[c]];
-    st->sigma_prev[0] = sh.scal[2];
+    if (!(crit == crit)) atomicCAS(&st->status, 0, kErrNumerical);
+    st->sigma_prev[0] = crit;
     st->conv = conv;
-    if (conv && a.init_phase == 0) st->zeta = st->beta_init * sh.sig[sh.order[0]];
+    if (conv && a.init_phase == 0) st->zeta = st->beta_init * sh.sig[0];
     if (conv && a.init_phase == 1) {
-      st->zeta = st->beta * sh.sig[sh.order[0]];
+      st->zeta = st->beta * sh.sig[0];
       st->k = 0;
     }
   }
-  __syncthreads();
   if (conv && a.init_phase == 1) {
-    prepare(a, sh);
+    trim_and_gram<T, WM>(a, sh);
+    if (!grid_barrier(st, sh)) return;
+    finish_bases<T, WM>(a, sh);
     return;
   }
-  // next bases: orth(Z V~) -> U~, orth(Z^T U~) -> V~
-  if (!cholqr(Y1, m, w, Y2, n, w, 3, true, part, st, sh, Ut, Vt)) return;
-  write_basis_copies<T>(a, w);
+  orth_second_pass<T, WM>(a, w, 3, sh);
 }
 
-template <typename T>
+template <typename T, int WM>
 __global__ void __launch_bounds__(ST, 1) small_kernel(SmallArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T>& sh = *reinterpret_cast<Smem<T>*>(smem_raw);
+  Smem<T, WM>& sh = *reinterpret_cast<Smem<T, WM>*>(smem_raw);
   if (a.mode == SM_UPDATE || a.mode == SM_RR) {
     if (a.st->done) return;
   }
   switch (a.mode) {
     case SM_UPDATE:
-      mode_update<T>(a, sh);
+      mode_update<T, WM>(a, sh);
       break;
     case SM_PREPARE:
-      prepare<T>(a, sh);
+      mode_prepare<T, WM>(a, sh);
       break;
     case SM_RR:
-      mode_rr<T>(a, sh);
+      mode_rr<T, WM>(a, sh);
       break;
     case SM_RAND:
-      mode_rand<T>(a, sh);
+      mode_rand<T, WM>(a, sh);
       break;
   }
+}
+
+template <typename T, int WM>
+void set_smem() {
+  cudaFuncSetAttribute(small_kernel<T, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<T, WM>));
+}
+
+template <typename T, int WM>
+cudaError_t launch_one(const SmallArgs& a, int grid, cudaStream_t s) {
+  SmallArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel((const void*)small_kernel<T, WM>, dim3(grid), dim3(ST), args,
+                                     sizeof(Smem<T, WM>), s);
 }
 
 }  // namespace
@@ -850,19 +1036,24 @@ __global__ void __launch_bounds__(ST, 1) small_kernel(SmallArgs a) {
 int small_grid_size(int device) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaFuncSetAttribute(small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<float>));
-  cudaFuncSetAttribute(small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<double>));
+  set_smem<float, 8>();
+  set_smem<float, 16>();
+  set_smem<double, 8>();
+  set_smem<double, 16>();
   return sms;  // one block per SM keeps the barrier short
 }
 
 cudaError_t launch_small(const SmallArgs& a, int grid, cudaStream_t s) {
-  SmallArgs copy = a;
-  void* args[] = {&copy};
-  if (a.prec == PREC_F32)
-    return cudaLaunchCooperativeKernel((const void*)small_kernel<float>, dim3(grid), dim3(ST), args,
-                                       sizeof(Smem<float>), s);
-  return cudaLaunchCooperativeKernel((const void*)small_kernel<double>, dim3(grid), dim3(ST), args,
-                                     sizeof(Smem<double>), s);
+  const bool init = (a.mode == SM_RR || a.mode == SM_RAND);
+  int need = a.r > a.Rit ? a.r : a.Rit;
+  if (init) {
+    need = need > a.b ? need : a.b;
+    need = need > a.Rc ? need : a.Rc;
+  }
+  if (a.r < 1 || need > MW) return cudaErrorInvalidValue;
+  const bool narrow = need <= 8;
+  if (a.prec == PREC_F32) return narrow ? launch_one<float, 8>(a, grid, s) : launch_one<float, 16>(a, grid, s);
+  return narrow ? launch_one<double, 8>(a, grid, s) : launch_one<double, 16>(a, grid, s);
 }
 
 }  // namespace rpca
