@@ -8,8 +8,10 @@
 // block, so the only cross-block traffic is the per-block Gram partials.
 //
 // Gram matrices are accumulated in double from the working-precision rows (a product of two
-// floats is exact in double), so one Cholesky factorisation gives the R factor of a QR to
-// double accuracy.  The Q factor of the projected products is never formed: with
+// floats is exact in double), so one Cholesky factorisation (in double in FP64 mode; in
+// FP32 mode in float after scaling the Gram matrix to unit diagonal) gives the R factor of
+// a QR without a second CholeskyQR pass.  The Q factor of the projected products is never
+// formed: with
 // (I - U~U~^T) Z V~ = W1 = Q1 R1 and Q1 = W1 T1 (T1 upper, T1 = R1^{-1} on the non-zero
 // pivots), Eq. (9) becomes U_{k+1} = U~ U_M[:r, :r] + W1 (T1 U_M[r:, :r]).
 //
@@ -30,9 +32,10 @@
 //   SM_RAND   : random orthonormal starting bases for SM_RR.
 //
 // The SVD is a one-sided Jacobi run by one warp with a column per lane, in single
-// precision; the singular values are then taken as the norms of the columns of M V formed
-// in double.  In FP64 mode V is first re-orthonormalised in double and double-precision
-// sweeps polish the result.
+// precision; in FP64 mode V is then re-orthonormalised in double and double-precision
+// sweeps polish the result.  Double-precision operations are long-latency on this part, so
+// the serial steps (factorisations, the SVD, the sums over blocks) keep them few and, where
+// they remain, arranged as trees rather than chains.
 #include <math.h>
 
 #include "common.cuh"
@@ -66,6 +69,8 @@ struct Smem {
   T mat[2][2 * WM * WM];   // per side: rows 0..w-1 act on the basis, rows w..2w-1 on W
   T tm[2][WM * WM];        // T factors in the working precision (zero-padded WM x WM)
   T sv[2][MW];             // sigma_c, 1/sigma_c
+  float fs[2][GSLOT];      // single-precision factor scratch
+  int pairs[32 * 32];      // Jacobi round-robin partner of each lane in each round
   int ok;
 };
 
@@ -143,18 +148,38 @@ __device__ __forceinline__ double gram_acc(const double* X, int wx, const double
   return acc;
 }
 
+// Pairwise sum of K (a power of two) values, in a fixed order.
+template <int K>
+__device__ __forceinline__ double tree_sum(double (&v)[K]) {
+#pragma unroll
+  for (int h = K / 2; h > 0; h >>= 1)
+#pragma unroll
+    for (int u = 0; u < h; ++u) v[u] += v[u + h];
+  return v[0];
+}
+
+// sh.red[j] <- sum over q < nparts of sh.red[q * cnt + j] (j < cnt), pairwise in a fixed
+// order (FP64 additions are long-latency here, so a tree beats a chain).  sh.red must be
+// written and synchronised before the call.
+template <typename S>
+__device__ void tree_combine(int cnt, int nparts, S& sh) {
+  const int t = threadIdx.x, q = t / cnt, j = t % cnt;
+  int h = 1;
+  while (h < nparts) h <<= 1;
+  for (h >>= 1; h > 0; h >>= 1) {
+    if (q < h && q + h < nparts) sh.red[q * cnt + j] += sh.red[(q + h) * cnt + j];
+    __syncthreads();
+  }
+}
+
 // Combines the per-thread shares of a P-entry Gram matrix into this block's partial.
 template <typename S>
 __device__ void gram_store(double acc, int P, void* part, int slot, S& sh) {
   const int t = threadIdx.x;
   sh.red[t] = acc;
   __syncthreads();
-  if (t < P) {
-    const int nl = ST / P;
-    double s = 0.0;
-    for (int q = 0; q < nl; ++q) s += sh.red[t + q * P];
-    slot_ptr(part, slot, blockIdx.x)[t] = s;
-  }
+  tree_combine(P, ST / P, sh);
+  if (t < P) slot_ptr(part, slot, blockIdx.x)[t] = sh.red[t];
   __syncthreads();
 }
 
@@ -179,17 +204,15 @@ __device__ void reduce_slots(const void* part, int slot0, int ns, int P, double*
           const int b = b0 + u * nch;
           v[u] = (b < nb) ? base[(size_t)b * GSLOT] : 0.0;
         }
-#pragma unroll
-        for (int u = 0; u < 16; ++u) s += v[u];
+        s += tree_sum<16>(v);
       }
     }
     sh.red[t] = s;
     __syncthreads();
+    tree_combine(cnt, nch, sh);
     if (t < cnt) {
-      double acc = 0.0;
-      for (int q = 0; q < nch; ++q) acc += sh.red[t + q * cnt];
       const int j = j0 + t;
-      G[(j / P) * GSLOT + (j % P)] = acc;
+      G[(j / P) * GSLOT + (j % P)] = sh.red[t];
     }
     __syncthreads();
   }
@@ -235,19 +258,72 @@ __device__ void tri_inverse_warp(const double* R, int w, double* Tm) {
   __syncwarp();
 }
 
+// The same two factors in single precision, for the FP32 mode: G (double) is scaled to unit
+// diagonal, G^ = D^-1/2 G D^-1/2, factored in float (a pivot below 1e-6 is dropped), and
+// R = R^ D^1/2, T = D^-1/2 R^-1 are returned in double.  A is a w x w float scratch.
+__device__ void factor_warp_f32(const double* G, int w, double* R, double* Tm, float* A) {
+  const int l = threadIdx.x & 31;
+  const float dl = (l < w) ? sqrtf((float)G[l * w + l]) : 0.f;
+  const float il = dl > 0.f ? 1.f / dl : 0.f;
+  for (int j = 0; j < w; ++j) {
+    const float ij = __shfl_sync(FULL, il, j);
+    if (l < w) A[j * w + l] = (l >= j) ? (float)G[j * w + l] * (ij * il) : 0.f;
+  }
+  __syncwarp();
+  for (int j = 0; j < w; ++j) {
+    const float d = A[j * w + j];
+    const bool good = d > 1e-6f;
+    const float rjj = good ? sqrtf(d) : 0.f;
+    const float inv = good ? 1.f / rjj : 0.f;
+    __syncwarp();
+    if (l >= j && l < w) A[j * w + l] = good ? ((l == j) ? rjj : A[j * w + l] * inv) : 0.f;
+    __syncwarp();
+    if (l > j && l < w)
+      for (int k = j + 1; k <= l; ++k) A[k * w + l] = fmaf(-A[j * w + k], A[j * w + l], A[k * w + l]);
+    __syncwarp();
+  }
+  // R = R^ D^1/2 (column l scaled by d_l); T^ = R^-1 row by row, then T = D^-1/2 T^
+  for (int j = 0; j < w; ++j)
+    if (l < w) R[j * w + l] = (double)A[j * w + l] * (double)dl;
+  const float rinv = (l < w && A[l * w + l] != 0.f) ? 1.f / A[l * w + l] : 0.f;
+  float trow[MW];
+#pragma unroll
+  for (int j = 0; j < MW; ++j) trow[j] = 0.f;
+#pragma unroll
+  for (int j = 0; j < MW; ++j) {
+    const float rj = __shfl_sync(FULL, rinv, j);
+    if (j < w && l < w && j >= l) {
+      float s = (l == j) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < MW; ++k)
+        if (k >= l && k < j) s = fmaf(-trow[k], A[k * w + j], s);
+      trow[j] = s * rj;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MW; ++j)
+    if (l < w && j < w) Tm[l * w + j] = (double)trow[j] * (double)il;
+  __syncwarp();
+}
+
+// R and T of one Gram matrix by the calling warp, in the precision of the mode.
+template <typename T, int WM>
+__device__ void factor_one(const double* G, int w, int s, Smem<T, WM>& sh) {
+  if (sizeof(T) == 8) {
+    cholesky_warp(G, w, sh.Rf[s]);
+    tri_inverse_warp(sh.Rf[s], w, sh.Tf[s]);
+  } else {
+    factor_warp_f32(G, w, sh.Rf[s], sh.Tf[s], sh.fs[s]);
+  }
+}
+
 // Both factors at once: warp 0 factors G[ga] into Rf[0]/Tf[0], warp 1 G[gb] into
 // Rf[1]/Tf[1]; then the T factors are copied to sh.tm in the working precision.
 template <typename T, int WM>
 __device__ void factor_pair(int w, int ga, int gb, Smem<T, WM>& sh) {
   const int warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    cholesky_warp(sh.G[ga], w, sh.Rf[0]);
-    tri_inverse_warp(sh.Rf[0], w, sh.Tf[0]);
-  }
-  if (warp == 1) {
-    cholesky_warp(sh.G[gb], w, sh.Rf[1]);
-    tri_inverse_warp(sh.Rf[1], w, sh.Tf[1]);
-  }
+  if (warp == 0) factor_one<T, WM>(sh.G[ga], w, 0, sh);
+  if (warp == 1) factor_one<T, WM>(sh.G[gb], w, 1, sh);
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * WM * WM; e += ST) {
     const int s = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
@@ -301,52 +377,72 @@ __device__ __forceinline__ void row_times(const T (&x)[WM], const T* A, T (&y)[W
   }
 }
 
-// One-sided Jacobi by one warp: lane j < N holds column j of X in x[] and of V in v[]
-// (entries >= N zero).  Columns are paired round-robin (lane 0 fixed, the others rotated);
-// both lanes of a pair compute the same rotation from the same numbers.  A pair rotates
-// while gamma^2 > tol2 * alpha * beta; the sweeps stop when no pair rotated.
-template <typename U, int NM>
-__device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_sweeps) {
+// Round-robin pairing of N columns (N + 1 if N is odd) for the Jacobi sweeps: lane 0 stays,
+// the others move one position per round; pairs[rd * 32 + lane] is the partner of `lane`
+// in round rd (itself if it has none).  Written by one warp.
+__device__ void jacobi_pairs(int N, int* pairs) {
   const int lane = threadIdx.x & 31;
   const int Np = N + (N & 1), L = Np - 1;
+  for (int rd = 0; rd < L; ++rd) {
+    int q = lane;
+    if (lane < Np) {
+      const int pos = (lane == 0) ? 0 : 1 + (lane - 1 + rd) % L;
+      const int pp = Np - 1 - pos;
+      q = (pp == 0) ? 0 : 1 + ((pp - 1 - rd) % L + L) % L;
+    }
+    pairs[rd * 32 + lane] = q;
+  }
+  __syncwarp();
+}
+
+// One-sided Jacobi by one warp: lane j < N holds column j of X in x[] and of V in v[]
+// (entries >= N zero).  Both lanes of a pair compute the same rotation from the same
+// numbers.  A pair rotates while gamma^2 > tol2 * alpha * beta; the sweeps stop when no
+// pair rotated.  All partner values are exchanged before the arithmetic so the shuffles
+// overlap (a single warp has nothing else to hide their latency).
+template <typename U, int NM>
+__device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_sweeps, const int* pairs) {
+  const int lane = threadIdx.x & 31;
+  const int L = N + (N & 1) - 1;
   const U big = sizeof(U) == 4 ? U(1e18) : U(1e150);
   for (int sweep = 0; sweep < max_sweeps && L > 0; ++sweep) {
     bool rot = false;
     for (int rd = 0; rd < L; ++rd) {
-      int q = lane;
-      if (lane < Np) {
-        const int pos = (lane == 0) ? 0 : 1 + (lane - 1 + rd) % L;
-        const int pp = Np - 1 - pos;
-        q = (pp == 0) ? 0 : 1 + ((pp - 1 - rd) % L + L) % L;
-      }
+      const int q = pairs[rd * 32 + lane];
       const bool low = lane < q;
-      U xq[NM];
-      U sa = U(0), sb = U(0), sg = U(0);
+      U xq[NM], vq[NM];
 #pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        xq[i] = __shfl_sync(FULL, x[i], q);
-        const U a = low ? x[i] : xq[i], b = low ? xq[i] : x[i];
-        sa = fma(a, a, sa);
-        sb = fma(b, b, sb);
-        sg = fma(a, b, sg);
+      for (int i = 0; i < NM; ++i) xq[i] = __shfl_sync(FULL, x[i], q);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) vq[i] = __shfl_sync(FULL, v[i], q);
+      U sa0 = U(0), sb0 = U(0), sg0 = U(0), sa1 = U(0), sb1 = U(0), sg1 = U(0);
+#pragma unroll
+      for (int i = 0; i < NM; i += 2) {
+        const U a0 = low ? x[i] : xq[i], b0 = low ? xq[i] : x[i];
+        sa0 = fma(a0, a0, sa0);
+        sb0 = fma(b0, b0, sb0);
+        sg0 = fma(a0, b0, sg0);
+        const U a1 = low ? x[i + 1] : xq[i + 1], b1 = low ? xq[i + 1] : x[i + 1];
+        sa1 = fma(a1, a1, sa1);
+        sb1 = fma(b1, b1, sb1);
+        sg1 = fma(a1, b1, sg1);
       }
+      const U sa = sa0 + sa1, sb = sb0 + sb1, sg = sg0 + sg1;
       bool doit = (q != lane) && sg != U(0) && sg * sg > tol2 * sa * sb;
-      U c = U(1), s = U(0);
       if (doit) {
         const U z = (sb - sa) / (U(2) * sg);
         const U az = fabs(z);
         U tt = (az > big) ? U(0.5) / az : U(1) / (az + sqrt(fma(z, z, U(1))));
         tt = (z < U(0)) ? -tt : tt;
-        c = U(1) / sqrt(fma(tt, tt, U(1)));
-        s = c * tt;
+        const U c = U(1) / sqrt(fma(tt, tt, U(1)));
+        const U sn = low ? -(c * tt) : (c * tt);  // low: c x - s xq; high: c x + s xq
         doit = tt != U(0);
-      }
-#pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        const U vq = __shfl_sync(FULL, v[i], q);
         if (doit) {
-          v[i] = low ? (c * v[i] - s * vq) : (s * vq + c * v[i]);
-          x[i] = low ? (c * x[i] - s * xq[i]) : (s * xq[i] + c * x[i]);
+#pragma unroll
+          for (int i = 0; i < NM; ++i) {
+            x[i] = fma(c, x[i], sn * xq[i]);
+            v[i] = fma(c, v[i], sn * vq[i]);
+          }
         }
       }
       rot = rot || doit;
@@ -358,11 +454,15 @@ __device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_swee
 // SVD of the N x N matrix in sh.M (N <= NM), by warp 0 (other threads return at once).
 // On return sh.sig holds the singular values in descending order and sh.UM / sh.VM the
 // matching left / right singular vectors (a zero singular value gives a zero left vector).
+// Single-precision one-sided Jacobi on M scaled to max |M_ij| = 1 keeps the small singular
+// values to high relative accuracy; in FP64 mode V is then re-orthonormalised in double
+// and double-precision sweeps on M V polish the result.
 template <typename T, int WM>
 __device__ void small_svd(int N, Smem<T, WM>& sh) {
   constexpr int NM = Smem<T, WM>::NM;
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
+  jacobi_pairs(N, sh.pairs);
   double mx = 0.0;
   for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.M[(e / N) * NM + (e % N)]));
 #pragma unroll
@@ -374,12 +474,13 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
     xf[i] = (lane < N && i < N) ? (float)(sh.M[i * NM + lane] * sc) : 0.f;
     vf[i] = (lane < N && i == lane) ? 1.f : 0.f;
   }
-  // single precision: rotate until every pair of columns is orthogonal to ~3e-6
-  jacobi_lanes<float, NM>(N, xf, vf, 1e-11f, 12);
+  // rotate until every pair of columns is orthogonal to ~3e-6
+  jacobi_lanes<float, NM>(N, xf, vf, 1e-11f, 12, sh.pairs);
+  double sg;
   double y[NM], vd[NM];
-#pragma unroll
-  for (int i = 0; i < NM; ++i) vd[i] = (double)vf[i];
   if (sizeof(T) == 8) {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) vd[i] = (double)vf[i];
     // V is orthogonal to single precision only: orthonormalise it in double (modified
     // Gram-Schmidt over the lanes) before the double-precision sweeps
     for (int j = 0; j < N; ++j) {
@@ -402,30 +503,44 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
         for (int i = 0; i < NM; ++i) vd[i] = fma(-d, vj[i], vd[i]);
       }
     }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < NM; ++k) s = fma(sh.M[i * NM + k], vd[k], s);
+      y[i] = (lane < N) ? s : 0.0;
+    }
+    jacobi_lanes<double, NM>(N, y, vd, 1e-28, 8, sh.pairs);
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) s2 = fma(y[i], y[i], s2);
+    sg = (lane < N) ? sqrt(s2) : -1.0;
+    const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) y[i] *= inv;
+  } else {
+    float s2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) s2 = fmaf(xf[i], xf[i], s2);
+    const float sf = sqrtf(s2);
+    const float inv = sf > 0.f ? 1.f / sf : 0.f;
+    sg = (lane < N) ? (double)sf * mx : -1.0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      y[i] = (double)(xf[i] * inv);
+      vd[i] = (double)vf[i];
+    }
   }
-#pragma unroll
-  for (int i = 0; i < NM; ++i) {
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < NM; ++k) s = fma(sh.M[i * NM + k], vd[k], s);
-    y[i] = (lane < N) ? s : 0.0;
-  }
-  if (sizeof(T) == 8) jacobi_lanes<double, NM>(N, y, vd, 1e-28, 8);
-  double s2 = 0.0;
-#pragma unroll
-  for (int i = 0; i < NM; ++i) s2 = fma(y[i], y[i], s2);
-  const double sg = (lane < N) ? sqrt(s2) : -1.0;
   int rank = 0;
   for (int i = 0; i < N; ++i) {
     const double si = __shfl_sync(FULL, sg, i);
     rank += (si > sg || (si == sg && i < lane)) ? 1 : 0;
   }
   if (lane < N) {
-    const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
     sh.sig[rank] = sg;
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-      sh.UM[rank * NM + i] = y[i] * inv;
+      sh.UM[rank * NM + i] = y[i];
       sh.VM[rank * NM + i] = vd[i];
     }
   }
@@ -899,14 +1014,8 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   {
     const int warp = t >> 5;
     if (warp == 0) small_svd<T, WM>(w, sh);
-    if (warp == 1) {
-      cholesky_warp(sh.G[1], w, sh.Rf[0]);
-      tri_inverse_warp(sh.Rf[0], w, sh.Tf[0]);
-    }
-    if (warp == 2) {
-      cholesky_warp(sh.G[2], w, sh.Rf[1]);
-      tri_inverse_warp(sh.Rf[1], w, sh.Tf[1]);
-    }
+    if (warp == 1) factor_one<T, WM>(sh.G[1], w, 0, sh);
+    if (warp == 2) factor_one<T, WM>(sh.G[2], w, 1, sh);
   }
   __syncthreads();
   // mat[0] rows 0..w-1: U_B[:, :r]; mat[1]: V_B[:, :r]; tm: T1, T2
