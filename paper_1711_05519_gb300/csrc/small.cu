@@ -7,11 +7,9 @@
 // 2r x 2r core M_k and its SVD) are computed redundantly, in the same order, by every
 // block, so the only cross-block traffic is the per-block Gram partials.
 //
-// Gram matrices are accumulated in double from the working-precision rows (a product of two
-// floats is exact in double), so one Cholesky factorisation (in double in FP64 mode; in
-// FP32 mode in float after scaling the Gram matrix to unit diagonal) gives the R factor of
-// a QR without a second CholeskyQR pass.  The Q factor of the projected products is never
-// formed: with
+// All of it runs in the working precision (double in FP64 mode, float in FP32 mode); sums
+// run as pairwise trees, and Cholesky factorisations scale the Gram matrix to unit
+// diagonal first.  The Q factor of the projected products is never formed: with
 // (I - U~U~^T) Z V~ = W1 = Q1 R1 and Q1 = W1 T1 (T1 upper, T1 = R1^{-1} on the non-zero
 // pivots), Eq. (9) becomes U_{k+1} = U~ U_M[:r, :r] + W1 (T1 U_M[r:, :r]).
 //
@@ -46,7 +44,7 @@ namespace {
 
 constexpr int ST = 256;             // threads per block
 constexpr int MW = 16;              // max width of the tall-skinny arrays
-constexpr int GSLOT = MW * MW;      // doubles per Gram partial
+constexpr int GSLOT = MW * MW;      // entries per Gram partial
 constexpr int kErrTimeout = 6;
 constexpr int kErrNumerical = 3;
 constexpr unsigned FULL = 0xffffffffu;
@@ -54,22 +52,22 @@ constexpr unsigned FULL = 0xffffffffu;
 template <typename T, int WM>
 struct Smem {
   static constexpr int NM = 2 * WM;  // max order of the small SVD
-  double red[ST];
-  double G[3][GSLOT];      // reduced Gram matrices (row-major, leading dimension w)
-  double Rf[2][GSLOT];     // Cholesky factors (upper)
-  double Tf[2][GSLOT];     // T factors: X T has orthonormal columns (upper)
-  double C[GSLOT];         // U~^T Y1 (leading dimension r)
-  double cmd[WM * WM];     // C zero-padded to WM x WM
-  double M[NM * NM];       // small SVD input (row-major, leading dimension NM, zero-padded)
-  double UM[NM * NM];      // left singular vectors, column c at UM[c * NM + i], descending
-  double VM[NM * NM];      // right singular vectors
-  double sig[NM];          // singular values, descending
-  double scal[4];
-  double stage[2][ST * WM];  // rows staged for the Gram sums (row stride WM)
+  T red[ST];
+  double dred[ST / 32];
+  T G[3][GSLOT];           // reduced Gram matrices (row-major, leading dimension w)
+  T Rf[2][GSLOT];          // Cholesky factors (upper)
+  T Tf[2][GSLOT];          // T factors: X T has orthonormal columns (upper)
+  T C[GSLOT];              // U~^T Y1 (leading dimension r)
+  T cm[WM * WM];           // C zero-padded to WM x WM
+  T M[NM * NM];            // small SVD input (row-major, leading dimension NM, zero-padded)
+  T UM[NM * NM];           // left singular vectors, column c at UM[c * NM + i], descending
+  T VM[NM * NM];           // right singular vectors
+  T sig[NM];               // singular values, descending
+  T scal[4];
+  T stage[2][ST * WM];     // rows staged for the Gram sums (row stride WM)
   T mat[2][2 * WM * WM];   // per side: rows 0..w-1 act on the basis, rows w..2w-1 on W
-  T tm[2][WM * WM];        // T factors in the working precision (zero-padded WM x WM)
+  T tm[2][WM * WM];        // T factors zero-padded to WM x WM
   T sv[2][MW];             // sigma_c, 1/sigma_c
-  float fs[2][GSLOT];      // single-precision factor scratch
   int pairs[32 * 32];      // Jacobi round-robin partner of each lane in each round
   int ok;
 };
@@ -117,29 +115,49 @@ __device__ __forceinline__ void block_range(int rows, int& lo, int& hi) {
   hi = min(rows, lo + chunk);
 }
 
-__device__ __forceinline__ double* slot_ptr(void* part, int slot, int block) {
-  return static_cast<double*>(part) + ((size_t)slot * gridDim.x + block) * GSLOT;
+template <typename T>
+__device__ __forceinline__ T* slot_ptr(void* part, int slot, int block) {
+  return static_cast<T*>(part) + ((size_t)slot * gridDim.x + block) * GSLOT;
 }
 
-// Sum of v over the block, the same fixed order in every block; the result in all threads.
+// Sums over the block, the same fixed order in every block; the result in all threads.
 template <typename S>
-__device__ double block_sum(double v, S& sh) {
+__device__ double block_sum_d(double v, S& sh) {
   const int t = threadIdx.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   __syncthreads();
-  if ((t & 31) == 0) sh.red[t >> 5] = v;
+  if ((t & 31) == 0) sh.dred[t >> 5] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int q = 0; q < ST / 32; ++q) s += sh.red[q];
+  double w[ST / 32];
+#pragma unroll
+  for (int q = 0; q < ST / 32; ++q) w[q] = sh.dred[q];
+#pragma unroll
+  for (int h = ST / 64; h > 0; h >>= 1)
+#pragma unroll
+    for (int q = 0; q < h; ++q) w[q] += w[q + h];
+  __syncthreads();
+  return w[0];
+}
+
+template <typename S>
+__device__ unsigned long long block_sum_u64(unsigned long long v, S& sh) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  __syncthreads();
+  if ((t & 31) == 0) sh.dred[t >> 5] = __longlong_as_double((long long)v);
+  __syncthreads();
+  unsigned long long s = 0;
+  for (int q = 0; q < ST / 32; ++q) s += (unsigned long long)__double_as_longlong(sh.dred[q]);
   __syncthreads();
   return s;
 }
 
 // Per-thread share of X^T Y over the staged rows (row stride WM): thread t takes entry
 // p = t % P and rows l, l + nl, ... with l = t / P, nl = ST / P (P = wx * wy <= 256).
-template <int WM>
-__device__ __forceinline__ double gram_acc(const double* X, int wx, const double* Y, int wy, int nrows, double acc) {
+template <typename T, int WM>
+__device__ __forceinline__ T gram_acc(const T* X, int wx, const T* Y, int wy, int nrows, T acc) {
   const int P = wx * wy, t = threadIdx.x, nl = ST / P, l = t / P;
   if (l < nl) {
     const int p = t % P, a = p / wy, b = p % wy;
@@ -149,8 +167,8 @@ __device__ __forceinline__ double gram_acc(const double* X, int wx, const double
 }
 
 // Pairwise sum of K (a power of two) values, in a fixed order.
-template <int K>
-__device__ __forceinline__ double tree_sum(double (&v)[K]) {
+template <typename T, int K>
+__device__ __forceinline__ T tree_sum(T (&v)[K]) {
 #pragma unroll
   for (int h = K / 2; h > 0; h >>= 1)
 #pragma unroll
@@ -159,8 +177,8 @@ __device__ __forceinline__ double tree_sum(double (&v)[K]) {
 }
 
 // sh.red[j] <- sum over q < nparts of sh.red[q * cnt + j] (j < cnt), pairwise in a fixed
-// order (FP64 additions are long-latency here, so a tree beats a chain).  sh.red must be
-// written and synchronised before the call.
+// order (a tree is shorter than a chain).  sh.red must be written and synchronised before
+// the call.
 template <typename S>
 __device__ void tree_combine(int cnt, int nparts, S& sh) {
   const int t = threadIdx.x, q = t / cnt, j = t % cnt;
@@ -173,38 +191,38 @@ __device__ void tree_combine(int cnt, int nparts, S& sh) {
 }
 
 // Combines the per-thread shares of a P-entry Gram matrix into this block's partial.
-template <typename S>
-__device__ void gram_store(double acc, int P, void* part, int slot, S& sh) {
+template <typename T, typename S>
+__device__ void gram_store(T acc, int P, void* part, int slot, S& sh) {
   const int t = threadIdx.x;
   sh.red[t] = acc;
   __syncthreads();
   tree_combine(P, ST / P, sh);
-  if (t < P) slot_ptr(part, slot, blockIdx.x)[t] = sh.red[t];
+  if (t < P) slot_ptr<T>(part, slot, blockIdx.x)[t] = sh.red[t];
   __syncthreads();
 }
 
 // G + s * GSLOT <- sum over blocks of slot (slot0 + s), entries 0..P-1, for s < ns.  The
 // summation order depends only on the grid size, so every block gets the same bits.
-template <typename S>
-__device__ void reduce_slots(const void* part, int slot0, int ns, int P, double* G, S& sh) {
+template <typename T, typename S>
+__device__ void reduce_slots(const void* part, int slot0, int ns, int P, T* G, S& sh) {
   const int t = threadIdx.x, nb = gridDim.x, total = ns * P;
-  const double* pb = static_cast<const double*>(part);
+  const T* pb = static_cast<const T*>(part);
   for (int j0 = 0; j0 < total; j0 += ST) {
     const int cnt = min(ST, total - j0);
     const int nch = min(32, ST / cnt);
     const int c = t / cnt;
-    double s = 0.0;
+    T s = T(0);
     if (c < nch) {
       const int j = j0 + t % cnt;
-      const double* base = pb + (size_t)(slot0 + j / P) * nb * GSLOT + (j % P);
+      const T* base = pb + (size_t)(slot0 + j / P) * nb * GSLOT + (j % P);
       for (int b0 = c; b0 < nb; b0 += 16 * nch) {
-        double v[16];
+        T v[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int b = b0 + u * nch;
-          v[u] = (b < nb) ? base[(size_t)b * GSLOT] : 0.0;
+          v[u] = (b < nb) ? base[(size_t)b * GSLOT] : T(0);
         }
-        s += tree_sum<16>(v);
+        s += tree_sum<T, 16>(v);
       }
     }
     sh.red[t] = s;
@@ -218,103 +236,55 @@ __device__ void reduce_slots(const void* part, int slot0, int ns, int P, double*
   }
 }
 
-// Upper Cholesky factor R (R^T R = G) of a w x w symmetric matrix, by one warp, in double.
-// A pivot below 1e-14 of the largest diagonal entry (a direction lost to rounding) gives
-// a zero row of R.
-__device__ void cholesky_warp(const double* G, int w, double* R) {
+// R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix, by one
+// warp in the working precision.  G is scaled to unit diagonal first, G^ = D^-1/2 G D^-1/2;
+// a pivot of G^ at or below 1e-6 (float) or 1e-14 (double), a direction lost to rounding,
+// gives a zero row of R and a zero column of T.  Then R = R^ D^1/2 and T = D^-1/2 R^-1,
+// where column j of R^-1 is (e_j - sum_{k<j} R^-1 e_k R^_kj) / R^_jj.
+template <typename T>
+__device__ void factor_warp(const T* G, int w, T* R, T* Tm) {
   const int l = threadIdx.x & 31;
-  for (int j = 0; j < w; ++j)
-    if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] : 0.0;
-  __syncwarp();
-  double scale = 0.0;
-  for (int j = 0; j < w; ++j) scale = fmax(scale, G[j * w + j]);
+  const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
+  const T dl = (l < w) ? sqrt(fmax(G[l * w + l], T(0))) : T(0);
+  const T il = dl > T(0) ? T(1) / dl : T(0);
   for (int j = 0; j < w; ++j) {
-    const double d = R[j * w + j];
-    const bool good = d > 1e-14 * scale && d > 0.0;
-    const double rjj = good ? sqrt(d) : 0.0;
-    const double inv = good ? 1.0 / rjj : 0.0;
+    const T ij = __shfl_sync(FULL, il, j);
+    if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] * (ij * il) : T(0);
+  }
+  __syncwarp();
+  for (int j = 0; j < w; ++j) {
+    const T d = R[j * w + j];
+    const bool good = d > tiny;
+    const T rjj = good ? sqrt(d) : T(0);
+    const T inv = good ? T(1) / rjj : T(0);
     __syncwarp();
-    if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : 0.0;
+    if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : T(0);
     __syncwarp();
     if (l > j && l < w)
-      for (int k = j + 1; k <= l; ++k) R[k * w + l] -= R[j * w + k] * R[j * w + l];
+      for (int k = j + 1; k <= l; ++k) R[k * w + l] = fma(-R[j * w + k], R[j * w + l], R[k * w + l]);
     __syncwarp();
   }
-}
-
-// T (upper, w x w) with X T = Q for X = Q R: column j of T is (e_j - sum_{k<j} T e_k R_kj)
-// / R_jj, or zero where R_jj is zero.  One full warp, lane = row of T.
-__device__ void tri_inverse_warp(const double* R, int w, double* Tm) {
-  const int l = threadIdx.x & 31;
-  const double rinv = (l < w && R[l * w + l] != 0.0) ? 1.0 / R[l * w + l] : 0.0;
+  const T rinv = (l < w && R[l * w + l] != T(0)) ? T(1) / R[l * w + l] : T(0);
   for (int j = 0; j < w; ++j) {
-    const double rj = __shfl_sync(FULL, rinv, j);
+    const T rj = __shfl_sync(FULL, rinv, j);
     if (l < w) {
-      double s = (l == j) ? 1.0 : 0.0;
-      for (int k = l; k < j; ++k) s -= Tm[l * w + k] * R[k * w + j];
-      Tm[l * w + j] = (j >= l) ? s * rj : 0.0;
+      T s = (l == j) ? T(1) : T(0);
+      for (int k = l; k < j; ++k) s = fma(-Tm[l * w + k], R[k * w + j], s);
+      Tm[l * w + j] = (j >= l) ? s * rj : T(0);
     }
   }
   __syncwarp();
-}
-
-// The same two factors in single precision, for the FP32 mode: G (double) is scaled to unit
-// diagonal, G^ = D^-1/2 G D^-1/2, factored in float (a pivot below 1e-6 is dropped), and
-// R = R^ D^1/2, T = D^-1/2 R^-1 are returned in double.  A is a w x w float scratch.
-__device__ void factor_warp_f32(const double* G, int w, double* R, double* Tm, float* A) {
-  const int l = threadIdx.x & 31;
-  const float dl = (l < w) ? sqrtf((float)G[l * w + l]) : 0.f;
-  const float il = dl > 0.f ? 1.f / dl : 0.f;
-  for (int j = 0; j < w; ++j) {
-    const float ij = __shfl_sync(FULL, il, j);
-    if (l < w) A[j * w + l] = (l >= j) ? (float)G[j * w + l] * (ij * il) : 0.f;
-  }
-  __syncwarp();
-  for (int j = 0; j < w; ++j) {
-    const float d = A[j * w + j];
-    const bool good = d > 1e-6f;
-    const float rjj = good ? sqrtf(d) : 0.f;
-    const float inv = good ? 1.f / rjj : 0.f;
-    __syncwarp();
-    if (l >= j && l < w) A[j * w + l] = good ? ((l == j) ? rjj : A[j * w + l] * inv) : 0.f;
-    __syncwarp();
-    if (l > j && l < w)
-      for (int k = j + 1; k <= l; ++k) A[k * w + l] = fmaf(-A[j * w + k], A[j * w + l], A[k * w + l]);
-    __syncwarp();
-  }
-  // R = R^ D^1/2 (column l scaled by d_l); T^ = R^-1 row by row, then T = D^-1/2 T^
   for (int j = 0; j < w; ++j)
-    if (l < w) R[j * w + l] = (double)A[j * w + l] * (double)dl;
-  const float rinv = (l < w && A[l * w + l] != 0.f) ? 1.f / A[l * w + l] : 0.f;
-  float trow[MW];
-#pragma unroll
-  for (int j = 0; j < MW; ++j) trow[j] = 0.f;
-#pragma unroll
-  for (int j = 0; j < MW; ++j) {
-    const float rj = __shfl_sync(FULL, rinv, j);
-    if (j < w && l < w && j >= l) {
-      float s = (l == j) ? 1.f : 0.f;
-#pragma unroll
-      for (int k = 0; k < MW; ++k)
-        if (k >= l && k < j) s = fmaf(-trow[k], A[k * w + j], s);
-      trow[j] = s * rj;
+    if (l < w) {
+      Tm[l * w + j] *= il;  // row l of T scaled by 1 / d_l
+      R[j * w + l] *= dl;   // column l of R scaled by d_l
     }
-  }
-#pragma unroll
-  for (int j = 0; j < MW; ++j)
-    if (l < w && j < w) Tm[l * w + j] = (double)trow[j] * (double)il;
   __syncwarp();
 }
 
-// R and T of one Gram matrix by the calling warp, in the precision of the mode.
 template <typename T, int WM>
-__device__ void factor_one(const double* G, int w, int s, Smem<T, WM>& sh) {
-  if (sizeof(T) == 8) {
-    cholesky_warp(G, w, sh.Rf[s]);
-    tri_inverse_warp(sh.Rf[s], w, sh.Tf[s]);
-  } else {
-    factor_warp_f32(G, w, sh.Rf[s], sh.Tf[s], sh.fs[s]);
-  }
+__device__ __forceinline__ void factor_one(const T* G, int w, int s, Smem<T, WM>& sh) {
+  factor_warp<T>(G, w, sh.Rf[s], sh.Tf[s]);
 }
 
 // Both factors at once: warp 0 factors G[ga] into Rf[0]/Tf[0], warp 1 G[gb] into
@@ -327,7 +297,7 @@ __device__ void factor_pair(int w, int ga, int gb, Smem<T, WM>& sh) {
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * WM * WM; e += ST) {
     const int s = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
-    sh.tm[s][q * WM + c] = (q < w && c < w) ? (T)sh.Tf[s][q * w + c] : T(0);
+    sh.tm[s][q * WM + c] = (q < w && c < w) ? sh.Tf[s][q * w + c] : T(0);
   }
   __syncthreads();
 }
@@ -360,9 +330,9 @@ __device__ __forceinline__ void store_copy(T* X, size_t i, int Rc, const T (&x)[
 }
 
 template <typename T, int WM>
-__device__ __forceinline__ void stage_row(double* S, int li, const T (&x)[WM]) {
+__device__ __forceinline__ void stage_row(T* S, int li, const T (&x)[WM]) {
 #pragma unroll
-  for (int j = 0; j < WM; ++j) S[li * WM + j] = (double)x[j];
+  for (int j = 0; j < WM; ++j) S[li * WM + j] = x[j];
 }
 
 // y = x A for a WM x WM matrix A in shared memory (row-major, leading dimension WM).
@@ -463,11 +433,11 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
   jacobi_pairs(N, sh.pairs);
-  double mx = 0.0;
+  T mx = T(0);
   for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.M[(e / N) * NM + (e % N)]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
-  const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+  const T sc = mx > T(0) ? T(1) / mx : T(1);
   float xf[NM], vf[NM];
 #pragma unroll
   for (int i = 0; i < NM; ++i) {
@@ -476,27 +446,27 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
   }
   // rotate until every pair of columns is orthogonal to ~3e-6
   jacobi_lanes<float, NM>(N, xf, vf, 1e-11f, 12, sh.pairs);
-  double sg;
-  double y[NM], vd[NM];
+  T sg;
+  T y[NM], vd[NM];
   if (sizeof(T) == 8) {
 #pragma unroll
-    for (int i = 0; i < NM; ++i) vd[i] = (double)vf[i];
+    for (int i = 0; i < NM; ++i) vd[i] = (T)vf[i];
     // V is orthogonal to single precision only: orthonormalise it in double (modified
     // Gram-Schmidt over the lanes) before the double-precision sweeps
     for (int j = 0; j < N; ++j) {
-      double s2 = 0.0;
+      T s2 = T(0);
 #pragma unroll
       for (int i = 0; i < NM; ++i) s2 = fma(vd[i], vd[i], s2);
       if (lane == j) {
-        const double inv = 1.0 / sqrt(s2);
+        const T inv = T(1) / sqrt(s2);
 #pragma unroll
         for (int i = 0; i < NM; ++i) vd[i] *= inv;
       }
-      double vj[NM];
+      T vj[NM];
 #pragma unroll
       for (int i = 0; i < NM; ++i) vj[i] = __shfl_sync(FULL, vd[i], j);
       if (lane > j && lane < N) {
-        double d = 0.0;
+        T d = T(0);
 #pragma unroll
         for (int i = 0; i < NM; ++i) d = fma(vd[i], vj[i], d);
 #pragma unroll
@@ -505,17 +475,17 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll
       for (int k = 0; k < NM; ++k) s = fma(sh.M[i * NM + k], vd[k], s);
-      y[i] = (lane < N) ? s : 0.0;
+      y[i] = (lane < N) ? s : T(0);
     }
-    jacobi_lanes<double, NM>(N, y, vd, 1e-28, 8, sh.pairs);
-    double s2 = 0.0;
+    jacobi_lanes<T, NM>(N, y, vd, T(1e-28), 8, sh.pairs);
+    T s2 = T(0);
 #pragma unroll
     for (int i = 0; i < NM; ++i) s2 = fma(y[i], y[i], s2);
-    sg = (lane < N) ? sqrt(s2) : -1.0;
-    const double inv = sg > 0.0 ? 1.0 / sg : 0.0;
+    sg = (lane < N) ? sqrt(s2) : T(-1);
+    const T inv = sg > T(0) ? T(1) / sg : T(0);
 #pragma unroll
     for (int i = 0; i < NM; ++i) y[i] *= inv;
   } else {
@@ -524,16 +494,16 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
     for (int i = 0; i < NM; ++i) s2 = fmaf(xf[i], xf[i], s2);
     const float sf = sqrtf(s2);
     const float inv = sf > 0.f ? 1.f / sf : 0.f;
-    sg = (lane < N) ? (double)sf * mx : -1.0;
+    sg = (lane < N) ? (T)(sf * (float)mx) : T(-1);
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-      y[i] = (double)(xf[i] * inv);
-      vd[i] = (double)vf[i];
+      y[i] = (T)(xf[i] * inv);
+      vd[i] = (T)vf[i];
     }
   }
   int rank = 0;
   for (int i = 0; i < N; ++i) {
-    const double si = __shfl_sync(FULL, sg, i);
+    const T si = __shfl_sync(FULL, sg, i);
     rank += (si > sg || (si == sg && i < lane)) ? 1 : 0;
   }
   if (lane < N) {
@@ -557,8 +527,8 @@ __device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long&
     s += a.resP[c];
     z += a.nnzP[c];
   }
-  res2 = block_sum(s, sh);
-  nnz = (unsigned long long)block_sum((double)z, sh);
+  res2 = block_sum_d(s, sh);
+  nnz = block_sum_u64(z, sh);
 }
 
 // Row i of Y (width w) <- fixed-order sum of the nsl pass partial slices (width R,
@@ -595,12 +565,12 @@ __device__ void trim_and_gram(const SmallArgs& a, Smem<T, WM>& sh) {
   const bool do_trim = a.st->trim != 0;
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? a.n : a.m;
-    const T cap = (T)sqrt(mu * r / rows);
+    const T cap = sqrt((T)mu * (T)r / (T)rows);
     const T* F = static_cast<const T*>(side ? a.V : a.U);
     T* Tt = static_cast<T*>(side ? a.Vt : a.Ut);
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T x[WM];
@@ -618,15 +588,15 @@ __device__ void trim_and_gram(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       stage_row<T, WM>(sh.stage[0], t, x);
       __syncthreads();
-      acc = gram_acc<WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
     gram_store(acc, r * r, a.part, 3 + side, sh);
   }
 }
 
-// After a barrier: U~ <- trimmed U T_u, V~ <- trimmed V T_v (one CholeskyQR with double
-// Gram matrices), and the copies read by the next pass: W = U Sigma, V, U~, V~ zero-padded
+// After a barrier: U~ <- trimmed U T_u, V~ <- trimmed V T_v (one CholeskyQR), and the
+// copies read by the next pass: W = U Sigma, V, U~, V~ zero-padded
 // to width Rit.  sh.sv[0] holds sigma.
 template <typename T, int WM>
 __device__ void finish_bases(const SmallArgs& a, Smem<T, WM>& sh) {
@@ -698,7 +668,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   {
     int lo, hi;
     block_range(m, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T y[WM], u[WM];
@@ -712,7 +682,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       stage_row<T, WM>(sh.stage[0], t, u);
       stage_row<T, WM>(sh.stage[1], t, y);
       __syncthreads();
-      acc = gram_acc<WM>(sh.stage[0], r, sh.stage[1], r, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[1], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
     gram_store(acc, r * r, a.part, 0, sh);
@@ -729,7 +699,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   reduce_slots(a.part, 0, 1, r * r, sh.C, sh);
   for (int e = t; e < WM * WM; e += ST) {
     const int q = e / WM, c = e % WM;
-    sh.cmd[e] = (q < r && c < r) ? sh.C[q * r + c] : 0.0;
+    sh.cm[e] = (q < r && c < r) ? sh.C[q * r + c] : T(0);
   }
   __syncthreads();
   for (int side = 0; side < 2; ++side) {
@@ -738,7 +708,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     const T* B = side ? Vt : Ut;
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T y[WM];
@@ -749,16 +719,16 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         load_row<T, WM>(B, i, r, b);
 #pragma unroll
         for (int c = 0; c < WM; ++c) {
-          double s = (double)y[c];
+          T s = y[c];
 #pragma unroll
-          for (int q = 0; q < WM; ++q) s -= (double)b[q] * (side ? sh.cmd[c * WM + q] : sh.cmd[q * WM + c]);
-          y[c] = (T)s;
+          for (int q = 0; q < WM; ++q) s = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], s);
+          y[c] = s;
         }
         store_row<T, WM>(Y, i, r, y);
       }
       stage_row<T, WM>(sh.stage[0], t, y);
       __syncthreads();
-      acc = gram_acc<WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
     gram_store(acc, r * r, a.part, 1 + side, sh);
@@ -771,7 +741,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   const int N = 2 * r;
   for (int e = t; e < NM * NM; e += ST) {
     const int row = e / NM, col = e % NM;
-    double v = 0.0;
+    T v = T(0);
     if (row < r && col < r)
       v = sh.C[row * r + col];
     else if (row < r && col >= r && col < N)
@@ -787,21 +757,21 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   // block of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2)
   for (int e = t; e < 2 * 2 * WM * WM; e += ST) {
     const int side = e / (2 * WM * WM), rem = e % (2 * WM * WM), row = rem / WM, c = rem % WM;
-    const double* Y = side ? sh.VM : sh.UM;
-    double v = 0.0;
+    const T* Y = side ? sh.VM : sh.UM;
+    T v = T(0);
     if (c < r) {
       if (row < r) {
         v = Y[c * NM + row];
       } else if (row < 2 * r) {
         const int q = row - r;
-        for (int kk = q; kk < r; ++kk) v += sh.Tf[side][q * r + kk] * Y[c * NM + r + kk];
+        for (int kk = q; kk < r; ++kk) v = fma(sh.Tf[side][q * r + kk], Y[c * NM + r + kk], v);
       }
     }
-    sh.mat[side][rem] = (T)v;
+    sh.mat[side][rem] = v;
   }
   if (t < MW) sh.sv[0][t] = (t < r) ? (T)sh.sig[t] : T(0);
   __syncthreads();
-  const double s1 = sh.sig[0], sr1 = sh.sig[r];
+  const double s1 = (double)sh.sig[0], sr1 = (double)sh.sig[r];
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
@@ -835,7 +805,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       st->zeta = beta * (sr1 + g * s1);
     else if (zmode == 1)
       st->zeta = beta * g * s1;
-    for (int i = 0; i < N; ++i) st->sigma[i] = sh.sig[i];
+    for (int i = 0; i < N; ++i) st->sigma[i] = (double)sh.sig[i];
     a.stats[k].sigma1 = s1;
     a.stats[k].sigma_r1 = sr1;
     st->k = k1;
@@ -880,7 +850,7 @@ __device__ void orth_first_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>& 
     T* Y = static_cast<T*>(side ? a.Y2 : a.Y1);
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T q[WM];
@@ -893,7 +863,7 @@ __device__ void orth_first_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>& 
       }
       stage_row<T, WM>(sh.stage[0], t, q);
       __syncthreads();
-      acc = gram_acc<WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
       __syncthreads();
     }
     gram_store(acc, w * w, a.part, s1 + side, sh);
@@ -936,7 +906,7 @@ __device__ void mode_rand(const SmallArgs& a, Smem<T, WM>& sh) {
     const unsigned long long seed = side ? (a.seed ^ 0x5bd1e995ull) : a.seed;
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T y[WM];
@@ -945,7 +915,7 @@ __device__ void mode_rand(const SmallArgs& a, Smem<T, WM>& sh) {
       if (i < hi) store_row<T, WM>(Y, i, w, y);
       stage_row<T, WM>(sh.stage[0], t, y);
       __syncthreads();
-      acc = gram_acc<WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
       __syncthreads();
     }
     gram_store(acc, w * w, a.part, 1 + side, sh);
@@ -978,7 +948,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
     const int rows = side ? n : m;
     int lo, hi;
     block_range(rows, lo, hi);
-    double accB = 0.0, accG = 0.0;
+    T accB = T(0), accG = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T y[WM], u[WM];
@@ -994,8 +964,8 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
       if (!side) stage_row<T, WM>(sh.stage[0], t, u);
       __syncthreads();
       const int nr = min(ST, hi - c0);
-      if (!side) accB = gram_acc<WM>(sh.stage[0], w, sh.stage[1], w, nr, accB);
-      accG = gram_acc<WM>(sh.stage[1], w, sh.stage[1], w, nr, accG);
+      if (!side) accB = gram_acc<T, WM>(sh.stage[0], w, sh.stage[1], w, nr, accB);
+      accG = gram_acc<T, WM>(sh.stage[1], w, sh.stage[1], w, nr, accG);
       __syncthreads();
     }
     if (!side) gram_store(accB, w * w, a.part, 0, sh);
@@ -1008,7 +978,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   reduce_slots(a.part, 0, 3, w * w, &sh.G[0][0], sh);  // G[0] = B, G[1], G[2] = Grams
   for (int e = t; e < NM * NM; e += ST) {
     const int row = e / NM, col = e % NM;
-    sh.M[e] = (row < w && col < w) ? sh.G[0][row * w + col] : 0.0;
+    sh.M[e] = (row < w && col < w) ? sh.G[0][row * w + col] : T(0);
   }
   __syncthreads();
   {
@@ -1021,14 +991,14 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   // mat[0] rows 0..w-1: U_B[:, :r]; mat[1]: V_B[:, :r]; tm: T1, T2
   for (int e = t; e < 2 * WM * WM; e += ST) {
     const int s = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
-    const double* Y = s ? sh.VM : sh.UM;
-    sh.mat[s][q * WM + c] = (q < w && c < r) ? (T)Y[c * NM + q] : T(0);
-    sh.tm[s][q * WM + c] = (q < w && c < w) ? (T)sh.Tf[s][q * w + c] : T(0);
+    const T* Y = s ? sh.VM : sh.UM;
+    sh.mat[s][q * WM + c] = (q < w && c < r) ? Y[c * NM + q] : T(0);
+    sh.tm[s][q * WM + c] = (q < w && c < w) ? sh.Tf[s][q * w + c] : T(0);
   }
   if (t < MW) {
-    const double sg = (t < r) ? sh.sig[t] : 0.0;
-    sh.sv[0][t] = (T)sg;
-    sh.sv[1][t] = (T)(sg > 0.0 ? 1.0 / sg : 0.0);
+    const T sg = (t < r) ? sh.sig[t] : T(0);
+    sh.sv[0][t] = sg;
+    sh.sv[1][t] = sg > T(0) ? T(1) / sg : T(0);
   }
   __syncthreads();
   // Top Ritz triplets: u_c = U~ U_B[:, c], v_c = V~ V_B[:, c], sigma_c.  Their residuals
@@ -1036,7 +1006,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   // Y2 U_B[:, c] - sigma_c v_c need no further pass over D; the sum of their squared
   // norms, each divided by sigma_c^2, decides convergence.
   const int nr = (a.init_phase == 0) ? 1 : r;
-  double res = 0.0;
+  T res = T(0);
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
@@ -1046,7 +1016,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
     const T* My = sh.mat[1 - side];  // product coefficients
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T q[WM];
@@ -1061,7 +1031,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
 #pragma unroll
         for (int c = 0; c < WM; ++c)
           if (c < nr) {
-            const double d = ((double)zy[c] - (double)sh.sv[0][c] * (double)f[c]) * (double)sh.sv[1][c];
+            const T d = fma(-sh.sv[0][c], f[c], zy[c]) * sh.sv[1][c];
             res = fma(d, d, res);
           }
         row_times<T, WM>(y, sh.tm[side], q);
@@ -1069,29 +1039,31 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       stage_row<T, WM>(sh.stage[0], t, q);
       __syncthreads();
-      acc = gram_acc<WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
       __syncthreads();
     }
     gram_store(acc, w * w, a.part, 3 + side, sh);
   }
-  const double rs = block_sum(res, sh);
-  if (t == 0) slot_ptr(a.part, 5, blockIdx.x)[0] = rs;
-  if (blockIdx.x == 0 && t < w) st->sigma[t] = sh.sig[t];
+  sh.red[t] = res;
+  __syncthreads();
+  tree_combine(1, ST, sh);
+  if (t == 0) slot_ptr<T>(a.part, 5, blockIdx.x)[0] = sh.red[0];
+  if (blockIdx.x == 0 && t < w) st->sigma[t] = (double)sh.sig[t];
   if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[t];
   if (!grid_barrier(st, sh)) return;
 
   // C: convergence; then either the bases for the next step or (top-r converged) Trim
   reduce_slots(a.part, 5, 1, 1, sh.scal, sh);
-  const double crit = sqrt(sh.scal[0]);
+  const double crit = sqrt((double)sh.scal[0]);
   const double tol = (a.init_phase == 0) ? sqrt(a.init_tol) : a.init_tol;
   const int conv = (a.rr_force || (!a.rr_first && crit <= tol)) ? 1 : 0;
   if (blockIdx.x == 0 && t == 0) {
     if (!(crit == crit)) atomicCAS(&st->status, 0, kErrNumerical);
     st->sigma_prev[0] = crit;
     st->conv = conv;
-    if (conv && a.init_phase == 0) st->zeta = st->beta_init * sh.sig[0];
+    if (conv && a.init_phase == 0) st->zeta = st->beta_init * (double)sh.sig[0];
     if (conv && a.init_phase == 1) {
-      st->zeta = st->beta * sh.sig[0];
+      st->zeta = st->beta * (double)sh.sig[0];
       st->k = 0;
     }
   }
