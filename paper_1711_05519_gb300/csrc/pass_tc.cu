@@ -13,13 +13,19 @@
 //
 // Per tile:
 //   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, 128-byte swizzle) plus the operand
-//                      images of V (tf32 hi/lo), V~ and U~ (bf16 hi/lo) -> stage s (3 stages)
-//   MMA (warp 1)     : L = [W_hi W_hi W_lo 0] [V_hi V_lo V_hi 0]^T, kind::tf32, M128 N64 K32
+//                      images of V (tf32 hi/lo), V~ and U~ (bf16 hi/lo) -> stage s (4 stages)
+//   L MMAs (warp 1)  : L = [W_hi W_hi W_lo 0] [V_hi V_lo V_hi 0]^T, kind::tf32, M128 N64 K32
 //                      (three-term split product: FP32-level accuracy of the K = r rebuild)
-//   epilogue (8 warps): L from TMEM, D from shared memory, threshold, residual, support
-//                      count, Z split into bf16 hi + lo, written K-major 128B-swizzled
-//   MMA (warp 1)     : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N16 K64 (x2)
+//   epilogue (16 warps): L from TMEM, D from shared memory, threshold, residual, support
+//                      count, Z split into bf16 hi + lo, written K-major 128B-swizzled over
+//                      the D tile it came from (Z_hi over the first box, Z_lo over the
+//                      second), so a stage carries its own Z and the epilogue never waits
+//                      for the MMAs of the previous tile
+//   Y MMAs (warp 2)  : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N16 K64 (x2)
 //                      Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N16 K128
+//                      then the stage is released to the producer
+// The L and Y products are issued by different threads: a single issuer would hold the Y
+// products of tile t (and so the release of its stage) behind the arrival of tile t + 1.
 // The column halves of the N16 accumulators (hi and lo parts of V~, U~) and the two M
 // halves of the Y2 accumulator (Z_hi, Z_lo) are added when the accumulators are drained.
 #include <cuda.h>
@@ -35,42 +41,44 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128, BN = 64;
-constexpr int NSTAGE = 3;
+constexpr int NSTAGE = 4;
 constexpr int D_BYTES = BM * BN * 4;          // 32 KB
 constexpr int VOP_BYTES = BN * 32 * 4;        // 8 KB  [64 x 32] tf32
 constexpr int VTOP_BYTES = 16 * 64 * 2;       // 2 KB  [16 x 64] bf16
 constexpr int UTOP_BYTES = 2 * 16 * 64 * 2;   // 4 KB  2 x [16 x 64] bf16
 constexpr int WOP_BYTES = BM * 32 * 4;        // 16 KB [128 x 32] tf32
 constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES + UTOP_BYTES;  // 46 KB
-constexpr int Z_BYTES = 2 * BM * BN * 2;      // hi + lo, 32 KB
+constexpr int Z_BYTES = 2 * BM * BN * 2;      // hi + lo, 32 KB, in place of the D tile
 constexpr int OFF_STAGE = 0;
-constexpr int OFF_Z = NSTAGE * STAGE_BYTES;
-constexpr int OFF_W = OFF_Z + Z_BYTES;
+constexpr int OFF_W = NSTAGE * STAGE_BYTES;
 constexpr int OFF_BAR = OFF_W + 2 * WOP_BYTES;
-constexpr int NBAR = 32;
+constexpr int NBAR = 48;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 256 + 1024;  // + alignment slack
-constexpr int THREADS = 320;                  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr int EPI_THREADS = 256;
+constexpr int EPI_WARPS = 16;
+constexpr int THREADS = 96 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 L MMAs, warp 2 Y MMAs, warps 3..18 epilogue
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr int TM_Y1 = 128, TM_Y2 = 160;
-static_assert(STAGE_BYTES % 1024 == 0 && OFF_Z % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned operands");
+static_assert(STAGE_BYTES % 1024 == 0 && OFF_W % 1024 == 0 && Z_BYTES == D_BYTES, "1024-byte aligned operands");
 static_assert(SMEM_BYTES <= 232448, "shared memory");
 
 // barrier slots
 enum {
-  B_FULL = 0,      // [3]
-  B_EMPTY = 3,     // [3]
-  B_LFULL = 6,     // [2]
-  B_LEMPTY = 8,    // [2]
-  B_ZFULL = 10,
-  B_ZEMPTY = 11,
-  B_WFULL = 12,    // [2]
-  B_WEMPTY = 14,   // [2]
-  B_Y1FULL = 16,   // [2]
-  B_Y1EMPTY = 18,  // [2]
-  B_YFIN = 20,
-  B_DRAIN = 21
+  B_FULL = 0,      // [NSTAGE]
+  B_EMPTY = 4,     // [NSTAGE]
+  B_ZFULL = 8,     // [NSTAGE]
+  B_LFULL = 12,    // [2]
+  B_LEMPTY = 14,   // [2]
+  B_WFULL = 16,    // [2]
+  B_WEMPTY = 18,   // [2]
+  B_Y1FULL = 20,   // [2]
+  B_Y1EMPTY = 22,  // [2]
+  B_YFIN = 24,
+  B_DRAIN = 25,
+  B_DREAD = 26,    // [NSTAGE][4]: the warps of lane quarter q have read their D values
+  B_LDRAIN = 42
 };
+static_assert(NSTAGE <= 4 && B_DREAD + 4 * NSTAGE <= B_LDRAIN && B_LDRAIN < NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -101,8 +109,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
-  __shared__ double red_res[8];
-  __shared__ unsigned long long red_nnz[8];
+  __shared__ double red_res[EPI_WARPS];
+  __shared__ unsigned long long red_nnz[EPI_WARPS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x;
@@ -117,19 +125,20 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&bar[B_FULL + s], 1);
       mbar_init(&bar[B_EMPTY + s], 1);
+      mbar_init(&bar[B_ZFULL + s], EPI_WARPS);
+      for (int qq = 0; qq < 4; ++qq) mbar_init(&bar[B_DREAD + 4 * s + qq], EPI_WARPS / 4);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bar[B_LFULL + i], 1);
-      mbar_init(&bar[B_LEMPTY + i], 8);
+      mbar_init(&bar[B_LEMPTY + i], EPI_WARPS);
       mbar_init(&bar[B_WFULL + i], 1);
       mbar_init(&bar[B_WEMPTY + i], 1);
       mbar_init(&bar[B_Y1FULL + i], 1);
       mbar_init(&bar[B_Y1EMPTY + i], 4);
     }
-    mbar_init(&bar[B_ZFULL], 8);
-    mbar_init(&bar[B_ZEMPTY], 1);
     mbar_init(&bar[B_YFIN], 1);
     mbar_init(&bar[B_DRAIN], 1);
+    mbar_init(&bar[B_LDRAIN], 1);
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -174,72 +183,71 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     for (int t = (issued > NSTAGE ? issued - NSTAGE : 0); t < issued; ++t)
       mbar_wait(&bar[B_FULL + (t % NSTAGE)], (t / NSTAGE) & 1, 100000000ull);
   } else if (ntiles > 0 && warp == 1 && lane == 0) {
-    // ------------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------------ L MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idL = instr_desc(128, 64, 2, 2, false, false);
+    for (int t = 0; t < ntiles && !abort_flag; ++t) {
+      const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, wb = rtl & 1;
+      bool ok = true;
+      if (ctl == 0) ok = ok && mbar_wait(&bar[B_WFULL + wb], (rtl >> 1) & 1);
+      ok = ok && mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1);
+      if (t >= 2) ok = ok && mbar_wait(&bar[B_LEMPTY + lb], ((t - 2) >> 1) & 1);
+      if (!ok) {
+        fail(a, &abort_flag);
+        break;
+      }
+      tc_fence_after();
+      const uint64_t dw = smem_desc(base + OFF_W + wb * WOP_BYTES, 16, 1024);
+      const uint64_t dv = smem_desc(base + OFF_STAGE + s * STAGE_BYTES + D_BYTES, 16, 1024);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);
+      mma_commit(&bar[B_LFULL + lb]);
+      if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
+    }
+    mma_commit(&bar[B_LDRAIN]);
+    mbar_wait(&bar[B_LDRAIN], 0, 100000000ull);
+  } else if (ntiles > 0 && warp == 2 && lane == 0) {
+    // ------------------------------------------------------------------ Y MMAs
+    const uint32_t base = smem_u32(sm);
     const uint32_t idY1 = instr_desc(128, 16, 1, 1, false, false);
     const uint32_t idY2 = instr_desc(128, 16, 1, 1, true, false);
-    for (int t = 0; t <= ntiles && !abort_flag; ++t) {
-      if (t < ntiles) {
-        const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, wb = rtl & 1;
-        bool ok = true;
-        if (ctl == 0) ok = ok && mbar_wait(&bar[B_WFULL + wb], (rtl >> 1) & 1);
-        ok = ok && mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1);
-        if (t >= 2) ok = ok && mbar_wait(&bar[B_LEMPTY + lb], ((t - 2) >> 1) & 1);
-        if (!ok) {
-          fail(a, &abort_flag);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t wop = base + OFF_W + wb * WOP_BYTES;
-        const uint32_t vop = base + OFF_STAGE + s * STAGE_BYTES + D_BYTES;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          mma_tf32(tmem + lb * BN, smem_desc(wop + 32 * k, 16, 1024), smem_desc(vop + 32 * k, 16, 1024), idL, k > 0);
-        mma_commit(&bar[B_LFULL + lb]);
-        if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
+    for (int tp = 0; tp < ntiles && !abort_flag; ++tp) {
+      const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE, yb = rtl & 1;
+      bool ok = mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1);
+      if (ok && ctl == 0 && rtl >= 2) ok = mbar_wait(&bar[B_Y1EMPTY + yb], ((rtl - 2) >> 1) & 1);
+      if (!ok) {
+        fail(a, &abort_flag);
+        break;
       }
-      if (t >= 1) {
-        const int tp = t - 1;
-        const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE, yb = rtl & 1;
-        bool ok = mbar_wait(&bar[B_ZFULL], tp & 1);
-        if (ok && ctl == 0 && rtl >= 2) ok = mbar_wait(&bar[B_Y1EMPTY + yb], ((rtl - 2) >> 1) & 1);
-        if (!ok) {
-          fail(a, &abort_flag);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t zhi = base + OFF_Z, zlo = base + OFF_Z + Z_BYTES / 2;
-        const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
-        const uint32_t vtop = stg + D_BYTES + VOP_BYTES, utop = stg + D_BYTES + VOP_BYTES + VTOP_BYTES;
+      tc_fence_after();
+      const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
+      const uint64_t dzh = smem_desc(stg, 16, 1024), dzl = smem_desc(stg + Z_BYTES / 2, 16, 1024);
+      const uint64_t dzm = smem_desc(stg, Z_BYTES / 2, 1024);
+      const uint64_t dvt = smem_desc(stg + D_BYTES + VOP_BYTES, 16, 1024);
+      const uint64_t dut = smem_desc(stg + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
+      const uint32_t y1 = tmem + TM_Y1 + yb * 16, y2 = tmem + TM_Y2 + ctl * 16;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+      for (int k = 0; k < 4; ++k) mma_f16(y1, dzh + 2 * k, dvt + 2 * k, idY1, !(ctl == 0 && k == 0));
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            mma_f16(tmem + TM_Y1 + yb * 16, smem_desc((h ? zlo : zhi) + 32 * k, 16, 1024),
-                    smem_desc(vtop + 32 * k, 16, 1024), idY1, !(ctl == 0 && h == 0 && k == 0));
+      for (int k = 0; k < 4; ++k) mma_f16(y1, dzl + 2 * k, dvt + 2 * k, idY1, true);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          mma_f16(tmem + TM_Y2 + ctl * 16, smem_desc(zhi + 2048 * k, Z_BYTES / 2, 1024),
-                  smem_desc(utop + (k >= 4 ? 2048 : 0) + 32 * (k & 3), 16, 1024), idY2, !(rtl == 0 && k == 0));
-        mma_commit(&bar[B_ZEMPTY]);
-        mma_commit(&bar[B_EMPTY + s]);
-        if (ctl == nct - 1) mma_commit(&bar[B_Y1FULL + yb]);
-      }
+      for (int k = 0; k < 8; ++k)
+        mma_f16(y2, dzm + 128 * k, dut + (k >= 4 ? 128 : 0) + 2 * (k & 3), idY2, !(rtl == 0 && k == 0));
+      mma_commit(&bar[B_EMPTY + s]);
+      if (ctl == nct - 1) mma_commit(&bar[B_Y1FULL + yb]);
     }
     mma_commit(&bar[B_YFIN]);
     mma_commit(&bar[B_DRAIN]);
     mbar_wait(&bar[B_DRAIN], 0, 100000000ull);  // all issued MMAs complete before TMEM is freed
-  } else if (warp >= 2) {
+  } else if (warp >= 3) {
     // ------------------------------------------------------------------ epilogue
-    const int q = warp & 3, h = (warp - 2) >> 2;
+    // warp (q, g): rows 32q .. 32q+31 (its TMEM lane quarter), columns 16g .. 16g+15
+    const int q = warp & 3, g = (warp - 3) >> 2;
     const int rowl = 32 * q + lane;
     const float zeta = static_cast<float>(a.st->zeta);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     float res = 0.f;
     unsigned nnz = 0;
-    uint8_t* zhi = sm + OFF_Z;
-    uint8_t* zlo = sm + OFF_Z + Z_BYTES / 2;
     for (int t = 0; t < ntiles && !abort_flag; ++t) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
       if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
@@ -247,20 +255,32 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         break;
       }
       tc_fence_after();
-      uint32_t lv[32];
-      tmem_ld32(tmem + lane_base + lb * BN + 32 * h, lv);
-      const uint8_t* drow = sm + OFF_STAGE + s * STAGE_BYTES + h * (D_BYTES / 2) + rowl * 128;
-      float z[32];
+      uint32_t lv[16];
+      tmem_ld16(tmem + lane_base + lb * BN + 16 * g, lv);
+      uint8_t* stg = sm + OFF_STAGE + s * STAGE_BYTES;
+      const uint8_t* drow = stg + (g >> 1) * (D_BYTES / 2) + rowl * 128;
+      float z[16];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
-        const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) z[4 * c + e] = dv[e];
+      for (int c = 0; c < 4; ++c) {
+        const int cc = 4 * (g & 1) + c;
+        const float4 d4 = *reinterpret_cast<const float4*>(drow + ((cc ^ (rowl & 7)) << 4));
+        z[4 * c + 0] = d4.x;
+        z[4 * c + 1] = d4.y;
+        z[4 * c + 2] = d4.z;
+        z[4 * c + 3] = d4.w;
       }
       tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
+      // every warp of these rows has its D values in registers before Z overwrites the tile
+      if (lane == 0) mbar_arrive(&bar[B_DREAD + 4 * s + q]);
+      if (!mbar_wait(&bar[B_DREAD + 4 * s + q], (t / NSTAGE) & 1)) {
+        fail(a, &abort_flag);
+        break;
+      }
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
+      for (int c = 0; c < 16; ++c) {
         const float l = __uint_as_float(lv[c]);
         const float rr = z[c] - l;
         const bool sflag = fabsf(rr) > zeta;
@@ -268,16 +288,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         nnz += sflag ? 1u : 0u;
         z[c] = sflag ? l : z[c];
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
-      if (t >= 1 && !mbar_wait(&bar[B_ZEMPTY], (t - 1) & 1)) {
-        fail(a, &abort_flag);
-        break;
-      }
-      // Z -> bf16 hi/lo, row rowl, columns 32h .. 32h+31 = 16-byte chunks 4h .. 4h+3
+      // Z -> bf16 hi/lo, row rowl, columns 16g .. 16g+15 = 16-byte chunks 2g, 2g+1
+      uint8_t* zhi = stg;
+      uint8_t* zlo = stg + Z_BYTES / 2;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < 2; ++c) {
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -288,14 +303,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           hw[e] = *reinterpret_cast<const uint32_t*>(&hi);
           lw[e] = *reinterpret_cast<const uint32_t*>(&lo);
         }
-        const int off = rowl * 128 + ((((4 * h + c) ^ (rowl & 7)) & 7) << 4);
+        const int off = rowl * 128 + ((((2 * g + c) ^ (rowl & 7)) & 7) << 4);
         *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bar[B_ZFULL]);
-      if (ctl == nct - 1 && h == 0) {
+      if (lane == 0) mbar_arrive(&bar[B_ZFULL + s]);
+      if (ctl == nct - 1 && g == 0) {
         // drain Y1 of this row tile
         if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {
           fail(a, &abort_flag);
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         if (lane == 0) mbar_arrive(&bar[B_Y1EMPTY + yb]);
       }
     }
-    // drain Y2: each warp takes the column tiles ctl = h, h + 2, ...; lane quarter q holds
+    // drain Y2: each warp takes the column tiles ctl = g, g + 4, ...; lane quarter q holds
     // accumulator rows 32q .. 32q+31 (rows 0..63: Z_hi part, 64..127: Z_lo part)
     if (ntiles > 0 && !abort_flag) {
       if (!mbar_wait(&bar[B_YFIN], 0)) {
@@ -322,7 +337,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       } else {
         tc_fence_after();
         float* scratch = reinterpret_cast<float*>(sm + OFF_STAGE);  // [nct][128][8], stages are idle now
-        for (int ctl = h; ctl < nct; ctl += 2) {
+        for (int ctl = g; ctl < nct; ctl += EPI_WARPS / 4) {
           uint32_t yv[16];
           tmem_ld16(tmem + lane_base + TM_Y2 + ctl * 16, yv);
           tmem_wait_ld();
@@ -335,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
     if (ntiles > 0 && !abort_flag) {
       const float* scratch = reinterpret_cast<const float*>(sm + OFF_STAGE);
-      const int et = tid - 64;
+      const int et = tid - 96;
       for (int e = et; e < nct * 64; e += EPI_THREADS) {
         const int ctl = e / 64, jl = e % 64;
         const int col = (ct0 + ctl) * BN + jl;
@@ -354,14 +369,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       nz += __shfl_xor_sync(0xffffffffu, nz, o);
     }
     if (lane == 0) {
-      red_res[warp - 2] = rd;
-      red_nnz[warp - 2] = nz;
+      red_res[warp - 3] = rd;
+      red_nnz[warp - 3] = nz;
     }
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
-    if (tid == 64) {
+    if (tid == 96) {
       double tr = 0.0;
       unsigned long long tz = 0;
-      for (int w = 0; w < 8; ++w) {
+      for (int w = 0; w < EPI_WARPS; ++w) {
         tr += red_res[w];
         tz += red_nnz[w];
       }
