@@ -14,18 +14,18 @@
 // Per tile:
 //   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, 128-byte swizzle) plus the operand
 //                      images of V (tf32 hi/lo), V~ and U~ (bf16 hi/lo) -> stage s (4 stages)
-//   L MMAs (warp 1)  : L = [W_hi W_hi W_lo 0] [V_hi V_lo V_hi 0]^T, kind::tf32, M128 N64 K32
+//   L MMAs (warp 1)  : L = [W_hi W_hi W_lo] [V_hi V_lo V_hi]^T, kind::tf32, M128 N64 K24
 //                      (three-term split product: FP32-level accuracy of the K = r rebuild)
-//   epilogue (16 warps): L from TMEM, D from shared memory, threshold, residual, support
-//                      count, Z split into bf16 hi + lo, written K-major 128B-swizzled over
-//                      the D tile it came from (Z_hi over the first box, Z_lo over the
-//                      second), so a stage carries its own Z and the epilogue never waits
-//                      for the MMAs of the previous tile
-//   Y MMAs (warp 2)  : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N16 K64 (x2)
-//                      Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N16 K128
-//                      then the stage is released to the producer
-// The L and Y products are issued by different threads: a single issuer would hold the Y
-// products of tile t (and so the release of its stage) behind the arrival of tile t + 1.
+//   epilogue (16 warps, two groups of 8 on alternate tiles): L from TMEM, D from shared
+//                      memory, threshold, residual, support count, Z split into bf16 hi + lo,
+//                      written K-major 128B-swizzled over the D tile it came from (Z_hi over
+//                      the first box, Z_lo over the second), so a stage carries its own Z
+//   Y1 MMAs (warp 2) : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N16 K64 (x2)
+//   Y2 MMAs (warp 3) : Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N16 K128;
+//                      the stage is released when both have completed
+// Each product has its own issuing thread: a tcgen05.mma of these small shapes costs about
+// 40 cycles of tensor-pipe time but about 55 cycles of issue time on one thread, and a single
+// issuer would also hold the Y products of tile t behind the TMA arrival of tile t + 1.
 // The column halves of the N16 accumulators (hi and lo parts of V~, U~) and the two M
 // halves of the Y2 accumulator (Z_hi, Z_lo) are added when the accumulators are drained.
 #include <cuda.h>
@@ -55,7 +55,7 @@ constexpr int OFF_BAR = OFF_W + 2 * WOP_BYTES;
 constexpr int NBAR = 48;
 constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 256 + 1024;  // + alignment slack
 constexpr int EPI_WARPS = 16;
-constexpr int THREADS = 96 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 L MMAs, warp 2 Y MMAs, warps 3..18 epilogue
+constexpr int THREADS = 128 + 32 * EPI_WARPS;  // warp 0 TMA, 1 L MMAs, 2 Y1 MMAs, 3 Y2 MMAs, 4..19 epilogue
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr int TM_Y1 = 128, TM_Y2 = 160;
@@ -76,9 +76,10 @@ enum {
   B_YFIN = 24,
   B_DRAIN = 25,
   B_DREAD = 26,    // [NSTAGE][4]: the warps of lane quarter q have read their D values
-  B_LDRAIN = 42
+  B_LDRAIN = 42,
+  B_Y1DRAIN = 43
 };
-static_assert(NSTAGE <= 4 && B_DREAD + 4 * NSTAGE <= B_LDRAIN && B_LDRAIN < NBAR, "barrier slots");
+static_assert(NSTAGE <= 4 && B_DREAD + 4 * NSTAGE <= B_LDRAIN && B_Y1DRAIN < NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -124,13 +125,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     abort_flag = 0;
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&bar[B_FULL + s], 1);
-      mbar_init(&bar[B_EMPTY + s], 1);
-      mbar_init(&bar[B_ZFULL + s], EPI_WARPS);
-      for (int qq = 0; qq < 4; ++qq) mbar_init(&bar[B_DREAD + 4 * s + qq], EPI_WARPS / 4);
+      mbar_init(&bar[B_EMPTY + s], 2);  // Y1 and Y2 issuers
+      mbar_init(&bar[B_ZFULL + s], EPI_WARPS / 2);
+      for (int qq = 0; qq < 4; ++qq) mbar_init(&bar[B_DREAD + 4 * s + qq], 2);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bar[B_LFULL + i], 1);
-      mbar_init(&bar[B_LEMPTY + i], EPI_WARPS);
+      mbar_init(&bar[B_LEMPTY + i], EPI_WARPS / 2);
       mbar_init(&bar[B_WFULL + i], 1);
       mbar_init(&bar[B_WEMPTY + i], 1);
       mbar_init(&bar[B_Y1FULL + i], 1);
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     mbar_init(&bar[B_YFIN], 1);
     mbar_init(&bar[B_DRAIN], 1);
     mbar_init(&bar[B_LDRAIN], 1);
+    mbar_init(&bar[B_Y1DRAIN], 1);
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -200,17 +202,16 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       const uint64_t dw = smem_desc(base + OFF_W + wb * WOP_BYTES, 16, 1024);
       const uint64_t dv = smem_desc(base + OFF_STAGE + s * STAGE_BYTES + D_BYTES, 16, 1024);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);
+      for (int k = 0; k < 3; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);  // 4th k-block is zero
       mma_commit(&bar[B_LFULL + lb]);
       if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
     }
     mma_commit(&bar[B_LDRAIN]);
     mbar_wait(&bar[B_LDRAIN], 0, 100000000ull);
   } else if (ntiles > 0 && warp == 2 && lane == 0) {
-    // ------------------------------------------------------------------ Y MMAs
+    // ------------------------------------------------------------------ Y1 MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idY1 = instr_desc(128, 16, 1, 1, false, false);
-    const uint32_t idY2 = instr_desc(128, 16, 1, 1, true, false);
     for (int tp = 0; tp < ntiles && !abort_flag; ++tp) {
       const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE, yb = rtl & 1;
       bool ok = mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1);
@@ -222,48 +223,67 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_after();
       const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
       const uint64_t dzh = smem_desc(stg, 16, 1024), dzl = smem_desc(stg + Z_BYTES / 2, 16, 1024);
-      const uint64_t dzm = smem_desc(stg, Z_BYTES / 2, 1024);
       const uint64_t dvt = smem_desc(stg + D_BYTES + VOP_BYTES, 16, 1024);
-      const uint64_t dut = smem_desc(stg + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
-      const uint32_t y1 = tmem + TM_Y1 + yb * 16, y2 = tmem + TM_Y2 + ctl * 16;
+      const uint32_t y1 = tmem + TM_Y1 + yb * 16;
 #pragma unroll
       for (int k = 0; k < 4; ++k) mma_f16(y1, dzh + 2 * k, dvt + 2 * k, idY1, !(ctl == 0 && k == 0));
 #pragma unroll
       for (int k = 0; k < 4; ++k) mma_f16(y1, dzl + 2 * k, dvt + 2 * k, idY1, true);
+      mma_commit(&bar[B_EMPTY + s]);
+      if (ctl == nct - 1) mma_commit(&bar[B_Y1FULL + yb]);
+    }
+    mma_commit(&bar[B_Y1DRAIN]);
+    mbar_wait(&bar[B_Y1DRAIN], 0, 100000000ull);
+  } else if (ntiles > 0 && warp == 3 && lane == 0) {
+    // ------------------------------------------------------------------ Y2 MMAs
+    const uint32_t base = smem_u32(sm);
+    const uint32_t idY2 = instr_desc(128, 16, 1, 1, true, false);
+    for (int tp = 0; tp < ntiles && !abort_flag; ++tp) {
+      const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE;
+      if (!mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1)) {
+        fail(a, &abort_flag);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
+      const uint64_t dzm = smem_desc(stg, Z_BYTES / 2, 1024);
+      const uint64_t dut = smem_desc(stg + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
+      const uint32_t y2 = tmem + TM_Y2 + ctl * 16;
 #pragma unroll
       for (int k = 0; k < 8; ++k)
         mma_f16(y2, dzm + 128 * k, dut + (k >= 4 ? 128 : 0) + 2 * (k & 3), idY2, !(rtl == 0 && k == 0));
       mma_commit(&bar[B_EMPTY + s]);
-      if (ctl == nct - 1) mma_commit(&bar[B_Y1FULL + yb]);
     }
     mma_commit(&bar[B_YFIN]);
     mma_commit(&bar[B_DRAIN]);
     mbar_wait(&bar[B_DRAIN], 0, 100000000ull);  // all issued MMAs complete before TMEM is freed
-  } else if (warp >= 3) {
+  } else if (warp >= 4) {
     // ------------------------------------------------------------------ epilogue
-    // warp (q, g): rows 32q .. 32q+31 (its TMEM lane quarter), columns 16g .. 16g+15
-    const int q = warp & 3, g = (warp - 3) >> 2;
+    // Two groups of 8 warps take alternate tiles (group grp: tiles grp, grp + 2, ...), so one
+    // group loads while the other computes.  Warp (q, h) of a group: rows 32q .. 32q+31 (its
+    // TMEM lane quarter), columns 32h .. 32h+31.
+    const int e = warp - 4, grp = e >> 3, gq = e >> 2;
+    const int q = warp & 3, h = (e >> 2) & 1;
     const int rowl = 32 * q + lane;
     const float zeta = static_cast<float>(a.st->zeta);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     float res = 0.f;
     unsigned nnz = 0;
-    for (int t = 0; t < ntiles && !abort_flag; ++t) {
+    for (int t = grp; t < ntiles && !abort_flag; t += 2) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
       if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
         fail(a, &abort_flag);
         break;
       }
       tc_fence_after();
-      uint32_t lv[16];
-      tmem_ld16(tmem + lane_base + lb * BN + 16 * g, lv);
+      uint32_t lv[32];
+      tmem_ld32(tmem + lane_base + lb * BN + 32 * h, lv);
       uint8_t* stg = sm + OFF_STAGE + s * STAGE_BYTES;
-      const uint8_t* drow = stg + (g >> 1) * (D_BYTES / 2) + rowl * 128;
-      float z[16];
+      const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
+      float z[32];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int cc = 4 * (g & 1) + c;
-        const float4 d4 = *reinterpret_cast<const float4*>(drow + ((cc ^ (rowl & 7)) << 4));
+      for (int c = 0; c < 8; ++c) {
+        const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
         z[4 * c + 0] = d4.x;
         z[4 * c + 1] = d4.y;
         z[4 * c + 2] = d4.z;
@@ -273,44 +293,48 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
-      // every warp of these rows has its D values in registers before Z overwrites the tile
+      // both warps of these rows hold their D values before Z overwrites the tile
       if (lane == 0) mbar_arrive(&bar[B_DREAD + 4 * s + q]);
       if (!mbar_wait(&bar[B_DREAD + 4 * s + q], (t / NSTAGE) & 1)) {
         fail(a, &abort_flag);
         break;
       }
+      const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const float l = __uint_as_float(lv[c]);
-        const float rr = z[c] - l;
-        const bool sflag = fabsf(rr) > zeta;
-        res = sflag ? res : fmaf(rr, rr, res);
-        nnz += sflag ? 1u : 0u;
-        z[c] = sflag ? l : z[c];
+      for (int c = 0; c < 32; c += 2) {
+        const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
+        const float2 r2 = __ffma2_rn(l2, m1, make_float2(z[c], z[c + 1]));  // D - L, exactly rounded
+        const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;
+        res = s0 ? res : fmaf(r2.x, r2.x, res);
+        res = s1 ? res : fmaf(r2.y, r2.y, res);
+        nnz += (s0 ? 1u : 0u) + (s1 ? 1u : 0u);
+        z[c] = s0 ? l2.x : z[c];
+        z[c + 1] = s1 ? l2.y : z[c + 1];
       }
-      // Z -> bf16 hi/lo, row rowl, columns 16g .. 16g+15 = 16-byte chunks 2g, 2g+1
+      // Z -> bf16 hi/lo, row rowl, columns 32h .. 32h+31 = 16-byte chunks 4h .. 4h+3
       uint8_t* zhi = stg;
       uint8_t* zlo = stg + Z_BYTES / 2;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < 4; ++c) {
         uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float z0 = z[8 * c + 2 * e], z1 = z[8 * c + 2 * e + 1];
-          const __nv_bfloat162 hi = __floats2bfloat162_rn(z0, z1);
+        for (int e2 = 0; e2 < 4; ++e2) {
+          const float2 zz = make_float2(z[8 * c + 2 * e2], z[8 * c + 2 * e2 + 1]);
+          const __nv_bfloat162 hi = __floats2bfloat162_rn(zz.x, zz.y);
           const float2 hf = __bfloat1622float2(hi);
-          const __nv_bfloat162 lo = __floats2bfloat162_rn(z0 - hf.x, z1 - hf.y);
-          hw[e] = *reinterpret_cast<const uint32_t*>(&hi);
-          lw[e] = *reinterpret_cast<const uint32_t*>(&lo);
+          const float2 lf = __ffma2_rn(hf, make_float2(-1.f, -1.f), zz);  // z - hi, exact
+          const __nv_bfloat162 lo = __floats2bfloat162_rn(lf.x, lf.y);
+          hw[e2] = *reinterpret_cast<const uint32_t*>(&hi);
+          lw[e2] = *reinterpret_cast<const uint32_t*>(&lo);
         }
-        const int off = rowl * 128 + ((((2 * g + c) ^ (rowl & 7)) & 7) << 4);
+        const int off = rowl * 128 + ((((4 * h + c) ^ (rowl & 7)) & 7) << 4);
         *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_ZFULL + s]);
-      if (ctl == nct - 1 && g == 0) {
+      if (ctl == nct - 1 && h == 0) {
         // drain Y1 of this row tile
         if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {
           fail(a, &abort_flag);
@@ -332,12 +356,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // drain Y2: each warp takes the column tiles ctl = g, g + 4, ...; lane quarter q holds
     // accumulator rows 32q .. 32q+31 (rows 0..63: Z_hi part, 64..127: Z_lo part)
     if (ntiles > 0 && !abort_flag) {
-      if (!mbar_wait(&bar[B_YFIN], 0)) {
+      // the Y2 products are complete (YFIN) and so are the Y1 products (Y1DRAIN): only then
+      // may the stages be reused as scratch
+      if (!mbar_wait(&bar[B_YFIN], 0) || !mbar_wait(&bar[B_Y1DRAIN], 0)) {
         fail(a, &abort_flag);
       } else {
         tc_fence_after();
         float* scratch = reinterpret_cast<float*>(sm + OFF_STAGE);  // [nct][128][8], stages are idle now
-        for (int ctl = g; ctl < nct; ctl += EPI_WARPS / 4) {
+        for (int ctl = gq; ctl < nct; ctl += EPI_WARPS / 4) {
           uint32_t yv[16];
           tmem_ld16(tmem + lane_base + TM_Y2 + ctl * 16, yv);
           tmem_wait_ld();
@@ -350,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
     if (ntiles > 0 && !abort_flag) {
       const float* scratch = reinterpret_cast<const float*>(sm + OFF_STAGE);
-      const int et = tid - 96;
+      const int et = tid - 128;
       for (int e = et; e < nct * 64; e += EPI_THREADS) {
         const int ctl = e / 64, jl = e % 64;
         const int col = (ct0 + ctl) * BN + jl;
@@ -369,11 +395,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       nz += __shfl_xor_sync(0xffffffffu, nz, o);
     }
     if (lane == 0) {
-      red_res[warp - 3] = rd;
-      red_nnz[warp - 3] = nz;
+      red_res[warp - 4] = rd;
+      red_nnz[warp - 4] = nz;
     }
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
-    if (tid == 96) {
+    if (tid == 128) {
       double tr = 0.0;
       unsigned long long tz = 0;
       for (int w = 0; w < EPI_WARPS; ++w) {
