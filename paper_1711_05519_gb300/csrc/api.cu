@@ -224,16 +224,6 @@ int run_small(rpca_ctx* c, const SmallArgs& a) {
   return RPCA_OK;
 }
 
-// Operand images for the tensor-core pass from the pass-precision copies of width R.
-int pack_images(rpca_ctx* c, int R) {
-  if (!use_tc(c, R)) return RPCA_OK;
-  prof_mark(c, false, true);
-  CK(launch_pack_tc_images(static_cast<const float*>(c->Wc), static_cast<const float*>(c->Vc),
-                           static_cast<const float*>(c->Utc), static_cast<const float*>(c->Vtc), (int)c->m, (int)c->n, R,
-                           c->wop, c->vop, c->vtop, c->utop, c->st, c->stream));
-  prof_mark(c, false, false);
-  return RPCA_OK;
-}
 
 // A x B CTA grid of the tensor-core pass: every CTA gets at least one 128-row and one
 // 64-column tile and at most 20 column tiles (tensor-memory budget); minimises the
@@ -312,6 +302,12 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.stats = c->stats;
   a.init_tol = c->p.init_tol;
   a.seed = 0x243f6a8885a308d3ull;
+  a.wop = c->wop;
+  a.vop = c->vop;
+  a.vtop = c->vtop;
+  a.utop = c->utop;
+  a.img_init = use_tc(c, c->Rb) ? 1 : 0;
+  a.img_iter = use_tc(c, c->Rr) ? 1 : 0;
   return a;
 }
 
@@ -513,7 +509,6 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   // D - S_{-1} (the pass with L = 0 and zeta_{-1} keeps exactly D_ij where |D_ij| <= zeta).
   SmallArgs ra = small_args(c, SM_RAND, c->Rb);
   if ((st = run_small(c, ra))) return st;
-  if ((st = pack_images(c, c->Rb))) return st;
   for (int phase = 0; phase < 2; ++phase) {
     bool conv = false;
     for (int q = 0; q < c->p.init_max_passes && !conv; ++q) {
@@ -527,8 +522,6 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       prof_collect(c, -1);
       if (flag_status(c)) return flag_status(c);
       conv = flag_conv(c) != 0;
-      // images for the next pass: init width, or the iteration width once phase B is done
-      if ((st = pack_images(c, (conv && phase == 1) ? c->Rr : c->Rb))) return st;
     }
   }
   c->ready = true;
@@ -563,7 +556,6 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     for (int i = 0; i < chunk; ++i) {
       if ((st = run_pass(c, c->Rr))) return st;
       if ((st = run_small(c, small_args(c, SM_UPDATE, c->Rr)))) return st;
-      if ((st = pack_images(c, c->Rr))) return st;
     }
     launched += chunk;
     if ((st = read_flags(c))) return st;

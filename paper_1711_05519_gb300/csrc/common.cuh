@@ -94,11 +94,6 @@ struct TcPassArgs {
 bool tc_pass_supported(int R);
 size_t tc_pass_smem();
 cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, cudaStream_t s);
-// Rewrites the operand images from the FP32 pass copies W, V, U~, V~ (width R <= 8).
-cudaError_t launch_pack_tc_images(const float* Wc, const float* Vc, const float* Utc, const float* Vtc, int m, int n,
-                                  int R, uint8_t* wop, uint8_t* vop, uint8_t* vtop, uint8_t* utop, const DevState* st,
-                                  cudaStream_t s);
-
 // Sparse extraction (three kernels): per-row counts, exclusive scan, ordered write.
 struct ExtractArgs {
   const void* D;
@@ -150,6 +145,15 @@ struct SmallArgs {
   unsigned long long seed;
   int rr_first;       // RR: first pass of a phase (no convergence test)
   int rr_force;       // RR: accept this step as converged (pass cap reached)
+  // Operand images of the tensor-core pass (tc_images.cuh), written with the copies when the
+  // pass that reads them is the tensor-core one: img_init for the width-Rc copies of the
+  // initialisation, img_iter for the width-Rit copies of the iteration.
+  uint8_t* wop;
+  uint8_t* vop;
+  uint8_t* vtop;
+  uint8_t* utop;
+  int img_init;
+  int img_iter;
 };
 cudaError_t launch_small(const SmallArgs& a, int grid, cudaStream_t s);
 int small_grid_size(int device);

@@ -32,6 +32,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tc_images.cuh"
 #include "tc_util.cuh"
 
 namespace rpca {
@@ -40,13 +41,13 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BN = 64;
+constexpr int BM = img::BM, BN = img::BN;
 constexpr int NSTAGE = 4;
 constexpr int D_BYTES = BM * BN * 4;          // 32 KB
-constexpr int VOP_BYTES = BN * 32 * 4;        // 8 KB  [64 x 32] tf32
-constexpr int VTOP_BYTES = 16 * 64 * 2;       // 2 KB  [16 x 64] bf16
-constexpr int UTOP_BYTES = 2 * 16 * 64 * 2;   // 4 KB  2 x [16 x 64] bf16
-constexpr int WOP_BYTES = BM * 32 * 4;        // 16 KB [128 x 32] tf32
+constexpr int VOP_BYTES = img::VOP_BYTES;     // 8 KB  [64 x 32] tf32
+constexpr int VTOP_BYTES = img::VTOP_BYTES;   // 2 KB  [16 x 64] bf16
+constexpr int UTOP_BYTES = img::UTOP_BYTES;   // 4 KB  2 x [16 x 64] bf16
+constexpr int WOP_BYTES = img::WOP_BYTES;     // 16 KB [128 x 32] tf32
 constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES + UTOP_BYTES;  // 46 KB
 constexpr int Z_BYTES = 2 * BM * BN * 2;      // hi + lo, 32 KB, in place of the D tile
 constexpr int OFF_STAGE = 0;
@@ -421,84 +422,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
 bool tc_pass_supported(int R) { return R <= 8; }
 
 size_t tc_pass_smem() { return SMEM_BYTES; }
-
-namespace {
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ int sw128(int row, int byte_in_row) {
-  return row * 128 + ((((byte_in_row >> 4) ^ (row & 7)) & 7) << 4) + (byte_in_row & 15);
-}
-
-// One thread per row of W / U~ (i < m) and per row of V / V~ (j < n).
-__global__ void pack_tc_images(const float* __restrict__ Wc, const float* __restrict__ Vc,
-                               const float* __restrict__ Utc, const float* __restrict__ Vtc, int m, int n, int R,
-                               uint8_t* __restrict__ wop, uint8_t* __restrict__ vop, uint8_t* __restrict__ vtop,
-                               uint8_t* __restrict__ utop, const DevState* st) {
-  if (st->done) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < m) {
-    const int i = idx, rt = i / BM, il = i % BM;
-    float hi[8], lo[8];
-    __nv_bfloat16 uh[8], ul[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float w = k < R ? Wc[(size_t)i * R + k] : 0.f;
-      hi[k] = tf32_rna(w);
-      lo[k] = w - hi[k];
-      const float u = k < R ? Utc[(size_t)i * R + k] : 0.f;
-      uh[k] = __float2bfloat16_rn(u);
-      ul[k] = __float2bfloat16_rn(u - __bfloat162float(uh[k]));
-    }
-    float* wt = reinterpret_cast<float*>(wop + (size_t)rt * WOP_BYTES);
-#pragma unroll
-    for (int kk = 0; kk < 32; ++kk) {
-      const float v = kk < 8 ? hi[kk] : kk < 16 ? hi[kk - 8] : kk < 24 ? lo[kk - 16] : 0.f;
-      wt[sw128(il, 4 * kk) >> 2] = v;
-    }
-    __nv_bfloat16* ut = reinterpret_cast<__nv_bfloat16*>(utop + (size_t)rt * UTOP_BYTES);
-    const int sub = il / 64, kl = il % 64;
-#pragma unroll
-    for (int nn = 0; nn < 16; ++nn) ut[(sub * 2048 + sw128(nn, 2 * kl)) >> 1] = nn < 8 ? uh[nn] : ul[nn - 8];
-  }
-  if (idx < n) {
-    const int j = idx, ct = j / BN, jl = j % BN;
-    float hi[8], lo[8];
-    __nv_bfloat16 vh[8], vl[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float v = k < R ? Vc[(size_t)j * R + k] : 0.f;
-      hi[k] = tf32_rna(v);
-      lo[k] = v - hi[k];
-      const float u = k < R ? Vtc[(size_t)j * R + k] : 0.f;
-      vh[k] = __float2bfloat16_rn(u);
-      vl[k] = __float2bfloat16_rn(u - __bfloat162float(vh[k]));
-    }
-    float* vt = reinterpret_cast<float*>(vop + (size_t)ct * VOP_BYTES);
-#pragma unroll
-    for (int kk = 0; kk < 32; ++kk) {
-      const float v = kk < 8 ? hi[kk] : kk < 16 ? lo[kk - 8] : kk < 24 ? hi[kk - 16] : 0.f;
-      vt[sw128(jl, 4 * kk) >> 2] = v;
-    }
-    __nv_bfloat16* tt = reinterpret_cast<__nv_bfloat16*>(vtop + (size_t)ct * VTOP_BYTES);
-#pragma unroll
-    for (int nn = 0; nn < 16; ++nn) tt[sw128(nn, 2 * jl) >> 1] = nn < 8 ? vh[nn] : vl[nn - 8];
-  }
-}
-
-}  // namespace
-
-cudaError_t launch_pack_tc_images(const float* Wc, const float* Vc, const float* Utc, const float* Vtc, int m, int n,
-                                  int R, uint8_t* wop, uint8_t* vop, uint8_t* vtop, uint8_t* utop, const DevState* st,
-                                  cudaStream_t s) {
-  const int rows = m > n ? m : n;
-  pack_tc_images<<<(rows + 255) / 256, 256, 0, s>>>(Wc, Vc, Utc, Vtc, m, n, R, wop, vop, vtop, utop, st);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, cudaStream_t s) {
   static bool attr = false;

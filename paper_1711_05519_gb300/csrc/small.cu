@@ -28,6 +28,8 @@
 //               top-r SVD of D - S_{-1}): Rayleigh-Ritz B = U~^T (Z V~), SVD(B), the Ritz
 //               residuals, and the next bases orth(Z V~), orth(Z^T U~) by CholeskyQR2.
 //   SM_RAND   : random orthonormal starting bases for SM_RR.
+// Where the next pass is the tensor-core one, the step that writes the pass copies also
+// writes that pass's operand images (tc_images.cuh) for the rows it owns.
 //
 // The SVD is a one-sided Jacobi run by one warp with a column per lane, in single
 // precision; in FP64 mode V is then re-orthonormalised in double and double-precision
@@ -37,6 +39,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "tc_images.cuh"
 
 namespace rpca {
 
@@ -555,6 +558,22 @@ __device__ __forceinline__ void reduce_row(const T* __restrict__ Pp, int nsl, si
     for (int j = 0; j < WM; ++j) y[j] += (j < w) ? p[(size_t)q * stride + j] : T(0);
 }
 
+// Row i of the tensor-core operand images: side 0 gives rows of W (= f) and U~ (= q), side 1
+// rows of V (= f) and V~ (= q); ranks up to 8.
+template <typename T, int WM>
+__device__ __forceinline__ void write_images(const SmallArgs& a, int side, int i, const T (&f)[WM], const T (&q)[WM]) {
+  float fv[8], qv[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    fv[j] = j < WM ? (float)f[j < WM ? j : 0] : 0.f;
+    qv[j] = j < WM ? (float)q[j < WM ? j : 0] : 0.f;
+  }
+  if (side == 0)
+    img::write_row_images(i, fv, qv, a.wop, a.utop);
+  else
+    img::write_col_images(i, fv, qv, a.vop, a.vtop);
+}
+
 // ---------------------------------------------------------------------------------------
 // Trim of the factors held (Algorithm 2) and the Gram matrices of the trimmed factors
 // (slots 3, 4).  The trimmed rows go to U~, V~ (orthonormalised by finish_bases).
@@ -623,6 +642,7 @@ __device__ void finish_bases(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       store_copy<T, WM>(d0, i, Rc, f);
       store_copy<T, WM>(d1, i, Rc, q);
+      if (sizeof(T) == 4 && WM == 8 && a.img_iter) write_images<T, WM>(a, side, i, f, q);
     }
   }
 }
@@ -893,6 +913,7 @@ __device__ void orth_second_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>&
       zero_row<T, WM>(z);
       store_copy<T, WM>(d0, i, Rc, q);
       store_copy<T, WM>(d1, i, Rc, z);
+      if (sizeof(T) == 4 && WM == 8 && a.img_init) write_images<T, WM>(a, side, i, z, q);
     }
   }
 }
