@@ -239,55 +239,78 @@ __device__ void reduce_slots(const void* part, int slot0, int ns, int P, T* G, S
   }
 }
 
-// R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix, by one
-// warp in the working precision.  G is scaled to unit diagonal first, G^ = D^-1/2 G D^-1/2;
-// a pivot of G^ at or below 1e-6 (float) or 1e-14 (double), a direction lost to rounding,
-// gives a zero row of R and a zero column of T.  Then R = R^ D^1/2 and T = D^-1/2 R^-1,
-// where column j of R^-1 is (e_j - sum_{k<j} R^-1 e_k R^_kj) / R^_jj.
-template <typename T>
+// R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix (w <= WM),
+// by one warp in the working precision, in registers: lane l holds column l.  G is scaled to
+// unit diagonal first, G^ = D^-1/2 G D^-1/2; a pivot of G^ at or below 1e-6 (float) or 1e-14
+// (double), a direction lost to rounding, gives a zero row of R and a zero column of T.  Then
+// R = R^ D^1/2 and T = D^-1/2 R^-1, column l of R^-1 by back substitution in lane l.
+template <typename T, int WM>
 __device__ void factor_warp(const T* G, int w, T* R, T* Tm) {
   const int l = threadIdx.x & 31;
   const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
   const T dl = (l < w) ? sqrt(fmax(G[l * w + l], T(0))) : T(0);
   const T il = dl > T(0) ? T(1) / dl : T(0);
-  for (int j = 0; j < w; ++j) {
-    const T ij = __shfl_sync(FULL, il, j);
-    if (l < w) R[j * w + l] = (l >= j) ? G[j * w + l] * (ij * il) : T(0);
+  T a[WM];  // column l of the working matrix
+#pragma unroll
+  for (int k = 0; k < WM; ++k) {
+    const T ik = __shfl_sync(FULL, il, k);
+    a[k] = (l < w && k < w) ? G[k * w + l] * (ik * il) : T(0);
   }
-  __syncwarp();
-  for (int j = 0; j < w; ++j) {
-    const T d = R[j * w + j];
-    const bool good = d > tiny;
-    const T rjj = good ? sqrt(d) : T(0);
-    const T inv = good ? T(1) / rjj : T(0);
-    __syncwarp();
-    if (l >= j && l < w) R[j * w + l] = good ? ((l == j) ? rjj : R[j * w + l] * inv) : T(0);
-    __syncwarp();
-    if (l > j && l < w)
-      for (int k = j + 1; k <= l; ++k) R[k * w + l] = fma(-R[j * w + k], R[j * w + l], R[k * w + l]);
-    __syncwarp();
-  }
-  const T rinv = (l < w && R[l * w + l] != T(0)) ? T(1) / R[l * w + l] : T(0);
-  for (int j = 0; j < w; ++j) {
-    const T rj = __shfl_sync(FULL, rinv, j);
-    if (l < w) {
-      T s = (l == j) ? T(1) : T(0);
-      for (int k = l; k < j; ++k) s = fma(-Tm[l * w + k], R[k * w + j], s);
-      Tm[l * w + j] = (j >= l) ? s * rj : T(0);
+  // right-looking Cholesky: step j fixes row j of R^ (a[j] of every lane becomes R^_jl)
+#pragma unroll
+  for (int j = 0; j < WM; ++j) {
+    if (j < w) {
+      const T d = __shfl_sync(FULL, a[j], j);
+      const bool good = d > tiny;
+      const T rjj = good ? sqrt(d) : T(0);
+      const T inv = good ? T(1) / rjj : T(0);
+      const T rjl = (l > j) ? a[j] * inv : ((l == j) ? rjj : T(0));
+      a[j] = rjl;
+#pragma unroll
+      for (int k = j + 1; k < WM; ++k) {
+        const T rjk = __shfl_sync(FULL, rjl, k);
+        a[k] = fma(-rjk, rjl, a[k]);
+      }
     }
   }
+  // R^ to shared memory (for the back substitutions), rows k <= l of column l
+#pragma unroll
+  for (int k = 0; k < WM; ++k)
+    if (l < w && k < w) R[k * w + l] = (k <= l) ? a[k] : T(0);
   __syncwarp();
-  for (int j = 0; j < w; ++j)
-    if (l < w) {
-      Tm[l * w + j] *= il;  // row l of T scaled by 1 / d_l
-      R[j * w + l] *= dl;   // column l of R scaled by d_l
+  // 1 / R^_ii from lane i
+  T rd = T(0);
+  if (l < w) {
+    const T dii = R[l * w + l];
+    rd = dii != T(0) ? T(1) / dii : T(0);
+  }
+  // column l of R^-1: t_i = (delta_il - sum_{k=i+1}^{l} R^_ik t_k) / R^_ii for i = l .. 0
+  T t[WM];
+#pragma unroll
+  for (int i = WM - 1; i >= 0; --i) {
+    const T ri = __shfl_sync(FULL, rd, i);
+    T sacc = (i == l) ? T(1) : T(0);
+#pragma unroll
+    for (int k = i + 1; k < WM; ++k)
+      if (k <= l && k < w) sacc = fma(-R[i * w + k], t[k], sacc);
+    t[i] = (i <= l && i < w) ? sacc * ri : T(0);
+  }
+  __syncwarp();
+  // T = D^-1/2 R^-1 (row i scaled by 1 / d_i), R = R^ D^1/2 (column l scaled by d_l)
+#pragma unroll
+  for (int i = 0; i < WM; ++i) {
+    const T ii = __shfl_sync(FULL, il, i);
+    if (l < w && i < w) {
+      Tm[i * w + l] = t[i] * ii;
+      R[i * w + l] = (i <= l) ? a[i] * dl : T(0);
     }
+  }
   __syncwarp();
 }
 
 template <typename T, int WM>
 __device__ __forceinline__ void factor_one(const T* G, int w, int s, Smem<T, WM>& sh) {
-  factor_warp<T>(G, w, sh.Rf[s], sh.Tf[s]);
+  factor_warp<T, WM>(G, w, sh.Rf[s], sh.Tf[s]);
 }
 
 // Both factors at once: warp 0 factors G[ga] into Rf[0]/Tf[0], warp 1 G[gb] into
@@ -1097,40 +1120,57 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   orth_second_pass<T, WM>(a, w, 3, sh);
 }
 
-template <typename T, int WM>
+// One kernel per mode: a launch then carries only the code of its own mode, which keeps its
+// instruction footprint small (the serial steps run once per launch, so they mostly execute
+// from a cold instruction cache).
+template <typename T, int WM, int MODE>
 __global__ void __launch_bounds__(ST, 1) small_kernel(SmallArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T, WM>& sh = *reinterpret_cast<Smem<T, WM>*>(smem_raw);
-  if (a.mode == SM_UPDATE || a.mode == SM_RR) {
+  if (MODE == SM_UPDATE || MODE == SM_RR) {
     if (a.st->done) return;
   }
-  switch (a.mode) {
-    case SM_UPDATE:
-      mode_update<T, WM>(a, sh);
-      break;
-    case SM_PREPARE:
-      mode_prepare<T, WM>(a, sh);
-      break;
-    case SM_RR:
-      mode_rr<T, WM>(a, sh);
-      break;
-    case SM_RAND:
-      mode_rand<T, WM>(a, sh);
-      break;
-  }
+  if (MODE == SM_UPDATE) mode_update<T, WM>(a, sh);
+  if (MODE == SM_PREPARE) mode_prepare<T, WM>(a, sh);
+  if (MODE == SM_RR) mode_rr<T, WM>(a, sh);
+  if (MODE == SM_RAND) mode_rand<T, WM>(a, sh);
+}
+
+template <typename T, int WM, int MODE>
+void set_smem_mode() {
+  cudaFuncSetAttribute(small_kernel<T, WM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(Smem<T, WM>));
 }
 
 template <typename T, int WM>
 void set_smem() {
-  cudaFuncSetAttribute(small_kernel<T, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<T, WM>));
+  set_smem_mode<T, WM, SM_UPDATE>();
+  set_smem_mode<T, WM, SM_PREPARE>();
+  set_smem_mode<T, WM, SM_RR>();
+  set_smem_mode<T, WM, SM_RAND>();
+}
+
+template <typename T, int WM, int MODE>
+cudaError_t launch_mode(const SmallArgs& a, int grid, cudaStream_t s) {
+  SmallArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel((const void*)small_kernel<T, WM, MODE>, dim3(grid), dim3(ST), args,
+                                     sizeof(Smem<T, WM>), s);
 }
 
 template <typename T, int WM>
 cudaError_t launch_one(const SmallArgs& a, int grid, cudaStream_t s) {
-  SmallArgs copy = a;
-  void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void*)small_kernel<T, WM>, dim3(grid), dim3(ST), args,
-                                     sizeof(Smem<T, WM>), s);
+  switch (a.mode) {
+    case SM_UPDATE:
+      return launch_mode<T, WM, SM_UPDATE>(a, grid, s);
+    case SM_PREPARE:
+      return launch_mode<T, WM, SM_PREPARE>(a, grid, s);
+    case SM_RR:
+      return launch_mode<T, WM, SM_RR>(a, grid, s);
+    case SM_RAND:
+      return launch_mode<T, WM, SM_RAND>(a, grid, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
