@@ -125,7 +125,7 @@ __device__ __forceinline__ T* slot_ptr(void* part, int slot, int block) {
 
 // Sums over the block, the same fixed order in every block; the result in all threads.
 template <typename S>
-__device__ double block_sum_d(double v, S& sh) {
+__device__ __noinline__ double block_sum_d(double v, S& sh) {
   const int t = threadIdx.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -144,7 +144,7 @@ __device__ double block_sum_d(double v, S& sh) {
 }
 
 template <typename S>
-__device__ unsigned long long block_sum_u64(unsigned long long v, S& sh) {
+__device__ __noinline__ unsigned long long block_sum_u64(unsigned long long v, S& sh) {
   const int t = threadIdx.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -183,7 +183,7 @@ __device__ __forceinline__ T tree_sum(T (&v)[K]) {
 // order (a tree is shorter than a chain).  sh.red must be written and synchronised before
 // the call.
 template <typename S>
-__device__ void tree_combine(int cnt, int nparts, S& sh) {
+__device__ __noinline__ void tree_combine(int cnt, int nparts, S& sh) {
   const int t = threadIdx.x, q = t / cnt, j = t % cnt;
   int h = 1;
   while (h < nparts) h <<= 1;
@@ -195,7 +195,7 @@ __device__ void tree_combine(int cnt, int nparts, S& sh) {
 
 // Combines the per-thread shares of a P-entry Gram matrix into this block's partial.
 template <typename T, typename S>
-__device__ void gram_store(T acc, int P, void* part, int slot, S& sh) {
+__device__ __noinline__ void gram_store(T acc, int P, void* part, int slot, S& sh) {
   const int t = threadIdx.x;
   sh.red[t] = acc;
   __syncthreads();
@@ -207,7 +207,7 @@ __device__ void gram_store(T acc, int P, void* part, int slot, S& sh) {
 // G + s * GSLOT <- sum over blocks of slot (slot0 + s), entries 0..P-1, for s < ns.  The
 // summation order depends only on the grid size, so every block gets the same bits.
 template <typename T, typename S>
-__device__ void reduce_slots(const void* part, int slot0, int ns, int P, T* G, S& sh) {
+__device__ __noinline__ void reduce_slots(const void* part, int slot0, int ns, int P, T* G, S& sh) {
   const int t = threadIdx.x, nb = gridDim.x, total = ns * P;
   const T* pb = static_cast<const T*>(part);
   for (int j0 = 0; j0 < total; j0 += ST) {
@@ -245,7 +245,7 @@ __device__ void reduce_slots(const void* part, int slot0, int ns, int P, T* G, S
 // (double), a direction lost to rounding, gives a zero row of R and a zero column of T.  Then
 // R = R^ D^1/2 and T = D^-1/2 R^-1, column l of R^-1 by back substitution in lane l.
 template <typename T, int WM>
-__device__ void factor_warp(const T* G, int w, T* R, T* Tm) {
+__device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm) {
   const int l = threadIdx.x & 31;
   const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
   const T dl = (l < w) ? sqrt(fmax(G[l * w + l], T(0))) : T(0);
