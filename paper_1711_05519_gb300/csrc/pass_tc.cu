@@ -189,8 +189,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // ------------------------------------------------------------------ L MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idL = instr_desc(128, 64, 2, 2, false, false);
-    for (int t = 0; t < ntiles && !abort_flag; ++t) {
-      const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, wb = rtl & 1;
+    const uint64_t dw0 = smem_desc(base + OFF_W, 16, 1024);
+    const uint64_t dv0 = smem_desc(base + OFF_STAGE + D_BYTES, 16, 1024);
+    int rtl = 0, ctl = 0;
+    for (int t = 0; t < ntiles && !abort_flag; ++t, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
+      const int s = t % NSTAGE, lb = t & 1, wb = rtl & 1;
       bool ok = true;
       if (ctl == 0) ok = ok && mbar_wait(&bar[B_WFULL + wb], (rtl >> 1) & 1);
       ok = ok && mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1);
@@ -200,8 +203,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         break;
       }
       tc_fence_after();
-      const uint64_t dw = smem_desc(base + OFF_W + wb * WOP_BYTES, 16, 1024);
-      const uint64_t dv = smem_desc(base + OFF_STAGE + s * STAGE_BYTES + D_BYTES, 16, 1024);
+      const uint64_t dw = dw0 + (uint64_t)(wb * (WOP_BYTES >> 4));
+      const uint64_t dv = dv0 + (uint64_t)(s * (STAGE_BYTES >> 4));
 #pragma unroll
       for (int k = 0; k < 3; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);  // 4th k-block is zero
       mma_commit(&bar[B_LFULL + lb]);
@@ -213,8 +216,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // ------------------------------------------------------------------ Y1 MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idY1 = instr_desc(128, 16, 1, 1, false, false);
-    for (int tp = 0; tp < ntiles && !abort_flag; ++tp) {
-      const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE, yb = rtl & 1;
+    const uint64_t dzh0 = smem_desc(base + OFF_STAGE, 16, 1024);
+    const uint64_t dvt0 = smem_desc(base + OFF_STAGE + D_BYTES + VOP_BYTES, 16, 1024);
+    int rtl = 0, ctl = 0;
+    for (int tp = 0; tp < ntiles && !abort_flag; ++tp, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
+      const int s = tp % NSTAGE, yb = rtl & 1;
       bool ok = mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1);
       if (ok && ctl == 0 && rtl >= 2) ok = mbar_wait(&bar[B_Y1EMPTY + yb], ((rtl - 2) >> 1) & 1);
       if (!ok) {
@@ -222,9 +228,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         break;
       }
       tc_fence_after();
-      const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
-      const uint64_t dzh = smem_desc(stg, 16, 1024), dzl = smem_desc(stg + Z_BYTES / 2, 16, 1024);
-      const uint64_t dvt = smem_desc(stg + D_BYTES + VOP_BYTES, 16, 1024);
+      const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
+      const uint64_t dzh = dzh0 + so, dzl = dzh0 + so + (uint64_t)((Z_BYTES / 2) >> 4), dvt = dvt0 + so;
       const uint32_t y1 = tmem + TM_Y1 + yb * 16;
 #pragma unroll
       for (int k = 0; k < 4; ++k) mma_f16(y1, dzh + 2 * k, dvt + 2 * k, idY1, !(ctl == 0 && k == 0));
@@ -239,16 +244,18 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // ------------------------------------------------------------------ Y2 MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idY2 = instr_desc(128, 16, 1, 1, true, false);
-    for (int tp = 0; tp < ntiles && !abort_flag; ++tp) {
-      const int rtl = tp / nct, ctl = tp % nct, s = tp % NSTAGE;
+    const uint64_t dzm0 = smem_desc(base + OFF_STAGE, Z_BYTES / 2, 1024);
+    const uint64_t dut0 = smem_desc(base + OFF_STAGE + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
+    int rtl = 0, ctl = 0;
+    for (int tp = 0; tp < ntiles && !abort_flag; ++tp, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
+      const int s = tp % NSTAGE;
       if (!mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1)) {
         fail(a, &abort_flag);
         break;
       }
       tc_fence_after();
-      const uint32_t stg = base + OFF_STAGE + s * STAGE_BYTES;
-      const uint64_t dzm = smem_desc(stg, Z_BYTES / 2, 1024);
-      const uint64_t dut = smem_desc(stg + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
+      const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
+      const uint64_t dzm = dzm0 + so, dut = dut0 + so;
       const uint32_t y2 = tmem + TM_Y2 + ctl * 16;
 #pragma unroll
       for (int k = 0; k < 8; ++k)
