@@ -301,6 +301,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.st = c->st;
   a.stats = c->stats;
   a.init_tol = c->p.init_tol;
+  a.init_max = c->p.init_max_passes;
   a.seed = 0x243f6a8885a308d3ull;
   a.wop = c->wop;
   a.vop = c->vop;
@@ -507,23 +508,31 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
 
   // Algorithm 3.  Phase A: sigma_1(D) with L = 0 and no threshold; phase B: top-r SVD of
   // D - S_{-1} (the pass with L = 0 and zeta_{-1} keeps exactly D_ij where |D_ij| <= zeta).
+  // The phase and step counters live in DevState; steps are queued in batches and the ones
+  // behind the final convergence return at once (DevState.done), so the host waits once per
+  // batch.  Each phase accepts its step init_max_passes - 1 as converged, so 2 init_max_passes
+  // steps always finish.
   SmallArgs ra = small_args(c, SM_RAND, c->Rb);
   if ((st = run_small(c, ra))) return st;
-  for (int phase = 0; phase < 2; ++phase) {
-    bool conv = false;
-    for (int q = 0; q < c->p.init_max_passes && !conv; ++q) {
+  const int cap = 2 * c->p.init_max_passes;
+  bool conv = false;
+  for (int steps = 0; steps < cap && !conv;) {
+    // each phase takes two steps at least (its first step is never accepted unless it is
+    // the last allowed one), so the first batch has four; later ones one each
+    int batch = (steps == 0) ? 4 : 1;
+    if (batch > cap - steps) batch = cap - steps;
+    for (int i = 0; i < batch; ++i) {
       if ((st = run_pass(c, c->Rb))) return st;
-      SmallArgs a = small_args(c, SM_RR, c->Rb);
-      a.init_phase = phase;
-      a.rr_first = (q == 0);
-      a.rr_force = (q == c->p.init_max_passes - 1);
-      if ((st = run_small(c, a))) return st;
-      if ((st = read_flags(c))) return st;
-      prof_collect(c, -1);
-      if (flag_status(c)) return flag_status(c);
-      conv = flag_conv(c) != 0;
+      if ((st = run_small(c, small_args(c, SM_RR, c->Rb)))) return st;
     }
+    steps += batch;
+    if ((st = read_flags(c))) return st;
+    prof_collect(c, -1);
+    if (flag_status(c)) return flag_status(c);
+    conv = flag_conv(c) != 0;
   }
+  if (!conv) return RPCA_ERR_NOT_CONVERGED;  // not reached: the last step of each phase is accepted
+  CK(cudaMemsetAsync(&c->st->done, 0, sizeof(int), c->stream));
   c->ready = true;
   return RPCA_OK;
 }

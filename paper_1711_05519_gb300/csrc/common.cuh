@@ -28,11 +28,12 @@ struct DevState {
   int k;                 // iteration index of the factors currently held
   int done;              // 1: converged or capped; passes and updates return at once
   int status;            // 0 or an rpca_status code raised on the device
-  int conv;              // init subspace iteration converged
+  int conv;              // initialisation finished (both subspace iterations converged)
   int max_iter;
   int zeta_mode;
   int trim;
-  int pad0;
+  int init_phase;        // initialisation: 0 = sigma_1(D), 1 = top-r SVD of D - S_{-1}
+  int init_step;         // Rayleigh-Ritz steps taken in the current phase
   unsigned bar_count;    // grid barrier
   unsigned bar_gen;
 };
@@ -140,11 +141,9 @@ struct SmallArgs {
   int Rit;                             // width of the copies written for an iteration pass
   DevState* st;
   DevStats* stats;
-  int init_phase;     // RR: 0 = sigma_1(D) (phase A), 1 = top-r of D - S_{-1} (phase B)
   double init_tol;
   unsigned long long seed;
-  int rr_first;       // RR: first pass of a phase (no convergence test)
-  int rr_force;       // RR: accept this step as converged (pass cap reached)
+  int init_max;       // RR: steps per phase at most (the last one is accepted as converged)
   // Operand images of the tensor-core pass (tc_images.cuh), written with the copies when the
   // pass that reads them is the tensor-core one: img_init for the width-Rc copies of the
   // initialisation, img_iter for the width-Rit copies of the iteration.

@@ -981,10 +981,14 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   const T* Vt = static_cast<const T*>(a.Vt);
   T* Y1 = static_cast<T*>(a.Y1);
   T* Y2 = static_cast<T*>(a.Y2);
+  // phase and step of the initialisation live on the device, so the host can queue steps
+  // without waiting for each one (read here, before block 0 updates them at the end)
+  const int phase = st->init_phase, step = st->init_step;
+  const bool first = step == 0, force = step >= a.init_max - 1;
   double res2;
   unsigned long long nnz;
   cta_totals(a, res2, nnz, sh);
-  if (a.init_phase == 0 && a.rr_first && blockIdx.x == 0 && t == 0) st->normD2 = res2;
+  if (phase == 0 && first && blockIdx.x == 0 && t == 0) st->normD2 = res2;
 
   // A: own rows of Y1 = Z V~, Y2 = Z^T U~; partials of B = U~^T Y1 (slot 0), Y1^T Y1
   // (slot 1) and Y2^T Y2 (slot 2)
@@ -1049,7 +1053,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   // Z v_c - sigma_c u_c = Y1 V_B[:, c] - sigma_c u_c and Z^T u_c - sigma_c v_c =
   // Y2 U_B[:, c] - sigma_c v_c need no further pass over D; the sum of their squared
   // norms, each divided by sigma_c^2, decides convergence.
-  const int nr = (a.init_phase == 0) ? 1 : r;
+  const int nr = (phase == 0) ? 1 : r;
   T res = T(0);
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
@@ -1099,19 +1103,26 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   // C: convergence; then either the bases for the next step or (top-r converged) Trim
   reduce_slots(a.part, 5, 1, 1, sh.scal, sh);
   const double crit = sqrt((double)sh.scal[0]);
-  const double tol = (a.init_phase == 0) ? sqrt(a.init_tol) : a.init_tol;
-  const int conv = (a.rr_force || (!a.rr_first && crit <= tol)) ? 1 : 0;
+  const double tol = (phase == 0) ? sqrt(a.init_tol) : a.init_tol;
+  const int conv = (force || (!first && crit <= tol)) ? 1 : 0;
   if (blockIdx.x == 0 && t == 0) {
     if (!(crit == crit)) atomicCAS(&st->status, 0, kErrNumerical);
     st->sigma_prev[0] = crit;
-    st->conv = conv;
-    if (conv && a.init_phase == 0) st->zeta = st->beta_init * (double)sh.sig[0];
-    if (conv && a.init_phase == 1) {
+    if (conv && phase == 0) {
+      st->zeta = st->beta_init * (double)sh.sig[0];
+      st->init_phase = 1;
+      st->init_step = 0;
+    } else if (conv && phase == 1) {
+      // initialisation finished: the steps still queued behind this one return at once
       st->zeta = st->beta * (double)sh.sig[0];
       st->k = 0;
+      st->conv = 1;
+      st->done = 1;
+    } else {
+      st->init_step = step + 1;
     }
   }
-  if (conv && a.init_phase == 1) {
+  if (conv && phase == 1) {
     trim_and_gram<T, WM>(a, sh);
     if (!grid_barrier(st, sh)) return;
     finish_bases<T, WM>(a, sh);
