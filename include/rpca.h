@@ -39,8 +39,26 @@ typedef enum {
 
 typedef enum { RPCA_DTYPE_F64 = 0, RPCA_DTYPE_F32 = 1 } rpca_dtype;
 
-/* Arithmetic of the fused pass.  The O((m+n) r) steps always run in FP64. */
-typedef enum { RPCA_PREC_FP64 = 0, RPCA_PREC_FP32 = 1 } rpca_precision;
+/* Arithmetic of the fused pass.
+ *   FP64, FP32: D and the pass in that precision.
+ *   BF16: the passes read D rounded to bf16 (a copy the context owns, 2 bytes per entry);
+ *     the rest of the pass as in FP32.  The iteration then solves the problem for bf16(D):
+ *     err_k measures against bf16(D), and once zeta_k falls below the rounding of D that
+ *     rounding enters S, so err_k keeps falling while L_k stops improving at the part of the
+ *     rounding the tangent space keeps (relative error of L about 1e-4 at n = 500 and 1e-5
+ *     at n = 10^4 for r = 5).
+ *   BF16_SPLIT: D is held as hi = bf16(D) and lo = bf16(D - hi) (4 bytes per entry); the
+ *     passes read hi alone until err_k < split_switch and hi + lo (D to 2^-17 relative)
+ *     after that, and only a pass that read hi + lo can end the run.
+ * Both pass kinds read the bf16 storage.  The BF16 modes are not part of the method in the
+ * paper (which states no precision): they apply its iteration to a quantised D and then to
+ * D itself.  The sparse output is extracted from D in FP32. */
+typedef enum {
+  RPCA_PREC_FP64 = 0,
+  RPCA_PREC_FP32 = 1,
+  RPCA_PREC_BF16 = 2,
+  RPCA_PREC_BF16_SPLIT = 3
+} rpca_precision;
 
 /* Threshold rule.  PAPER: zeta_{k+1} = beta (sigma_{r+1} + gamma^{k+1} sigma_1) of
  * P_T(D - S_k) (Algorithm 1).  SIMPLE: zeta_{k+1} = beta gamma^{k+1} sigma_1.
@@ -61,10 +79,13 @@ typedef struct {
   double init_tol;   /* residual of the top Ritz triplets that ends a subspace iteration;
                         0 selects 1e-13 (FP64) / 1e-5 (FP32)                             */
   int pass_kind;     /* rpca_pass_kind: kernel of the fused pass                          */
+  double split_switch; /* BF16_SPLIT: err_k level below which the passes read hi + lo; 0
+                          selects 1e-2 (must lie above the bf16 floor of err_k)            */
 } rpca_params;
 
 /* Kernel of the fused pass.  AUTO takes the tensor-core (tcgen05 + TMA) pass where it
- * applies (FP32, compiled rank <= 8, ld a multiple of 4, D 16-byte aligned) and the SIMT
+ * applies (padded rank <= 8; FP32 with ld a multiple of 4 and D 16-byte aligned, or a BF16
+ * mode) and the SIMT
  * pass otherwise; SIMT and TENSOR force one (TENSOR falls back to SIMT where it does not
  * apply). */
 typedef enum { RPCA_PASS_AUTO = 0, RPCA_PASS_SIMT = 1, RPCA_PASS_TENSOR = 2 } rpca_pass_kind;
@@ -94,7 +115,9 @@ void rpca_destroy(rpca_ctx* ctx);
  *   D: device, m x n, row-major with leading dimension ld, element type `dtype`.
  *   The context BORROWS D when dtype matches the precision (FP64/F64, FP32/F32): the
  *   caller keeps D alive and unchanged until rpca_destroy or the next rpca_init.  With
- *   an F64 input and FP32 precision the context keeps its own FP32 copy.
+ *   an F64 input and FP32 precision the context keeps its own FP32 copy.  In the BF16 modes
+ *   the context also keeps bf16 copies of D (hi, and lo for BF16_SPLIT; rows padded to a
+ *   multiple of 8 entries), made here.
  *   r: target rank, 1 <= r <= 16, 2r <= min(m, n).
  * sigma_1(D) and the top-r SVD of D - S_{-1} are computed by block subspace iteration
  * with one fused pass over D per step.  Synchronises the stream once per pass. */

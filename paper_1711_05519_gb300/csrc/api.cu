@@ -47,6 +47,11 @@ struct rpca_ctx {
   const void* D = nullptr;
   void* Down = nullptr;
   int vec = 0;
+  // bf16 storage of D (BF16 modes): hi part, then lo part (split mode), rows of ldb elements
+  int dmode = 0;
+  bool split = false;
+  void* Dhl = nullptr;
+  int64_t ldb = 0;
   // workspace
   // tall-skinny arrays in the working precision (tsize bytes per entry)
   void *U = nullptr, *sig = nullptr, *V = nullptr, *Ut = nullptr, *Vt = nullptr, *Y1 = nullptr, *Y2 = nullptr,
@@ -62,7 +67,7 @@ struct rpca_ctx {
   bool ready = false;
   // tensor-core pass
   bool tc_iter = false, tc_init = false;
-  CUtensorMap dmap;
+  CUtensorMap dmap, dmap_lo;
   int tcA = 0, tcB = 0, TR = 0, TC = 0;
   uint8_t *wop = nullptr, *vop = nullptr, *vtop = nullptr, *utop = nullptr;
   // allocation signature of the current workspace
@@ -89,7 +94,7 @@ void free_workspace(rpca_ctx* c) {
                    &c->Y1,  &c->Y2,   &c->part, &c->Wc,           &c->Vc,
                    &c->Utc,         &c->Vtc,          &c->P1,           &c->P2,           (void**)&c->resP,
                    (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
-                   &c->Down, (void**)&c->wop, (void**)&c->vop, (void**)&c->vtop, (void**)&c->utop};
+                   &c->Down, &c->Dhl, (void**)&c->wop, (void**)&c->vop, (void**)&c->vtop, (void**)&c->utop};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -189,6 +194,14 @@ int run_pass(rpca_ctx* c, int R) {
   a.resP = c->resP;
   a.nnzP = c->nnzP;
   a.vec = c->vec;
+  a.dm = 0;
+  a.Dlo = nullptr;
+  if (c->dmode) {
+    a.D = c->Dhl;
+    a.ld = c->ldb;
+    a.dm = 1;
+    a.Dlo = c->split ? static_cast<const uint8_t*>(c->Dhl) + (size_t)c->m * c->ldb * 2 : nullptr;
+  }
   prof_mark(c, true, true);
   if (use_tc(c, R)) {
     TcPassArgs t;
@@ -209,7 +222,7 @@ int run_pass(rpca_ctx* c, int R) {
     t.P2 = static_cast<float*>(c->P2);
     t.resP = c->resP;
     t.nnzP = c->nnzP;
-    CK(launch_fused_pass_tc(&c->dmap, t, c->stream));
+    CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
   } else {
     CK(launch_fused_pass(c->prec, R, a, c->stream));
   }
@@ -249,7 +262,9 @@ bool tc_partition(int TR, int TC, int nsm, int* A, int* B) {
   return true;
 }
 
-bool encode_dmap(rpca_ctx* c) {
+// Tensor map of an m x n row-major matrix with rows of `ld` elements, in boxes of 128 rows x
+// 128 bytes (32 FP32 or 64 bf16 elements) with the 128-byte swizzle.
+bool encode_map(CUtensorMap* map, const void* base, int64_t m, int64_t n, int64_t ld, bool bf16) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     cudaDriverEntryPointQueryResult q;
@@ -258,12 +273,22 @@ bool encode_dmap(rpca_ctx* c) {
         !enc)
       return false;
   }
-  cuuint64_t gdim[2] = {(cuuint64_t)c->n, (cuuint64_t)c->m};
-  cuuint64_t gstr[1] = {(cuuint64_t)c->ld * 4};
-  cuuint32_t box[2] = {32, 128}, es[2] = {1, 1};
-  return enc(&c->dmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(c->D), gdim, gstr, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const int es_bytes = bf16 ? 2 : 4;
+  cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t gstr[1] = {(cuuint64_t)(ld * es_bytes)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es_bytes), 128}, es[2] = {1, 1};
+  return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+             const_cast<void*>(base), gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// D as the tensor-core pass reads it: FP32 D, or the bf16 hi / lo parts.
+bool encode_dmap(rpca_ctx* c) {
+  if (!c->dmode) return encode_map(&c->dmap, c->D, c->m, c->n, c->ld, false);
+  const size_t part = (size_t)c->m * c->ldb * 2;
+  const void* lo = c->split ? static_cast<const void*>(static_cast<const uint8_t*>(c->Dhl) + part) : c->Dhl;
+  return encode_map(&c->dmap, c->Dhl, c->m, c->n, c->ldb, true) &&
+         encode_map(&c->dmap_lo, lo, c->m, c->n, c->ldb, true);
 }
 
 SmallArgs small_args(rpca_ctx* c, int mode, int R) {
@@ -363,14 +388,16 @@ int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
   *out = nullptr;
   const rpca_params& p = *params;
   if (!(p.beta > 0) || !(p.gamma >= 0 && p.gamma < 1) || !(p.tol >= 0) || p.max_iter < 0 ||
-      (p.precision != RPCA_PREC_FP32 && p.precision != RPCA_PREC_FP64) || p.zeta_mode < 0 || p.zeta_mode > 2 ||
-      p.beta_init < 0 || p.mu_trim < 0 || p.pass_kind < 0 || p.pass_kind > 2)
+      p.precision < RPCA_PREC_FP64 || p.precision > RPCA_PREC_BF16_SPLIT || p.zeta_mode < 0 || p.zeta_mode > 2 ||
+      p.beta_init < 0 || p.mu_trim < 0 || p.pass_kind < 0 || p.pass_kind > 2 || !(p.split_switch >= 0))
     return RPCA_ERR_INVALID_ARG;
   rpca_ctx* c = new (std::nothrow) rpca_ctx();
   if (!c) return RPCA_ERR_CUDA;
   c->p = p;
   if (c->p.init_max_passes <= 0) c->p.init_max_passes = 40;
-  c->prec = (p.precision == RPCA_PREC_FP32) ? PREC_F32 : PREC_F64;
+  c->prec = (p.precision == RPCA_PREC_FP64) ? PREC_F64 : PREC_F32;
+  c->dmode = (p.precision == RPCA_PREC_BF16 || p.precision == RPCA_PREC_BF16_SPLIT) ? 1 : 0;
+  c->split = p.precision == RPCA_PREC_BF16_SPLIT;
   c->tsize = (c->prec == PREC_F32) ? 4 : 8;
   if (c->p.init_tol <= 0) c->p.init_tol = (c->prec == PREC_F32) ? 1e-5 : 1e-13;
   c->stream = static_cast<cudaStream_t>(stream);
@@ -430,16 +457,25 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   }
   c->vec = ((reinterpret_cast<uintptr_t>(c->D) & 15) == 0 && ((c->ld * (int64_t)c->tsize) & 15) == 0) ? 1 : 0;
   c->tc_iter = c->tc_init = false;
-  if (c->prec == PREC_F32 && c->vec && c->p.pass_kind != RPCA_PASS_SIMT) {
+  if (c->prec == PREC_F32 && (c->vec || c->dmode) && c->p.pass_kind != RPCA_PASS_SIMT) {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     c->TR = (int)((m + 127) / 128);
     c->TC = (int)((n + 63) / 64);
-    if (nsm > 0 && tc_partition(c->TR, c->TC, nsm, &c->tcA, &c->tcB) && encode_dmap(c)) {
+    if (nsm > 0 && tc_partition(c->TR, c->TC, nsm, &c->tcA, &c->tcB)) {
       c->tc_iter = tc_pass_supported(c->Rr);
       c->tc_init = tc_pass_supported(c->Rb);
     }
   }
+  if (c->dmode) {
+    c->ldb = (n + 7) & ~7ll;  // 16-byte row stride
+    const size_t part = (size_t)m * c->ldb * 2;
+    if (!c->Dhl) CK(cudaMalloc(&c->Dhl, c->split ? 2 * part : part));
+    CK(launch_convert_f32_to_bf16x2(static_cast<const float*>(c->D), c->ld, c->Dhl,
+                                    c->split ? static_cast<uint8_t*>(c->Dhl) + part : nullptr, c->ldb, (int)m,
+                                    (int)n, c->stream));
+  }
+  if ((c->tc_iter || c->tc_init) && !encode_dmap(c)) c->tc_iter = c->tc_init = false;
 
   const int w = c->b > c->r ? c->b : c->r;
   const int Rmax = c->Rb > c->Rr ? c->Rb : c->Rr;
@@ -504,6 +540,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   h.zeta_mode = c->p.zeta_mode;
   h.trim = c->p.trim;
   h.zeta = INFINITY;
+  h.split_switch = c->split ? (c->p.split_switch > 0 ? c->p.split_switch : 1e-2) : 0.0;
   CK(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
 
   // Algorithm 3.  Phase A: sigma_1(D) with L = 0 and no threshold; phase B: top-r SVD of

@@ -29,6 +29,9 @@ struct DevState {
   int done;              // 1: converged or capped; passes and updates return at once
   int status;            // 0 or an rpca_status code raised on the device
   int conv;              // initialisation finished (both subspace iterations converged)
+  int use_lo;            // bf16 split storage of D: the passes also read the lo part
+  int pad1;
+  double split_switch;   // bf16 split storage: set use_lo once err_k falls below this
   int max_iter;
   int zeta_mode;
   int trim;
@@ -71,6 +74,10 @@ struct PassArgs {
   double* resP;     // per CTA: sum of R_ij^2 over the unthresholded entries
   unsigned long long* nnzP;  // per CTA: |supp(S)|
   int vec;          // 16-byte vector loads of D allowed
+  // dm = 1: D holds bf16(D) (the hi part) and Dlo the lo part (null if none), both with rows
+  // of ld elements, ld a multiple of 8; the pass reads D = hi (+ lo once DevState.use_lo).
+  int dm;
+  const void* Dlo;
 };
 
 // Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
@@ -94,7 +101,9 @@ struct TcPassArgs {
 };
 bool tc_pass_supported(int R);
 size_t tc_pass_smem();
-cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, cudaStream_t s);
+// dm = 0: FP32 D through dmap; dm = 1: bf16 hi (dmap) and lo (dmap_lo) parts of D.
+cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dmap_lo, int dm, const TcPassArgs& p,
+                                 cudaStream_t s);
 // Sparse extraction (three kernels): per-row counts, exclusive scan, ordered write.
 struct ExtractArgs {
   const void* D;
@@ -162,5 +171,8 @@ cudaError_t launch_convert_f64_to_f32(const double* src, long long ld_src, float
                                       cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float* src, long long ld_src, double* dst, int m, int n,
                                       cudaStream_t s);
+// hi = bf16_rn(d), lo = bf16_rn(d - hi) into rows of ld_dst elements; lo may be null.
+cudaError_t launch_convert_f32_to_bf16x2(const float* src, long long ld_src, void* hi, void* lo, long long ld_dst,
+                                         int m, int n, cudaStream_t s);
 
 }  // namespace rpca

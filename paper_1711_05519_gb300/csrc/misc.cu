@@ -1,5 +1,7 @@
 // Small helper kernels: precision conversion of D and the row-offset scan of the sparse
 // extraction.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace rpca {
@@ -23,6 +25,21 @@ __global__ void convert_f32_f64(const float* __restrict__ src, long long ld, dou
        e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / n, j = e % n;
     dst[e] = static_cast<double>(src[i * ld + j]);
+  }
+}
+
+// bf16 split storage of FP32 D: hi = bf16_rn(d), lo = bf16_rn(d - hi) (d - hi is exact in
+// FP32), rows of ld_dst elements; lo may be null.
+__global__ void convert_f32_bf16x2(const float* __restrict__ src, long long ld, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo, long long ld_dst, int m, int n) {
+  const long long total = (long long)m * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    const float d = src[i * ld + j];
+    const __nv_bfloat16 h = __float2bfloat16_rn(d);
+    hi[i * ld_dst + j] = h;
+    if (lo) lo[i * ld_dst + j] = __float2bfloat16_rn(d - __bfloat162float(h));
   }
 }
 
@@ -65,6 +82,13 @@ cudaError_t launch_convert_f64_to_f32(const double* src, long long ld, float* ds
 
 cudaError_t launch_convert_f32_to_f64(const float* src, long long ld, double* dst, int m, int n, cudaStream_t s) {
   convert_f32_f64<<<1024, 256, 0, s>>>(src, ld, dst, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_f32_to_bf16x2(const float* src, long long ld, void* hi, void* lo, long long ld_dst, int m,
+                                         int n, cudaStream_t s) {
+  convert_f32_bf16x2<<<1024, 256, 0, s>>>(src, ld, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo),
+                                          ld_dst, m, n);
   return cudaGetLastError();
 }
 

@@ -104,7 +104,38 @@ __device__ __forceinline__ void load_row_vec(const T* __restrict__ D, long long 
   }
 }
 
-template <typename T, int R>
+// bf16 storage of D: D[i][c .. c+4) = hi (+ lo when use_lo) with zero fill past the matrix
+// edge; rows of ld elements, ld a multiple of 8 and c a multiple of 4 (8-byte loads).
+__device__ __forceinline__ void load_row_bf16(const uint16_t* __restrict__ hi, const uint16_t* __restrict__ lo,
+                                              bool use_lo, long long ld, int m, int n, int i, int c,
+                                              float (&out)[4]) {
+  const long long o = (long long)i * ld + c;
+  if (i < m && c + 4 <= n) {
+    const uint2 h = __ldcs(reinterpret_cast<const uint2*>(hi + o));
+    out[0] = __uint_as_float(h.x << 16);
+    out[1] = __uint_as_float(h.x & 0xffff0000u);
+    out[2] = __uint_as_float(h.y << 16);
+    out[3] = __uint_as_float(h.y & 0xffff0000u);
+    if (use_lo) {
+      const uint2 l = __ldcs(reinterpret_cast<const uint2*>(lo + o));
+      out[0] += __uint_as_float(l.x << 16);
+      out[1] += __uint_as_float(l.x & 0xffff0000u);
+      out[2] += __uint_as_float(l.y << 16);
+      out[3] += __uint_as_float(l.y & 0xffff0000u);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const bool in = i < m && c + e < n;
+      float x = in ? __uint_as_float((uint32_t)hi[o + e] << 16) : 0.f;
+      if (in && use_lo) x += __uint_as_float((uint32_t)lo[o + e] << 16);
+      out[e] = x;
+    }
+  }
+}
+
+// DM = 0: D in the pass precision T; DM = 1 (T = float): bf16 storage of D (PassArgs.dm).
+template <typename T, int R, int DM>
 __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   using C = PassCfg<T, R>;
   using Lay = PassLayout<T, R>;
@@ -143,6 +174,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
 
   const T zeta = static_cast<T>(a.st->zeta);
   const bool vec = a.vec != 0;
+  const bool use_lo = DM == 1 && a.Dlo != nullptr && a.st->use_lo != 0;
   T res = T(0);
   unsigned nnz = 0;
   T* mySlot = sY2 + warp * R * BW;
@@ -160,7 +192,15 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
       const int cl = sc * SCW + lane * VW;  // local column of this lane's first column
       T d[TM][VW];
 #pragma unroll
-      for (int t = 0; t < TM; ++t) load_row_vec<T, VW>(D, a.ld, m, n, row0 + rl0 + t, col0 + cl, vec, d[t]);
+      for (int t = 0; t < TM; ++t) {
+        if constexpr (DM == 1) {
+          static_assert(VW == 4, "bf16 storage: four columns per lane");
+          load_row_bf16(static_cast<const uint16_t*>(a.D), static_cast<const uint16_t*>(a.Dlo), use_lo, a.ld, m,
+                        n, row0 + rl0 + t, col0 + cl, d[t]);
+        } else {
+          load_row_vec<T, VW>(D, a.ld, m, n, row0 + rl0 + t, col0 + cl, vec, d[t]);
+        }
+      }
       T v[VW][R], vt[VW][R], y2[VW][R];
 #pragma unroll
       for (int k = 0; k < R; ++k)
@@ -243,20 +283,29 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   }
 }
 
-template <typename T, int R>
-cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t s) {
+template <typename T, int R, int DM>
+cudaError_t launch_pass_dm(const PassArgs& a, cudaStream_t s) {
   using C = PassCfg<T, R>;
   using Lay = PassLayout<T, R>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<T, R, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Lay::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid((a.n + C::BW - 1) / C::BW, (a.m + C::BH - 1) / C::BH);
-  fused_pass_kernel<T, R><<<grid, Lay::THREADS, Lay::SMEM, s>>>(a);
+  fused_pass_kernel<T, R, DM><<<grid, Lay::THREADS, Lay::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, int R>
+cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.dm == 1) return launch_pass_dm<T, R, 1>(a, s);
+  }
+  if (a.dm != 0) return cudaErrorInvalidValue;
+  return launch_pass_dm<T, R, 0>(a, s);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -104,8 +104,15 @@ __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) 
   *abort_flag = 1;
 }
 
-__global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap, TcArgs a) {
+// DM = 0: D is FP32 (dmap, two 128 x 32 boxes per tile).  DM = 1: D is held as bf16 hi and
+// lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
+// DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
+// 32 KB and Z is written over it in the same layout.
+template <int DM>
+__global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap,
+                                                            const __grid_constant__ CUtensorMap dmap_lo, TcArgs a) {
   if (a.st->done) return;
+  const bool use_lo = DM == 1 && a.st->use_lo != 0;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
@@ -173,9 +180,15 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         break;
       }
       uint8_t* st = sm + OFF_STAGE + s * STAGE_BYTES;
-      mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES);
-      tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
-      tma_load_2d(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s]);
+      if (DM == 0) {
+        mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES);
+        tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
+        tma_load_2d(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s]);
+      } else {
+        mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES - (use_lo ? 0 : D_BYTES / 2));
+        tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
+        if (use_lo) tma_load_2d(st + D_BYTES / 2, &dmap_lo, ct * BN, rt * BM, &bar[B_FULL + s]);
+      }
       bulk_load(st + D_BYTES, a.vop + (size_t)ct * VOP_BYTES, VOP_BYTES, &bar[B_FULL + s]);
       bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
       bulk_load(st + D_BYTES + VOP_BYTES + VTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES,
@@ -287,25 +300,53 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       uint32_t lv[32];
       tmem_ld32(tmem + lane_base + lb * BN + 32 * h, lv);
       uint8_t* stg = sm + OFF_STAGE + s * STAGE_BYTES;
-      const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
       float z[32];
+      if (DM == 0) {
+        const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
-        z[4 * c + 0] = d4.x;
-        z[4 * c + 1] = d4.y;
-        z[4 * c + 2] = d4.z;
-        z[4 * c + 3] = d4.w;
+        for (int c = 0; c < 8; ++c) {
+          const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
+          z[4 * c + 0] = d4.x;
+          z[4 * c + 1] = d4.y;
+          z[4 * c + 2] = d4.z;
+          z[4 * c + 3] = d4.w;
+        }
+      } else {
+        // columns 32h .. 32h+31 of the bf16 row = 16-byte chunks 4h .. 4h+3 (8 values each)
+        const uint8_t* hrow = stg + rowl * 128;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int off = (((4 * h + c) ^ (rowl & 7)) & 7) << 4;
+          const uint4 hv = *reinterpret_cast<const uint4*>(hrow + off);
+          const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            z[8 * c + 2 * e2] = __uint_as_float(hw[e2] << 16);
+            z[8 * c + 2 * e2 + 1] = __uint_as_float(hw[e2] & 0xffff0000u);
+          }
+          if (use_lo) {
+            const uint4 lv4 = *reinterpret_cast<const uint4*>(hrow + D_BYTES / 2 + off);
+            const uint32_t lw[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+              z[8 * c + 2 * e2] += __uint_as_float(lw[e2] << 16);
+              z[8 * c + 2 * e2 + 1] += __uint_as_float(lw[e2] & 0xffff0000u);
+            }
+          }
+        }
       }
       tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
       // both warps of these rows hold their D values before Z overwrites the tile
-      if (lane == 0) mbar_arrive(&bar[B_DREAD + 4 * s + q]);
-      if (!mbar_wait(&bar[B_DREAD + 4 * s + q], (t / NSTAGE) & 1)) {
-        fail(a, &abort_flag);
-        break;
+      // (bf16 D: every warp overwrites exactly the bytes it read, no wait is needed)
+      if (DM == 0) {
+        if (lane == 0) mbar_arrive(&bar[B_DREAD + 4 * s + q]);
+        if (!mbar_wait(&bar[B_DREAD + 4 * s + q], (t / NSTAGE) & 1)) {
+          fail(a, &abort_flag);
+          break;
+        }
       }
       const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
@@ -430,10 +471,13 @@ bool tc_pass_supported(int R) { return R <= 8; }
 
 size_t tc_pass_smem() { return SMEM_BYTES; }
 
-cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, cudaStream_t s) {
+cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dmap_lo, int dm, const TcPassArgs& p,
+                                 cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(fused_pass_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_pass_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -455,7 +499,10 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const TcPassArgs& p, c
   a.P2 = p.P2;
   a.resP = p.resP;
   a.nnzP = p.nnzP;
-  fused_pass_tc<<<p.A * p.B, THREADS, SMEM_BYTES, s>>>(*dmap, a);
+  if (dm == 0)
+    fused_pass_tc<0><<<p.A * p.B, THREADS, SMEM_BYTES, s>>>(*dmap, *dmap, a);
+  else
+    fused_pass_tc<1><<<p.A * p.B, THREADS, SMEM_BYTES, s>>>(*dmap, *dmap_lo, a);
   return cudaGetLastError();
 }
 

@@ -15,7 +15,8 @@
 //
 // Modes:
 //   SM_UPDATE : after a fused pass of Algorithm 1.  err_k (Eq. (11)) from the per-CTA
-//               totals; stop if err_k < tol.  Otherwise
+//               totals; stop if err_k < tol (with bf16 split storage of D, only on a
+//               pass that read hi + lo; the switch to hi + lo is made here too).  Otherwise
 //                 A: Y1 = Z V~, Y2 = Z^T U~ (sums of the pass partials); C = U~^T Y1
 //                 B: W1 = Y1 - U~ C, W2 = Y2 - V~ C^T and their Gram matrices
 //                 C: R1, R2 (Cholesky), M = [[C, R2^T], [R1, 0]] and its SVD, zeta_{k+1}
@@ -582,7 +583,8 @@ __device__ __forceinline__ void reduce_row(const T* __restrict__ Pp, int nsl, si
 }
 
 // Row i of the tensor-core operand images: side 0 gives rows of W (= f) and U~ (= q), side 1
-// rows of V (= f) and V~ (= q); ranks up to 8.
+// rows of V (= f) and V~ (= q); ranks up to 8 (entries 8.. of a wider row are zero: the
+// width-16 steps of the initialisation write the iteration's images when r <= 8).
 template <typename T, int WM>
 __device__ __forceinline__ void write_images(const SmallArgs& a, int side, int i, const T (&f)[WM], const T (&q)[WM]) {
   float fv[8], qv[8];
@@ -665,7 +667,7 @@ __device__ void finish_bases(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       store_copy<T, WM>(d0, i, Rc, f);
       store_copy<T, WM>(d1, i, Rc, q);
-      if (sizeof(T) == 4 && WM == 8 && a.img_iter) write_images<T, WM>(a, side, i, f, q);
+      if (sizeof(T) == 4 && WM >= 8 && a.img_iter) write_images<T, WM>(a, side, i, f, q);
     }
   }
 }
@@ -702,7 +704,11 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     }
     return;
   }
-  if (err < st->tol || k >= st->max_iter) {
+  // bf16 split storage of D: while the passes read only the hi part, err_k measures against
+  // bf16(D) and cannot end the run; the next pass reads hi + lo once err_k is below the switch
+  // level (use_lo is written below, after grid barriers every CTA passes after this read)
+  const bool hi_only = st->split_switch > 0 && !st->use_lo;
+  if ((err < st->tol && !hi_only) || k >= st->max_iter) {
     if (blockIdx.x == 0 && t == 0) st->done = 1;
     return;
   }
@@ -851,6 +857,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     for (int i = 0; i < N; ++i) st->sigma[i] = (double)sh.sig[i];
     a.stats[k].sigma1 = s1;
     a.stats[k].sigma_r1 = sr1;
+    if (hi_only && (err < st->split_switch || err < st->tol)) st->use_lo = 1;
     st->k = k1;
   }
   __syncthreads();
@@ -936,7 +943,7 @@ __device__ void orth_second_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>&
       zero_row<T, WM>(z);
       store_copy<T, WM>(d0, i, Rc, q);
       store_copy<T, WM>(d1, i, Rc, z);
-      if (sizeof(T) == 4 && WM == 8 && a.img_init) write_images<T, WM>(a, side, i, z, q);
+      if (sizeof(T) == 4 && WM >= 8 && a.img_init) write_images<T, WM>(a, side, i, z, q);
     }
   }
 }

@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "rpca.h")
 
 OK, INVALID_ARG, CUDA_ERR, NUMERICAL, CAPACITY, NOT_CONVERGED, TIMEOUT, STATE = range(8)
 DTYPE_F64, DTYPE_F32 = 0, 1
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_split": 3}
 ZETA = {"paper": 0, "simple": 1, "external": 2}
 PASS_KIND = {"auto": 0, "simt": 1, "tensor": 2}
 
@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("init_max_passes", ctypes.c_int),
         ("init_tol", ctypes.c_double),
         ("pass_kind", ctypes.c_int),
+        ("split_switch", ctypes.c_double),
     ]
 
 
@@ -126,7 +127,8 @@ class Solver:
 
     def __init__(self, beta: float, gamma: float, tol: float, precision: str = "fp32", trim: bool = True,
                  zeta_mode: str = "paper", max_iter: int = 100, beta_init: float = 0.0, mu_trim: float = 0.0,
-                 init_max_passes: int = 0, init_tol: float = 0.0, pass_kind: str = "auto", stream=None):
+                 init_max_passes: int = 0, init_tol: float = 0.0, pass_kind: str = "auto",
+                 split_switch: float = 0.0, stream=None):
         L = lib()
         p = Params()
         L.rpca_params_default(ctypes.byref(p))
@@ -136,6 +138,7 @@ class Solver:
         p.precision, p.zeta_mode = PREC[precision], ZETA[zeta_mode]
         p.init_max_passes, p.init_tol = init_max_passes, init_tol
         p.pass_kind = PASS_KIND[pass_kind]
+        p.split_switch = split_switch
         self.params = p
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._ctx = ctypes.c_void_p()

@@ -115,6 +115,19 @@ def test_fp32_config1_matches_oracle():
     assert ok, diff
 
 
+@pytest.mark.parametrize("m,n,r", [(384, 320, 7), (256, 512, 8)])
+def test_fp32_tensor_iteration_after_width16_initialisation(m, n, r):
+    # r = 7, 8: the initialisation block is 16 wide (SIMT pass), the iteration rank 8
+    # (tensor-core pass), so the last initialisation step writes the iteration's operand images
+    inst = synth.planted_instance(m, n, r, 0.08, 1.0, m + n + r)
+    g = _gpu_run(inst, "fp32", 1e-5)
+    assert g["stats"][-1]["err"] < 1e-5
+    ref = _oracle_same_k(g["D"], inst, g["stats"][-1]["k"])
+    assert rel_fro(g["L"], ref["L"]) < 1e-5
+    diff, ok = support_mismatch(g["idx"], g["D"], ref["L"], ref["zeta"], band_abs_rel_D=1e-6)
+    assert ok, diff
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("m,n,r", [(333, 217, 3), (129, 515, 2), (600, 97, 1), (257, 263, 7)])
 def test_ragged_shapes(prec, m, n, r):
