@@ -6,11 +6,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
 #include "../../include/rpca.h"
 #include "common.cuh"
+#include "tc_images.cuh"
 
 namespace rpca {
 cudaError_t launch_pass_f32(int R, const PassArgs& a, cudaStream_t s);
@@ -69,7 +71,11 @@ struct rpca_ctx {
   bool tc_iter = false, tc_init = false;
   CUtensorMap dmap, dmap_lo;
   int tcA = 0, tcB = 0, TR = 0, TC = 0;
-  uint8_t *wop = nullptr, *vop = nullptr, *vtop = nullptr, *utop = nullptr;
+  float* Y2c = nullptr;  // Y2 chunk slots of the tensor-core pass
+  int y2_ch = 0, y2_ct = 0;
+  // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
+  uint8_t *wop[2] = {nullptr, nullptr}, *vop[2] = {nullptr, nullptr}, *vtop[2] = {nullptr, nullptr},
+          *utop[2] = {nullptr, nullptr};
   // allocation signature of the current workspace
   int64_t ws_m = -1, ws_n = -1;
   int ws_r = -1;
@@ -94,7 +100,9 @@ void free_workspace(rpca_ctx* c) {
                    &c->Y1,  &c->Y2,   &c->part, &c->Wc,           &c->Vc,
                    &c->Utc,         &c->Vtc,          &c->P1,           &c->P2,           (void**)&c->resP,
                    (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
-                   &c->Down, &c->Dhl, (void**)&c->wop, (void**)&c->vop, (void**)&c->vtop, (void**)&c->utop};
+                   &c->Down, &c->Dhl, (void**)&c->wop[0], (void**)&c->vop[0], (void**)&c->vtop[0],
+                   (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
+                   (void**)&c->utop[1], (void**)&c->Y2c};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -178,7 +186,8 @@ Grid pass_grid(const rpca_ctx* c, int R) {
   return Grid{gx, gy, gx * gy};
 }
 
-int run_pass(rpca_ctx* c, int R) {
+// One fused pass at compiled rank R: the initialisation's (init) or the iteration's.
+int run_pass(rpca_ctx* c, int R, bool init) {
   PassArgs a;
   a.D = c->D;
   a.ld = c->ld;
@@ -203,7 +212,7 @@ int run_pass(rpca_ctx* c, int R) {
     a.Dlo = c->split ? static_cast<const uint8_t*>(c->Dhl) + (size_t)c->m * c->ldb * 2 : nullptr;
   }
   prof_mark(c, true, true);
-  if (use_tc(c, R)) {
+  if (init ? c->tc_init : c->tc_iter) {
     TcPassArgs t;
     t.m = (int)c->m;
     t.n = (int)c->n;
@@ -212,16 +221,20 @@ int run_pass(rpca_ctx* c, int R) {
     t.B = c->tcB;
     t.TR = c->TR;
     t.TC = c->TC;
-    t.wop = c->wop;
-    t.vop = c->vop;
-    t.vtop = c->vtop;
-    t.utop = c->utop;
+    const int set = init ? 0 : 1;
+    t.wop = c->wop[set];
+    t.vop = c->vop[set];
+    t.vtop = c->vtop[set];
+    t.utop = c->utop[set];
     t.st = c->st;
     t.status = &c->st->status;
     t.P1 = static_cast<float*>(c->P1);
     t.P2 = static_cast<float*>(c->P2);
     t.resP = c->resP;
     t.nnzP = c->nnzP;
+    t.Y2c = c->Y2c;
+    t.ch_max = c->y2_ch;
+    t.ct_max = c->y2_ct;
     CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
   } else {
     CK(launch_fused_pass(c->prec, R, a, c->stream));
@@ -241,14 +254,14 @@ int run_small(rpca_ctx* c, const SmallArgs& a) {
 // A x B CTA grid of the tensor-core pass: every CTA gets at least one 128-row and one
 // 64-column tile and at most 20 column tiles (tensor-memory budget); minimises the
 // largest block of tiles.
-bool tc_partition(int TR, int TC, int nsm, int* A, int* B) {
+bool tc_partition(int TR, int TC, int nsm, int max_ct, int* A, int* B) {
   long best = -1;
   int bA = 0, bB = 0;
   for (int a = 1; a <= TR && a <= nsm; ++a) {
     int b = nsm / a;
     if (b > TC) b = TC;
     if (b < 1) continue;
-    if ((TC + b - 1) / b > 20) continue;
+    if ((TC + b - 1) / b > max_ct) continue;
     const long mx = (long)((TR + a - 1) / a) * ((TC + b - 1) / b);
     if (best < 0 || mx < best || (mx == best && a * b > bA * bB)) {
       best = mx;
@@ -328,12 +341,16 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.init_tol = c->p.init_tol;
   a.init_max = c->p.init_max_passes;
   a.seed = 0x243f6a8885a308d3ull;
-  a.wop = c->wop;
-  a.vop = c->vop;
-  a.vtop = c->vtop;
-  a.utop = c->utop;
-  a.img_init = use_tc(c, c->Rb) ? 1 : 0;
-  a.img_iter = use_tc(c, c->Rr) ? 1 : 0;
+  for (int set = 0; set < 2; ++set) {
+    a.wop[set] = c->wop[set];
+    a.vop[set] = c->vop[set];
+    a.vtop[set] = c->vtop[set];
+    a.utop[set] = c->utop[set];
+  }
+  a.img_rk[0] = tc_image_rank(c->Rb);
+  a.img_rk[1] = tc_image_rank(c->Rr);
+  a.img_init = c->tc_init ? 1 : 0;
+  a.img_iter = c->tc_iter ? 1 : 0;
   return a;
 }
 
@@ -462,9 +479,13 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     c->TR = (int)((m + 127) / 128);
     c->TC = (int)((n + 63) / 64);
-    if (nsm > 0 && tc_partition(c->TR, c->TC, nsm, &c->tcA, &c->tcB)) {
-      c->tc_iter = tc_pass_supported(c->Rr);
-      c->tc_init = tc_pass_supported(c->Rb);
+    const bool it = tc_pass_supported(c->Rr), in = tc_pass_supported(c->Rb);
+    int max_ct = 1 << 30;
+    if (it) max_ct = std::min(max_ct, tc_max_col_tiles(c->Rr));
+    if (in) max_ct = std::min(max_ct, tc_max_col_tiles(c->Rb));
+    if (nsm > 0 && (it || in) && tc_partition(c->TR, c->TC, nsm, max_ct, &c->tcA, &c->tcB)) {
+      c->tc_iter = it;
+      c->tc_init = in;
     }
   }
   if (c->dmode) {
@@ -512,14 +533,23 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   CK(cudaMalloc(&c->P1, p1 * c->tsize));
   CK(cudaMalloc(&c->P2, p2 * c->tsize));
   if (c->TR > 0) {
-    CK(cudaMalloc((void**)&c->wop, (size_t)c->TR * 16384));
-    CK(cudaMalloc((void**)&c->utop, (size_t)c->TR * 4096));
-    CK(cudaMalloc((void**)&c->vop, (size_t)c->TC * 8192));
-    CK(cudaMalloc((void**)&c->vtop, (size_t)c->TC * 2048));
-    CK(cudaMemsetAsync(c->wop, 0, (size_t)c->TR * 16384, c->stream));
-    CK(cudaMemsetAsync(c->utop, 0, (size_t)c->TR * 4096, c->stream));
-    CK(cudaMemsetAsync(c->vop, 0, (size_t)c->TC * 8192, c->stream));
-    CK(cudaMemsetAsync(c->vtop, 0, (size_t)c->TC * 2048, c->stream));
+    if (c->tc_iter || c->tc_init) {
+      const int rpc = (c->TR + c->tcA - 1) / c->tcA;
+      c->y2_ch = (rpc + kTcY2Chunk - 1) / kTcY2Chunk;
+      c->y2_ct = (c->TC + c->tcB - 1) / c->tcB;
+      CK(cudaMalloc((void**)&c->Y2c, (size_t)c->tcA * c->tcB * c->y2_ch * c->y2_ct * 128 * 16 * sizeof(float)));
+    }
+    // zero-filled: rows past m, n are never written and must read as zero
+    for (int set = 0; set < 2; ++set) {
+      CK(cudaMalloc((void**)&c->wop[set], (size_t)c->TR * img::WOP_MAX));
+      CK(cudaMalloc((void**)&c->utop[set], (size_t)c->TR * img::UTOP_MAX));
+      CK(cudaMalloc((void**)&c->vop[set], (size_t)c->TC * img::VOP_MAX));
+      CK(cudaMalloc((void**)&c->vtop[set], (size_t)c->TC * img::VTOP_MAX));
+      CK(cudaMemsetAsync(c->wop[set], 0, (size_t)c->TR * img::WOP_MAX, c->stream));
+      CK(cudaMemsetAsync(c->utop[set], 0, (size_t)c->TR * img::UTOP_MAX, c->stream));
+      CK(cudaMemsetAsync(c->vop[set], 0, (size_t)c->TC * img::VOP_MAX, c->stream));
+      CK(cudaMemsetAsync(c->vtop[set], 0, (size_t)c->TC * img::VTOP_MAX, c->stream));
+    }
   }
   c->ws_m = m;
   c->ws_n = n;
@@ -559,7 +589,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     int batch = (steps == 0) ? 4 : 1;
     if (batch > cap - steps) batch = cap - steps;
     for (int i = 0; i < batch; ++i) {
-      if ((st = run_pass(c, c->Rb))) return st;
+      if ((st = run_pass(c, c->Rb, true))) return st;
       if ((st = run_small(c, small_args(c, SM_RR, c->Rb)))) return st;
     }
     steps += batch;
@@ -600,7 +630,7 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
   while (!done && launched < n_iters) {
     const int chunk = (n_iters - launched) < 8 ? (n_iters - launched) : 8;
     for (int i = 0; i < chunk; ++i) {
-      if ((st = run_pass(c, c->Rr))) return st;
+      if ((st = run_pass(c, c->Rr, false))) return st;
       if ((st = run_small(c, small_args(c, SM_UPDATE, c->Rr)))) return st;
     }
     launched += chunk;

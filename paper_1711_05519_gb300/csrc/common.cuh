@@ -83,23 +83,35 @@ struct PassArgs {
 // Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
 cudaError_t launch_fused_pass(int prec, int R, const PassArgs& a, cudaStream_t s);
 
-// Tensor-core fused pass (FP32 D, compiled rank R <= 8); see pass_tc.cu.
+// Tensor-core fused pass (FP32 or bf16-stored D, compiled rank R <= 16); see pass_tc.cu.
 struct TcPassArgs {
   int m, n, R;
   int A, B;      // CTA grid: A row groups x B column groups
   int TR, TC;    // 128-row and 64-column tile counts
-  const uint8_t* wop;   // [TR] 16 KB images of [W_hi W_hi W_lo 0] (tf32, 128B-swizzled)
-  const uint8_t* vop;   // [TC] 8 KB images of [V_hi V_lo V_hi 0]
-  const uint8_t* vtop;  // [TC] 2 KB images of [V~_hi | V~_lo]^T (bf16)
-  const uint8_t* utop;  // [TR] 4 KB images of [U~_hi | U~_lo]^T (bf16)
+  // operand images (tc_images.cuh) in the layout of tc_image_rank(R): per row tile W and
+  // U~, per column tile V and V~
+  const uint8_t* wop;
+  const uint8_t* vop;
+  const uint8_t* vtop;
+  const uint8_t* utop;
   const DevState* st;
   int* status;
   float* P1;     // [B][m][R]
   float* P2;     // [A][n][R]
   double* resP;  // [A*B]
   unsigned long long* nnzP;
+  // Y2 chunk slots: [A*B][ch_max][ct_max][128][RK] FP32, ch_max >= ceil(row tiles per CTA /
+  // kTcY2Chunk), ct_max >= column tiles per CTA
+  float* Y2c;
+  int ch_max, ct_max;
 };
+// row tiles per Y2 accumulation chunk of the tensor-core pass
+constexpr int kTcY2Chunk = 4;
 bool tc_pass_supported(int R);
+// image layout (8 or 16) of the tensor-core pass for compiled rank R, and the most column
+// tiles one CTA of that pass may own (its Y2 accumulators stay in tensor memory)
+inline int tc_image_rank(int R) { return R <= 8 ? 8 : 16; }
+inline int tc_max_col_tiles(int R) { return R <= 8 ? 20 : 10; }
 size_t tc_pass_smem();
 // dm = 0: FP32 D through dmap; dm = 1: bf16 hi (dmap) and lo (dmap_lo) parts of D.
 cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dmap_lo, int dm, const TcPassArgs& p,
@@ -155,11 +167,13 @@ struct SmallArgs {
   int init_max;       // RR: steps per phase at most (the last one is accepted as converged)
   // Operand images of the tensor-core pass (tc_images.cuh), written with the copies when the
   // pass that reads them is the tensor-core one: img_init for the width-Rc copies of the
-  // initialisation, img_iter for the width-Rit copies of the iteration.
-  uint8_t* wop;
-  uint8_t* vop;
-  uint8_t* vtop;
-  uint8_t* utop;
+  // initialisation (image set 0), img_iter for the width-Rit copies of the iteration (set 1);
+  // img_rk[set] is the image layout (8 or 16) of that pass.
+  uint8_t* wop[2];
+  uint8_t* vop[2];
+  uint8_t* vtop[2];
+  uint8_t* utop[2];
+  int img_rk[2];
   int img_init;
   int img_iter;
 };

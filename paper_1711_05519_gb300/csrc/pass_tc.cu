@@ -1,4 +1,4 @@
-// Tensor-core fused pass (tcgen05 + TMA) for FP32 D and compiled rank R <= 8.
+// Tensor-core fused pass (tcgen05 + TMA) for FP32 or bf16-stored D and compiled rank R <= 16.
 //
 // Same quantities as the SIMT pass (pass_impl.cuh): per entry of D, rebuild L_ij, take
 // R_ij = D_ij - L_ij, the strict threshold S_ij = R_ij if |R_ij| > zeta_k (Eq. (10)),
@@ -11,22 +11,24 @@
 // stay in tensor memory, so each CTA writes one Y1 partial per row (slice b) and one Y2
 // partial per column (slice a).
 //
-// Per tile:
-//   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, 128-byte swizzle) plus the operand
-//                      images of V (tf32 hi/lo), V~ and U~ (bf16 hi/lo) -> stage s (4 stages)
-//   L MMAs (warp 1)  : L = [W_hi W_hi W_lo] [V_hi V_lo V_hi]^T, kind::tf32, M128 N64 K24
-//                      (three-term split product: FP32-level accuracy of the K = r rebuild)
+// Per tile (RK = 8 for R <= 8, RK = 16 for R <= 16: the operand image layout, tc_images.cuh):
+//   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, or one 128 x 64 bf16 box per part,
+//                      128-byte swizzle) plus the operand images of V (tf32 hi/lo), V~ and U~
+//                      (bf16 hi/lo) -> stage s (4 stages for RK = 8, 3 for RK = 16)
+//   L MMAs (warp 1)  : L = W_hi V_hi^T + W_hi V_lo^T + W_lo V_hi^T, kind::tf32, M128 N64,
+//                      3 (RK = 8) or 6 (RK = 16) k-steps of 8 (three-term split product:
+//                      FP32-level accuracy of the K = r rebuild)
 //   epilogue (16 warps, two groups of 8 on alternate tiles): L from TMEM, D from shared
 //                      memory, threshold, residual, support count, Z split into bf16 hi + lo,
 //                      written K-major 128B-swizzled over the D tile it came from (Z_hi over
 //                      the first box, Z_lo over the second), so a stage carries its own Z
-//   Y1 MMAs (warp 2) : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N16 K64 (x2)
-//   Y2 MMAs (warp 3) : Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N16 K128;
+//   Y1 MMAs (warp 2) : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N(2 RK) K64 (x2)
+//   Y2 MMAs (warp 3) : Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N(2 RK) K128;
 //                      the stage is released when both have completed
 // Each product has its own issuing thread: a tcgen05.mma of these small shapes costs about
 // 40 cycles of tensor-pipe time but about 55 cycles of issue time on one thread, and a single
 // issuer would also hold the Y products of tile t behind the TMA arrival of tile t + 1.
-// The column halves of the N16 accumulators (hi and lo parts of V~, U~) and the two M
+// The column halves of the N = 2 RK accumulators (hi and lo parts of V~, U~) and the two M
 // halves of the Y2 accumulator (Z_hi, Z_lo) are added when the accumulators are drained.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -42,26 +44,44 @@ namespace {
 using namespace tc;
 
 constexpr int BM = img::BM, BN = img::BN;
-constexpr int NSTAGE = 4;
-constexpr int D_BYTES = BM * BN * 4;          // 32 KB
-constexpr int VOP_BYTES = img::VOP_BYTES;     // 8 KB  [64 x 32] tf32
-constexpr int VTOP_BYTES = img::VTOP_BYTES;   // 2 KB  [16 x 64] bf16
-constexpr int UTOP_BYTES = img::UTOP_BYTES;   // 4 KB  2 x [16 x 64] bf16
-constexpr int WOP_BYTES = img::WOP_BYTES;     // 16 KB [128 x 32] tf32
-constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES + UTOP_BYTES;  // 46 KB
+constexpr int D_BYTES = BM * BN * 4;          // 32 KB: FP32 tile, or bf16 hi + lo tiles
 constexpr int Z_BYTES = 2 * BM * BN * 2;      // hi + lo, 32 KB, in place of the D tile
 constexpr int OFF_STAGE = 0;
-constexpr int OFF_W = NSTAGE * STAGE_BYTES;
-constexpr int OFF_BAR = OFF_W + 2 * WOP_BYTES;
-constexpr int NBAR = 48;
-constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 256 + 1024;  // + alignment slack
+constexpr int NBAR = 96;
+constexpr int G2 = kTcY2Chunk;  // row tiles per Y2 accumulation chunk
+constexpr int CT_BARS = 20;     // column tiles per CTA with their own Y2 chunk barriers
 constexpr int EPI_WARPS = 16;
 constexpr int THREADS = 128 + 32 * EPI_WARPS;  // warp 0 TMA, 1 L MMAs, 2 Y1 MMAs, 3 Y2 MMAs, 4..19 epilogue
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int TMEM_COLS = 512;
-constexpr int TM_Y1 = 128, TM_Y2 = 160;
-static_assert(STAGE_BYTES % 1024 == 0 && OFF_W % 1024 == 0 && Z_BYTES == D_BYTES, "1024-byte aligned operands");
-static_assert(SMEM_BYTES <= 232448, "shared memory");
+static_assert(Z_BYTES == D_BYTES, "Z replaces the D tile");
+
+// Shared-memory and tensor-memory plan for image layout RK.
+template <int RK>
+struct Cfg {
+  using Lay = img::Layout<RK>;
+  static constexpr int NSTAGE = RK == 8 ? 4 : 3;
+  static constexpr int VOP_BYTES = Lay::VOP_BYTES;    // 8 / 16 KB tf32
+  static constexpr int VTOP_BYTES = Lay::VTOP_BYTES;  // 2 / 4 KB  [2RK x 64] bf16
+  static constexpr int UTOP_BYTES = Lay::UTOP_BYTES;  // 4 / 8 KB  2 x [2RK x 64] bf16
+  static constexpr int WOP_BYTES = Lay::WOP_BYTES;    // 16 KB     [128 x 32] tf32
+  static constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES + UTOP_BYTES;  // 46 / 60 KB
+  static constexpr int OFF_W = NSTAGE * STAGE_BYTES;
+  static constexpr int OFF_BAR = OFF_W + 2 * WOP_BYTES;
+  static constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 256 + 1024;  // + alignment slack
+  static constexpr int NY = 2 * RK;                   // Y accumulator columns: hi and lo halves
+  static constexpr int LK = RK == 8 ? 3 : 6;          // k-steps of the L product
+  static constexpr int TM_Y1 = 2 * BN, TM_Y2 = TM_Y1 + 2 * NY;
+  static constexpr int MAX_CT = (TMEM_COLS - TM_Y2) / NY;  // column tiles whose Y2 fits in TMEM
+  static_assert(STAGE_BYTES % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned operands");
+  static_assert((D_BYTES + VOP_BYTES) % 1024 == 0 && (D_BYTES + VOP_BYTES + VTOP_BYTES) % 1024 == 0,
+                "1024-byte aligned images");
+  static_assert(SMEM_BYTES <= 232448, "shared memory");
+  static_assert(NSTAGE <= 4, "barrier slots");
+  // the Y2 drain uses the idle stages as [column tile][128][RK] FP32 scratch
+  static_assert(MAX_CT * BM * RK * 4 <= NSTAGE * STAGE_BYTES, "Y2 drain scratch");
+  static_assert(CT_BARS >= (RK == 8 ? 20 : 10), "Y2 chunk barriers for tc_max_col_tiles");
+};
 
 // barrier slots
 enum {
@@ -78,9 +98,11 @@ enum {
   B_DRAIN = 25,
   B_DREAD = 26,    // [NSTAGE][4]: the warps of lane quarter q have read their D values
   B_LDRAIN = 42,
-  B_Y1DRAIN = 43
+  B_Y1DRAIN = 43,
+  B_Y2DONE = 44,   // [CT_BARS]: the MMAs of a non-final Y2 chunk of column tile ctl completed
+  B_Y2FREE = 64    // [CT_BARS]: that chunk has been read out of tensor memory
 };
-static_assert(NSTAGE <= 4 && B_DREAD + 4 * NSTAGE <= B_LDRAIN && B_Y1DRAIN < NBAR, "barrier slots");
+static_assert(B_DREAD + 4 * 4 <= B_LDRAIN && B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -97,6 +119,8 @@ struct TcArgs {
   float* P2;
   double* resP;
   unsigned long long* nnzP;
+  float* Y2c;
+  int ch_max, ct_max;
 };
 
 __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) {
@@ -104,13 +128,26 @@ __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) 
   *abort_flag = 1;
 }
 
+// NY consecutive accumulator columns of this warp's 32 lanes.
+template <int NY>
+__device__ __forceinline__ void tmem_ld_y(uint32_t taddr, uint32_t (&v)[NY]) {
+  if constexpr (NY == 16)
+    tmem_ld16(taddr, v);
+  else
+    tmem_ld32(taddr, v);
+}
+
 // DM = 0: D is FP32 (dmap, two 128 x 32 boxes per tile).  DM = 1: D is held as bf16 hi and
 // lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
 // DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
-// 32 KB and Z is written over it in the same layout.
-template <int DM>
+// 32 KB and Z is written over it in the same layout.  RK: operand image layout (8 or 16).
+template <int DM, int RK>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap,
                                                             const __grid_constant__ CUtensorMap dmap_lo, TcArgs a) {
+  using C = Cfg<RK>;
+  constexpr int NSTAGE = C::NSTAGE, STAGE_BYTES = C::STAGE_BYTES, OFF_W = C::OFF_W, OFF_BAR = C::OFF_BAR;
+  constexpr int VOP_BYTES = C::VOP_BYTES, VTOP_BYTES = C::VTOP_BYTES, UTOP_BYTES = C::UTOP_BYTES;
+  constexpr int WOP_BYTES = C::WOP_BYTES, NY = C::NY, TM_Y1 = C::TM_Y1, TM_Y2 = C::TM_Y2;
   if (a.st->done) return;
   const bool use_lo = DM == 1 && a.st->use_lo != 0;
   extern __shared__ uint8_t smem_raw[];
@@ -128,6 +165,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   const int ct0 = (int)((long long)bi * a.TC / a.B), ct1 = (int)((long long)(bi + 1) * a.TC / a.B);
   const int nrt = rt1 - rt0, nct = ct1 - ct0;
   const int ntiles = nrt * nct;
+  // the host's partition keeps a CTA's column tiles within the tensor-memory and barrier
+  // budget and its row tiles within the chunk slots; refuse a launch that does not
+  if (nct > C::MAX_CT || nct > CT_BARS || nct > a.ct_max || (nrt + G2 - 1) / G2 > a.ch_max) {
+    if (tid == 0) atomicCAS(a.status, 0, 1);
+    return;
+  }
 
   if (tid == 0) {
     abort_flag = 0;
@@ -149,6 +192,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     mbar_init(&bar[B_DRAIN], 1);
     mbar_init(&bar[B_LDRAIN], 1);
     mbar_init(&bar[B_Y1DRAIN], 1);
+    for (int i = 0; i < CT_BARS; ++i) {
+      mbar_init(&bar[B_Y2DONE + i], 1);
+      mbar_init(&bar[B_Y2FREE + i], EPI_WARPS / 2);
+    }
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -218,8 +265,17 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_after();
       const uint64_t dw = dw0 + (uint64_t)(wb * (WOP_BYTES >> 4));
       const uint64_t dv = dv0 + (uint64_t)(s * (STAGE_BYTES >> 4));
+      if (RK == 8) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);  // 4th k-block is zero
+        for (int k = 0; k < 3; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);  // 4th k-block is zero
+      } else {
+        // [W_hi W_lo] . [V_hi V_hi] over the first column block, then W_hi . V_lo (second block)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          mma_tf32(tmem + lb * BN, dw + 2 * k, dv + ((BN * 128) >> 4) + 2 * k, idL, true);
+      }
       mma_commit(&bar[B_LFULL + lb]);
       if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
     }
@@ -228,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   } else if (ntiles > 0 && warp == 2 && lane == 0) {
     // ------------------------------------------------------------------ Y1 MMAs
     const uint32_t base = smem_u32(sm);
-    const uint32_t idY1 = instr_desc(128, 16, 1, 1, false, false);
+    const uint32_t idY1 = instr_desc(128, NY, 1, 1, false, false);
     const uint64_t dzh0 = smem_desc(base + OFF_STAGE, 16, 1024);
     const uint64_t dvt0 = smem_desc(base + OFF_STAGE + D_BYTES + VOP_BYTES, 16, 1024);
     int rtl = 0, ctl = 0;
@@ -243,7 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_after();
       const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
       const uint64_t dzh = dzh0 + so, dzl = dzh0 + so + (uint64_t)((Z_BYTES / 2) >> 4), dvt = dvt0 + so;
-      const uint32_t y1 = tmem + TM_Y1 + yb * 16;
+      const uint32_t y1 = tmem + TM_Y1 + yb * NY;
 #pragma unroll
       for (int k = 0; k < 4; ++k) mma_f16(y1, dzh + 2 * k, dvt + 2 * k, idY1, !(ctl == 0 && k == 0));
 #pragma unroll
@@ -256,24 +312,31 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   } else if (ntiles > 0 && warp == 3 && lane == 0) {
     // ------------------------------------------------------------------ Y2 MMAs
     const uint32_t base = smem_u32(sm);
-    const uint32_t idY2 = instr_desc(128, 16, 1, 1, true, false);
+    const uint32_t idY2 = instr_desc(128, NY, 1, 1, true, false);
     const uint64_t dzm0 = smem_desc(base + OFF_STAGE, Z_BYTES / 2, 1024);
     const uint64_t dut0 = smem_desc(base + OFF_STAGE + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
     int rtl = 0, ctl = 0;
     for (int tp = 0; tp < ntiles && !abort_flag; ++tp, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
       const int s = tp % NSTAGE;
-      if (!mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1)) {
+      // a Y2 accumulator restarts every G2 row tiles (the tensor-core accumulation of a long
+      // chain of products drifts); the epilogue has read the previous chunk out first
+      const bool restart = rtl % G2 == 0;
+      bool ok = mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1);
+      if (ok && restart && rtl > 0) ok = mbar_wait(&bar[B_Y2FREE + ctl], ((rtl / G2) - 1) & 1);
+      if (!ok) {
         fail(a, &abort_flag);
         break;
       }
       tc_fence_after();
       const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
       const uint64_t dzm = dzm0 + so, dut = dut0 + so;
-      const uint32_t y2 = tmem + TM_Y2 + ctl * 16;
+      const uint32_t y2 = tmem + TM_Y2 + ctl * NY;
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        mma_f16(y2, dzm + 128 * k, dut + (k >= 4 ? 128 : 0) + 2 * (k & 3), idY2, !(rtl == 0 && k == 0));
+        mma_f16(y2, dzm + 128 * k, dut + (k >= 4 ? ((UTOP_BYTES / 2) >> 4) : 0) + 2 * (k & 3), idY2,
+                !(restart && k == 0));
       mma_commit(&bar[B_EMPTY + s]);
+      if (rtl % G2 == G2 - 1 && rtl != nrt - 1) mma_commit(&bar[B_Y2DONE + ctl]);
     }
     mma_commit(&bar[B_YFIN]);
     mma_commit(&bar[B_DRAIN]);
@@ -292,6 +355,32 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     unsigned nnz = 0;
     for (int t = grp; t < ntiles && !abort_flag; t += 2) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
+      if (rtl % G2 == 0 && rtl > 0) {
+        // read chunk c - 1 of column tile ctl's Y2 accumulator (hi + lo column halves) out to
+        // its slot before this tile's products restart the accumulator
+        const int c = rtl / G2;
+        if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
+          fail(a, &abort_flag);
+          break;
+        }
+        tc_fence_after();
+        uint32_t yv[NY];
+        tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
+        float* slot = a.Y2c + ((((size_t)cta * a.ch_max + (c - 1)) * a.ct_max + ctl) * BM + rowl) * RK + h * (RK / 2);
+        float sv[RK / 2];  // k = h RK/2 + j (register indices fixed at compile time)
+#pragma unroll
+        for (int j = 0; j < RK / 2; ++j) {
+          const uint32_t x = h ? yv[RK / 2 + j] : yv[j], y = h ? yv[RK + RK / 2 + j] : yv[RK + j];
+          sv[j] = __uint_as_float(x) + __uint_as_float(y);
+        }
+#pragma unroll
+        for (int j = 0; j < RK / 2; j += 4)
+          *reinterpret_cast<float4*>(slot + j) = make_float4(sv[j], sv[j + 1], sv[j + 2], sv[j + 3]);
+      }
       if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
         fail(a, &abort_flag);
         break;
@@ -390,20 +479,27 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           break;
         }
         tc_fence_after();
-        uint32_t yv[16];
-        tmem_ld16(tmem + lane_base + TM_Y1 + yb * 16, yv);
+        uint32_t yv[NY];
+        tmem_ld_y<NY>(tmem + lane_base + TM_Y1 + yb * NY, yv);
         tmem_wait_ld();
         const int row = (rt0 + rtl) * BM + rowl;
-        if (row < a.m)
-          for (int k = 0; k < a.R; ++k)
-            a.P1[((size_t)bi * a.m + row) * a.R + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[8 + k]);
+        if (row < a.m) {
+#pragma unroll
+          for (int k = 0; k < RK; ++k)
+            if (k < a.R)
+              a.P1[((size_t)bi * a.m + row) * a.R + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[B_Y1EMPTY + yb]);
       }
     }
     // drain Y2: each warp takes the column tiles ctl = g, g + 4, ...; lane quarter q holds
-    // accumulator rows 32q .. 32q+31 (rows 0..63: Z_hi part, 64..127: Z_lo part)
+    // accumulator rows 32q .. 32q+31 (rows 0..63: Z_hi part, 64..127: Z_lo part).  The last
+    // chunk is in tensor memory, the earlier ones in their slots (written by any epilogue warp:
+    // the barrier below orders those stores before the reads)
+    asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
+    const int nch = (nrt + G2 - 1) / G2;
     if (ntiles > 0 && !abort_flag) {
       // the Y2 products are complete (YFIN) and so are the Y1 products (Y1DRAIN): only then
       // may the stages be reused as scratch
@@ -411,14 +507,29 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         fail(a, &abort_flag);
       } else {
         tc_fence_after();
-        float* scratch = reinterpret_cast<float*>(sm + OFF_STAGE);  // [nct][128][8], stages are idle now
+        float* scratch = reinterpret_cast<float*>(sm + OFF_STAGE);  // [nct][128][RK], stages are idle now
         for (int ctl = gq; ctl < nct; ctl += EPI_WARPS / 4) {
-          uint32_t yv[16];
-          tmem_ld16(tmem + lane_base + TM_Y2 + ctl * 16, yv);
+          uint32_t yv[NY];
+          tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
           tmem_wait_ld();
+          float acc[RK];
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            scratch[((size_t)ctl * BM + rowl) * 8 + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[8 + k]);
+          for (int k = 0; k < RK; ++k) acc[k] = 0.f;
+          for (int c = 0; c + 1 < nch; ++c) {
+            const float4* slot = reinterpret_cast<const float4*>(
+                a.Y2c + ((((size_t)cta * a.ch_max + c) * a.ct_max + ctl) * BM + rowl) * RK);
+#pragma unroll
+            for (int k4 = 0; k4 < RK / 4; ++k4) {
+              const float4 v = slot[k4];
+              acc[4 * k4] += v.x;
+              acc[4 * k4 + 1] += v.y;
+              acc[4 * k4 + 2] += v.z;
+              acc[4 * k4 + 3] += v.w;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < RK; ++k)
+            scratch[((size_t)ctl * BM + rowl) * RK + k] = acc[k] + (__uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]));
         }
       }
     }
@@ -432,7 +543,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         if (col < a.n)
           for (int k = 0; k < a.R; ++k)
             a.P2[((size_t)ai * a.n + col) * a.R + k] =
-                scratch[((size_t)ctl * BM + jl) * 8 + k] + scratch[((size_t)ctl * BM + 64 + jl) * 8 + k];
+                scratch[((size_t)ctl * BM + jl) * RK + k] + scratch[((size_t)ctl * BM + 64 + jl) * RK + k];
       }
     }
     // CTA totals of the residual and the support size
@@ -465,22 +576,32 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+static_assert(Cfg<8>::MAX_CT >= 20 && Cfg<16>::MAX_CT >= 10, "column tiles per CTA (tc_max_col_tiles)");
+
+template <int DM, int RK>
+cudaError_t set_tc_smem() {
+  return cudaFuncSetAttribute(fused_pass_tc<DM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<RK>::SMEM_BYTES);
+}
+
 }  // namespace
 
-bool tc_pass_supported(int R) { return R <= 8; }
+bool tc_pass_supported(int R) { return R >= 1 && R <= 16; }
 
-size_t tc_pass_smem() { return SMEM_BYTES; }
+size_t tc_pass_smem() { return Cfg<8>::SMEM_BYTES; }
 
 cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dmap_lo, int dm, const TcPassArgs& p,
                                  cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(fused_pass_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fused_pass_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = set_tc_smem<0, 8>();
+    if (e == cudaSuccess) e = set_tc_smem<1, 8>();
+    if (e == cudaSuccess) e = set_tc_smem<0, 16>();
+    if (e == cudaSuccess) e = set_tc_smem<1, 16>();
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  if (p.R < 1 || p.R > 16) return cudaErrorInvalidValue;
   TcArgs a;
   a.m = p.m;
   a.n = p.n;
@@ -499,10 +620,21 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.P2 = p.P2;
   a.resP = p.resP;
   a.nnzP = p.nnzP;
-  if (dm == 0)
-    fused_pass_tc<0><<<p.A * p.B, THREADS, SMEM_BYTES, s>>>(*dmap, *dmap, a);
-  else
-    fused_pass_tc<1><<<p.A * p.B, THREADS, SMEM_BYTES, s>>>(*dmap, *dmap_lo, a);
+  a.Y2c = p.Y2c;
+  a.ch_max = p.ch_max;
+  a.ct_max = p.ct_max;
+  const CUtensorMap& lo = dm ? *dmap_lo : *dmap;
+  if (p.R <= 8) {
+    if (dm == 0)
+      fused_pass_tc<0, 8><<<p.A * p.B, THREADS, Cfg<8>::SMEM_BYTES, s>>>(*dmap, lo, a);
+    else
+      fused_pass_tc<1, 8><<<p.A * p.B, THREADS, Cfg<8>::SMEM_BYTES, s>>>(*dmap, lo, a);
+  } else {
+    if (dm == 0)
+      fused_pass_tc<0, 16><<<p.A * p.B, THREADS, Cfg<16>::SMEM_BYTES, s>>>(*dmap, lo, a);
+    else
+      fused_pass_tc<1, 16><<<p.A * p.B, THREADS, Cfg<16>::SMEM_BYTES, s>>>(*dmap, lo, a);
+  }
   return cudaGetLastError();
 }
 

@@ -582,21 +582,31 @@ __device__ __forceinline__ void reduce_row(const T* __restrict__ Pp, int nsl, si
     for (int j = 0; j < WM; ++j) y[j] += (j < w) ? p[(size_t)q * stride + j] : T(0);
 }
 
-// Row i of the tensor-core operand images: side 0 gives rows of W (= f) and U~ (= q), side 1
-// rows of V (= f) and V~ (= q); ranks up to 8 (entries 8.. of a wider row are zero: the
-// width-16 steps of the initialisation write the iteration's images when r <= 8).
-template <typename T, int WM>
-__device__ __forceinline__ void write_images(const SmallArgs& a, int side, int i, const T (&f)[WM], const T (&q)[WM]) {
-  float fv[8], qv[8];
+// Row i of the tensor-core operand images of image set `set` (0: the initialisation's pass,
+// 1: the iteration's): side 0 gives rows of W (= f) and U~ (= q), side 1 rows of V (= f) and
+// V~ (= q), in the layout of that pass (img_rk); entries past WM are zero.
+template <int RK, typename T, int WM>
+__device__ __forceinline__ void write_images_rk(const SmallArgs& a, int set, int side, int i, const T (&f)[WM],
+                                                const T (&q)[WM]) {
+  float fv[RK], qv[RK];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < RK; ++j) {
     fv[j] = j < WM ? (float)f[j < WM ? j : 0] : 0.f;
     qv[j] = j < WM ? (float)q[j < WM ? j : 0] : 0.f;
   }
   if (side == 0)
-    img::write_row_images(i, fv, qv, a.wop, a.utop);
+    img::write_row_images<RK>(i, fv, qv, a.wop[set], a.utop[set]);
   else
-    img::write_col_images(i, fv, qv, a.vop, a.vtop);
+    img::write_col_images<RK>(i, fv, qv, a.vop[set], a.vtop[set]);
+}
+
+template <typename T, int WM>
+__device__ __noinline__ void write_images(const SmallArgs& a, int set, int side, int i, const T (&f)[WM],
+                                          const T (&q)[WM]) {
+  if (a.img_rk[set] == 8)
+    write_images_rk<8, T, WM>(a, set, side, i, f, q);
+  else
+    write_images_rk<16, T, WM>(a, set, side, i, f, q);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -667,7 +677,9 @@ __device__ void finish_bases(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       store_copy<T, WM>(d0, i, Rc, f);
       store_copy<T, WM>(d1, i, Rc, q);
-      if (sizeof(T) == 4 && WM >= 8 && a.img_iter) write_images<T, WM>(a, side, i, f, q);
+      if constexpr (sizeof(T) == 4) {
+        if (a.img_iter) write_images<T, WM>(a, 1, side, i, f, q);
+      }
     }
   }
 }
@@ -943,7 +955,9 @@ __device__ void orth_second_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>&
       zero_row<T, WM>(z);
       store_copy<T, WM>(d0, i, Rc, q);
       store_copy<T, WM>(d1, i, Rc, z);
-      if (sizeof(T) == 4 && WM >= 8 && a.img_init) write_images<T, WM>(a, side, i, z, q);
+      if constexpr (sizeof(T) == 4) {
+        if (a.img_init) write_images<T, WM>(a, 0, side, i, z, q);
+      }
     }
   }
 }

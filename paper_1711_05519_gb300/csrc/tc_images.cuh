@@ -1,13 +1,22 @@
 // Operand images of the tensor-core fused pass: the factors of L_k and the bases U~, V~ laid
 // out per 128-row / 64-column tile exactly as the MMAs read them from shared memory
-// (K-major, 128-byte swizzle), so the pass brings them in with plain bulk copies.
+// (K-major, 128-byte swizzle), so the pass brings them in with plain bulk copies.  Two
+// layouts, for padded ranks up to RK = 8 and up to RK = 16:
 //
+//   RK = 8
 //   W image  (per 128 rows, 16 KB):  [W_hi W_hi W_lo 0]  tf32, W = U_k Sigma_k
 //   V image  (per 64 columns, 8 KB): [V_hi V_lo V_hi 0]  tf32, so W V^T = W_hi V_hi^T +
 //                                    W_hi V_lo^T + W_lo V_hi^T (FP32-level accuracy)
-//   U~ image (per 128 rows, 4 KB):   [U~_hi | U~_lo]^T   bf16, two 64-row halves
-//   V~ image (per 64 columns, 2 KB): [V~_hi | V~_lo]^T   bf16
-// hi = round-to-nearest tf32 / bf16 of x, lo = the rounding of x - hi.  Ranks up to 8.
+//   RK = 16
+//   W image  (per 128 rows, 16 KB):  [W_hi W_lo]         tf32
+//   V image  (per 64 columns, 16 KB): [V_hi V_hi] [V_lo 0]  two 128-byte-wide column blocks;
+//                                    [W_hi W_lo] . [V_hi V_hi] + W_hi . V_lo gives the same
+//                                    three terms
+//   both
+//   U~ image (per 128 rows, 2 x 2RK x 64 bf16): [U~_hi | U~_lo]^T, two 64-row halves
+//   V~ image (per 64 columns, 2RK x 64 bf16):   [V~_hi | V~_lo]^T
+// hi = round-to-nearest tf32 / bf16 of x, lo = the rounding of x - hi.  Entries past the
+// rank are zero.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -17,10 +26,18 @@ namespace rpca {
 namespace img {
 
 constexpr int BM = 128, BN = 64;
-constexpr int WOP_BYTES = BM * 32 * 4;       // 16 KB [128 x 32] tf32
-constexpr int VOP_BYTES = BN * 32 * 4;       // 8 KB  [64 x 32] tf32
-constexpr int VTOP_BYTES = 16 * 64 * 2;      // 2 KB  [16 x 64] bf16
-constexpr int UTOP_BYTES = 2 * 16 * 64 * 2;  // 4 KB  2 x [16 x 64] bf16
+
+template <int RK>
+struct Layout {
+  static_assert(RK == 8 || RK == 16, "image ranks");
+  static constexpr int WOP_BYTES = BM * 32 * 4;                     // 16 KB
+  static constexpr int VOP_BYTES = BN * (RK == 8 ? 32 : 64) * 4;    // 8 / 16 KB
+  static constexpr int VTOP_BYTES = 2 * RK * BN * 2;                // 2 / 4 KB
+  static constexpr int UTOP_BYTES = 2 * (2 * RK * 64 * 2);          // 4 / 8 KB
+};
+// buffer sizes that hold either layout
+constexpr int WOP_MAX = Layout<16>::WOP_BYTES, VOP_MAX = Layout<16>::VOP_BYTES;
+constexpr int VTOP_MAX = Layout<16>::VTOP_BYTES, UTOP_MAX = Layout<16>::UTOP_BYTES;
 
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
@@ -33,54 +50,71 @@ __device__ __forceinline__ int sw128(int row, int byte_in_row) {
   return row * 128 + ((((byte_in_row >> 4) ^ (row & 7)) & 7) << 4) + (byte_in_row & 15);
 }
 
-// Row i of the W and U~ images from w[0..7] (row i of W = U Sigma) and u[0..7] (row i of U~),
-// both zero beyond the rank.
-__device__ __forceinline__ void write_row_images(int i, const float (&w)[8], const float (&u)[8], uint8_t* wop,
+// Row i of the W and U~ images from w[0..RK) (row i of W = U Sigma) and u[0..RK) (row i of U~).
+template <int RK>
+__device__ __forceinline__ void write_row_images(int i, const float (&w)[RK], const float (&u)[RK], uint8_t* wop,
                                                  uint8_t* utop) {
+  using Lay = Layout<RK>;
   const int rt = i / BM, il = i % BM;
-  float hi[8], lo[8];
-  __nv_bfloat16 uh[8], ul[8];
+  float hi[RK], lo[RK];
+  __nv_bfloat16 uh[RK], ul[RK];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < RK; ++k) {
     hi[k] = tf32_rna(w[k]);
     lo[k] = w[k] - hi[k];
     uh[k] = __float2bfloat16_rn(u[k]);
     ul[k] = __float2bfloat16_rn(u[k] - __bfloat162float(uh[k]));
   }
-  float* wt = reinterpret_cast<float*>(wop + (size_t)rt * WOP_BYTES);
+  float* wt = reinterpret_cast<float*>(wop + (size_t)rt * Lay::WOP_BYTES);
 #pragma unroll
   for (int kk = 0; kk < 32; ++kk) {
-    const float v = kk < 8 ? hi[kk] : kk < 16 ? hi[kk - 8] : kk < 24 ? lo[kk - 16] : 0.f;
+    float v;
+    if (RK == 8)
+      v = kk < 8 ? hi[kk % RK] : kk < 16 ? hi[(kk - 8) % RK] : kk < 24 ? lo[(kk - 16) % RK] : 0.f;
+    else
+      v = kk < 16 ? hi[kk % RK] : lo[(kk - 16) % RK];
     wt[sw128(il, 4 * kk) >> 2] = v;
   }
-  __nv_bfloat16* ut = reinterpret_cast<__nv_bfloat16*>(utop + (size_t)rt * UTOP_BYTES);
+  __nv_bfloat16* ut = reinterpret_cast<__nv_bfloat16*>(utop + (size_t)rt * Lay::UTOP_BYTES);
   const int sub = il / 64, kl = il % 64;
 #pragma unroll
-  for (int nn = 0; nn < 16; ++nn) ut[(sub * 2048 + sw128(nn, 2 * kl)) >> 1] = nn < 8 ? uh[nn] : ul[nn - 8];
+  for (int nn = 0; nn < 2 * RK; ++nn)
+    ut[(sub * (2 * RK * 128) + sw128(nn, 2 * kl)) >> 1] = nn < RK ? uh[nn % RK] : ul[(nn - RK) % RK];
 }
 
-// Row j of the V and V~ images from v[0..7] (row j of V) and t[0..7] (row j of V~).
-__device__ __forceinline__ void write_col_images(int j, const float (&v)[8], const float (&t)[8], uint8_t* vop,
+// Row j of the V and V~ images from v[0..RK) (row j of V) and t[0..RK) (row j of V~).
+template <int RK>
+__device__ __forceinline__ void write_col_images(int j, const float (&v)[RK], const float (&t)[RK], uint8_t* vop,
                                                  uint8_t* vtop) {
+  using Lay = Layout<RK>;
   const int ct = j / BN, jl = j % BN;
-  float hi[8], lo[8];
-  __nv_bfloat16 vh[8], vl[8];
+  float hi[RK], lo[RK];
+  __nv_bfloat16 vh[RK], vl[RK];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < RK; ++k) {
     hi[k] = tf32_rna(v[k]);
     lo[k] = v[k] - hi[k];
     vh[k] = __float2bfloat16_rn(t[k]);
     vl[k] = __float2bfloat16_rn(t[k] - __bfloat162float(vh[k]));
   }
-  float* vt = reinterpret_cast<float*>(vop + (size_t)ct * VOP_BYTES);
+  uint8_t* vt = vop + (size_t)ct * Lay::VOP_BYTES;
+  if (RK == 8) {
 #pragma unroll
-  for (int kk = 0; kk < 32; ++kk) {
-    const float x = kk < 8 ? hi[kk] : kk < 16 ? lo[kk - 8] : kk < 24 ? hi[kk - 16] : 0.f;
-    vt[sw128(jl, 4 * kk) >> 2] = x;
+    for (int kk = 0; kk < 32; ++kk) {
+      const float x = kk < 8 ? hi[kk % RK] : kk < 16 ? lo[(kk - 8) % RK] : kk < 24 ? hi[(kk - 16) % RK] : 0.f;
+      *reinterpret_cast<float*>(vt + sw128(jl, 4 * kk)) = x;
+    }
+  } else {
+    // column block 0: [V_hi V_hi]; column block 1 (BN x 128 bytes further): [V_lo 0]
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+      *reinterpret_cast<float*>(vt + sw128(jl, 4 * kk)) = hi[kk % RK];
+      *reinterpret_cast<float*>(vt + BN * 128 + sw128(jl, 4 * kk)) = kk < RK ? lo[kk % RK] : 0.f;
+    }
   }
-  __nv_bfloat16* tt = reinterpret_cast<__nv_bfloat16*>(vtop + (size_t)ct * VTOP_BYTES);
+  __nv_bfloat16* tt = reinterpret_cast<__nv_bfloat16*>(vtop + (size_t)ct * Lay::VTOP_BYTES);
 #pragma unroll
-  for (int nn = 0; nn < 16; ++nn) tt[sw128(nn, 2 * jl) >> 1] = nn < 8 ? vh[nn] : vl[nn - 8];
+  for (int nn = 0; nn < 2 * RK; ++nn) tt[sw128(nn, 2 * jl) >> 1] = nn < RK ? vh[nn % RK] : vl[(nn - RK) % RK];
 }
 
 }  // namespace img

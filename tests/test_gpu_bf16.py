@@ -84,12 +84,13 @@ def test_bf16_split_from_fp64_input():
     assert rel_fro(g["L"], inst.L) < 1e-5
 
 
+@pytest.mark.parametrize("kind", ["simt", "tensor"])
 @pytest.mark.parametrize("prec", ["bf16_split", "bf16"])
-def test_bf16_rank_10_on_the_simt_pass(prec):
-    # padded rank 10: the SIMT pass reads the bf16 storage
+def test_bf16_rank_10(prec, kind):
+    # padded rank 10 on either pass kind (the tensor-core one in its rank-16 image layout)
     inst = synth.planted_instance(400, 360, 10, 0.1, 1.0, 5)
-    g = _run(inst, prec, 1e-5, max_iter=60)
-    assert g["kinds"] == ("simt", "simt")
+    g = _run(inst, prec, 1e-5, max_iter=60, pass_kind=kind)
+    assert g["kinds"] == (kind, kind)
     if prec == "bf16_split":
         assert g["code"] == P.OK
         ref = _oracle(g["D"], inst, g["stats"][-1]["k"])

@@ -29,12 +29,13 @@ def _gpu_run(inst, prec, tol, r=None, **kw):
     D = torch.from_numpy(inst.D).to("cuda", dt)
     with _solver(p, prec, tol, **kw) as s:
         s.init(D, r)
+        kinds = s.pass_kind()
         code, stats = s.run()
         U, sig, V = (t.cpu().numpy() for t in s.lowrank())
         idx, val = (t.cpu().numpy() for t in s.sparse())
     Dh = D.double().cpu().numpy()
     return {"code": code, "stats": stats, "L": (U * sig) @ V.T, "U": U, "sig": sig, "V": V, "idx": idx,
-            "val": val, "D": Dh}
+            "val": val, "D": Dh, "kinds": kinds}
 
 
 def _oracle_same_k(D, inst, k, r=None, **kw):
@@ -115,12 +116,15 @@ def test_fp32_config1_matches_oracle():
     assert ok, diff
 
 
-@pytest.mark.parametrize("m,n,r", [(384, 320, 7), (256, 512, 8)])
-def test_fp32_tensor_iteration_after_width16_initialisation(m, n, r):
-    # r = 7, 8: the initialisation block is 16 wide (SIMT pass), the iteration rank 8
-    # (tensor-core pass), so the last initialisation step writes the iteration's operand images
+@pytest.mark.parametrize("m,n,r", [(384, 320, 7), (256, 512, 8), (256, 384, 9), (384, 320, 10), (300, 512, 12),
+                                   (512, 448, 16)])
+def test_fp32_tensor_pass_ranks_7_to_16(m, n, r):
+    # r = 7, 8: initialisation pass in the rank-16 image layout, iteration pass in the rank-8
+    # one (two image sets); r >= 9: both passes in the rank-16 layout (3 stages, N32 Y
+    # accumulators, 10 column tiles per CTA at most)
     inst = synth.planted_instance(m, n, r, 0.08, 1.0, m + n + r)
     g = _gpu_run(inst, "fp32", 1e-5)
+    assert g["kinds"] == ("tensor", "tensor")
     assert g["stats"][-1]["err"] < 1e-5
     ref = _oracle_same_k(g["D"], inst, g["stats"][-1]["k"])
     assert rel_fro(g["L"], ref["L"]) < 1e-5
