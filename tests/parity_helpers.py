@@ -18,3 +18,11 @@ def support_mismatch(gpu_idx, D, L_ref, zeta_ref, band_rel=1e-6, band_abs_rel_D=
 
 def rel_fro(A, B):
     return float(np.linalg.norm(A - B) / np.linalg.norm(B))
+
+
+def factored_rel_err(U, sig, V, P, Q):
+    """||U diag(sig) V^T - P Q^T||_F / ||P Q^T||_F from r x r products (no m x n array)."""
+    A2 = np.sum((sig[:, None] * (U.T @ U)) * ((V.T @ V) * sig[None, :]))
+    B2 = np.sum((P.T @ P) * (Q.T @ Q))
+    AB = np.trace(np.diag(sig) @ (U.T @ P) @ (Q.T @ V))
+    return float(np.sqrt(max(A2 + B2 - 2.0 * AB, 0.0)) / np.sqrt(B2))
