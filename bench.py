@@ -353,6 +353,69 @@ def video_section(dev):
             "noise_floor_rel": float(v.noise * np.sqrt(v.m * v.n) / np.linalg.norm(Lt))}
 
 
+def _factored_rel_err(U, sig, V, P, Q):
+    """||U diag(sig) V^T - P Q^T||_F / ||P Q^T||_F from r x r products."""
+    A2 = np.sum((sig[:, None] * (U.T @ U)) * ((V.T @ V) * sig[None, :]))
+    B2 = np.sum((P.T @ P) * (Q.T @ Q))
+    AB = np.trace(np.diag(sig) @ (U.T @ P) @ (Q.T @ V))
+    return float(np.sqrt(max(A2 + B2 - 2.0 * AB, 0.0)) / np.sqrt(B2))
+
+
+def precision_section(dev):
+    """The bf16 storage modes of D against plain FP32 on the mixed-precision workload
+    (m = n = 2*10^4, r = 10, alpha = 0.2, c = 3, gamma = 0.5, tol 1e-5) and on the 10^4
+    workload: time to tol from D resident in HBM (initialisation included, as in the main
+    line), and the error of L_k against the planted L* per iteration (the FP64 oracle
+    recovers L* to 1e-10 on the 500 x 500 workload, so this is the error against FP64)."""
+    import paper_1711_05519_gb300 as P
+
+    out = {}
+    for name, (m, r, alpha, c) in (("mixed_precision_20000_r10", (20000, 10, 0.2, 3.0)),
+                                   ("planted_10000_r5", (M, RANK, ALPHA, CMAG))):
+        inst = synth.planted_instance(m, m, r, alpha, c, SEED)
+        p = inst.params()
+        D = torch.from_numpy(inst.D.astype(np.float32)).to(dev)
+        sec = {"workload": f"planted m=n={m} r={r} alpha={alpha} c={c} seed {SEED}, tol {TOL}"}
+        for prec in ("fp32", "bf16_split", "bf16"):
+            tol = TOL if prec != "bf16" else 0.0
+            with P.Solver(p["beta"], p["gamma"], tol, precision=prec, beta_init=p["beta_init"], mu_trim=p["mu"],
+                          max_iter=100 if prec != "bf16" else 25) as s:
+                times = []
+                for rep in range(4 if prec != "bf16" else 1):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    s.init(D, r)
+                    code, stats = s.run()
+                    e1.record()
+                    torch.cuda.synchronize(dev)
+                    if rep or prec == "bf16":
+                        times.append(e0.elapsed_time(e1))
+                U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
+                entry = {"L_rel_err": _factored_rel_err(U, sig, V, inst.P, inst.Q), "iterations": stats[-1]["k"],
+                         "err": stats[-1]["err"], "pass_kind": s.pass_kind()[0]}
+                if prec != "bf16":
+                    entry["ms_to_tol"] = round(statistics.median(times), 3)
+                    entry["converged"] = code == P.OK
+                if prec == "bf16_split" and name.startswith("mixed"):
+                    # per-iteration error of L_k against L* (untimed rerun, one iteration per call)
+                    s.init(D, r)
+                    per = []
+                    while True:
+                        code, st = s.iterate(1)
+                        U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
+                        for x in st:
+                            per.append([x["k"], float("%.3e" % x["err"]),
+                                        float("%.3e" % _factored_rel_err(U, sig, V, inst.P, inst.Q))])
+                        if code == P.OK or not st:
+                            break
+                    entry["per_iteration_k_err_Lerr"] = per
+                sec[prec] = entry
+        out[name] = sec
+        del D, inst
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +529,7 @@ def main():
         extras["unfused_iteration_ms"] = round(unfused_iteration_ms(D, p, solver), 3)
         extras["learned_schedule"] = learned_section(dev)
         extras["video_shaped"] = video_section(dev)
+        extras["precision_modes"] = precision_section(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
