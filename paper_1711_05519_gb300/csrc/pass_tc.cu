@@ -13,11 +13,12 @@
 //
 // Per tile (RK = 8 for R <= 8, RK = 16 for R <= 16: the operand image layout, tc_images.cuh):
 //   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, or one 128 x 64 bf16 box per part,
-//                      128-byte swizzle) plus the operand images of V (tf32 hi/lo), V~ and U~
-//                      (bf16 hi/lo) -> stage s (4 stages for RK = 8, 3 for RK = 16)
+//                      128-byte swizzle) plus the operand images of V (tf32 hi/lo) and V~
+//                      (bf16 hi/lo) -> stage s (5 stages for RK = 8, 4 for RK = 16); the W
+//                      and U~ images once per 128-row block (double-buffered)
 //   L MMAs (warp 1)  : L = W_hi V_hi^T + W_hi V_lo^T + W_lo V_hi^T, kind::tf32, M128 N64,
-//                      3 (RK = 8) or 6 (RK = 16) k-steps of 8 (three-term split product:
-//                      FP32-level accuracy of the K = r rebuild)
+//                      3 (RK = 8) or 6 (RK = 16) k-steps of 8 over the [hi | lo] images
+//                      (three-term split product: FP32-level accuracy of the K = r rebuild)
 //   epilogue (16 warps, two groups of 8 on alternate tiles): L from TMEM, D from shared
 //                      memory, threshold, residual, support count, Z split into bf16 hi + lo,
 //                      written K-major 128B-swizzled over the D tile it came from (Z_hi over
@@ -47,7 +48,7 @@ constexpr int BM = img::BM, BN = img::BN;
 constexpr int D_BYTES = BM * BN * 4;          // 32 KB: FP32 tile, or bf16 hi + lo tiles
 constexpr int Z_BYTES = 2 * BM * BN * 2;      // hi + lo, 32 KB, in place of the D tile
 constexpr int OFF_STAGE = 0;
-constexpr int NBAR = 96;
+constexpr int NBAR = 112;
 constexpr int G2 = kTcY2Chunk;  // row tiles per Y2 accumulation chunk
 constexpr int CT_BARS = 20;     // column tiles per CTA with their own Y2 chunk barriers
 constexpr int EPI_WARPS = 16;
@@ -60,24 +61,29 @@ static_assert(Z_BYTES == D_BYTES, "Z replaces the D tile");
 template <int RK>
 struct Cfg {
   using Lay = img::Layout<RK>;
-  static constexpr int NSTAGE = RK == 8 ? 4 : 3;
-  static constexpr int VOP_BYTES = Lay::VOP_BYTES;    // 8 / 16 KB tf32
-  static constexpr int VTOP_BYTES = Lay::VTOP_BYTES;  // 2 / 4 KB  [2RK x 64] bf16
-  static constexpr int UTOP_BYTES = Lay::UTOP_BYTES;  // 4 / 8 KB  2 x [2RK x 64] bf16
-  static constexpr int WOP_BYTES = Lay::WOP_BYTES;    // 16 KB     [128 x 32] tf32
-  static constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES + UTOP_BYTES;  // 46 / 60 KB
-  static constexpr int OFF_W = NSTAGE * STAGE_BYTES;
-  static constexpr int OFF_BAR = OFF_W + 2 * WOP_BYTES;
+  static constexpr int NSTAGE = RK == 8 ? 5 : 4;
+  static constexpr int VOP_BYTES = Lay::VOP_BYTES;    // 4 / 8 KB   [64 x 2RK] tf32
+  static constexpr int VTOP_BYTES = Lay::VTOP_BYTES;  // 2 / 4 KB   [2RK x 64] bf16
+  static constexpr int UTOP_BYTES = Lay::UTOP_BYTES;  // 4 / 8 KB   2 x [2RK x 64] bf16
+  static constexpr int WOP_BYTES = Lay::WOP_BYTES;    // 8 / 16 KB  [128 x 2RK] tf32
+  static constexpr int STAGE_BYTES = D_BYTES + VOP_BYTES + VTOP_BYTES;  // 38 / 44 KB
+  static constexpr int OFF_W = NSTAGE * STAGE_BYTES;  // [2] W images
+  static constexpr int OFF_U = OFF_W + 2 * WOP_BYTES;  // [2] U~ images
+  static constexpr int OFF_BAR = OFF_U + 2 * UTOP_BYTES;
   static constexpr int SMEM_BYTES = OFF_BAR + NBAR * 8 + 256 + 1024;  // + alignment slack
+  // W and V images: 64-byte rows with the 64-byte swizzle (RK = 8) or 128-byte rows with the
+  // 128-byte swizzle; 8-row groups SBO apart; descriptor swizzle codes 4 and 2
+  static constexpr uint32_t TF_SBO = 8 * Lay::ROW_BYTES, TF_SWZ = RK == 8 ? 4 : 2;
   static constexpr int NY = 2 * RK;                   // Y accumulator columns: hi and lo halves
   static constexpr int LK = RK == 8 ? 3 : 6;          // k-steps of the L product
   static constexpr int TM_Y1 = 2 * BN, TM_Y2 = TM_Y1 + 2 * NY;
   static constexpr int MAX_CT = (TMEM_COLS - TM_Y2) / NY;  // column tiles whose Y2 fits in TMEM
-  static_assert(STAGE_BYTES % 1024 == 0 && OFF_W % 1024 == 0, "1024-byte aligned operands");
-  static_assert((D_BYTES + VOP_BYTES) % 1024 == 0 && (D_BYTES + VOP_BYTES + VTOP_BYTES) % 1024 == 0,
-                "1024-byte aligned images");
+  static_assert(STAGE_BYTES % 1024 == 0 && OFF_W % 1024 == 0 && OFF_U % 1024 == 0 && WOP_BYTES % 1024 == 0 &&
+                    UTOP_BYTES % 1024 == 0,
+                "1024-byte aligned operands");
+  static_assert((D_BYTES + VOP_BYTES) % 1024 == 0, "1024-byte aligned images");
   static_assert(SMEM_BYTES <= 232448, "shared memory");
-  static_assert(NSTAGE <= 4, "barrier slots");
+  static_assert(NSTAGE <= 8, "barrier slots");
   // the Y2 drain uses the idle stages as [column tile][128][RK] FP32 scratch
   static_assert(MAX_CT * BM * RK * 4 <= NSTAGE * STAGE_BYTES, "Y2 drain scratch");
   static_assert(CT_BARS >= (RK == 8 ? 20 : 10), "Y2 chunk barriers for tc_max_col_tiles");
@@ -85,24 +91,24 @@ struct Cfg {
 
 // barrier slots
 enum {
-  B_FULL = 0,      // [NSTAGE]
-  B_EMPTY = 4,     // [NSTAGE]
-  B_ZFULL = 8,     // [NSTAGE]
-  B_LFULL = 12,    // [2]
-  B_LEMPTY = 14,   // [2]
-  B_WFULL = 16,    // [2]
-  B_WEMPTY = 18,   // [2]
-  B_Y1FULL = 20,   // [2]
-  B_Y1EMPTY = 22,  // [2]
-  B_YFIN = 24,
-  B_DRAIN = 25,
-  B_DREAD = 26,    // [NSTAGE][4]: the warps of lane quarter q have read their D values
-  B_LDRAIN = 42,
-  B_Y1DRAIN = 43,
-  B_Y2DONE = 44,   // [CT_BARS]: the MMAs of a non-final Y2 chunk of column tile ctl completed
-  B_Y2FREE = 64    // [CT_BARS]: that chunk has been read out of tensor memory
+  B_FULL = 0,      // [NSTAGE <= 8]
+  B_EMPTY = 8,     // [NSTAGE]
+  B_ZFULL = 16,    // [NSTAGE]
+  B_LFULL = 24,    // [2]
+  B_LEMPTY = 26,   // [2]
+  B_WFULL = 28,    // [2] W and U~ images of a 128-row block
+  B_WEMPTY = 30,   // [2] released by the last L and the last Y2 products of the block
+  B_Y1FULL = 32,   // [2]
+  B_Y1EMPTY = 34,  // [2]
+  B_YFIN = 36,
+  B_DRAIN = 37,
+  B_DREAD = 38,    // [NSTAGE][4]: the warps of lane quarter q have read their D values
+  B_LDRAIN = 70,
+  B_Y1DRAIN = 71,
+  B_Y2DONE = 72,   // [CT_BARS]: the MMAs of a non-final Y2 chunk of column tile ctl completed
+  B_Y2FREE = 92    // [CT_BARS]: that chunk has been read out of tensor memory
 };
-static_assert(B_DREAD + 4 * 4 <= B_LDRAIN && B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
+static_assert(B_DREAD + 4 * 8 <= B_LDRAIN && B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -145,7 +151,8 @@ template <int DM, int RK>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap,
                                                             const __grid_constant__ CUtensorMap dmap_lo, TcArgs a) {
   using C = Cfg<RK>;
-  constexpr int NSTAGE = C::NSTAGE, STAGE_BYTES = C::STAGE_BYTES, OFF_W = C::OFF_W, OFF_BAR = C::OFF_BAR;
+  constexpr int NSTAGE = C::NSTAGE, STAGE_BYTES = C::STAGE_BYTES, OFF_W = C::OFF_W, OFF_U = C::OFF_U;
+  constexpr int OFF_BAR = C::OFF_BAR;
   constexpr int VOP_BYTES = C::VOP_BYTES, VTOP_BYTES = C::VTOP_BYTES, UTOP_BYTES = C::UTOP_BYTES;
   constexpr int WOP_BYTES = C::WOP_BYTES, NY = C::NY, TM_Y1 = C::TM_Y1, TM_Y2 = C::TM_Y2;
   if (a.st->done) return;
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       mbar_init(&bar[B_LFULL + i], 1);
       mbar_init(&bar[B_LEMPTY + i], EPI_WARPS / 2);
       mbar_init(&bar[B_WFULL + i], 1);
-      mbar_init(&bar[B_WEMPTY + i], 1);
+      mbar_init(&bar[B_WEMPTY + i], 2);  // L and Y2 issuers
       mbar_init(&bar[B_Y1FULL + i], 1);
       mbar_init(&bar[B_Y1EMPTY + i], 4);
     }
@@ -219,8 +226,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           fail(a, &abort_flag);
           break;
         }
-        mbar_arrive_expect_tx(&bar[B_WFULL + wb], WOP_BYTES);
+        mbar_arrive_expect_tx(&bar[B_WFULL + wb], WOP_BYTES + UTOP_BYTES);
         bulk_load(sm + OFF_W + wb * WOP_BYTES, a.wop + (size_t)rt * WOP_BYTES, WOP_BYTES, &bar[B_WFULL + wb]);
+        bulk_load(sm + OFF_U + wb * UTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES, &bar[B_WFULL + wb]);
       }
       if (t >= NSTAGE && !mbar_wait(&bar[B_EMPTY + s], ((t - NSTAGE) / NSTAGE) & 1)) {
         fail(a, &abort_flag);
@@ -238,8 +246,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
       bulk_load(st + D_BYTES, a.vop + (size_t)ct * VOP_BYTES, VOP_BYTES, &bar[B_FULL + s]);
       bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
-      bulk_load(st + D_BYTES + VOP_BYTES + VTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES,
-                &bar[B_FULL + s]);
       issued = t + 1;
     }
     // wait (bounded) for this thread's copies still in flight before the CTA may exit
@@ -249,8 +255,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // ------------------------------------------------------------------ L MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idL = instr_desc(128, 64, 2, 2, false, false);
-    const uint64_t dw0 = smem_desc(base + OFF_W, 16, 1024);
-    const uint64_t dv0 = smem_desc(base + OFF_STAGE + D_BYTES, 16, 1024);
+    const uint64_t dw0 = smem_desc(base + OFF_W, 16, C::TF_SBO, C::TF_SWZ);
+    const uint64_t dv0 = smem_desc(base + OFF_STAGE + D_BYTES, 16, C::TF_SBO, C::TF_SWZ);
     int rtl = 0, ctl = 0;
     for (int t = 0; t < ntiles && !abort_flag; ++t, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
       const int s = t % NSTAGE, lb = t & 1, wb = rtl & 1;
@@ -265,16 +271,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_after();
       const uint64_t dw = dw0 + (uint64_t)(wb * (WOP_BYTES >> 4));
       const uint64_t dv = dv0 + (uint64_t)(s * (STAGE_BYTES >> 4));
-      if (RK == 8) {
+      // k-steps of 8 (32 bytes = 2 descriptor units): hi blocks at 0, lo blocks at 2 RK / 8 x 2
+      constexpr int LO = RK / 4;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);  // 4th k-block is zero
-      } else {
-        // [W_hi W_lo] . [V_hi V_hi] over the first column block, then W_hi . V_lo (second block)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) mma_tf32(tmem + lb * BN, dw + 2 * k, dv + 2 * k, idL, k > 0);
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-          mma_tf32(tmem + lb * BN, dw + 2 * k, dv + ((BN * 128) >> 4) + 2 * k, idL, true);
+      for (int kb = 0; kb < RK / 8; ++kb) {
+        mma_tf32(tmem + lb * BN, dw + 2 * kb, dv + 2 * kb, idL, kb > 0);            // W_hi V_hi
+        mma_tf32(tmem + lb * BN, dw + 2 * kb, dv + LO + 2 * kb, idL, true);         // W_hi V_lo
+        mma_tf32(tmem + lb * BN, dw + LO + 2 * kb, dv + 2 * kb, idL, true);         // W_lo V_hi
       }
       mma_commit(&bar[B_LFULL + lb]);
       if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
@@ -314,14 +317,16 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const uint32_t base = smem_u32(sm);
     const uint32_t idY2 = instr_desc(128, NY, 1, 1, true, false);
     const uint64_t dzm0 = smem_desc(base + OFF_STAGE, Z_BYTES / 2, 1024);
-    const uint64_t dut0 = smem_desc(base + OFF_STAGE + D_BYTES + VOP_BYTES + VTOP_BYTES, 16, 1024);
+    const uint64_t dut0 = smem_desc(base + OFF_U, 16, 1024);
     int rtl = 0, ctl = 0;
     for (int tp = 0; tp < ntiles && !abort_flag; ++tp, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
       const int s = tp % NSTAGE;
       // a Y2 accumulator restarts every G2 row tiles (the tensor-core accumulation of a long
       // chain of products drifts); the epilogue has read the previous chunk out first
       const bool restart = rtl % G2 == 0;
+      const int wb = rtl & 1;
       bool ok = mbar_wait(&bar[B_ZFULL + s], (tp / NSTAGE) & 1);
+      if (ok && ctl == 0) ok = mbar_wait(&bar[B_WFULL + wb], (rtl >> 1) & 1);  // U~ image of the block
       if (ok && restart && rtl > 0) ok = mbar_wait(&bar[B_Y2FREE + ctl], ((rtl / G2) - 1) & 1);
       if (!ok) {
         fail(a, &abort_flag);
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
       tc_fence_after();
       const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
-      const uint64_t dzm = dzm0 + so, dut = dut0 + so;
+      const uint64_t dzm = dzm0 + so, dut = dut0 + (uint64_t)(wb * (UTOP_BYTES >> 4));
       const uint32_t y2 = tmem + TM_Y2 + ctl * NY;
 #pragma unroll
       for (int k = 0; k < 8; ++k)
@@ -337,6 +342,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
                 !(restart && k == 0));
       mma_commit(&bar[B_EMPTY + s]);
       if (rtl % G2 == G2 - 1 && rtl != nrt - 1) mma_commit(&bar[B_Y2DONE + ctl]);
+      if (ctl == nct - 1) mma_commit(&bar[B_WEMPTY + wb]);
     }
     mma_commit(&bar[B_YFIN]);
     mma_commit(&bar[B_DRAIN]);
