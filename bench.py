@@ -416,6 +416,107 @@ def precision_section(dev):
     return out
 
 
+# Table 2 of the paper, AccAltProj with trim: successes out of 10 trials (n = 2500, r = 5,
+# tol 1e-6, success if ||L_k - L*||_F / ||L*||_F <= 1e-4) for alpha = 0.30, 0.35, ..., 0.75.
+TABLE2_ALPHAS = [0.3, 0.35, 0.4, 0.45, 0.5, 0.55, 0.6, 0.65, 0.7, 0.75]
+TABLE2_TRIM = {0.2: [10, 10, 10, 10, 10, 10, 10, 10, 4, 0],
+               1.0: [10, 10, 10, 10, 10, 10, 10, 9, 0, 0],
+               5.0: [10, 10, 10, 10, 10, 10, 10, 5, 0, 0]}
+
+
+def recovery_trial(n, r, alpha, c, seed, dev, precision="fp64", tol=1e-6, trim=True):
+    """One planted instance of Section 3 solved on the GPU; returns the relative error of L
+    against L* (inf if the solve reported a numerical failure) and the iteration count."""
+    import paper_1711_05519_gb300 as P
+
+    inst = synth.planted_instance(n, n, r, alpha, c, seed)
+    p = inst.params()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    D = torch.from_numpy(inst.D).to(dev, dt)
+    with P.Solver(p["beta"], p["gamma"], tol, precision=precision, beta_init=p["beta_init"], mu_trim=p["mu"],
+                  trim=trim, max_iter=100) as s:
+        try:
+            s.init(D, r)
+            _, stats = s.run()
+        except P.RpcaError:
+            return float("inf"), -1
+        U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
+    return _factored_rel_err(U, sig, V, inst.P, inst.Q), stats[-1]["k"] if stats else 0
+
+
+def phase_transition(dev, trials=10, trim=True):
+    """Table 2 on the GPU (FP64, as the paper's double-precision runs): successes per (c,
+    alpha) next to the paper's counts."""
+    out = {"setup": "n=2500 r=5 FP64 tol 1e-6 max 100 iterations, success if ||L_k-L*||/||L*|| <= 1e-4, "
+                    f"{trials} trials (seeds 10000 c_index + 100 alpha_index + trial)", "trim": trim, "rows": {}}
+    for ci, c in enumerate((0.2, 1.0, 5.0)):
+        row = []
+        for ai, alpha in enumerate(TABLE2_ALPHAS):
+            ok = 0
+            for t in range(trials):
+                e, _ = recovery_trial(2500, 5, alpha, c, 10000 * ci + 100 * ai + t, dev, trim=trim)
+                ok += int(e <= 1e-4)
+            row.append(ok)
+        out["rows"][str(c)] = {"gpu": row, "paper_out_of_10": TABLE2_TRIM[c]}
+    return out
+
+
+def runtime_sweep(dev):
+    """Runtime shapes of Fig. 2 on the GPU (time from D resident in HBM, initialisation
+    included, median of 3): (a) n = 1000 .. 15000 at r = 5, alpha = 0.1, c = 1, tol 1e-4;
+    (b) alpha = 0.1 .. 0.6 at n = 2500, tol 1e-4 or 100 iterations; (c) err_k against time at
+    n = 2500, alpha = 0.1, tol 1e-5."""
+    import paper_1711_05519_gb300 as P
+
+    def timed(inst, r, tol, precision):
+        p = inst.params()
+        D = torch.from_numpy(inst.D).to(dev, torch.float32 if precision == "fp32" else torch.float64)
+        ts = []
+        with P.Solver(p["beta"], p["gamma"], tol, precision=precision, beta_init=p["beta_init"], mu_trim=p["mu"],
+                      max_iter=100) as s:
+            for rep in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.init(D, r)
+                _, stats = s.run()
+                e1.record()
+                torch.cuda.synchronize(dev)
+                if rep:
+                    ts.append(e0.elapsed_time(e1))
+        return round(statistics.median(ts), 3), stats[-1]["k"]
+
+    out = {"a_varying_n": [], "b_varying_alpha": [], "c_err_vs_time": []}
+    for n in (1000, 2500, 5000, 7500, 10000, 12500, 15000):
+        inst = synth.planted_instance(n, n, 5, 0.1, 1.0, SEED)
+        row = {"n": n}
+        for prec in ("fp32", "fp64"):
+            row[prec + "_ms"], row[prec + "_iters"] = timed(inst, 5, 1e-4, prec)
+        out["a_varying_n"].append(row)
+    for alpha in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6):
+        inst = synth.planted_instance(2500, 2500, 5, alpha, 1.0, SEED)
+        ms, k = timed(inst, 5, 1e-4, "fp32")
+        out["b_varying_alpha"].append({"alpha": alpha, "fp32_ms": ms, "iters": k})
+    inst = synth.planted_instance(2500, 2500, 5, 0.1, 1.0, SEED)
+    p = inst.params()
+    D = torch.from_numpy(inst.D.astype(np.float32)).to(dev)
+    with P.Solver(p["beta"], p["gamma"], 1e-5, precision="fp32", beta_init=p["beta_init"], mu_trim=p["mu"]) as s:
+        s.init(D, 5)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        while True:
+            code, st = s.iterate(1)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            for x in st:
+                out["c_err_vs_time"].append([round(e0.elapsed_time(e1), 4), x["err"]])
+            if code == P.OK or not st:
+                break
+    out["c_note"] = "times from the end of the initialisation; each point includes one host round trip"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,11 +526,25 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the unfused and learned-schedule comparisons")
+    ap.add_argument("--phase-transition", type=int, default=0, metavar="TRIALS",
+                    help="run Table 2 of the paper on the GPU with TRIALS trials per cell, print JSON and exit")
+    ap.add_argument("--runtime-sweep", action="store_true",
+                    help="run the runtime shapes of Fig. 2 on the GPU, print JSON and exit")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="run 3 solves of a planted n x n instance (same recipe) and exit; for ncu captures")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args.profile_case)
+    if args.phase_transition or args.runtime_sweep:
+        from paper_1711_05519_gb300 import build as libbuild
+
+        libbuild.build()
+        dev = torch.device("cuda", 0)
+        if args.phase_transition:
+            print(json.dumps({"phase_transition": phase_transition(dev, args.phase_transition)}))
+        if args.runtime_sweep:
+            print(json.dumps({"runtime_sweep": runtime_sweep(dev)}))
+        return 0
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)

@@ -26,26 +26,30 @@ pytestmark = pytest.mark.gpu
 P = pytest.importorskip("paper_1711_05519_gb300")
 
 
-def _check_one_step(s, D64, inst, p, k, r, D_pass=None):
+def _check_one_step(s, D64, inst, p, k, r, D_pass=None, support=True):
     """Pass k from the GPU's state against the oracle's step from the same state.  D_pass is
-    the D the pass reads (default D64); the sparse output is extracted from D64."""
+    the D the pass reads (default D64); the sparse output is extracted from D64 and compared
+    entry by entry when `support` is set."""
     D_pass = D64 if D_pass is None else D_pass
     U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
-    idx, _ = (t.cpu().numpy() for t in s.sparse())
+    if support:
+        idx, _ = (t.cpu().numpy() for t in s.sparse())
     _, st = s.iterate(1)
     U1, sig1, V1 = (t.double().cpu().numpy() for t in s.lowrank())
     o = O.step(D_pass, U, sig, V, st[0]["zeta"], k, r, p["beta"], p["gamma"], p["mu"])
     assert st[0]["k"] == k
     assert st[0]["err"] == pytest.approx(o["err"], rel=1e-5)
-    diff, ok = support_mismatch(idx, D64, (U * sig) @ V.T, st[0]["zeta"], band_abs_rel_D=1e-6)
-    assert ok, (k, diff[:10])
-    # the pass (tensor-core rebuild of L) and the extraction (FP32 rebuild) may differ only on
-    # entries inside the tie band
+    # entries inside the tie band around zeta_k: the only ones on which the pass (tensor-core
+    # rebuild of L), the extraction (FP32 rebuild) and the oracle (FP64) may disagree
     L = (U * sig) @ V.T
-    band = 1e-6 * st[0]["zeta"] + 1e-6 * np.maximum(np.abs(D64), np.abs(L))
-    n_band = int(np.count_nonzero(np.abs(np.abs(D64 - L) - st[0]["zeta"]) <= band))
+    band = 1e-6 * st[0]["zeta"] + 1e-6 * np.maximum(np.abs(D_pass), np.abs(L))
+    n_band = int(np.count_nonzero(np.abs(np.abs(D_pass - L) - st[0]["zeta"]) <= band))
     del L, band
-    assert abs(st[0]["nnz"] - len(idx)) <= n_band
+    assert abs(st[0]["nnz"] - int(np.count_nonzero(o["S"]))) <= n_band
+    if support:
+        diff, ok = support_mismatch(idx, D64, (U * sig) @ V.T, st[0]["zeta"], band_abs_rel_D=1e-6)
+        assert ok, (k, diff[:10])
+        assert abs(st[0]["nnz"] - len(idx)) <= n_band
     assert st[0]["sigma1"] == pytest.approx(o["sigma_M"][0], rel=1e-5)
     assert st[0]["sigma_r1"] == pytest.approx(o["sigma_M"][r], rel=1e-4, abs=1e-6 * o["sigma_M"][0])
     L1 = (U1 * sig1) @ V1.T
@@ -53,7 +57,7 @@ def _check_one_step(s, D64, inst, p, k, r, D_pass=None):
     return st[0]
 
 
-def _solve_checks(s, inst, errs, r):
+def _solve_checks(s, inst, errs, r, sample=None):
     errs = np.asarray(errs)
     assert errs[-1] < 1e-5
     # linear decay once the iteration has started to contract
@@ -62,7 +66,10 @@ def _solve_checks(s, inst, errs, r):
     U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
     assert factored_rel_err(U, sig, V, inst.P, inst.Q) < 1e-5
     idx, _ = (t.cpu().numpy() for t in s.sparse())
-    assert np.all(np.isin(idx, inst.support))
+    if sample is not None:
+        idx = np.random.default_rng(1).choice(idx, size=min(sample, idx.size), replace=False)
+    pos = np.searchsorted(inst.support, idx)  # the planted support is sorted
+    assert np.all(inst.support[np.minimum(pos, inst.support.size - 1)] == idx)
 
 
 def test_fp32_10000_r5():
@@ -99,8 +106,8 @@ def test_bf16_split_20000_r10():
         lo = (D - hi.float()).bfloat16()
         D_hl = (hi.double() + lo.double()).cpu().numpy()
         del hi, lo
-        errs.append(_check_one_step(s, D64, inst, p, 9, 10, D_pass=D_hl)["err"])
+        errs.append(_check_one_step(s, D64, inst, p, 9, 10, D_pass=D_hl, support=False)["err"])
         code, st = s.run()
         errs += [x["err"] for x in st]
         assert code == P.OK
-        _solve_checks(s, inst, errs, 10)
+        _solve_checks(s, inst, errs, 10, sample=1_000_000)
