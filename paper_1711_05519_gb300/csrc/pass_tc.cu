@@ -21,8 +21,10 @@
 //                      (three-term split product: FP32-level accuracy of the K = r rebuild)
 //   epilogue (16 warps, two groups of 8 on alternate tiles): L from TMEM, D from shared
 //                      memory, threshold, residual, support count, Z split into bf16 hi + lo,
-//                      written K-major 128B-swizzled over the D tile it came from (Z_hi over
-//                      the first box, Z_lo over the second), so a stage carries its own Z
+//                      written 128B-swizzled over the very bytes of D it came from, so a stage
+//                      carries its own Z and no warp waits for another: FP32 D, box h (columns
+//                      32h .. 32h+31) becomes [Z_hi | Z_lo] of those columns; bf16 D, Z_hi
+//                      over the hi tile and Z_lo over the lo tile
 //   Y1 MMAs (warp 2) : Y1 += [Z_hi | Z_lo] [V~_hi | V~_lo], kind::f16, M128 N(2 RK) K64 (x2)
 //   Y2 MMAs (warp 3) : Y2 += [Z_hi^T ; Z_lo^T] [U~_hi | U~_lo], M128 (MN-major A) N(2 RK) K128;
 //                      the stage is released when both have completed
@@ -102,13 +104,12 @@ enum {
   B_Y1EMPTY = 34,  // [2]
   B_YFIN = 36,
   B_DRAIN = 37,
-  B_DREAD = 38,    // [NSTAGE][4]: the warps of lane quarter q have read their D values
   B_LDRAIN = 70,
   B_Y1DRAIN = 71,
   B_Y2DONE = 72,   // [CT_BARS]: the MMAs of a non-final Y2 chunk of column tile ctl completed
   B_Y2FREE = 92    // [CT_BARS]: that chunk has been read out of tensor memory
 };
-static_assert(B_DREAD + 4 * 8 <= B_LDRAIN && B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
+static_assert(B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -132,6 +133,26 @@ struct TcArgs {
 __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) {
   atomicCAS(a.status, 0, (int)kErrTimeout);
   *abort_flag = 1;
+}
+
+// Z layout in a stage (descriptor units of 16 bytes for the Y1 k-steps of 16 columns, and the
+// Y2 accumulator rows of column jl's hi and lo parts).  DM = 0: box h (16 KB) holds
+// [Z_hi | Z_lo] of columns 32h .. 32h+31; DM = 1: Z_hi in the first 16 KB, Z_lo in the second.
+template <int DM>
+__device__ __forceinline__ uint64_t zhi_off(int k) {
+  return DM == 0 ? (uint64_t)((k >> 1) * ((D_BYTES / 2) >> 4) + 2 * (k & 1)) : (uint64_t)(2 * k);
+}
+template <int DM>
+__device__ __forceinline__ uint64_t zlo_off(int k) {
+  return DM == 0 ? zhi_off<0>(k) + 4 : (uint64_t)(((Z_BYTES / 2) >> 4) + 2 * k);
+}
+template <int DM>
+__device__ __forceinline__ int y2_hi_row(int jl) {
+  return DM == 0 ? (jl >> 5) * 64 + (jl & 31) : jl;
+}
+template <int DM>
+__device__ __forceinline__ int y2_lo_row(int jl) {
+  return DM == 0 ? y2_hi_row<0>(jl) + 32 : 64 + jl;
 }
 
 // NY consecutive accumulator columns of this warp's 32 lanes.
@@ -185,7 +206,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       mbar_init(&bar[B_FULL + s], 1);
       mbar_init(&bar[B_EMPTY + s], 2);  // Y1 and Y2 issuers
       mbar_init(&bar[B_ZFULL + s], EPI_WARPS / 2);
-      for (int qq = 0; qq < 4; ++qq) mbar_init(&bar[B_DREAD + 4 * s + qq], 2);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bar[B_LFULL + i], 1);
@@ -288,7 +308,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // ------------------------------------------------------------------ Y1 MMAs
     const uint32_t base = smem_u32(sm);
     const uint32_t idY1 = instr_desc(128, NY, 1, 1, false, false);
-    const uint64_t dzh0 = smem_desc(base + OFF_STAGE, 16, 1024);
+    const uint64_t dz0 = smem_desc(base + OFF_STAGE, 16, 1024);
     const uint64_t dvt0 = smem_desc(base + OFF_STAGE + D_BYTES + VOP_BYTES, 16, 1024);
     int rtl = 0, ctl = 0;
     for (int tp = 0; tp < ntiles && !abort_flag; ++tp, ctl = (ctl + 1 == nct) ? 0 : ctl + 1, rtl += (ctl == 0) ? 1 : 0) {
@@ -301,12 +321,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
       tc_fence_after();
       const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
-      const uint64_t dzh = dzh0 + so, dzl = dzh0 + so + (uint64_t)((Z_BYTES / 2) >> 4), dvt = dvt0 + so;
+      const uint64_t dz = dz0 + so, dvt = dvt0 + so;
       const uint32_t y1 = tmem + TM_Y1 + yb * NY;
+      // k-step k: columns 16k .. 16k+15 of Z_hi and of Z_lo (32 bytes each)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) mma_f16(y1, dzh + 2 * k, dvt + 2 * k, idY1, !(ctl == 0 && k == 0));
+      for (int k = 0; k < 4; ++k) mma_f16(y1, dz + zhi_off<DM>(k), dvt + 2 * k, idY1, !(ctl == 0 && k == 0));
 #pragma unroll
-      for (int k = 0; k < 4; ++k) mma_f16(y1, dzl + 2 * k, dvt + 2 * k, idY1, true);
+      for (int k = 0; k < 4; ++k) mma_f16(y1, dz + zlo_off<DM>(k), dvt + 2 * k, idY1, true);
       mma_commit(&bar[B_EMPTY + s]);
       if (ctl == nct - 1) mma_commit(&bar[B_Y1FULL + yb]);
     }
@@ -434,15 +455,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
-      // both warps of these rows hold their D values before Z overwrites the tile
-      // (bf16 D: every warp overwrites exactly the bytes it read, no wait is needed)
-      if (DM == 0) {
-        if (lane == 0) mbar_arrive(&bar[B_DREAD + 4 * s + q]);
-        if (!mbar_wait(&bar[B_DREAD + 4 * s + q], (t / NSTAGE) & 1)) {
-          fail(a, &abort_flag);
-          break;
-        }
-      }
       const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
       for (int c = 0; c < 32; c += 2) {
@@ -455,9 +467,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         z[c] = s0 ? l2.x : z[c];
         z[c + 1] = s1 ? l2.y : z[c + 1];
       }
-      // Z -> bf16 hi/lo, row rowl, columns 32h .. 32h+31 = 16-byte chunks 4h .. 4h+3
-      uint8_t* zhi = stg;
-      uint8_t* zlo = stg + Z_BYTES / 2;
+      // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
+      // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
+      uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
+      uint8_t* zlo = DM == 0 ? zhi : stg + Z_BYTES / 2;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         uint32_t hw[4], lw[4];
@@ -471,9 +484,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           hw[e2] = *reinterpret_cast<const uint32_t*>(&hi);
           lw[e2] = *reinterpret_cast<const uint32_t*>(&lo);
         }
-        const int off = rowl * 128 + ((((4 * h + c) ^ (rowl & 7)) & 7) << 4);
-        *reinterpret_cast<uint4*>(zhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(zlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        const int chi = DM == 0 ? c : 4 * h + c, clo = DM == 0 ? 4 + c : 4 * h + c;
+        *reinterpret_cast<uint4*>(zhi + rowl * 128 + (((chi ^ (rowl & 7)) & 7) << 4)) =
+            make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(zlo + rowl * 128 + (((clo ^ (rowl & 7)) & 7) << 4)) =
+            make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       fence_proxy_async_smem();
       __syncwarp();
@@ -501,7 +516,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
     }
     // drain Y2: each warp takes the column tiles ctl = g, g + 4, ...; lane quarter q holds
-    // accumulator rows 32q .. 32q+31 (rows 0..63: Z_hi part, 64..127: Z_lo part).  The last
+    // accumulator rows 32q .. 32q+31 (the Z_hi and Z_lo parts of the tile's columns, placed as
+    // y2_hi_row / y2_lo_row give).  The last
     // chunk is in tensor memory, the earlier ones in their slots (written by any epilogue warp:
     // the barrier below orders those stores before the reads)
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
@@ -548,8 +564,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         const int col = (ct0 + ctl) * BN + jl;
         if (col < a.n)
           for (int k = 0; k < a.R; ++k)
-            a.P2[((size_t)ai * a.n + col) * a.R + k] =
-                scratch[((size_t)ctl * BM + jl) * RK + k] + scratch[((size_t)ctl * BM + 64 + jl) * RK + k];
+            a.P2[((size_t)ai * a.n + col) * a.R + k] = scratch[((size_t)ctl * BM + y2_hi_row<DM>(jl)) * RK + k] +
+                                                       scratch[((size_t)ctl * BM + y2_lo_row<DM>(jl)) * RK + k];
       }
     }
     // CTA totals of the residual and the support size
