@@ -82,7 +82,16 @@ struct rpca_ctx {
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_free;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pass, ev_other;
+  // profiling timeline: events at kernel boundaries (a kernel's end event is the next
+  // kernel's begin event while nothing else was queued in between) and the intervals
+  // {begin index, end index, is-pass} between them
+  struct Span {
+    int b, e;
+    bool pass;
+  };
+  std::vector<cudaEvent_t> ev_line;
+  std::vector<Span> spans;
+  bool line_open = false;
   double pass_ms = 0, other_ms = 0;
   int64_t pass_n = 0, other_n = 0;
 };
@@ -121,57 +130,52 @@ cudaEvent_t take_event(rpca_ctx* c) {
   return e;
 }
 
-// Event pair around one launch: call with begin=true before and begin=false after.
+// Marks the start (begin = true) or the end of one profiled launch.
 void prof_mark(rpca_ctx* c, bool pass, bool begin) {
   if (!c->prof) return;
-  auto& v = pass ? c->ev_pass : c->ev_other;
-  cudaEvent_t e = take_event(c);
-  cudaEventRecord(e, c->stream);
-  if (begin)
-    v.push_back({e, nullptr});
-  else
-    v.back().second = e;
+  if (begin) {
+    if (!c->line_open) {
+      cudaEvent_t e = take_event(c);
+      cudaEventRecord(e, c->stream);
+      c->ev_line.push_back(e);
+    }
+    c->spans.push_back({(int)c->ev_line.size() - 1, -1, pass});
+  } else {
+    cudaEvent_t e = take_event(c);
+    cudaEventRecord(e, c->stream);
+    c->ev_line.push_back(e);
+    c->spans.back().e = (int)c->ev_line.size() - 1;
+    c->line_open = true;
+  }
 }
 
-// Accumulates the recorded pairs (the stream must be synchronised); only the first
-// `effective_pass` pass pairs count (later ones were skipped on the device).
+// Something other than a profiled launch was queued (or the host waited): the next launch
+// starts a new span.
+void prof_break(rpca_ctx* c) { c->line_open = false; }
+
+// Accumulates the recorded spans (the stream must be synchronised).  Only the first
+// `effective_pass` pass spans count as passes: pass launches past that count returned at
+// once on the device and are counted with the other kernels, so the pass average covers
+// only passes that did work.
 void prof_collect(rpca_ctx* c, int64_t effective_pass) {
-  auto drain = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, double& ms, int64_t& n, int64_t lim) {
-    int64_t i = 0;
-    for (auto& pr : v) {
-      if (pr.second && (lim < 0 || i < lim)) {
-        float t = 0.f;
-        cudaEventElapsedTime(&t, pr.first, pr.second);
-        ms += t;
-        ++n;
-      }
-      ++i;
-      c->ev_free.push_back(pr.first);
-      if (pr.second) c->ev_free.push_back(pr.second);
+  int64_t ip = 0;
+  for (const auto& sp : c->spans) {
+    if (sp.e < 0) continue;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, c->ev_line[sp.b], c->ev_line[sp.e]);
+    if (sp.pass && (effective_pass < 0 || ip < effective_pass)) {
+      c->pass_ms += t;
+      ++c->pass_n;
+    } else {
+      c->other_ms += t;
+      ++c->other_n;
     }
-    v.clear();
-  };
-  // pass launches past the effective count returned at once on the device: they are
-  // counted with the other kernels so the pass average covers only passes that did work
-  int64_t i = 0;
-  for (auto& pr : c->ev_pass) {
-    if (pr.second) {
-      float t = 0.f;
-      cudaEventElapsedTime(&t, pr.first, pr.second);
-      if (effective_pass < 0 || i < effective_pass) {
-        c->pass_ms += t;
-        ++c->pass_n;
-      } else {
-        c->other_ms += t;
-        ++c->other_n;
-      }
-    }
-    ++i;
-    c->ev_free.push_back(pr.first);
-    if (pr.second) c->ev_free.push_back(pr.second);
+    if (sp.pass) ++ip;
   }
-  c->ev_pass.clear();
-  drain(c->ev_other, c->other_ms, c->other_n, -1);
+  for (cudaEvent_t e : c->ev_line) c->ev_free.push_back(e);
+  c->ev_line.clear();
+  c->spans.clear();
+  c->line_open = false;
 }
 
 struct Grid {
@@ -355,6 +359,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
 }
 
 int read_flags(rpca_ctx* c) {
+  prof_break(c);
   CK(cudaMemcpyAsync(c->h_flags, &c->st->k, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return RPCA_OK;
@@ -579,6 +584,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   // behind the final convergence return at once (DevState.done), so the host waits once per
   // batch.  Each phase accepts its step init_max_passes - 1 as converged, so 2 init_max_passes
   // steps always finish.
+  prof_break(c);
   SmallArgs ra = small_args(c, SM_RAND, c->Rb);
   if ((st = run_small(c, ra))) return st;
   const int cap = 2 * c->p.init_max_passes;
@@ -703,6 +709,7 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
   a.idx = (long long*)idx;
   a.val = val;
   a.vec = c->vec;
+  prof_break(c);
   prof_mark(c, false, true);
   CK(launch_extract_count(c->prec, c->Rr, a, c->stream));
   prof_mark(c, false, false);
@@ -713,6 +720,7 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
   CK(cudaMemcpyAsync(&total, c->rowoff + c->m, sizeof(total), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *nnz = (int64_t)total;
+  prof_break(c);
   if ((int64_t)total > cap) {
     prof_collect(c, 0);
     return RPCA_ERR_CAPACITY;
