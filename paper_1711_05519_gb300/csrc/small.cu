@@ -448,6 +448,26 @@ __device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_swee
   }
 }
 
+// Single-precision one-sided Jacobi on the columns of sc * M (N <= NJ <= NM) with V, in
+// registers sized NJ; results returned zero-padded to NM.
+template <int NJ, int NM, typename T>
+__device__ __forceinline__ void jacobi_f32_sized(int N, const T* M, T sc, const int* pairs, float (&x)[NM],
+                                                 float (&v)[NM]) {
+  const int lane = threadIdx.x & 31;
+  float xj[NJ], vj[NJ];
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) {
+    xj[i] = (lane < N && i < N) ? (float)(M[i * NM + lane] * sc) : 0.f;
+    vj[i] = (lane < N && i == lane) ? 1.f : 0.f;
+  }
+  jacobi_lanes<float, NJ>(N, xj, vj, 1e-11f, 12, pairs);
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    x[i] = i < NJ ? xj[i < NJ ? i : 0] : 0.f;
+    v[i] = i < NJ ? vj[i < NJ ? i : 0] : 0.f;
+  }
+}
+
 // SVD of the N x N matrix in sh.M (N <= NM), by warp 0 (other threads return at once).
 // On return sh.sig holds the singular values in descending order and sh.UM / sh.VM the
 // matching left / right singular vectors (a zero singular value gives a zero left vector).
@@ -466,13 +486,16 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
   const T sc = mx > T(0) ? T(1) / mx : T(1);
   float xf[NM], vf[NM];
-#pragma unroll
-  for (int i = 0; i < NM; ++i) {
-    xf[i] = (lane < N && i < N) ? (float)(sh.M[i * NM + lane] * sc) : 0.f;
-    vf[i] = (lane < N && i == lane) ? 1.f : 0.f;
-  }
-  // rotate until every pair of columns is orthogonal to ~3e-6
-  jacobi_lanes<float, NM>(N, xf, vf, 1e-11f, 12, sh.pairs);
+  // rotate until every pair of columns is orthogonal to ~3e-6, on registers sized to N
+  // (the padding entries are zero and would only add exact zeros)
+  if (N <= 8)
+    jacobi_f32_sized<8, NM>(N, sh.M, sc, sh.pairs, xf, vf);
+  else if (N <= 12)
+    jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.M, sc, sh.pairs, xf, vf);
+  else if (N <= 16 || NM <= 16)
+    jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.M, sc, sh.pairs, xf, vf);
+  else
+    jacobi_f32_sized<NM, NM>(N, sh.M, sc, sh.pairs, xf, vf);
   T sg;
   T y[NM], vd[NM];
   if (sizeof(T) == 8) {
