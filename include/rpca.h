@@ -84,10 +84,9 @@ typedef struct {
 } rpca_params;
 
 /* Kernel of the fused pass.  AUTO takes the tensor-core (tcgen05 + TMA) pass where it
- * applies (padded rank <= 8; FP32 with ld a multiple of 4 and D 16-byte aligned, or a BF16
- * mode) and the SIMT
- * pass otherwise; SIMT and TENSOR force one (TENSOR falls back to SIMT where it does not
- * apply). */
+ * applies (padded rank <= 16; FP32 with ld a multiple of 4 and D 16-byte aligned, or a BF16
+ * mode) and the SIMT pass otherwise; SIMT and TENSOR force one (TENSOR falls back to SIMT
+ * where it does not apply). */
 typedef enum { RPCA_PASS_AUTO = 0, RPCA_PASS_SIMT = 1, RPCA_PASS_TENSOR = 2 } rpca_pass_kind;
 
 typedef struct {
