@@ -158,10 +158,17 @@ int rpca_solve(const float* D, int64_t m, int64_t n, int r, double beta, double 
 
 /* As rpca_solve, with every array in HOST memory (D float32; outputs double/int64).  The
  * host-to-device copy of D and the device-to-host copies of the outputs are part of the
- * call. */
+ * call.  The device buffers, stream and context it needs are kept between calls (one set per
+ * process for the current device, grown when a call needs more) so that repeated calls do not
+ * allocate; calls are serialised by a lock.  A CUDA error frees the set; so does
+ * rpca_solve_host_release. */
 int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, double gamma,
                     double tol, double* U, double* sigma, double* V, int64_t* s_idx,
                     double* s_val, int64_t s_cap, int64_t* nnz, int* iters, double* err);
+
+/* Frees the device buffers, stream and context kept by rpca_solve_host (the next call
+ * allocates them again).  Not part of the paper's method. */
+void rpca_solve_host_release(void);
 
 /* ---------------------------------------------------------------------------------------
  * Learned threshold schedule: stateless pass and adjoint pass.

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -755,6 +756,29 @@ int rpca_get_profile(rpca_ctx* c, double* pass_ms, int64_t* pass_launches, doubl
   return RPCA_OK;
 }
 
+// init + iterate to tolerance + outputs on context c (parameters beta, gamma, tol set here).
+static int solve_on(rpca_ctx* c, const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol,
+                    double* U, double* sigma, double* V, int64_t* s_idx, double* s_val, int64_t s_cap, int64_t* nnz,
+                    int* iters, double* err) {
+  c->p.beta = beta;
+  c->p.gamma = gamma;
+  c->p.tol = tol;
+  int result = rpca_init(c, D, m, n, n, RPCA_DTYPE_F32, r);
+  if (!result) {
+    std::vector<rpca_iter_stats> hs((size_t)c->p.max_iter + 1);
+    int done = 0;
+    result = rpca_iterate(c, c->p.max_iter + 1, hs.data(), &done);
+    if (iters) *iters = done > 0 ? hs[done - 1].k : 0;
+    if (err) *err = done > 0 ? hs[done - 1].err : NAN;
+    if (result == RPCA_OK || result == RPCA_ERR_NOT_CONVERGED) {
+      int s2 = rpca_get_lowrank(c, U, sigma, V);
+      if (!s2) s2 = rpca_get_sparse(c, s_idx, s_val, s_cap, nnz);
+      if (s2) result = s2;
+    }
+  }
+  return result;
+}
+
 static int solve_device(const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol,
                         double* U, double* sigma, double* V, int64_t* s_idx, double* s_val, int64_t s_cap,
                         int64_t* nnz, int* iters, double* err, cudaStream_t stream) {
@@ -766,21 +790,50 @@ static int solve_device(const float* D, int64_t m, int64_t n, int r, double beta
   rpca_ctx* c = nullptr;
   int st = rpca_create(&c, &p, stream);
   if (st) return st;
-  int result = rpca_init(c, D, m, n, n, RPCA_DTYPE_F32, r);
-  if (!result) {
-    std::vector<rpca_iter_stats> hs((size_t)p.max_iter + 1);
-    int done = 0;
-    result = rpca_iterate(c, p.max_iter + 1, hs.data(), &done);
-    if (iters) *iters = done > 0 ? hs[done - 1].k : 0;
-    if (err) *err = done > 0 ? hs[done - 1].err : NAN;
-    if (result == RPCA_OK || result == RPCA_ERR_NOT_CONVERGED) {
-      int s2 = rpca_get_lowrank(c, U, sigma, V);
-      if (!s2) s2 = rpca_get_sparse(c, s_idx, s_val, s_cap, nnz);
-      if (s2) result = s2;
-    }
-  }
+  const int result = solve_on(c, D, m, n, r, beta, gamma, tol, U, sigma, V, s_idx, s_val, s_cap, nnz, iters, err);
   rpca_destroy(c);
   return result;
+}
+
+// Device buffers, stream and context of rpca_solve_host, kept between calls (grown as
+// needed) so that repeated calls pay for the copies and the solve, not for allocation.
+// Serialised by a mutex; freed by rpca_solve_host_release (or with the process).
+struct HostSolveCache {
+  int device = -1;
+  size_t d_elems = 0, u_elems = 0, v_elems = 0, cap = 0;
+  float* dD = nullptr;
+  double *dU = nullptr, *dS = nullptr, *dV = nullptr, *dval = nullptr;
+  int64_t* didx = nullptr;
+  cudaStream_t s = nullptr;
+  rpca_ctx* ctx = nullptr;
+};
+static std::mutex g_host_mu;
+static HostSolveCache* g_host = nullptr;  // heap object: no destructor runs at process exit
+
+static void host_cache_free(HostSolveCache* h) {
+  if (!h || h->device < 0) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  if (h->s) cudaStreamSynchronize(h->s);
+  if (h->ctx) rpca_destroy(h->ctx);
+  void* ptrs[] = {h->dD, h->dU, h->dS, h->dV, h->dval, h->didx};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (h->s) cudaStreamDestroy(h->s);
+  if (cur != h->device) cudaSetDevice(cur);
+  *h = HostSolveCache();
+}
+
+// Grows a cached device array to at least `need` elements of `size` bytes.
+static bool grow(void** p, size_t* have, size_t need, size_t size) {
+  if (*p && *have >= need) return true;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc(p, need * size) != cudaSuccess) return false;
+  *have = need;
+  return true;
 }
 
 int rpca_solve(const float* D, int64_t m, int64_t n, int r, double beta, double gamma, double tol, double* U,
@@ -796,42 +849,69 @@ int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, do
   if (!D || !U || !sigma || !V || !nnz || m < 1 || n < 1 || r < 1 || r > kMaxR || s_cap < 0 ||
       (s_cap > 0 && (!s_idx || !s_val)))
     return RPCA_ERR_INVALID_ARG;
-  float* dD = nullptr;
-  double *dU = nullptr, *dS = nullptr, *dV = nullptr, *dval = nullptr;
-  int64_t* didx = nullptr;
-  cudaStream_t s = nullptr;
-  int result = RPCA_OK;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RPCA_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RPCA_ERR_CUDA;
+  if (!g_host) g_host = new (std::nothrow) HostSolveCache();
+  if (!g_host) return RPCA_ERR_CUDA;
+  HostSolveCache& h = *g_host;
+  if (h.device != dev) {
+    host_cache_free(&h);
+    h.device = dev;
+  }
+  if (!h.s && cudaStreamCreateWithFlags(&h.s, cudaStreamNonBlocking) != cudaSuccess) {
+    host_cache_free(&h);
+    return RPCA_ERR_CUDA;
+  }
+  if (!h.ctx) {
+    rpca_params p;
+    rpca_params_default(&p);
+    p.beta = beta;
+    p.gamma = gamma;
+    p.tol = tol;
+    if (rpca_create(&h.ctx, &p, h.s) != RPCA_OK) {
+      h.ctx = nullptr;
+      host_cache_free(&h);
+      return RPCA_ERR_CUDA;
+    }
+  }
+  size_t s_have = h.cap, i_have = h.cap;
   const size_t cap = s_cap > 0 ? (size_t)s_cap : 1;
-  if (cudaMalloc(&dD, sizeof(float) * m * n) || cudaMalloc(&dU, sizeof(double) * m * r) ||
-      cudaMalloc(&dS, sizeof(double) * r) || cudaMalloc(&dV, sizeof(double) * n * r) ||
-      cudaMalloc(&didx, sizeof(int64_t) * cap) || cudaMalloc(&dval, sizeof(double) * cap)) {
-    result = RPCA_ERR_CUDA;
-  } else if (cudaMemcpyAsync(dD, D, sizeof(float) * m * n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+  size_t sig_have = h.dS ? kMaxR : 0;
+  if (!grow((void**)&h.dD, &h.d_elems, (size_t)m * n, sizeof(float)) ||
+      !grow((void**)&h.dU, &h.u_elems, (size_t)m * r, sizeof(double)) ||
+      !grow((void**)&h.dV, &h.v_elems, (size_t)n * r, sizeof(double)) ||
+      !grow((void**)&h.dS, &sig_have, kMaxR, sizeof(double)) || !grow((void**)&h.didx, &i_have, cap, sizeof(int64_t)) ||
+      !grow((void**)&h.dval, &s_have, cap, sizeof(double))) {
+    host_cache_free(&h);
+    return RPCA_ERR_CUDA;
+  }
+  h.cap = std::min(i_have, s_have);
+  int result = RPCA_OK;
+  if (cudaMemcpyAsync(h.dD, D, sizeof(float) * m * n, cudaMemcpyHostToDevice, h.s) != cudaSuccess) {
     result = RPCA_ERR_CUDA;
   } else {
-    result = solve_device(dD, m, n, r, beta, gamma, tol, dU, dS, dV, s_cap > 0 ? didx : nullptr,
-                          s_cap > 0 ? dval : nullptr, s_cap, nnz, iters, err, s);
+    result = solve_on(h.ctx, h.dD, m, n, r, beta, gamma, tol, h.dU, h.dS, h.dV, s_cap > 0 ? h.didx : nullptr,
+                      s_cap > 0 ? h.dval : nullptr, s_cap, nnz, iters, err);
     if (result == RPCA_OK || result == RPCA_ERR_NOT_CONVERGED) {
       const int64_t nz = (*nnz < s_cap) ? *nnz : s_cap;
-      if (cudaMemcpyAsync(U, dU, sizeof(double) * m * r, cudaMemcpyDeviceToHost, s) ||
-          cudaMemcpyAsync(sigma, dS, sizeof(double) * r, cudaMemcpyDeviceToHost, s) ||
-          cudaMemcpyAsync(V, dV, sizeof(double) * n * r, cudaMemcpyDeviceToHost, s) ||
-          (nz > 0 && cudaMemcpyAsync(s_idx, didx, sizeof(int64_t) * nz, cudaMemcpyDeviceToHost, s)) ||
-          (nz > 0 && cudaMemcpyAsync(s_val, dval, sizeof(double) * nz, cudaMemcpyDeviceToHost, s)) ||
-          cudaStreamSynchronize(s))
+      if (cudaMemcpyAsync(U, h.dU, sizeof(double) * m * r, cudaMemcpyDeviceToHost, h.s) ||
+          cudaMemcpyAsync(sigma, h.dS, sizeof(double) * r, cudaMemcpyDeviceToHost, h.s) ||
+          cudaMemcpyAsync(V, h.dV, sizeof(double) * n * r, cudaMemcpyDeviceToHost, h.s) ||
+          (nz > 0 && cudaMemcpyAsync(s_idx, h.didx, sizeof(int64_t) * nz, cudaMemcpyDeviceToHost, h.s)) ||
+          (nz > 0 && cudaMemcpyAsync(s_val, h.dval, sizeof(double) * nz, cudaMemcpyDeviceToHost, h.s)) ||
+          cudaStreamSynchronize(h.s))
         result = RPCA_ERR_CUDA;
     }
   }
-  cudaStreamSynchronize(s);
-  cudaFree(dD);
-  cudaFree(dU);
-  cudaFree(dS);
-  cudaFree(dV);
-  cudaFree(didx);
-  cudaFree(dval);
-  cudaStreamDestroy(s);
+  if (cudaStreamSynchronize(h.s) != cudaSuccess) result = RPCA_ERR_CUDA;
+  if (result == RPCA_ERR_CUDA) host_cache_free(&h);  // start from scratch after a CUDA error
   return result;
+}
+
+void rpca_solve_host_release(void) {
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  if (g_host) host_cache_free(g_host);
 }
 
 }  // extern "C"

@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
     L.rpca_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Params), vp]
     L.rpca_destroy.argtypes = [vp]
     L.rpca_destroy.restype = None
+    L.rpca_solve_host_release.argtypes = []
+    L.rpca_solve_host_release.restype = None
     L.rpca_init.argtypes = [vp, vp, i64, i64, i64, i32, i32]
     L.rpca_iterate.argtypes = [vp, i32, ctypes.POINTER(IterStats), pint]
     L.rpca_set_zeta.argtypes = [vp, dbl]
@@ -256,7 +258,8 @@ def solve(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s_cap:
 def solve_host(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s_cap: int,
                out: dict | None = None) -> dict:
     """rpca_solve_host on a float32 CPU tensor (ideally pinned); outputs are CPU tensors
-    (pass ``out`` from a previous call to reuse them)."""
+    (pass ``out`` from a previous call to reuse them).  The library keeps its device buffers
+    between calls; solve_host_release() frees them."""
     if D.is_cuda or D.dtype != torch.float32 or not D.is_contiguous():
         raise ValueError("D must be a contiguous float32 CPU tensor")
     m, n = D.shape
@@ -275,3 +278,8 @@ def solve_host(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s
     _check(code, "rpca_solve_host", allow=(OK, NOT_CONVERGED))
     out.update(status=code, nnz=nnz.value, iters=iters.value, err=err.value)
     return out
+
+
+def solve_host_release() -> None:
+    """Frees the device buffers and context that rpca_solve_host keeps between calls."""
+    lib().rpca_solve_host_release()

@@ -203,3 +203,23 @@ def test_solve_device_and_host_entry_points():
     assert np.array_equal(Ld, Lh)
     assert np.array_equal(out_d["idx"].cpu().numpy(), out_h["idx"][: out_h["nnz"]].numpy())
     assert rel_fro(Ld, inst.L) < 1e-4
+
+
+def test_host_entry_point_keeps_and_regrows_its_buffers():
+    # rpca_solve_host keeps its device buffers between calls: a larger problem regrows them,
+    # a smaller one reuses them, and after the release the next call allocates again; each
+    # result equals the device entry point's on the same input
+    cases = [(300, 250, 3, 31), (420, 380, 5, 32), (300, 250, 3, 31)]
+    for i, (m, n, r, seed) in enumerate(cases):
+        inst = synth.planted_instance(m, n, r, 0.1, 1.0, seed)
+        p = inst.params()
+        D = torch.from_numpy(inst.D).float()
+        out_d = P.solve(D.cuda(), r, p["beta"], p["gamma"], 1e-5)
+        out_h = P.solve_host(D.pin_memory(), r, p["beta"], p["gamma"], 1e-5, s_cap=m * n)
+        assert out_h["status"] == out_d["status"] == P.OK
+        Ld = (out_d["U"].cpu().numpy() * out_d["sigma"].cpu().numpy()) @ out_d["V"].cpu().numpy().T
+        Lh = (out_h["U"].numpy() * out_h["sigma"].numpy()) @ out_h["V"].numpy().T
+        assert np.array_equal(Ld, Lh), i
+        assert np.array_equal(out_d["idx"].cpu().numpy(), out_h["idx"][: out_h["nnz"]].numpy()), i
+        if i == 1:
+            P.solve_host_release()
