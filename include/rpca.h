@@ -48,7 +48,7 @@ typedef enum { RPCA_DTYPE_F64 = 0, RPCA_DTYPE_F32 = 1 } rpca_dtype;
  *     rounding the tangent space keeps (relative error of L about 1e-4 at n = 500 and 1e-5
  *     at n = 10^4 for r = 5).
  *   BF16_SPLIT: D is held as hi = bf16(D) and lo = bf16(D - hi) (4 bytes per entry); the
- *     passes read hi alone until err_k < split_switch and hi + lo (D to 2^-17 relative)
+ *     passes read hi alone until err_k < split_switch and hi + lo (D to 2^-16 relative)
  *     after that, and only a pass that read hi + lo can end the run.
  * Both pass kinds read the bf16 storage.  The BF16 modes are not part of the method in the
  * paper (which states no precision): they apply its iteration to a quantised D and then to

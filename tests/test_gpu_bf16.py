@@ -3,7 +3,7 @@
 The paper states no precision.  In these modes the passes read D as bf16: BF16 alone
 solves the problem for bf16(D), so err_k (measured against bf16(D)) stops near the bf16
 rounding of D and L_k stops near L* only to the part of that rounding the tangent space
-keeps, about sqrt((m + n) r / (m n)) of it.  BF16_SPLIT reads hi + lo (D to 2^-17 relative)
+keeps, about sqrt((m + n) r / (m n)) of it.  BF16_SPLIT reads hi + lo (D to 2^-16 relative)
 once err_k < 1e-2 and is held to the FP32 tolerances.
 
 Stated tolerances (relative Frobenius):
