@@ -59,7 +59,6 @@ struct rpca_ctx {
   // tall-skinny arrays in the working precision (tsize bytes per entry)
   void *U = nullptr, *sig = nullptr, *V = nullptr, *Ut = nullptr, *Vt = nullptr, *Y1 = nullptr, *Y2 = nullptr,
        *part = nullptr;
-  double* lowrank_tmp = nullptr;  // unused
   void *Wc = nullptr, *Vc = nullptr, *Utc = nullptr, *Vtc = nullptr, *P1 = nullptr, *P2 = nullptr;
   double* resP = nullptr;
   unsigned long long* nnzP = nullptr;
