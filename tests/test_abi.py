@@ -37,3 +37,34 @@ def test_host_only_calls(lib):
     assert lib.rpca_create(ctypes.byref(ctx), ctypes.byref(bad), None) == P.INVALID_ARG
     assert lib.rpca_solve_host(None, 10, 10, 1, 0.1, 0.5, 1e-5, None, None, None, None, None, 0, None, None,
                                None) == P.INVALID_ARG
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of rpca_params and rpca_iter_stats against the C compiler's layout
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = P.rpca._HERE.rsplit("/", 1)[0]
+    fields = {"rpca_params": [f for f, _ in P.rpca.Params._fields_],
+              "rpca_iter_stats": [f for f, _ in P.rpca.IterStats._fields_]}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rpca.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", root + "/include", str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        st, f, v = line.split()
+        got[(st, f)] = int(v)
+    for st, cls in (("rpca_params", P.rpca.Params), ("rpca_iter_stats", P.rpca.IterStats)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
