@@ -148,6 +148,19 @@ int rpca_get_lowrank(rpca_ctx* ctx, double* U, double* sigma, double* V);
  * and writes only *nnz (host).  Takes three passes over D; synchronises the stream. */
 int rpca_get_sparse(rpca_ctx* ctx, int64_t* idx, double* val, int64_t cap, int64_t* nnz);
 
+/* Iteration state for a checkpoint: *k (host) = index of the iterate L_k the context holds,
+ * *zeta (host) = the threshold zeta_k its next pass uses.  Synchronises the stream. */
+int rpca_get_state(rpca_ctx* ctx, int* k, double* zeta);
+
+/* Resumes from a checkpoint of the factors (rpca_get_lowrank) and of rpca_get_state, e.g.
+ * after the process that held them failed: U (m x r), sigma (r), V (n x r) are device FP64
+ * arrays as rpca_get_lowrank writes them; k and zeta as rpca_get_state returned them.  The
+ * context must have been initialised (rpca_init) on the same D and rank; its iterate is
+ * replaced, Trim and the bases for the next pass are recomputed (Algorithm 2), and
+ * rpca_iterate continues from iteration k.  Only the factors are checkpointed, never an
+ * m x n array.  Not part of the paper's method.  Synchronises the stream. */
+int rpca_set_lowrank(rpca_ctx* ctx, const double* U, const double* sigma, const double* V, int k, double zeta);
+
 /* One call: init + iterate to tolerance + outputs.  D, U, sigma, V, s_idx, s_val are
  * device pointers; D is float32, m x n, leading dimension n; FP32 precision.  *nnz,
  * *iters, *err are host.  If s_cap < nnz the sparse part is not written and
@@ -169,6 +182,13 @@ int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, do
 /* Frees the device buffers, stream and context kept by rpca_solve_host (the next call
  * allocates them again).  Not part of the paper's method. */
 void rpca_solve_host_release(void);
+
+/* Self-test of the bounded device-side waits, on the current device: a kernel waits for an
+ * mbarrier phase that nothing completes (1 ms limit) and a kernel waits at a grid barrier that
+ * one of its two blocks never reaches (1 s limit).  Each records RPCA_ERR_TIMEOUT instead of
+ * hanging; *mbar_status and *grid_status (host) receive the recorded codes.  The context stays
+ * usable.  Not part of the paper's method. */
+int rpca_selftest_waits(int* mbar_status, int* grid_status);
 
 /* ---------------------------------------------------------------------------------------
  * Learned threshold schedule: stateless pass and adjoint pass.

@@ -689,6 +689,47 @@ int rpca_get_lowrank(rpca_ctx* c, double* U, double* sigma, double* V) {
   return RPCA_OK;
 }
 
+int rpca_get_state(rpca_ctx* c, int* k, double* zeta) {
+  if (!c || !k || !zeta) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  CK(cudaMemcpyAsync(k, &c->st->k, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(zeta, &c->st->zeta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPCA_OK;
+}
+
+int rpca_set_lowrank(rpca_ctx* c, const double* U, const double* sigma, const double* V, int k, double zeta) {
+  if (!c || !U || !sigma || !V || k < 0 || !(zeta >= 0)) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  if (k > c->p.max_iter) return RPCA_ERR_INVALID_ARG;
+  if (c->prec == PREC_F64) {
+    CK(cudaMemcpyAsync(c->U, U, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->sig, sigma, sizeof(double) * c->r, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->V, V, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(launch_convert_f64_to_f32(U, c->r, static_cast<float*>(c->U), (int)c->m, c->r, c->stream));
+    CK(launch_convert_f64_to_f32(sigma, c->r, static_cast<float*>(c->sig), 1, c->r, c->stream));
+    CK(launch_convert_f64_to_f32(V, c->r, static_cast<float*>(c->V), (int)c->n, c->r, c->stream));
+  }
+  // iteration state: L_k held, zeta_k for the next pass, running again
+  const int zero = 0;
+  CK(cudaMemcpyAsync(&c->st->k, &k, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&c->st->zeta, &zeta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&c->st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&c->st->use_lo, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  // Trim (Algorithm 2), orthonormal bases and the copies (and images) read by the next pass
+  int st = run_small(c, small_args(c, SM_PREPARE, c->Rr));
+  if (st) return st;
+  if ((st = read_flags(c))) return st;
+  prof_collect(c, 0);
+  return flag_status(c);
+}
+
+int rpca_selftest_waits(int* mbar_status, int* grid_status) {
+  if (!mbar_status || !grid_status) return RPCA_ERR_INVALID_ARG;
+  return run_wait_selftest(mbar_status, grid_status) == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
+}
+
 int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t* nnz) {
   if (!c || !nnz || cap < 0 || (cap > 0 && (!idx || !val))) return RPCA_ERR_INVALID_ARG;
   if (!c->ready) return RPCA_ERR_STATE;

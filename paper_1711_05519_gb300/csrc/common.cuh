@@ -178,6 +178,9 @@ struct SmallArgs {
   int img_iter;
 };
 cudaError_t launch_small(const SmallArgs& a, int grid, cudaStream_t s);
+// Runs the bounded-wait self-test kernels (small.cu) on the current device and returns the
+// status each recorded (RPCA_ERR_TIMEOUT expected).
+cudaError_t run_wait_selftest(int* mbar_status, int* grid_status);
 int small_grid_size(int device);
 
 cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s);

@@ -41,6 +41,7 @@
 
 #include "common.cuh"
 #include "tc_images.cuh"
+#include "tc_util.cuh"
 
 namespace rpca {
 
@@ -1228,6 +1229,28 @@ cudaError_t launch_one(const SmallArgs& a, int grid, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+// Self-test of the bounded waits: an mbarrier phase that nothing completes, waited for with a
+// 1 ms limit, and a grid barrier that one of two blocks never reaches (1 s limit).  Both end
+// with a TIMEOUT status and return; nothing else is in flight.
+struct BarrierFlag {
+  int ok;
+};
+
+__global__ void selftest_mbar_kernel(int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    *out = tc::mbar_wait(&bar, 0, 1000000ull) ? 0 : (int)kErrTimeout;
+  }
+}
+
+__global__ void selftest_grid_kernel(DevState* st) {
+  __shared__ BarrierFlag sh;
+  if (blockIdx.x == 1) return;  // never arrives
+  grid_barrier(st, sh);
+}
+
 }  // namespace
 
 int small_grid_size(int device) {
@@ -1251,6 +1274,26 @@ cudaError_t launch_small(const SmallArgs& a, int grid, cudaStream_t s) {
   const bool narrow = need <= 8;
   if (a.prec == PREC_F32) return narrow ? launch_one<float, 8>(a, grid, s) : launch_one<float, 16>(a, grid, s);
   return narrow ? launch_one<double, 8>(a, grid, s) : launch_one<double, 16>(a, grid, s);
+}
+
+cudaError_t run_wait_selftest(int* mbar_status, int* grid_status) {
+  int* d_out = nullptr;
+  DevState* st = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d_out, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&st, sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMemset(d_out, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(DevState));
+  if (e == cudaSuccess) {
+    selftest_mbar_kernel<<<1, 32>>>(d_out);
+    selftest_grid_kernel<<<2, 32>>>(st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(mbar_status, d_out, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(grid_status, &st->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (d_out) cudaFree(d_out);
+  if (st) cudaFree(st);
+  return e;
 }
 
 }  // namespace rpca

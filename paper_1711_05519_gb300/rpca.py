@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
     L.rpca_destroy.restype = None
     L.rpca_solve_host_release.argtypes = []
     L.rpca_solve_host_release.restype = None
+    L.rpca_set_lowrank.argtypes = [vp, vp, vp, vp, i32, dbl]
+    L.rpca_get_state.argtypes = [vp, pint, ctypes.POINTER(dbl)]
     L.rpca_init.argtypes = [vp, vp, i64, i64, i64, i32, i32]
     L.rpca_iterate.argtypes = [vp, i32, ctypes.POINTER(IterStats), pint]
     L.rpca_set_zeta.argtypes = [vp, dbl]
@@ -219,6 +221,20 @@ class Solver:
                                       ctypes.c_void_p(V.data_ptr())), "rpca_get_lowrank")
         return U, s, V
 
+    def state(self) -> tuple[int, float]:
+        """(k, zeta_k): index of the iterate held and the threshold of the next pass."""
+        k, z = ctypes.c_int(0), ctypes.c_double(0)
+        _check(lib().rpca_get_state(self._ctx, ctypes.byref(k), ctypes.byref(z)), "rpca_get_state")
+        return k.value, z.value
+
+    def set_lowrank(self, U: torch.Tensor, sigma: torch.Tensor, V: torch.Tensor, k: int, zeta: float) -> None:
+        """Resumes from a factor checkpoint (lowrank() and state() of an earlier context on
+        the same D); call after init()."""
+        dev = self._D.device
+        U, sigma, V = (t.to(dev, torch.float64).contiguous() for t in (U, sigma, V))
+        _check(lib().rpca_set_lowrank(self._ctx, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
+                                      ctypes.c_void_p(V.data_ptr()), int(k), float(zeta)), "rpca_set_lowrank")
+
     def sparse(self):
         """supp(S_k) as ascending linear indices i*n + j, and the values S_ij."""
         nnz = ctypes.c_int64(0)
@@ -278,6 +294,13 @@ def solve_host(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s
     _check(code, "rpca_solve_host", allow=(OK, NOT_CONVERGED))
     out.update(status=code, nnz=nnz.value, iters=iters.value, err=err.value)
     return out
+
+
+def selftest_waits() -> tuple[int, int]:
+    """Status codes recorded by the bounded-wait self-test kernels (TIMEOUT expected)."""
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().rpca_selftest_waits(ctypes.byref(a), ctypes.byref(b)), "rpca_selftest_waits")
+    return a.value, b.value
 
 
 def solve_host_release() -> None:

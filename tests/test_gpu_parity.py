@@ -223,3 +223,44 @@ def test_host_entry_point_keeps_and_regrows_its_buffers():
         assert np.array_equal(out_d["idx"].cpu().numpy(), out_h["idx"][: out_h["nnz"]].numpy()), i
         if i == 1:
             P.solve_host_release()
+
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_resume_from_factor_checkpoint(prec):
+    # a solve interrupted after 5 iterations (its process "fails": the context is dropped) and
+    # resumed in a new context from the factors and (k, zeta_k) alone ends where the
+    # uninterrupted solve ends
+    inst = synth.planted_instance(500, 440, 5, 0.1, 1.0, 41)
+    p = inst.params()
+    D = torch.from_numpy(inst.D).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    with _solver(p, prec, tol) as s:
+        s.init(D, 5)
+        code0, st0 = s.run()
+        L0 = [t.cpu().numpy() for t in s.lowrank()]
+    with _solver(p, prec, tol) as s:
+        s.init(D, 5)
+        s.iterate(5)
+        ckpt = [t.clone() for t in s.lowrank()] + list(s.state())
+    assert ckpt[3] == 5
+    with _solver(p, prec, tol) as s:
+        s.init(D, 5)
+        s.set_lowrank(*ckpt)
+        assert s.state() == (5, ckpt[4])
+        code1, st1 = s.run()
+        L1 = [t.cpu().numpy() for t in s.lowrank()]
+    assert code0 == code1 == P.OK
+    assert st1[0]["k"] == 5 and st1[-1]["k"] == st0[-1]["k"]
+    # same iterates up to rounding (Trim and the bases are recomputed from the checkpoint)
+    assert [x["err"] for x in st1] == pytest.approx([x["err"] for x in st0[5:]], rel=1e-3)
+    A, B = [(U * s) @ V.T for U, s, V in (L0, L1)]
+    assert rel_fro(B, A) < (1e-9 if prec == "fp64" else 1e-5)
+
+
+def test_bounded_waits_report_timeout_and_leave_the_context_usable():
+    mbar_status, grid_status = P.selftest_waits()
+    assert mbar_status == P.TIMEOUT and grid_status == P.TIMEOUT
+    inst = synth.planted_instance(200, 180, 3, 0.1, 1.0, 2)
+    g = _gpu_run(inst, "fp32", 1e-5)
+    assert g["code"] == P.OK
