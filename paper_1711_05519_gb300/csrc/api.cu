@@ -455,8 +455,8 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   c->n = n;
   c->r = r;
   c->Rr = padded_rank(r);
-  // block size of the initial subspace iteration: oversample to 8 columns for r <= 6 (so
-  // the tensor-core pass, compiled for ranks up to 8, runs the initialisation as well)
+  // block size of the initial subspace iteration: oversample to 8 columns for r <= 6 (the
+  // tensor-core pass then runs the initialisation in its rank-8 image layout), else 2r up to 16
   int b = (r <= 6) ? 8 : ((2 * r <= 16) ? 2 * r : 16);
   const int64_t mn_min = m < n ? m : n;
   if (b > mn_min) b = (int)(mn_min & ~1ll);
