@@ -167,7 +167,7 @@ __device__ __forceinline__ void tmem_ld_y(uint32_t taddr, uint32_t (&v)[NY]) {
 // DM = 0: D is FP32 (dmap, two 128 x 32 boxes per tile).  DM = 1: D is held as bf16 hi and
 // lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
 // DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
-// 32 KB and Z is written over it in the same layout.  RK: operand image layout (8 or 16).
+// 32 KB and Z is written over it (where: zhi_off / zlo_off).  RK: operand image layout (8 or 16).
 template <int DM, int RK>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap,
                                                             const __grid_constant__ CUtensorMap dmap_lo, TcArgs a) {
@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       tc_fence_after();
       const uint64_t dw = dw0 + (uint64_t)(wb * (WOP_BYTES >> 4));
       const uint64_t dv = dv0 + (uint64_t)(s * (STAGE_BYTES >> 4));
-      // k-steps of 8 (32 bytes = 2 descriptor units): hi blocks at 0, lo blocks at 2 RK / 8 x 2
+      // k-steps of 8 tf32 (32 bytes = 2 descriptor units); each row is [hi | lo], the lo half
+      // starting RK tf32 = RK / 4 units in
       constexpr int LO = RK / 4;
 #pragma unroll
       for (int kb = 0; kb < RK / 8; ++kb) {
