@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -97,7 +98,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the samples go to a temporary file (kept for inspection, one per GPU index)
+        self.path = os.path.join(tempfile.gettempdir(), f"rpca_bench_clocks_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
