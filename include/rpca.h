@@ -148,18 +148,25 @@ int rpca_get_lowrank(rpca_ctx* ctx, double* U, double* sigma, double* V);
  * and writes only *nnz (host).  Takes three passes over D; synchronises the stream. */
 int rpca_get_sparse(rpca_ctx* ctx, int64_t* idx, double* val, int64_t cap, int64_t* nnz);
 
+/* Bit of the checkpoint flags: the passes of a BF16_SPLIT solve read hi + lo. */
+#define RPCA_STATE_READS_LO 1
+
 /* Iteration state for a checkpoint: *k (host) = index of the iterate L_k the context holds,
- * *zeta (host) = the threshold zeta_k its next pass uses.  Synchronises the stream. */
-int rpca_get_state(rpca_ctx* ctx, int* k, double* zeta);
+ * *zeta (host) = the threshold zeta_k its next pass uses, *flags (host, may be NULL) = the
+ * RPCA_STATE_* bits of the solve.  Synchronises the stream. */
+int rpca_get_state(rpca_ctx* ctx, int* k, double* zeta, int* flags);
 
 /* Resumes from a checkpoint of the factors (rpca_get_lowrank) and of rpca_get_state, e.g.
  * after the process that held them failed: U (m x r), sigma (r), V (n x r) are device FP64
- * arrays as rpca_get_lowrank writes them; k and zeta as rpca_get_state returned them.  The
- * context must have been initialised (rpca_init) on the same D and rank; its iterate is
- * replaced, Trim and the bases for the next pass are recomputed (Algorithm 2), and
- * rpca_iterate continues from iteration k.  Only the factors are checkpointed, never an
- * m x n array.  Not part of the paper's method.  Synchronises the stream. */
-int rpca_set_lowrank(rpca_ctx* ctx, const double* U, const double* sigma, const double* V, int k, double zeta);
+ * arrays as rpca_get_lowrank writes them; k, zeta and flags as rpca_get_state returned them.
+ * The context must have been initialised (rpca_init) on the same D, rank and precision; its
+ * iterate is replaced, Trim and the bases for the next pass are recomputed (Algorithm 2), and
+ * rpca_iterate continues from iteration k on the path the interrupted solve would have taken
+ * (with RPCA_STATE_READS_LO a BF16_SPLIT solve keeps reading hi + lo).  Only the factors are
+ * checkpointed, never an m x n array.  Not part of the paper's method.  Synchronises the
+ * stream. */
+int rpca_set_lowrank(rpca_ctx* ctx, const double* U, const double* sigma, const double* V, int k, double zeta,
+                     int flags);
 
 /* One call: init + iterate to tolerance + outputs.  D, U, sigma, V, s_idx, s_val are
  * device pointers; D is float32, m x n, leading dimension n; FP32 precision.  *nnz,
@@ -226,9 +233,9 @@ int rpca_learn_pass_adjoint(const void* D, int64_t m, int64_t n, int64_t ld, int
 
 /* rpca_get_sparse without any device allocation (the paper has no counterpart; this is a
  * service of the library).  Some callers cannot call cudaMalloc: code that runs inside a
- * framework owning all device memory through its own pool, code with a fixed device-memory
- * budget set at start-up, or latency-critical loops that must not take the implicit
- * synchronisation of an allocation.  This entry point writes the same support list as
+ * framework owning all device memory through its own caching pool (a raw cudaMalloc beside
+ * the pool can fail or fragment what the pool has reserved), or code with a fixed
+ * device-memory budget set at start-up.  This entry point writes the same support list as
  * rpca_get_sparse for the low-rank estimate L = U diag(sigma) V^T and threshold zeta:
  * linear indices i*n + j in ascending order of every entry with |D_ij - L_ij| > zeta, and
  * the values D_ij - L_ij, computed in FP32 as the FP32 pass does.
@@ -238,11 +245,12 @@ int rpca_learn_pass_adjoint(const void* D, int64_t m, int64_t n, int64_t ld, int
  * It allocates nothing: its per-row scratch lives in a static device array of
  * 2 * RPCA_NOALLOC_MAX_ROWS + 1 64-bit words (1 MiB) that every GPU loading the library
  * holds until the process exits.  m above RPCA_NOALLOC_MAX_ROWS returns
- * RPCA_ERR_INVALID_ARG; cap < nnz returns RPCA_ERR_CAPACITY with *nnz set.  The first call
- * on a device looks up the scratch address on that device (make that first call before
- * any stream capture).  All calls share the scratch and each call rewrites what it reads,
- * so calls that overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Synchronises the stream. */
+ * RPCA_ERR_INVALID_ARG; cap < nnz returns RPCA_ERR_CAPACITY with *nnz set.  Each call looks
+ * up the scratch address in the current device's context (a host-side query).  All calls
+ * share the scratch and each call rewrites what it reads, so calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.  The call
+ * blocks the host: it synchronises the stream twice (after the count, to read the total back,
+ * and after the write). */
 int rpca_get_sparse_noalloc(const float* D, int64_t m, int64_t n, int64_t ld, int r, const double* U,
                             const double* sigma, const double* V, double zeta, int64_t* idx,
                             double* val, int64_t cap, int64_t* nnz, void* stream);

@@ -689,17 +689,21 @@ int rpca_get_lowrank(rpca_ctx* c, double* U, double* sigma, double* V) {
   return RPCA_OK;
 }
 
-int rpca_get_state(rpca_ctx* c, int* k, double* zeta) {
+int rpca_get_state(rpca_ctx* c, int* k, double* zeta, int* flags) {
   if (!c || !k || !zeta) return RPCA_ERR_INVALID_ARG;
   if (!c->ready) return RPCA_ERR_STATE;
+  int use_lo = 0;
   CK(cudaMemcpyAsync(k, &c->st->k, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(zeta, &c->st->zeta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&use_lo, &c->st->use_lo, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (flags) *flags = use_lo ? RPCA_STATE_READS_LO : 0;
   return RPCA_OK;
 }
 
-int rpca_set_lowrank(rpca_ctx* c, const double* U, const double* sigma, const double* V, int k, double zeta) {
-  if (!c || !U || !sigma || !V || k < 0 || !(zeta >= 0)) return RPCA_ERR_INVALID_ARG;
+int rpca_set_lowrank(rpca_ctx* c, const double* U, const double* sigma, const double* V, int k, double zeta,
+                     int flags) {
+  if (!c || !U || !sigma || !V || k < 0 || !(zeta >= 0) || (flags & ~RPCA_STATE_READS_LO)) return RPCA_ERR_INVALID_ARG;
   if (!c->ready) return RPCA_ERR_STATE;
   if (k > c->p.max_iter) return RPCA_ERR_INVALID_ARG;
   if (c->prec == PREC_F64) {
@@ -711,12 +715,14 @@ int rpca_set_lowrank(rpca_ctx* c, const double* U, const double* sigma, const do
     CK(launch_convert_f64_to_f32(sigma, c->r, static_cast<float*>(c->sig), 1, c->r, c->stream));
     CK(launch_convert_f64_to_f32(V, c->r, static_cast<float*>(c->V), (int)c->n, c->r, c->stream));
   }
-  // iteration state: L_k held, zeta_k for the next pass, running again
+  // iteration state: L_k held, zeta_k for the next pass, running again; a BF16_SPLIT solve
+  // that had switched to hi + lo keeps reading it
   const int zero = 0;
+  const int use_lo = (c->split && (flags & RPCA_STATE_READS_LO)) ? 1 : 0;
   CK(cudaMemcpyAsync(&c->st->k, &k, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(&c->st->zeta, &zeta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(&c->st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(&c->st->use_lo, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&c->st->use_lo, &use_lo, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   // Trim (Algorithm 2), orthonormal bases and the copies (and images) read by the next pass
   int st = run_small(c, small_args(c, SM_PREPARE, c->Rr));
   if (st) return st;

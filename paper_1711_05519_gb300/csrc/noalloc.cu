@@ -6,8 +6,6 @@
 // the same as the extraction kernels of rpca_get_sparse (FP32 rebuild of L_ij from
 // W = U diag(sigma) and V in the same summation order, strict threshold), so both give the
 // same support and values.
-#include <mutex>
-
 #include "../../include/rpca.h"
 #include "common.cuh"
 
@@ -15,26 +13,19 @@ namespace rpca {
 namespace {
 
 constexpr int kMaxRows = RPCA_NOALLOC_MAX_ROWS;
-constexpr int kMaxDevices = 64;
 
 // Scratch shared by every call on a device: [0, m) row counts, [m, 2m+1) row offsets.
 // Each call overwrites all 2m+1 entries it uses before reading them.
 static __device__ __align__(256) unsigned long long g_rows[2 * kMaxRows + 1];
 
-std::mutex g_mutex;
-unsigned long long* g_rows_addr[kMaxDevices] = {};
-
-// Device address of g_rows on the current device, looked up once per device.
+// Device address of g_rows in the current device's context.  In host code the symbol is only
+// a stand-in, so the address is looked up, and it is looked up on every call: the lookup is a
+// host-side query that allocates nothing, and a cached address would go stale if the caller
+// reset the device (the module, and with it g_rows, is then loaded again, possibly elsewhere).
 int scratch_address(unsigned long long** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RPCA_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_rows_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_rows) != cudaSuccess || !p) return RPCA_ERR_CUDA;
-    g_rows_addr[dev] = static_cast<unsigned long long*>(p);
-  }
-  *out = g_rows_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_rows) != cudaSuccess || !p) return RPCA_ERR_CUDA;
+  *out = static_cast<unsigned long long*>(p);
   return RPCA_OK;
 }
 

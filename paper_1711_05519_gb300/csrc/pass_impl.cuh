@@ -175,7 +175,9 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   const T zeta = static_cast<T>(a.st->zeta);
   const bool vec = a.vec != 0;
   const bool use_lo = DM == 1 && a.Dlo != nullptr && a.st->use_lo != 0;
-  T res = T(0);
+  // residual: the TM x VW terms of one sub-chunk are summed in T, the sub-chunk sums in
+  // double (one FP32 chain over the ~10^3 terms a thread sees would bias err_k)
+  double res = 0.0;
   unsigned nnz = 0;
   T* mySlot = sY2 + warp * R * BW;
 
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
           vt[c][k] = sVt[k * BW + cl + c];
           y2[c][k] = T(0);
         }
+      T rsc = T(0);
 #pragma unroll
       for (int t = 0; t < TM; ++t) {
         T w[R], ut[R];
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
           const T l = rebuild<T, R>(w, v[c]);
           const T rr = d[t][c] - l;
           const bool s = fabs(rr) > zeta;
-          res = s ? res : fma(rr, rr, res);
+          rsc = s ? rsc : fma(rr, rr, rsc);
           nnz += s ? 1u : 0u;
           const T z = s ? l : d[t][c];
 #pragma unroll
@@ -233,6 +236,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
           }
         }
       }
+      res += static_cast<double>(rsc);
 #pragma unroll
       for (int k = 0; k < R; ++k)
 #pragma unroll
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   // CTA totals of the residual and the support size.
   __shared__ double sres[8];
   __shared__ unsigned long long snnz[8];
-  double rd = warp_sum(static_cast<double>(res));
+  double rd = warp_sum(res);
   unsigned long long nz = nnz;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);

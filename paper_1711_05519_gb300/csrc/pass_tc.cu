@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
 
   if (ntiles > 0 && warp == 0 && lane == 0) {
     // ------------------------------------------------------------------ producer
-    int issued = 0;
+    int issued = 0, w_issued = 0;
     for (int t = 0; t < ntiles && !abort_flag; ++t) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE;
       const int rt = rt0 + rtl, ct = ct0 + ctl;
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         mbar_arrive_expect_tx(&bar[B_WFULL + wb], WOP_BYTES + UTOP_BYTES);
         bulk_load(sm + OFF_W + wb * WOP_BYTES, a.wop + (size_t)rt * WOP_BYTES, WOP_BYTES, &bar[B_WFULL + wb]);
         bulk_load(sm + OFF_U + wb * UTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES, &bar[B_WFULL + wb]);
+        w_issued = rtl + 1;
       }
       if (t >= NSTAGE && !mbar_wait(&bar[B_EMPTY + s], ((t - NSTAGE) / NSTAGE) & 1)) {
         fail(a, &abort_flag);
@@ -268,9 +269,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
       issued = t + 1;
     }
-    // wait (bounded) for this thread's copies still in flight before the CTA may exit
+    // wait (bounded) for this thread's copies still in flight before the CTA may exit: the
+    // last NSTAGE stage loads and the last two W / U~ image loads (after an abort some of them
+    // may never have been consumed)
     for (int t = (issued > NSTAGE ? issued - NSTAGE : 0); t < issued; ++t)
       mbar_wait(&bar[B_FULL + (t % NSTAGE)], (t / NSTAGE) & 1, 100000000ull);
+    for (int i = (w_issued > 2 ? w_issued - 2 : 0); i < w_issued; ++i)
+      mbar_wait(&bar[B_WFULL + (i & 1)], (i >> 1) & 1, 100000000ull);
   } else if (ntiles > 0 && warp == 1 && lane == 0) {
     // ------------------------------------------------------------------ L MMAs
     const uint32_t base = smem_u32(sm);
@@ -379,7 +384,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const int rowl = 32 * q + lane;
     const float zeta = static_cast<float>(a.st->zeta);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    float res = 0.f;
+    // residual: each tile's 32 squared terms of this thread are summed in FP32, the tile sums
+    // in FP64 (a thread sees thousands of terms per pass; one FP32 chain over all of them
+    // would bias err_k by up to ~1e-4 relative)
+    double res = 0.0;
     unsigned nnz = 0;
     for (int t = grp; t < ntiles && !abort_flag; t += 2) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
@@ -457,17 +465,19 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
       const float2 m1 = make_float2(-1.f, -1.f);
+      float rt0 = 0.f, rt1 = 0.f;
 #pragma unroll
       for (int c = 0; c < 32; c += 2) {
         const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
         const float2 r2 = __ffma2_rn(l2, m1, make_float2(z[c], z[c + 1]));  // D - L, exactly rounded
         const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;
-        res = s0 ? res : fmaf(r2.x, r2.x, res);
-        res = s1 ? res : fmaf(r2.y, r2.y, res);
+        rt0 = s0 ? rt0 : fmaf(r2.x, r2.x, rt0);
+        rt1 = s1 ? rt1 : fmaf(r2.y, r2.y, rt1);
         nnz += (s0 ? 1u : 0u) + (s1 ? 1u : 0u);
         z[c] = s0 ? l2.x : z[c];
         z[c + 1] = s1 ? l2.y : z[c + 1];
       }
+      res += (double)(rt0 + rt1);
       // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
       // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
       uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
@@ -570,7 +580,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
     }
     // CTA totals of the residual and the support size
-    double rd = (double)res;
+    double rd = res;
     unsigned long long nz = nnz;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -21,6 +21,7 @@ DTYPE_F64, DTYPE_F32 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_split": 3}
 ZETA = {"paper": 0, "simple": 1, "external": 2}
 PASS_KIND = {"auto": 0, "simt": 1, "tensor": 2}
+STATE_READS_LO = 1
 
 
 class RpcaError(RuntimeError):
@@ -81,8 +82,8 @@ def lib() -> ctypes.CDLL:
     L.rpca_destroy.restype = None
     L.rpca_solve_host_release.argtypes = []
     L.rpca_solve_host_release.restype = None
-    L.rpca_set_lowrank.argtypes = [vp, vp, vp, vp, i32, dbl]
-    L.rpca_get_state.argtypes = [vp, pint, ctypes.POINTER(dbl)]
+    L.rpca_set_lowrank.argtypes = [vp, vp, vp, vp, i32, dbl, i32]
+    L.rpca_get_state.argtypes = [vp, pint, ctypes.POINTER(dbl), pint]
     L.rpca_init.argtypes = [vp, vp, i64, i64, i64, i32, i32]
     L.rpca_iterate.argtypes = [vp, i32, ctypes.POINTER(IterStats), pint]
     L.rpca_set_zeta.argtypes = [vp, dbl]
@@ -221,19 +222,22 @@ class Solver:
                                       ctypes.c_void_p(V.data_ptr())), "rpca_get_lowrank")
         return U, s, V
 
-    def state(self) -> tuple[int, float]:
-        """(k, zeta_k): index of the iterate held and the threshold of the next pass."""
-        k, z = ctypes.c_int(0), ctypes.c_double(0)
-        _check(lib().rpca_get_state(self._ctx, ctypes.byref(k), ctypes.byref(z)), "rpca_get_state")
-        return k.value, z.value
+    def state(self) -> tuple[int, float, int]:
+        """(k, zeta_k, flags): index of the iterate held, the threshold of the next pass and
+        the RPCA_STATE_* bits (1: a BF16_SPLIT solve reads hi + lo)."""
+        k, z, f = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_int(0)
+        _check(lib().rpca_get_state(self._ctx, ctypes.byref(k), ctypes.byref(z), ctypes.byref(f)), "rpca_get_state")
+        return k.value, z.value, f.value
 
-    def set_lowrank(self, U: torch.Tensor, sigma: torch.Tensor, V: torch.Tensor, k: int, zeta: float) -> None:
+    def set_lowrank(self, U: torch.Tensor, sigma: torch.Tensor, V: torch.Tensor, k: int, zeta: float,
+                    flags: int = 0) -> None:
         """Resumes from a factor checkpoint (lowrank() and state() of an earlier context on
         the same D); call after init()."""
         dev = self._D.device
         U, sigma, V = (t.to(dev, torch.float64).contiguous() for t in (U, sigma, V))
         _check(lib().rpca_set_lowrank(self._ctx, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
-                                      ctypes.c_void_p(V.data_ptr()), int(k), float(zeta)), "rpca_set_lowrank")
+                                      ctypes.c_void_p(V.data_ptr()), int(k), float(zeta), int(flags)),
+               "rpca_set_lowrank")
 
     def sparse(self):
         """supp(S_k) as ascending linear indices i*n + j, and the values S_ij."""

@@ -37,8 +37,8 @@ def test_host_only_calls(lib):
     assert lib.rpca_create(ctypes.byref(ctx), ctypes.byref(bad), None) == P.INVALID_ARG
     assert lib.rpca_solve_host(None, 10, 10, 1, 0.1, 0.5, 1e-5, None, None, None, None, None, 0, None, None,
                                None) == P.INVALID_ARG
-    assert lib.rpca_set_lowrank(None, None, None, None, 0, 0.0) == P.INVALID_ARG
-    assert lib.rpca_get_state(None, None, None) == P.INVALID_ARG
+    assert lib.rpca_set_lowrank(None, None, None, None, 0, 0.0, 0) == P.INVALID_ARG
+    assert lib.rpca_get_state(None, None, None, None) == P.INVALID_ARG
     assert lib.rpca_selftest_waits(None, None) == P.INVALID_ARG
     lib.rpca_solve_host_release()  # nothing kept yet: a no-op
 

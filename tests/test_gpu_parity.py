@@ -226,34 +226,37 @@ def test_host_entry_point_keeps_and_regrows_its_buffers():
 
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "bf16_split"])
 def test_resume_from_factor_checkpoint(prec):
-    # a solve interrupted after 5 iterations (its process "fails": the context is dropped) and
-    # resumed in a new context from the factors and (k, zeta_k) alone ends where the
-    # uninterrupted solve ends
+    # a solve interrupted after ck iterations (its process "fails": the context is dropped) and
+    # resumed in a new context from the factors and (k, zeta_k, flags) alone ends where the
+    # uninterrupted solve ends; the BF16_SPLIT checkpoint is taken after its passes switched
+    # to hi + lo
     inst = synth.planted_instance(500, 440, 5, 0.1, 1.0, 41)
     p = inst.params()
     D = torch.from_numpy(inst.D).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
     tol = 1e-10 if prec == "fp64" else 1e-5
+    ck = 8 if prec == "bf16_split" else 5
     with _solver(p, prec, tol) as s:
         s.init(D, 5)
         code0, st0 = s.run()
         L0 = [t.cpu().numpy() for t in s.lowrank()]
     with _solver(p, prec, tol) as s:
         s.init(D, 5)
-        s.iterate(5)
+        s.iterate(ck)
         ckpt = [t.clone() for t in s.lowrank()] + list(s.state())
-    assert ckpt[3] == 5
+    assert ckpt[3] == ck
+    assert ckpt[5] == (P.rpca.STATE_READS_LO if prec == "bf16_split" else 0)
     with _solver(p, prec, tol) as s:
         s.init(D, 5)
         s.set_lowrank(*ckpt)
-        assert s.state() == (5, ckpt[4])
+        assert s.state() == tuple(ckpt[3:])
         code1, st1 = s.run()
         L1 = [t.cpu().numpy() for t in s.lowrank()]
     assert code0 == code1 == P.OK
-    assert st1[0]["k"] == 5 and st1[-1]["k"] == st0[-1]["k"]
+    assert st1[0]["k"] == ck and st1[-1]["k"] == st0[-1]["k"]
     # same iterates up to rounding (Trim and the bases are recomputed from the checkpoint)
-    assert [x["err"] for x in st1] == pytest.approx([x["err"] for x in st0[5:]], rel=1e-3)
+    assert [x["err"] for x in st1] == pytest.approx([x["err"] for x in st0[ck:]], rel=1e-3)
     A, B = [(U * s) @ V.T for U, s, V in (L0, L1)]
     assert rel_fro(B, A) < (1e-9 if prec == "fp64" else 1e-5)
 

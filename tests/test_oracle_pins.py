@@ -243,6 +243,29 @@ def test_initialisation_meets_theorem2_bounds(config1_run):
     assert init["sigma1_D"] == pytest.approx(np.linalg.norm(inst.D, 2), rel=1e-12)
 
 
+def _schedule_tracks_gamma_power(res, inst, p, tol=0.02):
+    """On a planted instance sigma_1(P_T(D - S_k)) settles at sigma_1(L*) within the first
+    iterations and sigma_{r+1}(P_T(D - S_k)) is negligible beside gamma^{k+1} sigma_1, so the
+    schedule of Algorithm 1 started from zeta_0 = beta sigma_1(D - S_{-1}) (Algorithm 3) must
+    follow zeta_k = beta gamma^k sigma_1(L*) at every k, which is the gamma^k rate of Theorem 1.
+    sigma_1(L*) comes from a dense SVD of the planted matrix, not from the oracle."""
+    s1L = np.linalg.norm(inst.L, 2)
+    z = np.asarray(res["history"]["zeta"])
+    c = z / (p["beta"] * p["gamma"] ** np.arange(len(z)) * s1L)
+    return bool(len(z) > 10 and np.all(np.abs(c - 1.0) < tol))
+
+
+def test_threshold_schedule_tracks_gamma_power(config1_run):
+    inst, p, res = config1_run
+    assert _schedule_tracks_gamma_power(res, inst, p)
+    # zeta_0 of Algorithm 3 against a dense spectral norm of D - S_{-1}
+    init = res["init"]
+    assert init["zeta"] == pytest.approx(p["beta"] * np.linalg.norm(inst.D - init["S_init"], 2), rel=1e-12)
+    # zeta_{k+1} / zeta_k = gamma from the first step on (k + 1 in the exponent, not k)
+    z = np.asarray(res["history"]["zeta"])
+    assert np.allclose(z[1:] / z[:-1], p["gamma"], rtol=0.01)
+
+
 def test_iterates_obey_theorem1_l2_bound(config1_run):
     """Theorem 1's L bound, ||L - L_k||_2 <= 8 alpha mu r gamma^k sigma_1^L, along the path."""
     inst, p, res = config1_run
@@ -331,7 +354,17 @@ def _route_no_projection(Z, Ut, Vt, r):
     return np.hstack([Ut, Q1]) @ UM[:, :r], sM[:r], np.hstack([Vt, Q2]) @ VMt.T[:, :r], sM
 
 
-def test_pins_catch_planted_mistakes():
+def test_pins_catch_planted_mistakes(monkeypatch):
+    # the threshold exponent: gamma^k in place of gamma^{k+1} (Algorithm 1)
+    inst = synth.planted_instance(500, 500, 5, 0.1, 1.0, 0)
+    p = inst.params()
+    good = O.next_threshold
+    monkeypatch.setattr(O, "next_threshold",
+                        lambda beta, gamma, k_next, sM, r, zeta_mode="paper": good(beta, gamma, k_next - 1, sM, r,
+                                                                                   zeta_mode))
+    bad = O.accaltproj(inst.D, 5, p["beta"], p["gamma"], 1e-10, p["mu"], beta_init=p["beta_init"])
+    assert not _schedule_tracks_gamma_power(bad, inst, p)
+    monkeypatch.setattr(O, "next_threshold", good)
     rng = np.random.default_rng(9)
     for bad in (_proj_dropped_term, _proj_wrong_sign, _proj_swapped):
         assert not all(_check_projector(bad, O.complement_project, rng, 12, 12, 2) for _ in range(3))
