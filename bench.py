@@ -213,6 +213,132 @@ def time_oracle_sample(inst, iters_to_tol: int, n_iter_sample: int = 2):
             "per_iter_ms": round(per_iter * 1e3, 1), "init_ms": round(t_init * 1e3, 1)}
 
 
+# ---------------------------------------------------------------------------------------
+# Error of the GPU results against the FP64 oracle at the same iteration count
+# ---------------------------------------------------------------------------------------
+
+def video_params(v):
+    """Parameters of the video-shaped workload: the Section 3 choices with mu of the planted
+    rank-2 background, gamma = 0.7 as in the paper's video runs, tol 1e-4."""
+    from synth.planted import incoherence, paper_parameters
+
+    mu = incoherence(np.stack([v.background, np.ones(v.m)], axis=1), np.stack([np.ones(v.n), v.ramp], axis=1))
+    p = paper_parameters(mu, v.m, v.n, 2, float(v.fg_mask.mean()))
+    p["gamma"] = 0.7
+    return p
+
+
+def workload(job):
+    """(D as the FP32 GPU path sees it, widened to FP64; parameters) of a named workload."""
+    if job["kind"] == "video":
+        v = synth.video_instance(seed=job["seed"])
+        return v.D.astype(np.float32).astype(np.float64), video_params(v)
+    inst = synth.planted_instance(job["m"], job["n"], job["r"], job["alpha"], job["c"], job["seed"])
+    return inst.D.astype(np.float32).astype(np.float64), inst.params()
+
+
+def oracle_trajectory(job):
+    """Runs in a spawned process: the FP64 oracle on one workload, Algorithm 3 and then
+    `kmax` steps of Algorithm 1, returning W_k = U_k Sigma_k and V_k for k = 0 .. kmax."""
+    from oracle import accaltproj as O
+
+    t0 = time.perf_counter()
+    D, p = workload(job)
+    r = job["r"]
+    ini = O.initialize(D, r, p["beta_init"], p["beta"])
+    U, s, V, z = ini["U"], ini["sigma"], ini["V"], ini["zeta"]
+    traj = [(U * s, V)]
+    for k in range(job["kmax"]):
+        st = O.step(D, U, s, V, z, k, r, p["beta"], p["gamma"], p["mu"])
+        U, s, V, z = st["U"], st["sigma"], st["V"], st["zeta"]
+        traj.append((U * s, V))
+    return job["name"], traj, time.perf_counter() - t0
+
+
+ORACLE_JOBS = [
+    {"name": "planted_10000_r5", "kind": "planted", "m": M, "n": N, "r": RANK, "alpha": ALPHA, "c": CMAG,
+     "seed": SEED, "kmax": 25},
+    {"name": "mixed_precision_20000_r10", "kind": "planted", "m": 20000, "n": 20000, "r": 10, "alpha": 0.2, "c": 3.0,
+     "seed": SEED, "kmax": 25},
+    {"name": "video_shaped", "kind": "video", "seed": 0, "r": 2, "kmax": 30},
+]
+
+
+class OracleRuns:
+    """The oracle trajectories of ORACLE_JOBS, computed by spawned worker processes on the
+    host cores while the GPU runs the other sections (each worker confined to the cores the
+    bench's own process leaves free, with a share of the BLAS threads)."""
+
+    def __init__(self, jobs, keep_cores=2):
+        import multiprocessing as mp
+
+        cores = sorted(os.sched_getaffinity(0))
+        free = cores[keep_cores:] if len(cores) > keep_cores + len(jobs) else cores
+        self.threads = max(1, len(free) // len(jobs))
+        saved_env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        saved_aff = os.sched_getaffinity(0)
+        for k in saved_env:
+            os.environ[k] = str(self.threads)
+        os.sched_setaffinity(0, free)  # inherited by the workers
+        try:
+            self.pool = mp.get_context("spawn").Pool(len(jobs))
+            self.pending = [self.pool.apply_async(oracle_trajectory, (j,)) for j in jobs]
+        finally:
+            os.sched_setaffinity(0, saved_aff)
+            for k, v in saved_env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.cores = len(free)
+        self.results = None
+
+    def get(self):
+        if self.results is None:
+            self.results = {}
+            for a in self.pending:
+                name, traj, secs = a.get()
+                self.results[name] = (traj, secs)
+            self.pool.close()
+            self.pool.join()
+        return self.results
+
+
+def vs_oracle(runs, name, k, U, sig, V):
+    """||L_gpu - L_oracle,k||_F / ||L_oracle,k||_F at the GPU's iteration count k."""
+    traj, _ = runs.get()[name]
+    if k is None or k >= len(traj):
+        return None
+    W, Vo = traj[k]
+    return _factored_rel_err(U, sig, V, W, Vo)
+
+
+def oracle_parity(runs, fac, extras):
+    """Relative Frobenius error of each GPU result against the FP64 oracle's L_k at the same
+    iteration count k; also written into the entries of `extras` it belongs to."""
+    out = {}
+    for (name, what), val in fac.items():
+        if what.endswith("_per_iteration"):
+            continue
+        k, U, sig, V = val
+        e = vs_oracle(runs, name, k, U, sig, V)
+        out.setdefault(name, {})[what] = e
+        if name == "video_shaped":
+            extras["video_shaped"]["L_rel_err_vs_oracle"] = e
+        elif what in extras.get("precision_modes", {}).get(name, {}):
+            extras["precision_modes"][name][what]["L_rel_err_vs_oracle"] = e
+    per = fac.get(("mixed_precision_20000_r10", "bf16_split_per_iteration"))
+    if per:
+        rows = [[k, None if e is None else float("%.3e" % e)]
+                for k, e in ((k, vs_oracle(runs, "mixed_precision_20000_r10", k, U, s_, V)) for k, U, s_, V in per)]
+        extras["precision_modes"]["mixed_precision_20000_r10"]["bf16_split"]["per_iteration_k_Lerr_vs_oracle"] = rows
+    out["oracle_seconds"] = {name: round(secs, 1) for name, (_, secs) in runs.get().items()}
+    out["oracle_cores"] = runs.cores
+    out["note"] = ("||L_gpu,k - L_oracle,k||_F / ||L_oracle,k||_F with the FP64 oracle run for the same number k of "
+                   "iterations of Algorithm 1 from its own initialisation (Algorithm 3) on the FP32-rounded D")
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -327,15 +453,13 @@ def video_section(dev):
     """The video-shaped workload (176 x 144 frames x 2000 frames, rank-2 background, three
     moving rectangles, noise 1e-3; r = 2, gamma = 0.7, tol 1e-4): solve time from D resident
     in HBM, iterations, background error against the planted one and the noise floor."""
-    from synth.planted import incoherence, paper_parameters
     import paper_1711_05519_gb300 as P
 
     v = synth.video_instance(seed=0)
-    mu = incoherence(np.stack([v.background, np.ones(v.m)], axis=1), np.stack([np.ones(v.n), v.ramp], axis=1))
-    p = paper_parameters(mu, v.m, v.n, 2, float(v.fg_mask.mean()))
+    p = video_params(v)
     D = torch.from_numpy(v.D.astype(np.float32)).to(dev)
     times = []
-    with P.Solver(p["beta"], 0.7, 1e-4, precision="fp32", beta_init=p["beta_init"], mu_trim=p["mu"],
+    with P.Solver(p["beta"], p["gamma"], 1e-4, precision="fp32", beta_init=p["beta_init"], mu_trim=p["mu"],
                   max_iter=100) as s:
         for rep in range(4):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -349,26 +473,30 @@ def video_section(dev):
         U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
     L = (U * sig) @ V.T
     Lt = v.L
-    return {"workload": "video-shaped 25344 x 2000, r=2, gamma=0.7, tol 1e-4, FP32", "ms": round(statistics.median(times), 3),
-            "iterations": stats[-1]["k"], "err": stats[-1]["err"],
-            "L_rel_err": float(np.linalg.norm(L - Lt) / np.linalg.norm(Lt)),
-            "noise_floor_rel": float(v.noise * np.sqrt(v.m * v.n) / np.linalg.norm(Lt))}
+    out = {"workload": "video-shaped 25344 x 2000, r=2, gamma=0.7, tol 1e-4, FP32",
+           "ms": round(statistics.median(times), 3), "iterations": stats[-1]["k"], "err": stats[-1]["err"],
+           "L_rel_err": float(np.linalg.norm(L - Lt) / np.linalg.norm(Lt)),
+           "noise_floor_rel": float(v.noise * np.sqrt(v.m * v.n) / np.linalg.norm(Lt))}
+    return out, (stats[-1]["k"], U, sig, V)
 
 
 def _factored_rel_err(U, sig, V, P, Q):
-    """||U diag(sig) V^T - P Q^T||_F / ||P Q^T||_F from r x r products."""
-    A2 = np.sum((sig[:, None] * (U.T @ U)) * ((V.T @ V) * sig[None, :]))
-    B2 = np.sum((P.T @ P) * (Q.T @ Q))
-    AB = np.trace(np.diag(sig) @ (U.T @ P) @ (Q.T @ V))
-    return float(np.sqrt(max(A2 + B2 - 2.0 * AB, 0.0)) / np.sqrt(B2))
+    """||U diag(sig) V^T - P Q^T||_F / ||P Q^T||_F from thin QR factors (no m x n array):
+    X Y^T with X = [U diag(sig), -P], Y = [V, Q] has the norm of R_X R_Y^T, which the QR
+    gives to rounding level (a difference of squared norms would stop at ~1e-8)."""
+    rx = np.linalg.qr(np.hstack([U * sig, -P]), mode="r")
+    ry = np.linalg.qr(np.hstack([V, Q]), mode="r")
+    rp = np.linalg.qr(P, mode="r")
+    rq = np.linalg.qr(Q, mode="r")
+    return float(np.linalg.norm(rx @ ry.T) / np.linalg.norm(rp @ rq.T))
 
 
-def precision_section(dev):
+def precision_section(dev, fac):
     """The bf16 storage modes of D against plain FP32 on the mixed-precision workload
     (m = n = 2*10^4, r = 10, alpha = 0.2, c = 3, gamma = 0.5, tol 1e-5) and on the 10^4
     workload: time to tol from D resident in HBM (initialisation included, as in the main
-    line), and the error of L_k against the planted L* per iteration (the FP64 oracle
-    recovers L* to 1e-10 on the 500 x 500 workload, so this is the error against FP64)."""
+    line), the error of L_k against the planted L*, and (filled in later from `fac`) against
+    the FP64 oracle at the same iteration count, per iteration for BF16_SPLIT."""
     import paper_1711_05519_gb300 as P
 
     out = {}
@@ -393,6 +521,7 @@ def precision_section(dev):
                     if rep or prec == "bf16":
                         times.append(e0.elapsed_time(e1))
                 U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
+                fac[(name, prec)] = (stats[-1]["k"], U, sig, V)
                 entry = {"L_rel_err": _factored_rel_err(U, sig, V, inst.P, inst.Q), "iterations": stats[-1]["k"],
                          "err": stats[-1]["err"], "pass_kind": s.pass_kind()[0]}
                 if prec != "bf16":
@@ -401,15 +530,18 @@ def precision_section(dev):
                 if prec == "bf16_split" and name.startswith("mixed"):
                     # per-iteration error of L_k against L* (untimed rerun, one iteration per call)
                     s.init(D, r)
-                    per = []
+                    per, per_fac = [], []
                     while True:
                         code, st = s.iterate(1)
                         U, sig, V = (t.double().cpu().numpy() for t in s.lowrank())
+                        k_held = s.state()[0]
                         for x in st:
                             per.append([x["k"], float("%.3e" % x["err"]),
                                         float("%.3e" % _factored_rel_err(U, sig, V, inst.P, inst.Q))])
+                        per_fac.append((k_held, U, sig, V))
                         if code == P.OK or not st:
                             break
+                    fac[(name, "bf16_split_per_iteration")] = per_fac
                     entry["per_iteration_k_err_Lerr"] = per
                 sec[prec] = entry
         out[name] = sec
@@ -528,6 +660,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the unfused and learned-schedule comparisons")
+    ap.add_argument("--no-oracle-parity", action="store_true",
+                    help="skip the FP64 oracle runs that give each result's error against the oracle")
     ap.add_argument("--phase-transition", type=int, default=0, metavar="TRIALS",
                     help="run Table 2 of the paper on the GPU with TRIALS trials per cell, print JSON and exit")
     ap.add_argument("--runtime-sweep", action="store_true",
@@ -641,23 +775,34 @@ def main():
         e2e = {"value": round(e2e_ms, 2), "unit": "ms", "h2d_bytes_per_step": M * N * 4,
                "d2h_bytes_per_step": 8 * (M + N) * RANK + 8 * RANK + 16 * nnz}
 
-    extras = {}
-    if rank == 0 and not args.no_extras:
-        extras["unfused_iteration_ms"] = round(unfused_iteration_ms(D, p, solver), 3)
-        extras["learned_schedule"] = learned_section(dev)
-        extras["video_shaped"] = video_section(dev)
-        extras["precision_modes"] = precision_section(dev)
+    U_h, s_h, V_h = (t.double().cpu().numpy() for t in solver.lowrank())
 
+    # the oracle baseline is timed alone on the host cores, before anything else runs there
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle_sample(inst, iters)
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # oracle trajectories for the error of every result against FP64, computed on the
+        # host cores while the GPU runs the other workloads
+        runs = OracleRuns(ORACLE_JOBS) if not args.no_oracle_parity else None
+        fac = {("planted_10000_r5", "fp32_headline"): (iters, U_h, s_h, V_h)}
+        extras["unfused_iteration_ms"] = round(unfused_iteration_ms(D, p, solver), 3)
+        extras["learned_schedule"] = learned_section(dev)
+        extras["video_shaped"], fac[("video_shaped", "fp32")] = video_section(dev)
+        extras["precision_modes"] = precision_section(dev, fac)
+        if runs is not None:
+            extras["oracle_parity"] = oracle_parity(runs, fac, extras)
+
     if rank == 0:
+        lerr = extras.get("oracle_parity", {}).get("planted_10000_r5", {}).get("fp32_headline")
         line = {"metric": METRIC, "value": round(ms_per_step, 3), "unit": "ms", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (planted instance of Section 3, seeded)",
                 "config": config({"iterations_to_tol": iters, "final_err": stats[-1]["err"],
+                                  "L_rel_err_vs_oracle": lerr,
                                   "iteration_ms": round(statistics.median(run_ms) / (iters + 1), 4),
                                   "init_ms": round(ms_per_step - statistics.median(run_ms), 3)}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,

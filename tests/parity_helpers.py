@@ -21,8 +21,11 @@ def rel_fro(A, B):
 
 
 def factored_rel_err(U, sig, V, P, Q):
-    """||U diag(sig) V^T - P Q^T||_F / ||P Q^T||_F from r x r products (no m x n array)."""
-    A2 = np.sum((sig[:, None] * (U.T @ U)) * ((V.T @ V) * sig[None, :]))
-    B2 = np.sum((P.T @ P) * (Q.T @ Q))
-    AB = np.trace(np.diag(sig) @ (U.T @ P) @ (Q.T @ V))
-    return float(np.sqrt(max(A2 + B2 - 2.0 * AB, 0.0)) / np.sqrt(B2))
+    """||U diag(sig) V^T - P Q^T||_F / ||P Q^T||_F from thin QR factors (no m x n array):
+    X Y^T with X = [U diag(sig), -P], Y = [V, Q] has the norm of R_X R_Y^T, which the QR
+    gives to rounding level (a difference of squared norms would stop at ~1e-8)."""
+    rx = np.linalg.qr(np.hstack([U * sig, -P]), mode="r")
+    ry = np.linalg.qr(np.hstack([V, Q]), mode="r")
+    rp = np.linalg.qr(P, mode="r")
+    rq = np.linalg.qr(Q, mode="r")
+    return float(np.linalg.norm(rx @ ry.T) / np.linalg.norm(rp @ rq.T))
