@@ -62,8 +62,23 @@ typedef enum {
 
 /* Threshold rule.  PAPER: zeta_{k+1} = beta (sigma_{r+1} + gamma^{k+1} sigma_1) of
  * P_T(D - S_k) (Algorithm 1).  SIMPLE: zeta_{k+1} = beta gamma^{k+1} sigma_1.
- * EXTERNAL: the caller sets zeta before each iteration with rpca_set_zeta. */
-typedef enum { RPCA_ZETA_PAPER = 0, RPCA_ZETA_SIMPLE = 1, RPCA_ZETA_EXTERNAL = 2 } rpca_zeta_mode;
+ * EXTERNAL: the caller sets zeta before each iteration with rpca_set_zeta.
+ * LEARNED (not in the paper): zeta_{k+1} = zeta^plain_{k+1} exp(clamp(g(s_k), -log 4, log 4)),
+ *   zeta^plain the PAPER rule and g a 6 -> 32 -> 32 -> 1 tanh network (FP32) on the statistics
+ *   s_k = [log sigma_1, log(sigma_{r+1}/sigma_1), log err_k, fraction of the entries whose
+ *   support membership changed since pass k - 1 (0 at k = 0), (k + 1) / K, log(zeta_k/sigma_1)],
+ *   evaluated on the device inside the iteration; parameters and K from rpca_set_schedule.
+ *   The passes then also keep the support of the last two passes as bitmasks (2 m n / 8 bytes). */
+typedef enum {
+  RPCA_ZETA_PAPER = 0,
+  RPCA_ZETA_SIMPLE = 1,
+  RPCA_ZETA_EXTERNAL = 2,
+  RPCA_ZETA_LEARNED = 3
+} rpca_zeta_mode;
+
+/* Number of FP32 parameters of the LEARNED threshold network, packed (row-major weight
+ * matrices, output index first): W1 [32][6] | b1 [32] | W2 [32][32] | b2 [32] | w3 [32] | b3. */
+#define RPCA_SCHEDULE_PARAMS 1313
 
 typedef struct {
   double beta;       /* threshold parameter of Algorithm 1                               */
@@ -96,6 +111,10 @@ typedef struct {
   double sigma1;       /* sigma_1 of P_T(D - S_k) (0 if the iteration stopped at k)       */
   double sigma_r1;     /* sigma_{r+1} of P_T(D - S_k)                                    */
   int64_t nnz;         /* |supp(S_k)|                                                    */
+  double zeta_next_plain; /* zeta^plain_{k+1} of Algorithm 1 (0 if the iteration stopped)   */
+  double g;            /* LEARNED: clamped network output g(s_k); zeta_{k+1} = plain e^g  */
+  double features[6];  /* LEARNED: the statistics s_k the network read (0 otherwise)       */
+  int64_t support_changes; /* LEARNED: entries whose support membership changed since k-1 */
 } rpca_iter_stats;
 
 typedef struct rpca_ctx rpca_ctx;
@@ -137,6 +156,19 @@ int rpca_get_pass_kind(rpca_ctx* ctx, int* iteration_kind, int* init_kind);
 
 /* Sets zeta_k for the next pass (zeta_mode EXTERNAL). */
 int rpca_set_zeta(rpca_ctx* ctx, double zeta);
+
+/* zeta_mode LEARNED: the network parameters (device, RPCA_SCHEDULE_PARAMS floats, copied into
+ * the context) and the unrolled depth K of the statistic (k + 1) / K.  Must be called before
+ * rpca_iterate (RPCA_ERR_STATE otherwise); RPCA_ERR_STATE in the other modes. */
+int rpca_set_schedule(rpca_ctx* ctx, const float* theta, int depth);
+
+/* Copies the four operands the next pass reads, into caller-owned device buffers of the
+ * context's working precision (float in FP32 / BF16 modes, double in FP64): W = U_k Sigma_k
+ * (m x R), V_k (n x R), and the trimmed orthonormal bases U~_k (m x R), V~_k (n x R) of
+ * Section 2.1, row-major, zero-padded to the width R written to *width (host; the padded
+ * rank, at most 16).  A checkpoint of the iterate in the form the pass uses; the learned
+ * schedule trains on them.  Not part of the paper's method. */
+int rpca_get_pass_operands(rpca_ctx* ctx, void* W, void* V, void* Ut, void* Vt, int* width);
 
 /* Copies the current low-rank factors L_k = U diag(sigma) V^T into caller-owned device
  * buffers: U (m x r), sigma (r), V (n x r), all double, row-major. */

@@ -13,6 +13,7 @@
 
 #include "../../include/rpca.h"
 #include "common.cuh"
+#include "mlp.cuh"
 #include "tc_images.cuh"
 
 namespace rpca {
@@ -67,6 +68,14 @@ struct rpca_ctx {
   int* h_flags = nullptr;  // pinned: done, k, status, conv
   unsigned long long *rowcnt = nullptr, *rowoff = nullptr;
   bool ready = false;
+  // learned threshold schedule: network parameters (mlp.cuh), unrolled depth, support
+  // bitmasks of the last two passes and per-CTA support-change counts
+  float* theta = nullptr;
+  int depth = 0;
+  bool theta_set = false;
+  unsigned* masks = nullptr;
+  long long mask_wr = 0;
+  unsigned long long* chgP = nullptr;
   // tensor-core pass
   bool tc_iter = false, tc_init = false;
   CUtensorMap dmap, dmap_lo;
@@ -111,7 +120,7 @@ void free_workspace(rpca_ctx* c) {
                    (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
                    &c->Down, &c->Dhl, (void**)&c->wop[0], (void**)&c->vop[0], (void**)&c->vtop[0],
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
-                   (void**)&c->utop[1], (void**)&c->Y2c};
+                   (void**)&c->utop[1], (void**)&c->Y2c, (void**)&c->masks, (void**)&c->chgP};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -183,6 +192,8 @@ struct Grid {
 };
 bool use_tc(const rpca_ctx* c, int R) { return (R == c->Rr) ? c->tc_iter : (R == c->Rb ? c->tc_init : false); }
 
+bool learned(const rpca_ctx* c) { return c->p.zeta_mode == RPCA_ZETA_LEARNED; }
+
 Grid pass_grid(const rpca_ctx* c, int R) {
   if (use_tc(c, R)) return Grid{c->tcB, c->tcA, c->tcA * c->tcB};
   const PassGeom g = pass_geometry(c->prec, R);
@@ -192,7 +203,7 @@ Grid pass_grid(const rpca_ctx* c, int R) {
 
 // One fused pass at compiled rank R: the initialisation's (init) or the iteration's.
 int run_pass(rpca_ctx* c, int R, bool init) {
-  PassArgs a;
+  PassArgs a{};
   a.D = c->D;
   a.ld = c->ld;
   a.m = (int)c->m;
@@ -215,9 +226,14 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     a.dm = 1;
     a.Dlo = c->split ? static_cast<const uint8_t*>(c->Dhl) + (size_t)c->m * c->ldb * 2 : nullptr;
   }
+  // the learned schedule's support-change statistic: bitmasks in the iteration's passes
+  const bool track = learned(c) && !init;
+  a.masks = track ? c->masks : nullptr;
+  a.mask_wr = c->mask_wr;
+  a.chgP = track ? c->chgP : nullptr;
   prof_mark(c, true, true);
   if (init ? c->tc_init : c->tc_iter) {
-    TcPassArgs t;
+    TcPassArgs t{};
     t.m = (int)c->m;
     t.n = (int)c->n;
     t.R = R;
@@ -239,6 +255,9 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.Y2c = c->Y2c;
     t.ch_max = c->y2_ch;
     t.ct_max = c->y2_ct;
+    t.masks = a.masks;
+    t.mask_wr = a.mask_wr;
+    t.chgP = a.chgP;
     CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
   } else {
     CK(launch_fused_pass(c->prec, R, a, c->stream));
@@ -326,6 +345,9 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.P2 = c->P2;
   a.resP = c->resP;
   a.nnzP = c->nnzP;
+  a.chgP = (learned(c) && mode == SM_UPDATE) ? c->chgP : nullptr;
+  a.theta = c->theta;
+  a.depth = c->depth;
   a.U = c->U;
   a.sig = c->sig;
   a.V = c->V;
@@ -410,7 +432,7 @@ int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
   *out = nullptr;
   const rpca_params& p = *params;
   if (!(p.beta > 0) || !(p.gamma >= 0 && p.gamma < 1) || !(p.tol >= 0) || p.max_iter < 0 ||
-      p.precision < RPCA_PREC_FP64 || p.precision > RPCA_PREC_BF16_SPLIT || p.zeta_mode < 0 || p.zeta_mode > 2 ||
+      p.precision < RPCA_PREC_FP64 || p.precision > RPCA_PREC_BF16_SPLIT || p.zeta_mode < 0 || p.zeta_mode > 3 ||
       p.beta_init < 0 || p.mu_trim < 0 || p.pass_kind < 0 || p.pass_kind > 2 || !(p.split_switch >= 0))
     return RPCA_ERR_INVALID_ARG;
   rpca_ctx* c = new (std::nothrow) rpca_ctx();
@@ -439,6 +461,7 @@ void rpca_destroy(rpca_ctx* c) {
   prof_collect(c, 0);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   free_workspace(c);
+  if (c->theta) cudaFree(c->theta);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   delete c;
 }
@@ -556,6 +579,15 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       CK(cudaMemsetAsync(c->vtop[set], 0, (size_t)c->TC * img::VTOP_MAX, c->stream));
     }
   }
+  if (learned(c)) {
+    // words per row: the tensor-core pass uses 2 per 64-column tile, the SIMT pass VW per
+    // sub-chunk of 32 VW columns (VW = 4 in FP32, 2 in FP64)
+    const long long wr_tc = 2 * ((n + 63) / 64), wr_simt = (c->prec == PREC_F32) ? 4 * ((n + 127) / 128) : wr_tc;
+    c->mask_wr = wr_tc > wr_simt ? wr_tc : wr_simt;
+    CK(cudaMalloc((void**)&c->masks, sizeof(unsigned) * 2 * (size_t)m * c->mask_wr));
+    CK(cudaMemsetAsync(c->masks, 0, sizeof(unsigned) * 2 * (size_t)m * c->mask_wr, c->stream));
+    if ((st = dalloc(&c->chgP, ncta))) return st;
+  }
   c->ws_m = m;
   c->ws_n = n;
   c->ws_r = r;
@@ -627,7 +659,7 @@ int rpca_set_zeta(rpca_ctx* c, double zeta) {
 int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
   if (n_done) *n_done = 0;
   if (!c || n_iters < 0) return RPCA_ERR_INVALID_ARG;
-  if (!c->ready) return RPCA_ERR_STATE;
+  if (!c->ready || (learned(c) && !c->theta_set)) return RPCA_ERR_STATE;
   int st;
   if ((st = read_flags(c))) return st;
   const int k0 = flag_k(c);
@@ -663,6 +695,10 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
       out[i].sigma1 = hs[i].sigma1;
       out[i].sigma_r1 = hs[i].sigma_r1;
       out[i].nnz = hs[i].nnz;
+      out[i].zeta_next_plain = hs[i].zeta_next_plain;
+      out[i].g = hs[i].g;
+      for (int f = 0; f < 6; ++f) out[i].features[f] = hs[i].feat[f];
+      out[i].support_changes = hs[i].changes;
     }
   if (n_done) *n_done = count;
   if (flag_done(c)) {
@@ -672,6 +708,28 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     return (last.err < c->p.tol) ? RPCA_OK : RPCA_ERR_NOT_CONVERGED;
   }
   return RPCA_ERR_NOT_CONVERGED;
+}
+
+int rpca_set_schedule(rpca_ctx* c, const float* theta, int depth) {
+  if (!c || !theta || depth < 1) return RPCA_ERR_INVALID_ARG;
+  if (!learned(c)) return RPCA_ERR_STATE;
+  if (!c->theta) CK(cudaMalloc((void**)&c->theta, sizeof(float) * mlp::NPARAM));
+  CK(cudaMemcpyAsync(c->theta, theta, sizeof(float) * mlp::NPARAM, cudaMemcpyDeviceToDevice, c->stream));
+  c->depth = depth;
+  c->theta_set = true;
+  return RPCA_OK;
+}
+
+int rpca_get_pass_operands(rpca_ctx* c, void* W, void* V, void* Ut, void* Vt, int* width) {
+  if (!c || !W || !V || !Ut || !Vt || !width) return RPCA_ERR_INVALID_ARG;
+  if (!c->ready) return RPCA_ERR_STATE;
+  *width = c->Rr;
+  const size_t rm = (size_t)c->m * c->Rr * c->tsize, rn = (size_t)c->n * c->Rr * c->tsize;
+  CK(cudaMemcpyAsync(W, c->Wc, rm, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(Ut, c->Utc, rm, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(V, c->Vc, rn, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(Vt, c->Vtc, rn, cudaMemcpyDeviceToDevice, c->stream));
+  return RPCA_OK;
 }
 
 int rpca_get_lowrank(rpca_ctx* c, double* U, double* sigma, double* V) {

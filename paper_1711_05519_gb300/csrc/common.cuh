@@ -46,6 +46,12 @@ struct DevStats {
   double err, zeta, sigma1, sigma_r1, res2;
   long long nnz;
   int k, pad;
+  // learned threshold schedule (zeta mode LEARNED; zero otherwise): zeta^plain_{k+1} of
+  // Algorithm 1, the clamped network output g(s_k), the statistics s_k (mlp.cuh) and the
+  // number of entries whose support membership changed since pass k - 1
+  double zeta_next_plain, g;
+  float feat[6];
+  long long changes;
 };
 
 // Precision of the fused pass (what D is read as and what the m x n arithmetic uses).
@@ -78,6 +84,11 @@ struct PassArgs {
   // of ld elements, ld a multiple of 8; the pass reads D = hi (+ lo once DevState.use_lo).
   int dm;
   const void* Dlo;
+  // support bitmasks (null unless the learned schedule needs the support change): two
+  // buffers of m x mask_wr words; pass k writes buffer k % 2 and compares with the other
+  unsigned* masks;
+  long long mask_wr;
+  unsigned long long* chgP;  // per CTA: entries whose support membership changed
 };
 
 // Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
@@ -104,6 +115,10 @@ struct TcPassArgs {
   // kTcY2Chunk), ct_max >= column tiles per CTA
   float* Y2c;
   int ch_max, ct_max;
+  // support bitmasks as in PassArgs (null: not tracked)
+  unsigned* masks;
+  long long mask_wr;
+  unsigned long long* chgP;
 };
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
@@ -151,6 +166,9 @@ struct SmallArgs {
   const void* P2;
   const double* resP;
   const unsigned long long* nnzP;
+  const unsigned long long* chgP;  // per-CTA support changes (null: not tracked)
+  const float* theta;              // learned schedule: network parameters (mlp.cuh)
+  int depth;                       // learned schedule: unrolled depth K of the statistic (k+1)/K
   // Arrays below hold the kernel's working precision (double in FP64 mode, float in
   // FP32 mode).
   void* U; void* sig; void* V;         // factors of L_k (m x r, r, n x r)

@@ -178,8 +178,14 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   // residual: the TM x VW terms of one sub-chunk are summed in T, the sub-chunk sums in
   // double (one FP32 chain over the ~10^3 terms a thread sees would bias err_k)
   double res = 0.0;
-  unsigned nnz = 0;
+  unsigned nnz = 0, chg = 0;
   T* mySlot = sY2 + warp * R * BW;
+  // support bitmasks (learned schedule): word (i, chunk, c) holds, in bit l, the entry of row
+  // i at column chunk * SCW + l * VW + c; pass k writes buffer k % 2 and compares with the other
+  const bool track = a.masks != nullptr;
+  const long long mask_sz = a.mask_wr * (long long)m;
+  unsigned* mask_new = track ? a.masks + ((a.st->k & 1) ? mask_sz : 0) : nullptr;
+  const unsigned* mask_old = track ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
 
   for (int rb = 0; rb < NRB; ++rb) {
     const int rl0 = rb * WARPS * TM + warp * TM;  // local row of this warp's first row
@@ -213,6 +219,8 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
           y2[c][k] = T(0);
         }
       T rsc = T(0);
+      static_assert(TM * VW <= 32, "support bits of a sub-chunk fit one word");
+      unsigned sb = 0;
 #pragma unroll
       for (int t = 0; t < TM; ++t) {
         T w[R], ut[R];
@@ -228,6 +236,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
           const bool s = fabs(rr) > zeta;
           rsc = s ? rsc : fma(rr, rr, rsc);
           nnz += s ? 1u : 0u;
+          sb |= (s ? 1u : 0u) << (t * VW + c);
           const T z = s ? l : d[t][c];
 #pragma unroll
           for (int k = 0; k < R; ++k) {
@@ -237,6 +246,22 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
         }
       }
       res += static_cast<double>(rsc);
+      if (track) {
+        const long long chunk = (col0 + sc * SCW) / SCW;
+#pragma unroll
+        for (int t = 0; t < TM; ++t)
+#pragma unroll
+          for (int c = 0; c < VW; ++c) {
+            const unsigned w = __ballot_sync(0xffffffffu, (sb >> (t * VW + c)) & 1u);
+            const int i = row0 + rl0 + t;
+            if (lane == t * VW + c && i < m) {
+              const long long wi = (long long)i * a.mask_wr + chunk * VW + c;
+              const unsigned old = mask_old[wi];
+              mask_new[wi] = w;
+              chg += __popc(w ^ old);
+            }
+          }
+      }
 #pragma unroll
       for (int k = 0; k < R; ++k)
 #pragma unroll
@@ -264,26 +289,32 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   }
   // CTA totals of the residual and the support size.
   __shared__ double sres[8];
-  __shared__ unsigned long long snnz[8];
+  __shared__ unsigned long long snnz[8], schg[8];
   double rd = warp_sum(res);
-  unsigned long long nz = nnz;
+  unsigned long long nz = nnz, cz = chg;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    cz += __shfl_xor_sync(0xffffffffu, cz, o);
+  }
   if (lane == 0) {
     sres[warp] = rd;
     snnz[warp] = nz;
+    schg[warp] = cz;
   }
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    unsigned long long z = 0;
+    unsigned long long z = 0, cc = 0;
     for (int w = 0; w < WARPS; ++w) {
       t += sres[w];
       z += snnz[w];
+      cc += schg[w];
     }
     const int cta = blockIdx.y * gridDim.x + blockIdx.x;
     a.resP[cta] = t;
     a.nnzP[cta] = z;
+    if (track) a.chgP[cta] = cc;
   }
 }
 

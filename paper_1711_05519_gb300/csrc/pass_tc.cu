@@ -128,6 +128,9 @@ struct TcArgs {
   unsigned long long* nnzP;
   float* Y2c;
   int ch_max, ct_max;
+  unsigned* masks;
+  long long mask_wr;
+  unsigned long long* chgP;
 };
 
 __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) {
@@ -168,7 +171,10 @@ __device__ __forceinline__ void tmem_ld_y(uint32_t taddr, uint32_t (&v)[NY]) {
 // lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
 // DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
 // 32 KB and Z is written over it (where: zhi_off / zlo_off).  RK: operand image layout (8 or 16).
-template <int DM, int RK>
+// MASK: also write the support as a bitmask (word 2 ct + h of row i holds columns
+// 64 ct + 32 h .. + 31) and count the entries whose membership differs from the previous
+// pass's bitmask (the learned schedule's support-change statistic).
+template <int DM, int RK, bool MASK>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap,
                                                             const __grid_constant__ CUtensorMap dmap_lo, TcArgs a) {
   using C = Cfg<RK>;
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ double red_res[EPI_WARPS];
-  __shared__ unsigned long long red_nnz[EPI_WARPS];
+  __shared__ unsigned long long red_nnz[EPI_WARPS], red_chg[EPI_WARPS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x;
@@ -384,11 +390,16 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const int rowl = 32 * q + lane;
     const float zeta = static_cast<float>(a.st->zeta);
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    // residual: each tile's 32 squared terms of this thread are summed in FP32, the tile sums
-    // in FP64 (a thread sees thousands of terms per pass; one FP32 chain over all of them
-    // would bias err_k by up to ~1e-4 relative)
-    double res = 0.0;
-    unsigned nnz = 0;
+    // residual: each tile's 32 squared terms of this thread are summed in a chain of their
+    // own and only the tile sums (~40 per pass) are added up, so no FP32 chain is longer than
+    // ~40 terms (one chain over the thousands of terms a thread sees per pass biased err_k by
+    // up to ~1e-4 relative); the totals over threads are taken in FP64
+    float res = 0.f;
+    unsigned nnz = 0, chg = 0;
+    // support bitmasks of this pass (k even: buffer 0) and of the previous one
+    const long long mask_sz = a.mask_wr * (long long)a.m;
+    unsigned* mask_new = MASK ? a.masks + ((a.st->k & 1) ? mask_sz : 0) : nullptr;
+    const unsigned* mask_old = MASK ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
     for (int t = grp; t < ntiles && !abort_flag; t += 2) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
       if (rtl % G2 == 0 && rtl > 0) {
@@ -465,19 +476,30 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
       const float2 m1 = make_float2(-1.f, -1.f);
-      float rt0 = 0.f, rt1 = 0.f;
+      float rq = 0.f;
+      uint32_t bits = 0;
 #pragma unroll
       for (int c = 0; c < 32; c += 2) {
         const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
         const float2 r2 = __ffma2_rn(l2, m1, make_float2(z[c], z[c + 1]));  // D - L, exactly rounded
         const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;
-        rt0 = s0 ? rt0 : fmaf(r2.x, r2.x, rt0);
-        rt1 = s1 ? rt1 : fmaf(r2.y, r2.y, rt1);
+        rq = s0 ? rq : fmaf(r2.x, r2.x, rq);
+        rq = s1 ? rq : fmaf(r2.y, r2.y, rq);
         nnz += (s0 ? 1u : 0u) + (s1 ? 1u : 0u);
+        if (MASK) bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
         z[c] = s0 ? l2.x : z[c];
         z[c + 1] = s1 ? l2.y : z[c + 1];
       }
-      res += (double)(rt0 + rt1);
+      res += rq;
+      if (MASK) {
+        const int row = (rt0 + rtl) * BM + rowl;
+        if (row < a.m) {
+          const long long w = (long long)row * a.mask_wr + 2 * (ct0 + ctl) + h;
+          const unsigned old = mask_old[w];
+          mask_new[w] = bits;
+          chg += __popc(bits ^ old);
+        }
+      }
       // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
       // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
       uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
@@ -580,27 +602,31 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
     }
     // CTA totals of the residual and the support size
-    double rd = res;
-    unsigned long long nz = nnz;
+    double rd = (double)res;
+    unsigned long long nz = nnz, cz = chg;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       rd += __shfl_xor_sync(0xffffffffu, rd, o);
       nz += __shfl_xor_sync(0xffffffffu, nz, o);
+      if (MASK) cz += __shfl_xor_sync(0xffffffffu, cz, o);
     }
     if (lane == 0) {
       red_res[warp - 4] = rd;
       red_nnz[warp - 4] = nz;
+      red_chg[warp - 4] = cz;
     }
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
     if (tid == 128) {
       double tr = 0.0;
-      unsigned long long tz = 0;
+      unsigned long long tz = 0, tc = 0;
       for (int w = 0; w < EPI_WARPS; ++w) {
         tr += red_res[w];
         tz += red_nnz[w];
+        tc += red_chg[w];
       }
       a.resP[cta] = tr;
       a.nnzP[cta] = tz;
+      if (MASK) a.chgP[cta] = tc;
     }
   }
   tc_fence_before();
@@ -611,10 +637,19 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
 
 static_assert(Cfg<8>::MAX_CT >= 20 && Cfg<16>::MAX_CT >= 10, "column tiles per CTA (tc_max_col_tiles)");
 
-template <int DM, int RK>
+template <int DM, int RK, bool MASK>
 cudaError_t set_tc_smem() {
-  return cudaFuncSetAttribute(fused_pass_tc<DM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(fused_pass_tc<DM, RK, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Cfg<RK>::SMEM_BYTES);
+}
+
+template <int DM, int RK>
+cudaError_t launch_tc(const CUtensorMap& dmap, const CUtensorMap& lo, const TcArgs& a, cudaStream_t s) {
+  if (a.masks)
+    fused_pass_tc<DM, RK, true><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+  else
+    fused_pass_tc<DM, RK, false><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -627,10 +662,14 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
                                  cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_tc_smem<0, 8>();
-    if (e == cudaSuccess) e = set_tc_smem<1, 8>();
-    if (e == cudaSuccess) e = set_tc_smem<0, 16>();
-    if (e == cudaSuccess) e = set_tc_smem<1, 16>();
+    cudaError_t e = set_tc_smem<0, 8, false>();
+    if (e == cudaSuccess) e = set_tc_smem<1, 8, false>();
+    if (e == cudaSuccess) e = set_tc_smem<0, 16, false>();
+    if (e == cudaSuccess) e = set_tc_smem<1, 16, false>();
+    if (e == cudaSuccess) e = set_tc_smem<0, 8, true>();
+    if (e == cudaSuccess) e = set_tc_smem<1, 8, true>();
+    if (e == cudaSuccess) e = set_tc_smem<0, 16, true>();
+    if (e == cudaSuccess) e = set_tc_smem<1, 16, true>();
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -656,19 +695,13 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.Y2c = p.Y2c;
   a.ch_max = p.ch_max;
   a.ct_max = p.ct_max;
+  a.masks = p.masks;
+  a.mask_wr = p.mask_wr;
+  a.chgP = p.chgP;
+  if (a.masks && (!a.chgP || a.mask_wr < 2ll * a.TC)) return cudaErrorInvalidValue;
   const CUtensorMap& lo = dm ? *dmap_lo : *dmap;
-  if (p.R <= 8) {
-    if (dm == 0)
-      fused_pass_tc<0, 8><<<p.A * p.B, THREADS, Cfg<8>::SMEM_BYTES, s>>>(*dmap, lo, a);
-    else
-      fused_pass_tc<1, 8><<<p.A * p.B, THREADS, Cfg<8>::SMEM_BYTES, s>>>(*dmap, lo, a);
-  } else {
-    if (dm == 0)
-      fused_pass_tc<0, 16><<<p.A * p.B, THREADS, Cfg<16>::SMEM_BYTES, s>>>(*dmap, lo, a);
-    else
-      fused_pass_tc<1, 16><<<p.A * p.B, THREADS, Cfg<16>::SMEM_BYTES, s>>>(*dmap, lo, a);
-  }
-  return cudaGetLastError();
+  if (p.R <= 8) return dm == 0 ? launch_tc<0, 8>(*dmap, lo, a, s) : launch_tc<1, 8>(*dmap, lo, a, s);
+  return dm == 0 ? launch_tc<0, 16>(*dmap, lo, a, s) : launch_tc<1, 16>(*dmap, lo, a, s);
 }
 
 }  // namespace rpca

@@ -40,6 +40,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "mlp.cuh"
 #include "tc_images.cuh"
 #include "tc_util.cuh"
 
@@ -569,17 +570,20 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
 }
 
 template <typename T, int WM>
-__device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long& nnz, Smem<T, WM>& sh) {
+__device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long& nnz, Smem<T, WM>& sh,
+                           unsigned long long* changes = nullptr) {
   // every block sums the per-CTA totals in the same order
   const int t = threadIdx.x;
   double s = 0.0;
-  unsigned long long z = 0;
+  unsigned long long z = 0, c2 = 0;
   for (int c = t; c < a.n_cta; c += ST) {
     s += a.resP[c];
     z += a.nnzP[c];
+    if (changes && a.chgP) c2 += a.chgP[c];
   }
   res2 = block_sum_d(s, sh);
   nnz = block_sum_u64(z, sh);
+  if (changes) *changes = a.chgP ? block_sum_u64(c2, sh) : 0ull;
 }
 
 // Row i of Y (width w) <- fixed-order sum of the nsl pass partial slices (width R,
@@ -719,8 +723,8 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   T* Y1 = static_cast<T*>(a.Y1);
   T* Y2 = static_cast<T*>(a.Y2);
   double res2;
-  unsigned long long nnz;
-  cta_totals(a, res2, nnz, sh);
+  unsigned long long nnz, changes;
+  cta_totals(a, res2, nnz, sh, &changes);
   const double err = sqrt(res2 / st->normD2);
   const int k = st->k;
   if (blockIdx.x == 0 && t == 0) {
@@ -732,6 +736,10 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     s.k = k;
     s.sigma1 = 0.0;
     s.sigma_r1 = 0.0;
+    s.zeta_next_plain = 0.0;
+    s.g = 0.0;
+    for (int i = 0; i < mlp::IN; ++i) s.feat[i] = 0.f;
+    s.changes = (k > 0 && a.chgP) ? (long long)changes : 0;
   }
   if (!(err == err) || isinf(err)) {
     if (blockIdx.x == 0 && t == 0) {
@@ -880,21 +888,41 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     }
   }
   if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[t];
-  if (blockIdx.x == 0 && t == ST - 32) {  // a warp with no rows when m, n <= 224 * grid
+  if (blockIdx.x == 0 && t >= ST - 32) {  // a warp with no rows when m, n <= 224 * grid
+    const int lane = t & 31;
     const int k1 = k + 1;
     const double gamma = st->gamma, beta = st->beta;
     const int zmode = st->zeta_mode;
     double g = 1.0;  // gamma^(k+1) by repeated multiplication (k is small)
     for (int i = 0; i < k1; ++i) g *= gamma;
-    if (zmode == 0)
-      st->zeta = beta * (sr1 + g * s1);
-    else if (zmode == 1)
-      st->zeta = beta * g * s1;
-    for (int i = 0; i < N; ++i) st->sigma[i] = (double)sh.sig[i];
-    a.stats[k].sigma1 = s1;
-    a.stats[k].sigma_r1 = sr1;
-    if (hi_only && (err < st->split_switch || err < st->tol)) st->use_lo = 1;
-    st->k = k1;
+    const double plain = beta * (sr1 + g * s1);  // Algorithm 1
+    double zeta_new = st->zeta;                   // EXTERNAL: the caller sets it
+    if (zmode == 0) {
+      zeta_new = plain;
+    } else if (zmode == 1) {
+      zeta_new = beta * g * s1;
+    } else if (zmode == 3) {
+      // learned schedule: zeta_{k+1} = zeta^plain_{k+1} exp(clamp(g(s_k))), the network run by
+      // this warp on the statistics of this iteration (mlp.cuh)
+      float f[mlp::IN], h1, h2;
+      const double change = (k > 0 && a.chgP) ? (double)changes / ((double)m * (double)n) : 0.0;
+      mlp::features(s1, sr1, err, change, k, a.depth, st->zeta, f);
+      const float gc = mlp::clamp_g(mlp::forward_warp(a.theta, f, h1, h2));
+      zeta_new = plain * (double)expf(gc);
+      if (lane == 0) {
+        for (int i = 0; i < mlp::IN; ++i) a.stats[k].feat[i] = f[i];
+        a.stats[k].g = (double)gc;
+      }
+    }
+    if (lane == 0) {
+      st->zeta = zeta_new;
+      a.stats[k].zeta_next_plain = plain;
+      for (int i = 0; i < N; ++i) st->sigma[i] = (double)sh.sig[i];
+      a.stats[k].sigma1 = s1;
+      a.stats[k].sigma_r1 = sr1;
+      if (hi_only && (err < st->split_switch || err < st->tol)) st->use_lo = 1;
+      st->k = k1;
+    }
   }
   __syncthreads();
   trim_and_gram<T, WM>(a, sh);
