@@ -260,6 +260,36 @@ int rpca_learn_pass_adjoint(const void* D, int64_t m, int64_t n, int64_t ld, int
                             double resb, void* Utb, void* Vtb, void* Wb, void* Vb, double* zetab,
                             void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Training the LEARNED threshold schedule (not part of the paper's method).  All device
+ * pointers; all calls enqueue on `stream` and return.
+ *
+ * rpca_schedule_forward: for n statistic vectors feats (n x 6 float, the s_k of
+ *   rpca_iter_stats.features) and plain thresholds plain (n double, zeta^plain_{k+1}),
+ *   zeta[i] = plain[i] exp(clamp(g(feats[i]), -log 4, log 4)) (n double) and, if g is not
+ *   NULL, the clamped g (n float): the same arithmetic as the LEARNED iteration.
+ * rpca_schedule_backward: theta_bar (RPCA_SCHEDULE_PARAMS floats, overwritten) = gradient of
+ *   sum_i zeta_bar[i] zeta[i] with respect to the parameters, by a hand-written backward pass
+ *   of the network (zero through a saturated clamp); samples summed in order (deterministic).
+ * rpca_adam_step: one Adam update (bias-corrected, step >= 1) of theta (count floats) from
+ *   grad, with first / second moment buffers m1, m2 (count floats each, zero at step 1).
+ * rpca_projection_loss: the training loss of iteration k,
+ *   ||P_T Z - L*||_F^2 / ||L*||_F^2 with P_T Z = F G^T, F = [U~, Y1 - U~ C], G = [Y2, V~],
+ *   C = U~^T Y1 (Eq. (6), from the pass products Y1 = Z V~ (m x R) and Y2 = Z^T U~ (n x R)
+ *   of rpca_learn_pass; U~ (m x R), V~ (n x R) of the same dtype; only the first r columns
+ *   are used), L* = P Q^T (P m x rp, Q n x rp, double, row-major), into *loss (device
+ *   double), and its gradients Y1b (m x R), Y2b (n x R) with respect to Y1, Y2 (padding
+ *   columns zero).  work: device doubles, 2 r (m + n).  r <= R <= 16, rp <= 16. */
+int rpca_schedule_forward(const float* theta, const float* feats, const double* plain, int n, double* zeta, float* g,
+                          void* stream);
+int rpca_schedule_backward(const float* theta, const float* feats, const double* plain, const double* zeta_bar, int n,
+                           float* theta_bar, void* stream);
+int rpca_adam_step(float* theta, const float* grad, float* m1, float* m2, int count, int step, double lr, double beta1,
+                   double beta2, double eps, void* stream);
+int rpca_projection_loss(const void* Y1, const void* Y2, const void* Ut, const void* Vt, int64_t m, int64_t n, int R,
+                         int r, int dtype, const double* P, const double* Q, int rp, double* loss, void* Y1b, void* Y2b,
+                         double* work, void* stream);
+
 /* Largest m accepted by rpca_get_sparse_noalloc. */
 #define RPCA_NOALLOC_MAX_ROWS 65536
 

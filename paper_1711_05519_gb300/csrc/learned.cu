@@ -289,3 +289,268 @@ extern "C" int rpca_learn_pass_adjoint(const void* D, int64_t m, int64_t n, int6
   const cudaError_t e = dtype == RPCA_DTYPE_F32 ? launch_learn<float, true>(r, a, s) : launch_learn<double, true>(r, a, s);
   return e == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------------------
+// Threshold network of the learned schedule (mlp.cuh): batched forward, hand-written
+// backward and the Adam update used to train it.
+// ---------------------------------------------------------------------------------------
+#include "mlp.cuh"
+
+namespace rpca {
+namespace {
+
+// One warp per statistic vector: zeta_i = plain_i exp(clamp(g(s_i))).
+__global__ void __launch_bounds__(32) schedule_forward_kernel(const float* __restrict__ theta,
+                                                             const float* __restrict__ feats,
+                                                             const double* __restrict__ plain, int n,
+                                                             double* __restrict__ zeta, float* __restrict__ gout) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  float s[mlp::IN], h1, h2;
+#pragma unroll
+  for (int q = 0; q < mlp::IN; ++q) s[q] = feats[i * mlp::IN + q];
+  const float gc = mlp::clamp_g(mlp::forward_warp(theta, s, h1, h2));
+  if ((threadIdx.x & 31) == 0) {
+    zeta[i] = plain[i] * (double)expf(gc);
+    if (gout) gout[i] = gc;
+  }
+}
+
+// Gradient of sum_i zeta_bar_i zeta_i with respect to the parameters, one warp, samples in
+// order (deterministic).  Lane j owns hidden unit j of both layers: row j of W2 and of W1.
+// Through the clamp the derivative is zero where the output is saturated; d zeta / d g = zeta.
+__global__ void __launch_bounds__(32) schedule_backward_kernel(const float* __restrict__ theta,
+                                                              const float* __restrict__ feats,
+                                                              const double* __restrict__ plain,
+                                                              const double* __restrict__ zeta_bar, int n,
+                                                              float* __restrict__ grad) {
+  using namespace mlp;
+  const int j = threadIdx.x & 31;
+  float gW1[IN], gW2[H], gb1 = 0.f, gb2 = 0.f, gw3 = 0.f, gb3 = 0.f;
+#pragma unroll
+  for (int q = 0; q < IN; ++q) gW1[q] = 0.f;
+#pragma unroll
+  for (int q = 0; q < H; ++q) gW2[q] = 0.f;
+  for (int i = 0; i < n; ++i) {
+    float s[IN], h1, h2;
+#pragma unroll
+    for (int q = 0; q < IN; ++q) s[q] = feats[i * IN + q];
+    const float g = forward_warp(theta, s, h1, h2);
+    const float gc = clamp_g(g);
+    const double z = plain[i] * (double)expf(gc);
+    const float dg = (g > -kLog4 && g < kLog4) ? (float)(zeta_bar[i] * z) : 0.f;
+    gb3 += dg;
+    gw3 = fmaf(dg, h2, gw3);
+    const float dz2 = dg * theta[OFF_W3 + j] * (1.f - h2 * h2);
+    gb2 += dz2;
+#pragma unroll 8
+    for (int q = 0; q < H; ++q) gW2[q] = fmaf(dz2, __shfl_sync(0xffffffffu, h1, q), gW2[q]);
+    // dh1_j = sum_q W2[q][j] dz2_q
+    float dh1 = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < H; ++q) dh1 = fmaf(theta[OFF_W2 + q * H + j], __shfl_sync(0xffffffffu, dz2, q), dh1);
+    const float dz1 = dh1 * (1.f - h1 * h1);
+    gb1 += dz1;
+#pragma unroll
+    for (int q = 0; q < IN; ++q) gW1[q] = fmaf(dz1, s[q], gW1[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < IN; ++q) grad[OFF_W1 + j * IN + q] = gW1[q];
+  grad[OFF_B1 + j] = gb1;
+#pragma unroll
+  for (int q = 0; q < H; ++q) grad[OFF_W2 + j * H + q] = gW2[q];
+  grad[OFF_B2 + j] = gb2;
+  grad[OFF_W3 + j] = gw3;
+  if (j == 0) grad[OFF_B3] = gb3;
+}
+
+__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ grad, float* __restrict__ m1,
+                            float* __restrict__ m2, int count, double lr, double b1, double b2, double eps, double bc1,
+                            double bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double g = grad[i];
+  const double a = b1 * m1[i] + (1.0 - b1) * g;
+  const double v = b2 * m2[i] + (1.0 - b2) * g * g;
+  m1[i] = (float)a;
+  m2[i] = (float)v;
+  theta[i] = (float)(theta[i] - lr * (a / bc1) / (sqrt(v / bc2) + eps));
+}
+
+// ---------------------------------------------------------------------------------------
+// Training loss of the learned schedule: with Y1 = Z V~ and Y2 = Z^T U~ from a pass,
+// P_T Z = F G^T (Eq. (6)), F = [U~, Y1 - U~ C], G = [Y2, V~], C = U~^T Y1; the loss is
+// ||F G^T - P Q^T||_F^2 / ||P Q^T||_F^2 and its gradient with respect to Y1 and Y2 (U~, V~,
+// P, Q held fixed).  One block; every sum over rows is a fixed-order tree, so the result is
+// deterministic.  Work: F (m x 2r), G (n x 2r) in double.
+// ---------------------------------------------------------------------------------------
+constexpr int LT = 1024;
+
+// out[a * cy + b] = sum over rows of X(i, a) Y(i, b) for a < cx, b < cy; X, Y are callables.
+template <typename FX, typename FY>
+__device__ void block_gram(int rows, int cx, int cy, FX X, FY Y, double* out, double* red) {
+  const int t = threadIdx.x, E = cx * cy;
+  for (int e0 = 0; e0 < E; e0 += LT) {
+    const int cnt = min(LT, E - e0), groups = LT / cnt;
+    const int e = e0 + t % cnt, gidx = t / cnt;
+    double acc = 0.0;
+    if (gidx < groups) {
+      const int a = e / cy, b = e % cy;
+      for (int i = gidx; i < rows; i += groups) acc = fma(X(i, a), Y(i, b), acc);
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < cnt) {
+      double s = 0.0;
+      for (int g = 0; g < groups; ++g) s += red[g * cnt + t];
+      out[e0 + t] = s;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LT) projection_loss_kernel(const T* __restrict__ Y1, const T* __restrict__ Y2,
+                                                             const T* __restrict__ Ut, const T* __restrict__ Vt,
+                                                             int m, int n, int R, int r, const double* __restrict__ P,
+                                                             const double* __restrict__ Q, int rp, double* loss,
+                                                             T* __restrict__ Y1b, T* __restrict__ Y2b,
+                                                             double* __restrict__ F, double* __restrict__ G) {
+  __shared__ double red[LT];
+  __shared__ double C[16 * 16], A[32 * 32], B[32 * 32], Hq[16 * 32], E[32 * 16], PP[16 * 16], QQ[16 * 16], X[16 * 16];
+  __shared__ double sc;
+  const int t = threadIdx.x, w = 2 * r;
+  // G = [Y2, V~]
+  for (int e = t; e < n * w; e += LT) {
+    const int j = e / w, a = e % w;
+    G[e] = a < r ? (double)Y2[(size_t)j * R + a] : (double)Vt[(size_t)j * R + a - r];
+  }
+  __syncthreads();
+  auto gG = [&](int i, int a) { return G[(size_t)i * w + a]; };
+  auto gQ = [&](int i, int a) { return Q[(size_t)i * rp + a]; };
+  auto gP = [&](int i, int a) { return P[(size_t)i * rp + a]; };
+  auto gU = [&](int i, int a) { return (double)Ut[(size_t)i * R + a]; };
+  auto gY1 = [&](int i, int a) { return (double)Y1[(size_t)i * R + a]; };
+  block_gram(n, w, w, gG, gG, A, red);   // G^T G
+  block_gram(n, rp, w, gQ, gG, Hq, red);  // Q^T G
+  block_gram(n, rp, rp, gQ, gQ, QQ, red);
+  block_gram(m, rp, rp, gP, gP, PP, red);
+  block_gram(m, r, r, gU, gY1, C, red);   // C = U~^T Y1
+  // F = [U~, Y1 - U~ C]
+  for (int i = t; i < m; i += LT) {
+    for (int a = 0; a < r; ++a) {
+      double v = gY1(i, a);
+      for (int q = 0; q < r; ++q) v = fma(-gU(i, q), C[q * r + a], v);
+      F[(size_t)i * w + a] = gU(i, a);
+      F[(size_t)i * w + r + a] = v;
+    }
+  }
+  __syncthreads();
+  auto gF = [&](int i, int a) { return F[(size_t)i * w + a]; };
+  block_gram(m, w, w, gF, gF, B, red);    // F^T F
+  block_gram(m, w, rp, gF, gP, E, red);   // F^T P
+  if (t == 0) {
+    double nl = 0.0, ab = 0.0, eh = 0.0;
+    for (int a = 0; a < rp; ++a)
+      for (int b = 0; b < rp; ++b) nl += PP[a * rp + b] * QQ[a * rp + b];
+    for (int a = 0; a < w; ++a)
+      for (int b = 0; b < w; ++b) ab += B[a * w + b] * A[a * w + b];
+    for (int a = 0; a < w; ++a)
+      for (int c = 0; c < rp; ++c) eh += E[a * rp + c] * Hq[c * w + a];
+    *loss = (ab - 2.0 * eh + nl) / nl;
+    sc = 2.0 / nl;
+  }
+  __syncthreads();
+  const double s2 = sc;
+  // Y2b = first r columns of dG = (2 / ||L*||^2) (G F^T F - Q (F^T P)^T)
+  for (int e = t; e < n * R; e += LT) {
+    const int j = e / R, a = e % R;
+    double v = 0.0;
+    if (a < r) {
+      for (int b = 0; b < w; ++b) v = fma(G[(size_t)j * w + b], B[b * w + a], v);
+      for (int c = 0; c < rp; ++c) v = fma(-Q[(size_t)j * rp + c], E[a * rp + c], v);
+      v *= s2;
+    }
+    Y2b[e] = (T)v;
+  }
+  // dW1 = last r columns of dF = (2 / ||L*||^2) (F G^T G - P Q^T G), written row by row over
+  // the W1 half of F (each row is read before it is overwritten)
+  __syncthreads();
+  for (int i = t; i < m; i += LT) {
+    double d[16];
+    for (int a = 0; a < r; ++a) {
+      double v = 0.0;
+      for (int b = 0; b < w; ++b) v = fma(F[(size_t)i * w + b], A[b * w + r + a], v);
+      for (int c = 0; c < rp; ++c) v = fma(-P[(size_t)i * rp + c], Hq[c * w + r + a], v);
+      d[a] = v * s2;
+    }
+    for (int a = 0; a < r; ++a) F[(size_t)i * w + r + a] = d[a];
+  }
+  __syncthreads();
+  auto gD = [&](int i, int a) { return F[(size_t)i * w + r + a]; };
+  block_gram(m, r, r, gU, gD, X, red);  // X = U~^T dW1
+  // Y1b = (I - U~ U~^T) dW1
+  for (int e = t; e < m * R; e += LT) {
+    const int i = e / R, a = e % R;
+    double v = 0.0;
+    if (a < r) {
+      v = F[(size_t)i * w + r + a];
+      for (int q = 0; q < r; ++q) v = fma(-gU(i, q), X[q * r + a], v);
+    }
+    Y1b[e] = (T)v;
+  }
+}
+
+}  // namespace
+}  // namespace rpca
+
+extern "C" int rpca_schedule_forward(const float* theta, const float* feats, const double* plain, int n, double* zeta,
+                                     float* g, void* stream) {
+  if (!theta || !feats || !plain || !zeta || n < 0) return RPCA_ERR_INVALID_ARG;
+  if (n == 0) return RPCA_OK;
+  rpca::schedule_forward_kernel<<<n, 32, 0, static_cast<cudaStream_t>(stream)>>>(theta, feats, plain, n, zeta, g);
+  return cudaGetLastError() == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
+}
+
+extern "C" int rpca_schedule_backward(const float* theta, const float* feats, const double* plain,
+                                      const double* zeta_bar, int n, float* theta_bar, void* stream) {
+  if (!theta || !feats || !plain || !zeta_bar || !theta_bar || n < 0) return RPCA_ERR_INVALID_ARG;
+  rpca::schedule_backward_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(theta, feats, plain, zeta_bar, n,
+                                                                                   theta_bar);
+  return cudaGetLastError() == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
+}
+
+extern "C" int rpca_adam_step(float* theta, const float* grad, float* m1, float* m2, int count, int step, double lr,
+                              double beta1, double beta2, double eps, void* stream) {
+  if (!theta || !grad || !m1 || !m2 || count < 0 || step < 1 || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) ||
+      !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return RPCA_ERR_INVALID_ARG;
+  if (count == 0) return RPCA_OK;
+  const double bc1 = 1.0 - pow(beta1, step), bc2 = 1.0 - pow(beta2, step);
+  rpca::adam_kernel<<<(count + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(theta, grad, m1, m2, count, lr,
+                                                                                          beta1, beta2, eps, bc1, bc2);
+  return cudaGetLastError() == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
+}
+
+extern "C" int rpca_projection_loss(const void* Y1, const void* Y2, const void* Ut, const void* Vt, int64_t m, int64_t n,
+                                    int R, int r, int dtype, const double* P, const double* Q, int rp, double* loss,
+                                    void* Y1b, void* Y2b, double* work, void* stream) {
+  if (!Y1 || !Y2 || !Ut || !Vt || !P || !Q || !loss || !Y1b || !Y2b || !work || m < 1 || n < 1 || r < 1 || r > R ||
+      R > 16 || rp < 1 || rp > 16 || (dtype != RPCA_DTYPE_F32 && dtype != RPCA_DTYPE_F64) || m > (1 << 26) ||
+      n > (1 << 26))
+    return RPCA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* F = work;
+  double* G = work + (size_t)m * 2 * r;
+  if (dtype == RPCA_DTYPE_F32)
+    rpca::projection_loss_kernel<float><<<1, rpca::LT, 0, s>>>(
+        static_cast<const float*>(Y1), static_cast<const float*>(Y2), static_cast<const float*>(Ut),
+        static_cast<const float*>(Vt), (int)m, (int)n, R, r, P, Q, rp, loss, static_cast<float*>(Y1b),
+        static_cast<float*>(Y2b), F, G);
+  else
+    rpca::projection_loss_kernel<double><<<1, rpca::LT, 0, s>>>(
+        static_cast<const double*>(Y1), static_cast<const double*>(Y2), static_cast<const double*>(Ut),
+        static_cast<const double*>(Vt), (int)m, (int)n, R, r, P, Q, rp, loss, static_cast<double*>(Y1b),
+        static_cast<double*>(Y2b), F, G);
+  return cudaGetLastError() == cudaSuccess ? RPCA_OK : RPCA_ERR_CUDA;
+}

@@ -1,34 +1,39 @@
-"""Learned threshold schedule for an unrolled AccAltProj.
+"""Learned threshold schedule for AccAltProj, trained and run through the library.
 
-A small network g_theta maps per-iteration statistics to a multiplier of the paper's
-threshold (Algorithm 1):
+A small network g_theta (6 -> 32 -> 32 -> 1, tanh, FP32) maps per-iteration statistics to a
+multiplier of the paper's threshold (Algorithm 1):
 
     zeta_{k+1} = beta (sigma_{r+1} + gamma^{k+1} sigma_1) * exp(clamp(g_theta(s_k), -log 4, log 4))
 
 with s_k = [log sigma_1, log(sigma_{r+1}/sigma_1), log err_k, fraction of the support that
-changed, k/K, log(zeta_k/sigma_1)].  The plain schedule is g = 0 (the output layer starts at
-zero, so an untrained network reproduces it).
+changed since pass k - 1, (k+1)/K, log(zeta_k/sigma_1)].  The plain schedule is g = 0 (a zero
+output layer), so an untrained network reproduces it.  The network is evaluated on the device
+inside the library's iteration (zeta mode "learned"); nothing of it runs in Python.
 
-Training unrolls K iterations.  The m x n work of each iteration is the library's pass with
-the soft gate g(R; zeta) = sigmoid((|R| - zeta)/(tau zeta)) (rpca_learn_pass) and its
-hand-written adjoint (rpca_learn_pass_adjoint) behind `LearnPass`, a torch.autograd.Function.
-The loss of iteration k is the relative distance of the tangent-space projection
-P_T(D - S_k(zeta_k)) to the planted L*, computed from the pass products alone (the
-projection has rank <= 2r); the factors between iterations are checkpointed and detached,
-so each zeta_k is judged by the projection it produces (truncated back-propagation of
-depth one).  The O((m + n) r) algebra of the unrolled iterations (trim, QR, 2r x 2r SVD,
-loss) uses torch tensor ops on the GPU; every m x n step runs in the library's kernels.
+Training unrolls K iterations of the library's own iteration in that mode.  For each
+iteration k >= 1 it recomputes zeta_k from the recorded statistics s_{k-1} (ScheduleZeta,
+rpca_schedule_forward / rpca_schedule_backward), evaluates the m x n pass at the recorded
+operands with the soft gate g(R; zeta) = sigmoid((|R| - zeta)/(tau zeta)) (LearnPass,
+rpca_learn_pass / rpca_learn_pass_adjoint) and the loss ||P_T(D - S_k(zeta_k)) - L*||_F^2 /
+||L*||_F^2 from the pass products (ProjectionLoss, rpca_projection_loss).  The operands of
+each iteration are checkpointed (O((m + n) r) per iteration, never an m x n array) and held
+fixed, so each zeta_k is judged by the projection it produces (back-propagation truncated to
+one iteration).  The objective is the mean of log loss_k; Adam (rpca_adam_step) updates the
+parameters.  Every step of the forward and backward computation is a kernel of the library;
+torch supplies device memory, streams and the autograd bookkeeping.
 """
 from __future__ import annotations
 
 import ctypes
 import math
 
+import numpy as np
 import torch
 
-from .rpca import CUDA_ERR, RpcaError, _check, lib
+from .rpca import SCHEDULE_PARAMS, Solver, _check, lib
 
 LOG4 = math.log(4.0)
+HIDDEN, INPUTS = 32, 6
 
 
 def _ptr(t):
@@ -56,6 +61,10 @@ def _bind():
     L._learn_bound = True
     return L
 
+
+# ---------------------------------------------------------------------------------------
+# The soft-gated pass and its adjoint
+# ---------------------------------------------------------------------------------------
 
 def learn_pass(D, W, V, Ut, Vt, zeta, tau, mask_old=None, mask_new=None):
     """Forward pass (no autograd): returns Y1, Y2 and stats [res2, hard nnz, changes]."""
@@ -103,186 +112,190 @@ class LearnPass(torch.autograd.Function):
     def backward(ctx, gY1, gY2, gres):
         D, W, V, Ut, Vt, zeta = ctx.saved_tensors
         if gY1 is None:
-            gY1 = torch.zeros_like(W[:, :1].expand(-1, W.shape[1]))
+            gY1 = torch.zeros_like(W)
         if gY2 is None:
-            gY2 = torch.zeros_like(V[:, :1].expand(-1, V.shape[1]))
+            gY2 = torch.zeros_like(V)
         resb = float(gres) if gres is not None else 0.0
         Utb, Vtb, Wb, Vb, zb = learn_pass_adjoint(D, W, V, Ut, Vt, zeta, ctx.tau, gY1.to(D.dtype), gY2.to(D.dtype),
                                                   resb)
         return None, Wb, Vb, Utb, Vtb, zb.to(ctx.zeta_dtype).reshape(ctx.zeta_shape), None
 
 
-class ThresholdMLP(torch.nn.Module):
-    """6 -> 32 -> 32 -> 1 (tanh); the output layer starts at zero (plain schedule)."""
+# ---------------------------------------------------------------------------------------
+# The threshold network and the training loss
+# ---------------------------------------------------------------------------------------
 
-    def __init__(self, hidden: int = 32):
-        super().__init__()
-        self.net = torch.nn.Sequential(torch.nn.Linear(6, hidden), torch.nn.Tanh(), torch.nn.Linear(hidden, hidden),
-                                       torch.nn.Tanh(), torch.nn.Linear(hidden, 1))
-        torch.nn.init.zeros_(self.net[-1].weight)
-        torch.nn.init.zeros_(self.net[-1].bias)
+def schedule_forward(theta, feats, plain):
+    """zeta_i = plain_i exp(clamp(g(feats_i))) and the clamped g, by the library's kernel."""
+    n = feats.shape[0]
+    zeta = torch.empty(n, dtype=torch.float64, device=feats.device)
+    g = torch.empty(n, dtype=torch.float32, device=feats.device)
+    feats, plain = feats.contiguous(), plain.contiguous()
+    _check(lib().rpca_schedule_forward(_ptr(theta), _ptr(feats), _ptr(plain), n, _ptr(zeta), _ptr(g), _stream()),
+           "rpca_schedule_forward")
+    return zeta, g
 
-    def forward(self, s):
-        return torch.clamp(self.net(s), -LOG4, LOG4).squeeze(-1)
+
+def schedule_backward(theta, feats, plain, zeta_bar):
+    grad = torch.empty(SCHEDULE_PARAMS, dtype=torch.float32, device=feats.device)
+    feats, plain, zeta_bar = feats.contiguous(), plain.contiguous(), zeta_bar.contiguous()
+    _check(lib().rpca_schedule_backward(_ptr(theta), _ptr(feats), _ptr(plain), _ptr(zeta_bar), feats.shape[0],
+                                        _ptr(grad), _stream()), "rpca_schedule_backward")
+    return grad
+
+
+class ScheduleZeta(torch.autograd.Function):
+    """(theta, s (n x 6 float32), zeta^plain (n float64)) -> zeta (n float64)."""
+
+    @staticmethod
+    def forward(ctx, theta, feats, plain):
+        theta = theta.contiguous()
+        zeta, _ = schedule_forward(theta, feats, plain)
+        ctx.save_for_backward(theta, feats, plain)
+        return zeta
+
+    @staticmethod
+    def backward(ctx, zeta_bar):
+        theta, feats, plain = ctx.saved_tensors
+        return schedule_backward(theta, feats, plain, zeta_bar.to(torch.float64)), None, None
+
+
+def projection_loss(Y1, Y2, Ut, Vt, P, Q, r):
+    """loss_k (device float64 scalar) and its gradients with respect to Y1, Y2."""
+    m, R = Y1.shape
+    n = Y2.shape[0]
+    loss = torch.empty((), dtype=torch.float64, device=Y1.device)
+    Y1b, Y2b = torch.empty_like(Y1), torch.empty_like(Y2)
+    work = torch.empty(2 * r * (m + n), dtype=torch.float64, device=Y1.device)
+    args = [x.contiguous() for x in (Y1, Y2, Ut, Vt)]
+    P, Q = P.contiguous(), Q.contiguous()
+    _check(lib().rpca_projection_loss(*(_ptr(x) for x in args), m, n, R, r, _dtype_code(Y1), _ptr(P), _ptr(Q),
+                                      P.shape[1], _ptr(loss), _ptr(Y1b), _ptr(Y2b), _ptr(work), _stream()),
+           "rpca_projection_loss")
+    return loss, Y1b, Y2b
+
+
+class ProjectionLoss(torch.autograd.Function):
+    """(Y1, Y2; U~, V~, P, Q held fixed) -> ||P_T Z - P Q^T||_F^2 / ||P Q^T||_F^2."""
+
+    @staticmethod
+    def forward(ctx, Y1, Y2, Ut, Vt, P, Q, r):
+        loss, Y1b, Y2b = projection_loss(Y1, Y2, Ut, Vt, P, Q, r)
+        ctx.save_for_backward(Y1b, Y2b)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gloss):
+        Y1b, Y2b = ctx.saved_tensors
+        return Y1b * gloss.to(Y1b.dtype), Y2b * gloss.to(Y2b.dtype), None, None, None, None, None
 
 
 # ---------------------------------------------------------------------------------------
-# O((m + n) r) algebra of one iteration (Section 2.1), torch ops, FP64
+# Parameters, training and evaluation
 # ---------------------------------------------------------------------------------------
 
-def trimmed_bases(U, V, mu, r, trim=True):
-    """Trim (Algorithm 2) and orthonormal bases of the trimmed factors."""
-    if not trim:
-        return U, V
-    m, n = U.shape[0], V.shape[0]
-    cu, cv = math.sqrt(mu * r / m), math.sqrt(mu * r / n)
-    A = U * torch.clamp(cu / U.norm(dim=1, keepdim=True).clamp_min(1e-300), max=1.0)
-    B = V * torch.clamp(cv / V.norm(dim=1, keepdim=True).clamp_min(1e-300), max=1.0)
-    return torch.linalg.qr(A)[0], torch.linalg.qr(B)[0]
+def init_theta(seed=0, device="cuda"):
+    """Packed parameters (see include/rpca.h): hidden layers drawn like torch.nn.Linear's
+    default (uniform +-1/sqrt(fan_in)), output layer zero (the plain schedule)."""
+    rng = np.random.default_rng(seed)
+    th = np.zeros(SCHEDULE_PARAMS, dtype=np.float32)
+    o = 0
+    for rows, cols in ((HIDDEN, INPUTS), (HIDDEN, HIDDEN)):
+        b = 1.0 / math.sqrt(cols)
+        th[o:o + rows * cols] = rng.uniform(-b, b, rows * cols)
+        o += rows * cols
+        th[o:o + rows] = rng.uniform(-b, b, rows)
+        o += rows
+    return torch.from_numpy(th).to(device)
 
 
-def tangent_update(Y1, Y2, Ut, Vt, r):
-    """H_r(P_T Z) from Y1 = Z V~, Y2 = Z^T U~ by the QR + 2r x 2r SVD route."""
-    C = Ut.T @ Y1
-    Q1, R1 = torch.linalg.qr(Y1 - Ut @ C)
-    Q2, R2 = torch.linalg.qr(Y2 - Vt @ C.T)
-    Z0 = torch.zeros(r, r, dtype=Y1.dtype, device=Y1.device)
-    M = torch.cat([torch.cat([C, R2.T], 1), torch.cat([R1, Z0], 1)], 0)
-    UM, s, VMt = torch.linalg.svd(M)
-    U = torch.cat([Ut, Q1], 1) @ UM[:, :r]
-    V = torch.cat([Vt, Q2], 1) @ VMt.T[:, :r]
-    return U, s[:r], V, s
+def save_theta(theta, path):
+    np.savez(path, theta=theta.detach().cpu().numpy().astype(np.float32))
 
 
-def projection_loss(Y1, Y2, Ut, Vt, P, Q, normL2):
-    """||P_T Z - L*||_F^2 / ||L*||_F^2 with P_T Z = [U~, Y1 - U~C] [Y2, V~]^T (Eq. (6))
-    and L* = P Q^T, from small Gram products only."""
-    C = Ut.T @ Y1
-    F = torch.cat([Ut, Y1 - Ut @ C], 1)
-    G = torch.cat([Y2, Vt], 1)
-    ff = F.T @ F
-    gg = G.T @ G
-    cross = (F.T @ P) @ (Q.T @ G)
-    return (torch.trace(ff @ gg) - 2.0 * torch.trace(cross) + normL2) / normL2
+def load_theta(path, device="cuda"):
+    return torch.from_numpy(np.load(path)["theta"].astype(np.float32)).to(device)
 
 
-class Unrolled:
-    """K iterations of AccAltProj from the library's initialisation, with the plain or a
-    learned threshold schedule."""
+def _solver(x, tol, max_iter, zeta_mode="learned", precision="fp32"):
+    return Solver(x["beta"], x["gamma"], tol, precision=precision, zeta_mode=zeta_mode, beta_init=2 * x["beta"],
+                  mu_trim=x["mu"], max_iter=max_iter)
 
-    def __init__(self, D, r, beta, gamma, mu, K=12, tau=0.05, pass_dtype=torch.float32, trim=True):
-        self.D = D.to(pass_dtype).contiguous()
-        self.r, self.beta, self.gamma, self.mu, self.K, self.tau = r, beta, gamma, mu, K, tau
-        self.trim = trim
-        from .rpca import Solver
 
-        with Solver(beta, gamma, 0.0, precision="fp64" if pass_dtype == torch.float64 else "fp32",
-                    beta_init=2 * beta, mu_trim=mu) as s:
-            s.init(self.D, r)
-            U, sig, V = s.lowrank()
-        self.U0, self.s0, self.V0 = U, sig, V
-        m, n = D.shape
-        self.words = (n + 31) // 32
-        self.mask = [torch.zeros(m * self.words, dtype=torch.int32, device=D.device) for _ in range(2)]
-        self.normD = float(torch.linalg.norm(self.D.double()))
-        self.R = _padded(r)
-
-    def _pad(self, X):
-        if X.shape[1] == self.R:
-            return X.to(self.D.dtype).contiguous()
-        return torch.nn.functional.pad(X, (0, self.R - X.shape[1])).to(self.D.dtype).contiguous()
-
-    def run(self, mlp=None, P=None, Q=None, hard=False, tol=None, max_iter=None):
-        """Runs K iterations (or, with `tol`, until err_k < tol, at most `max_iter`).
-        Returns (losses per iteration, final relative error, final factors); with `tol` the
-        number of passes run is in self.passes."""
-        r = self.r
-        K = self.K if tol is None else (max_iter or 100)
-        U, s, V = self.U0, self.s0, self.V0
-        zeta = torch.tensor(self.beta * float(s[0]), dtype=torch.float64, device=self.D.device)
-        normL2 = None
-        if P is not None:
-            normL2 = torch.trace((P.T @ P) @ (Q.T @ Q))
-        losses = []
-        err = 1.0
-        prev_mask = None
-        tau = 0.0 if hard else self.tau
-        for k in range(K):
-            Ut, Vt = trimmed_bases(U, V, self.mu, r, self.trim)
-            W = U * s
-            cur = self.mask[k % 2]
-            Y1, Y2, stats = learn_pass(self.D, self._pad(W), self._pad(V), self._pad(Ut), self._pad(Vt),
-                                       zeta.detach().reshape(()).contiguous(), 0.0, prev_mask, cur)
-            err = math.sqrt(max(float(stats[0]), 0.0)) / self.normD
-            self.passes = k + 1
-            if tol is not None and err < tol:
+def unrolled_trace(x, theta, K, precision="fp32"):
+    """Runs K iterations of the library in zeta mode "learned" on instance x and returns, per
+    iteration k, the operands (W, V, U~, V~) of pass k and its statistics record."""
+    ops, stats = [], []
+    with _solver(x, 0.0, K, precision=precision) as s:
+        s.set_schedule(theta, K)
+        s.init(x["D"], x["r"])
+        for _ in range(K):
+            ops.append(s.pass_operands())
+            _, st = s.iterate(1)
+            if not st:
+                ops.pop()
                 break
-            change = float(stats[2]) / (self.D.shape[0] * self.D.shape[1]) if prev_mask is not None else 0.0
-            prev_mask = cur
-            if normL2 is not None and not hard:
-                Y1s, Y2s, _ = LearnPass.apply(self.D, self._pad(W), self._pad(V), self._pad(Ut), self._pad(Vt),
-                                              zeta, tau)
-                losses.append(projection_loss(Y1s[:, :r].double(), Y2s[:, :r].double(), Ut, Vt, P, Q, normL2))
-            U, s, V, sM = tangent_update(Y1[:, :r].double(), Y2[:, :r].double(), Ut, Vt, r)
-            plain = self.beta * (sM[r] + self.gamma ** (k + 1) * sM[0])
-            if mlp is None:
-                zeta = plain.detach()
-            else:
-                feats = torch.stack([torch.log(sM[0]), torch.log(sM[r].clamp_min(1e-300) / sM[0]),
-                                     torch.log(torch.tensor(max(err, 1e-300), dtype=torch.float64, device=sM.device)),
-                                     torch.tensor(change, dtype=torch.float64, device=sM.device),
-                                     torch.tensor((k + 1) / self.K, dtype=torch.float64, device=sM.device),
-                                     torch.log(zeta.detach() / sM[0])]).float().detach()
-                zeta = plain.detach() * torch.exp(mlp(feats[None])[0].double())
-        return losses, err, (U, s, V)
+            stats.extend(st)
+    return ops, stats
 
 
-def save_mlp(mlp: "ThresholdMLP", path: str) -> None:
-    import numpy as np
-
-    np.savez(path, **{k: v.detach().cpu().numpy() for k, v in mlp.state_dict().items()})
-
-
-def load_mlp(path: str, device="cuda") -> "ThresholdMLP":
-    import numpy as np
-
-    mlp = ThresholdMLP()
-    data = np.load(path)
-    mlp.load_state_dict({k: torch.from_numpy(data[k]) for k in data.files})
-    return mlp.to(device)
-
-
-def _padded(r: int) -> int:
-    for R in (1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16):
-        if R >= r:
-            return R
-    raise ValueError(r)
+def unrolled_loss(x, theta, K, tau, trace=None):
+    """Objective of one training instance: mean over k = 1 .. K-1 of log loss_k (a tensor
+    attached to theta through the library's backward kernels).  `trace` (operands and
+    statistics of an unrolled_trace) holds the trajectory fixed; by default it is run with
+    the current parameters."""
+    ops, stats = trace if trace is not None else unrolled_trace(x, theta.detach(), K)
+    dev = x["D"].device
+    feats = torch.tensor([st["features"] for st in stats[:-1]], dtype=torch.float32, device=dev)
+    plain = torch.tensor([st["zeta_next_plain"] for st in stats[:-1]], dtype=torch.float64, device=dev)
+    zetas = ScheduleZeta.apply(theta, feats, plain)
+    losses = []
+    for k in range(1, len(ops)):
+        W, V, Ut, Vt = ops[k]
+        Y1, Y2, _ = LearnPass.apply(x["D"], W, V, Ut, Vt, zetas[k - 1], tau)
+        losses.append(ProjectionLoss.apply(Y1, Y2, Ut, Vt, x["P"], x["Q"], x["r"]))
+    return torch.stack(losses).log().mean(), zetas, stats
 
 
-def final_error(factors, P, Q):
-    U, s, V = factors
-    W = U * s
-    normL2 = torch.trace((P.T @ P) @ (Q.T @ Q))
-    d2 = torch.trace((W.T @ W) @ (V.T @ V)) - 2 * torch.trace((W.T @ P) @ (Q.T @ V)) + normL2
-    return float(torch.sqrt(d2.clamp_min(0) / normL2))
+class Adam:
+    """Adam on the packed parameters, by the library's rpca_adam_step."""
+
+    def __init__(self, theta, lr=1e-2, betas=(0.9, 0.999), eps=1e-8):
+        self.theta, self.lr, self.betas, self.eps = theta, lr, betas, eps
+        self.m1 = torch.zeros_like(theta)
+        self.m2 = torch.zeros_like(theta)
+        self.t = 0
+
+    def step(self, grad):
+        self.t += 1
+        grad = grad.contiguous()
+        _check(lib().rpca_adam_step(_ptr(self.theta), _ptr(grad), _ptr(self.m1), _ptr(self.m2), self.theta.numel(),
+                                    self.t, self.lr, self.betas[0], self.betas[1], self.eps, _stream()),
+               "rpca_adam_step")
 
 
 def train(instances, K=12, steps=100, lr=1e-2, tau=0.05, seed=0, log=None):
-    """Trains a ThresholdMLP on planted instances: list of dicts with D (CUDA), r, beta,
-    gamma, mu, P, Q (CUDA FP64)."""
-    torch.manual_seed(seed)
-    dev = instances[0]["D"].device
-    mlp = ThresholdMLP().to(dev)
-    opt = torch.optim.Adam(mlp.parameters(), lr=lr)
-    runners = [Unrolled(x["D"], x["r"], x["beta"], x["gamma"], x["mu"], K=K, tau=tau) for x in instances]
+    """Trains the schedule on planted instances: list of dicts with D (CUDA float32), r,
+    beta, gamma, mu, P, Q (CUDA float64, L* = P Q^T).  Returns the packed parameters."""
+    theta = init_theta(seed, device=instances[0]["D"].device)
+    opt = Adam(theta, lr=lr)
     for step in range(steps):
         x = instances[step % len(instances)]
-        run = runners[step % len(instances)]
-        losses, _, _ = run.run(mlp=mlp, P=x["P"], Q=x["Q"])
-        loss = torch.stack([torch.log(l.clamp_min(1e-300)) for l in losses]).mean()
-        opt.zero_grad()
-        loss.backward()
-        opt.step()
+        leaf = theta.detach().clone().requires_grad_(True)
+        J, _, _ = unrolled_loss(x, leaf, K, tau)
+        J.backward()
+        opt.step(leaf.grad)
         if log is not None:
-            log.append(float(loss.detach()))
-    return mlp
+            log.append(float(J.detach()))
+    return theta
+
+
+def solve(x, theta=None, tol=1e-5, K=12, max_iter=100, precision="fp32"):
+    """Solves instance x to tol through the library, with the learned schedule (theta) or the
+    paper's (theta None).  Returns (status, per-pass statistics, factors)."""
+    with _solver(x, tol, max_iter, zeta_mode="learned" if theta is not None else "paper", precision=precision) as s:
+        if theta is not None:
+            s.set_schedule(theta, K)
+        s.init(x["D"], x["r"])
+        code, stats = s.run()
+        return code, stats, s.lowrank()

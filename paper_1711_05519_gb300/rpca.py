@@ -19,7 +19,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "rpca.h")
 OK, INVALID_ARG, CUDA_ERR, NUMERICAL, CAPACITY, NOT_CONVERGED, TIMEOUT, STATE = range(8)
 DTYPE_F64, DTYPE_F32 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_split": 3}
-ZETA = {"paper": 0, "simple": 1, "external": 2}
+ZETA = {"paper": 0, "simple": 1, "external": 2, "learned": 3}
+SCHEDULE_PARAMS = 1313
 PASS_KIND = {"auto": 0, "simt": 1, "tensor": 2}
 STATE_READS_LO = 1
 
@@ -56,6 +57,10 @@ class IterStats(ctypes.Structure):
         ("sigma1", ctypes.c_double),
         ("sigma_r1", ctypes.c_double),
         ("nnz", ctypes.c_int64),
+        ("zeta_next_plain", ctypes.c_double),
+        ("g", ctypes.c_double),
+        ("features", ctypes.c_double * 6),
+        ("support_changes", ctypes.c_int64),
     ]
 
 
@@ -93,12 +98,20 @@ def lib() -> ctypes.CDLL:
     L.rpca_get_profile.argtypes = [vp, pdbl, pi64, pdbl, pi64]
     L.rpca_get_pass_kind.argtypes = [vp, pint, pint]
     L.rpca_get_sparse_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp, dbl, vp, vp, i64, pi64, vp]
+    L.rpca_set_schedule.argtypes = [vp, vp, i32]
+    L.rpca_get_pass_operands.argtypes = [vp, vp, vp, vp, vp, pint]
+    L.rpca_schedule_forward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.rpca_schedule_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+    L.rpca_adam_step.argtypes = [vp, vp, vp, vp, i32, i32, dbl, dbl, dbl, dbl, vp]
+    L.rpca_projection_loss.argtypes = [vp, vp, vp, vp, i64, i64, i32, i32, i32, vp, vp, i32, vp, vp, vp, vp, vp]
     solve_args = [vp, i64, i64, i32, dbl, dbl, dbl, vp, vp, vp, vp, vp, i64, pi64, pint, pdbl]
     L.rpca_solve.argtypes = solve_args
     L.rpca_solve_host.argtypes = solve_args
     for name in ("rpca_params_default", "rpca_create", "rpca_init", "rpca_iterate", "rpca_set_zeta",
                  "rpca_get_lowrank", "rpca_get_sparse", "rpca_solve", "rpca_solve_host", "rpca_set_profiling",
-                 "rpca_get_profile", "rpca_get_sparse_noalloc", "rpca_get_pass_kind"):
+                 "rpca_get_profile", "rpca_get_sparse_noalloc", "rpca_get_pass_kind", "rpca_set_schedule",
+                 "rpca_get_pass_operands", "rpca_schedule_forward", "rpca_schedule_backward", "rpca_adam_step",
+                 "rpca_projection_loss"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -187,7 +200,8 @@ class Solver:
         code = lib().rpca_iterate(self._ctx, n_iters, buf, ctypes.byref(done))
         _check(code, "rpca_iterate", allow=(OK, NOT_CONVERGED))
         stats = [{"k": s.k, "err": s.err, "zeta": s.zeta, "sigma1": s.sigma1, "sigma_r1": s.sigma_r1,
-                  "nnz": s.nnz} for s in buf[: done.value]]
+                  "nnz": s.nnz, "zeta_next_plain": s.zeta_next_plain, "g": s.g, "features": list(s.features),
+                  "support_changes": s.support_changes} for s in buf[: done.value]]
         return code, stats
 
     def run(self, max_passes: int | None = None) -> tuple[int, list[dict]]:
@@ -212,6 +226,29 @@ class Solver:
 
     def set_zeta(self, zeta: float) -> None:
         _check(lib().rpca_set_zeta(self._ctx, zeta), "rpca_set_zeta")
+
+    def set_schedule(self, theta: torch.Tensor, depth: int) -> None:
+        """zeta_mode "learned": network parameters (CUDA float32, SCHEDULE_PARAMS values) and
+        the unrolled depth K."""
+        if not (theta.is_cuda and theta.dtype == torch.float32 and theta.numel() == SCHEDULE_PARAMS):
+            raise ValueError("theta must be a CUDA float32 tensor of SCHEDULE_PARAMS values")
+        self._theta = theta.contiguous()
+        _check(lib().rpca_set_schedule(self._ctx, ctypes.c_void_p(self._theta.data_ptr()), int(depth)),
+               "rpca_set_schedule")
+
+    def pass_operands(self):
+        """(W, V, U~, V~) the next pass reads, copies in the working precision, padded width."""
+        dev = self._D.device
+        dt = torch.float64 if self.params.precision == PREC["fp64"] else torch.float32
+        R = _padded_rank(self.r)
+        W, Ut = (torch.empty(self.m, R, dtype=dt, device=dev) for _ in range(2))
+        V, Vt = (torch.empty(self.n, R, dtype=dt, device=dev) for _ in range(2))
+        w = ctypes.c_int(0)
+        _check(lib().rpca_get_pass_operands(self._ctx, ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                            ctypes.c_void_p(Ut.data_ptr()), ctypes.c_void_p(Vt.data_ptr()),
+                                            ctypes.byref(w)), "rpca_get_pass_operands")
+        assert w.value == R
+        return W, V, Ut, Vt
 
     def lowrank(self):
         dev = self._D.device
@@ -250,6 +287,13 @@ class Solver:
         _check(lib().rpca_get_sparse(self._ctx, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
                                      nnz.value, ctypes.byref(nnz)), "rpca_get_sparse")
         return idx[: nnz.value], val[: nnz.value]
+
+
+def _padded_rank(r: int) -> int:
+    for R in (1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16):
+        if R >= r:
+            return R
+    raise ValueError(r)
 
 
 def solve(D: torch.Tensor, r: int, beta: float, gamma: float, tol: float, s_cap: int | None = None) -> dict:

@@ -1,10 +1,11 @@
-"""Trains the learned threshold schedule and writes its weights.
+"""Trains the learned threshold schedule and writes its packed parameters.
 
 Training instances follow the planted recipe of Section 3 at m = n = 3000 with r drawn from
 {3, 5, 10}, alpha ~ U[0.05, 0.3] and c ~ U[0.5, 3]; each training step unrolls 12
-iterations of AccAltProj on one instance (soft gate, tau = 0.05).  Usage:
+iterations of the library's iteration on one instance (soft gate, tau = 0.05) and updates
+the parameters with the library's backward and Adam kernels.  Usage:
 
-    python -m paper_1711_05519_gb300.train_schedule --out paper_1711_05519_gb300/schedule_mlp.npz
+    python -m paper_1711_05519_gb300.train_schedule --out paper_1711_05519_gb300/schedule_theta.npz
 """
 from __future__ import annotations
 
@@ -42,14 +43,18 @@ def main():
     ap.add_argument("--instances", type=int, default=8)
     ap.add_argument("--steps", type=int, default=160)
     ap.add_argument("--lr", type=float, default=1e-2)
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedule_mlp.npz"))
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedule_theta.npz"))
     args = ap.parse_args()
+    from paper_1711_05519_gb300 import build
+
+    build.build()
     rng = np.random.default_rng(1000)
     train = [make_instance(args.n, 1000 + i, rng) for i in range(args.instances)]
     log = []
     t0 = time.time()
-    mlp = PL.train(train, K=12, steps=args.steps, lr=args.lr, log=log)
-    PL.save_mlp(mlp, args.out)
+    theta = PL.train(train, K=12, steps=args.steps, lr=args.lr, log=log)
+    torch.cuda.synchronize()
+    PL.save_theta(theta, args.out)
     print(json.dumps({"trained_s": round(time.time() - t0, 1), "loss_first": log[:5], "loss_last": log[-5:],
                       "out": args.out}))
 

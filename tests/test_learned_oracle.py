@@ -68,3 +68,71 @@ def test_autograd_matches_central_differences():
     hz = 1e-7 * zeta
     fdz = (J(W, V, Ut, Vt, zeta + hz) - J(W, V, Ut, Vt, zeta - hz)) / (2 * hz)
     assert gz == pytest.approx(fdz, rel=1e-6, abs=1e-8)
+
+
+# ---------------------------------------------------------------------------------------
+# Threshold network and training loss of the learned schedule
+# ---------------------------------------------------------------------------------------
+
+def _theta(rng, out_scale=0.3):
+    th = torch.from_numpy(rng.uniform(-0.4, 0.4, 1313))
+    th[1280:1312] *= out_scale / 0.4
+    return th
+
+
+def test_schedule_network_reduces_to_the_paper_rule():
+    rng = np.random.default_rng(0)
+    th = _theta(rng)
+    s = torch.from_numpy(rng.standard_normal((9, 6)))
+    plain = torch.from_numpy(rng.uniform(0.1, 2.0, 9))
+    # zero output layer: g = 0 and the schedule is Algorithm 1's own
+    z = th.clone()
+    z[1280:] = 0.0
+    assert torch.equal(OL.learned_zeta(z, s, plain), plain)
+    # a saturated output is clamped to a factor of 4 either way
+    big = z.clone()
+    big[1312] = 50.0
+    assert torch.allclose(OL.learned_zeta(big, s, plain), 4.0 * plain, rtol=1e-15)
+    big[1312] = -50.0
+    assert torch.allclose(OL.learned_zeta(big, s, plain), plain / 4.0, rtol=1e-15)
+    # the packing: output = w3 . h2 + b3 with h2 from a hand-evaluated first unit path
+    W1, b1, W2, b2, w3, b3 = OL.unpack_schedule(th)
+    h1 = np.tanh(W1.numpy() @ s[0].numpy() + b1.numpy())
+    h2 = np.tanh(W2.numpy() @ h1 + b2.numpy())
+    assert float(OL.schedule_net(th, s[:1])[0]) == pytest.approx(float(w3.numpy() @ h2 + float(b3)), rel=1e-14)
+
+
+def test_schedule_network_gradient_matches_central_differences():
+    rng = np.random.default_rng(1)
+    th = _theta(rng).requires_grad_(True)
+    s = torch.from_numpy(rng.standard_normal((7, 6)))
+    plain = torch.from_numpy(rng.uniform(0.1, 2.0, 7))
+    zb = torch.from_numpy(rng.standard_normal(7))
+    (zb * OL.learned_zeta(th, s, plain)).sum().backward()
+    d = torch.from_numpy(rng.standard_normal(1313))
+    h = 1e-6
+    f = lambda t: float((zb * OL.learned_zeta(t, s, plain)).sum())
+    fd = (f(th.detach() + h * d) - f(th.detach() - h * d)) / (2 * h)
+    assert float((th.grad * d).sum()) == pytest.approx(fd, rel=1e-7)
+
+
+def test_projection_loss_is_the_tangent_projection_error():
+    rng = np.random.default_rng(2)
+    m, n, r, rp = 30, 24, 3, 2
+    Ut = np.linalg.qr(rng.standard_normal((m, r)))[0]
+    Vt = np.linalg.qr(rng.standard_normal((n, r)))[0]
+    Z = rng.standard_normal((m, n))
+    P, Q = rng.standard_normal((m, rp)), rng.standard_normal((n, rp))
+    t = torch.from_numpy
+    got = OL.projection_loss(t(Z @ Vt), t(Z.T @ Ut), t(Ut), t(Vt), t(P), t(Q))
+    want = np.linalg.norm(O.tangent_project(Z, Ut, Vt) - P @ Q.T) ** 2 / np.linalg.norm(P @ Q.T) ** 2
+    assert float(got) == pytest.approx(want, rel=1e-12)
+    # gradient in Y1, Y2 against central differences
+    Y1 = t(Z @ Vt).requires_grad_(True)
+    Y2 = t(Z.T @ Ut).requires_grad_(True)
+    OL.projection_loss(Y1, Y2, t(Ut), t(Vt), t(P), t(Q)).backward()
+    d1, d2 = t(rng.standard_normal((m, r))), t(rng.standard_normal((n, r)))
+    f = lambda a, b: float(OL.projection_loss(a, b, t(Ut), t(Vt), t(P), t(Q)))
+    h = 1e-6
+    fd = (f(Y1.detach() + h * d1, Y2.detach() + h * d2) - f(Y1.detach() - h * d1, Y2.detach() - h * d2)) / (2 * h)
+    assert float((Y1.grad * d1).sum() + (Y2.grad * d2).sum()) == pytest.approx(fd, rel=1e-7)
