@@ -96,7 +96,18 @@ typedef struct {
   int pass_kind;     /* rpca_pass_kind: kernel of the fused pass                          */
   double split_switch; /* BF16_SPLIT: err_k level below which the passes read hi + lo; 0
                           selects 1e-2 (must lie above the bf16 floor of err_k)            */
+  int observed;      /* rpca_observed: which entries of D are observed                    */
 } rpca_params;
+
+/* Observed entries.  ALL: the problem of the paper, every entry of D is observed.
+ * NAN: robust PCA from a subset of the entries (the question the paper's closing section
+ *   leaves open; not part of its method): an entry of D that is NaN is unobserved.  With
+ *   P_Obs keeping the observed entries and p = |Obs| / (m n) (counted in rpca_init), every
+ *   step of Algorithms 1-3 goes through P_Obs: the initialisation works on P_Obs(D) / p, the
+ *   iteration takes L_{k+1} = H_r(P_T(L_k + P_Obs(D - L_k - S_k) / p)), S and err_k are
+ *   taken on the observed entries only (err_k = ||P_Obs(D - L_k - S_k)|| / ||P_Obs(D)||).
+ *   Not with zeta_mode LEARNED. */
+typedef enum { RPCA_OBS_ALL = 0, RPCA_OBS_NAN = 1 } rpca_observed;
 
 /* Kernel of the fused pass.  AUTO takes the tensor-core (tcgen05 + TMA) pass where it
  * applies (padded rank <= 16; FP32 with ld a multiple of 4 and D 16-byte aligned, or a BF16

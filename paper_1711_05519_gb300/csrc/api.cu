@@ -76,6 +76,7 @@ struct rpca_ctx {
   unsigned* masks = nullptr;
   long long mask_wr = 0;
   unsigned long long* chgP = nullptr;
+  unsigned long long* obs_count = nullptr;  // partial observation: observed entries of D
   // tensor-core pass
   bool tc_iter = false, tc_init = false;
   CUtensorMap dmap, dmap_lo;
@@ -231,6 +232,7 @@ int run_pass(rpca_ctx* c, int R, bool init) {
   a.masks = track ? c->masks : nullptr;
   a.mask_wr = c->mask_wr;
   a.chgP = track ? c->chgP : nullptr;
+  a.partial = c->p.observed == RPCA_OBS_NAN ? 1 : 0;
   prof_mark(c, true, true);
   if (init ? c->tc_init : c->tc_iter) {
     TcPassArgs t{};
@@ -258,6 +260,7 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.masks = a.masks;
     t.mask_wr = a.mask_wr;
     t.chgP = a.chgP;
+    t.partial = a.partial;
     CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
   } else {
     CK(launch_fused_pass(c->prec, R, a, c->stream));
@@ -433,7 +436,9 @@ int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
   const rpca_params& p = *params;
   if (!(p.beta > 0) || !(p.gamma >= 0 && p.gamma < 1) || !(p.tol >= 0) || p.max_iter < 0 ||
       p.precision < RPCA_PREC_FP64 || p.precision > RPCA_PREC_BF16_SPLIT || p.zeta_mode < 0 || p.zeta_mode > 3 ||
-      p.beta_init < 0 || p.mu_trim < 0 || p.pass_kind < 0 || p.pass_kind > 2 || !(p.split_switch >= 0))
+      p.beta_init < 0 || p.mu_trim < 0 || p.pass_kind < 0 || p.pass_kind > 2 || !(p.split_switch >= 0) ||
+      p.observed < RPCA_OBS_ALL || p.observed > RPCA_OBS_NAN ||
+      (p.observed == RPCA_OBS_NAN && p.zeta_mode == RPCA_ZETA_LEARNED))
     return RPCA_ERR_INVALID_ARG;
   rpca_ctx* c = new (std::nothrow) rpca_ctx();
   if (!c) return RPCA_ERR_CUDA;
@@ -462,6 +467,7 @@ void rpca_destroy(rpca_ctx* c) {
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   free_workspace(c);
   if (c->theta) cudaFree(c->theta);
+  if (c->obs_count) cudaFree(c->obs_count);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   delete c;
 }
@@ -594,6 +600,17 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   }
   CK(cudaMemsetAsync(c->stats, 0, sizeof(DevStats) * ((size_t)c->p.max_iter + 2), c->stream));
   CK(cudaMemsetAsync(c->sig, 0, 16 * c->tsize, c->stream));
+  // partial observation: p = |observed entries| / (m n)
+  double inv_p = 1.0;
+  if (c->p.observed == RPCA_OBS_NAN) {
+    if (!c->obs_count) CK(cudaMalloc((void**)&c->obs_count, sizeof(unsigned long long)));
+    unsigned long long cnt = 0;
+    CK(launch_count_observed(c->D, c->ld, (int)m, (int)n, c->prec == PREC_F32, c->obs_count, c->stream));
+    CK(cudaMemcpyAsync(&cnt, c->obs_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (cnt == 0) return RPCA_ERR_INVALID_ARG;
+    inv_p = (double)m * (double)n / (double)cnt;
+  }
 
   DevState h;
   memset(&h, 0, sizeof(h));
@@ -608,6 +625,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   h.trim = c->p.trim;
   h.zeta = INFINITY;
   h.split_switch = c->split ? (c->p.split_switch > 0 ? c->p.split_switch : 1e-2) : 0.0;
+  h.inv_p = inv_p;
   CK(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
 
   // Algorithm 3.  Phase A: sigma_1(D) with L = 0 and no threshold; phase B: top-r SVD of

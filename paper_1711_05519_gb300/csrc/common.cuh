@@ -32,6 +32,7 @@ struct DevState {
   int use_lo;            // bf16 split storage of D: the passes also read the lo part
   int pad1;
   double split_switch;   // bf16 split storage: set use_lo once err_k falls below this
+  double inv_p;          // partial observation: m n / |observed entries| (1 otherwise)
   int max_iter;
   int zeta_mode;
   int trim;
@@ -89,6 +90,9 @@ struct PassArgs {
   unsigned* masks;
   long long mask_wr;
   unsigned long long* chgP;  // per CTA: entries whose support membership changed
+  // partial observation: NaN entries of D are unobserved; the pass then takes
+  // Z = L + (D - L - S) / p on observed entries and Z = L elsewhere (DevState.inv_p = 1 / p)
+  int partial;
 };
 
 // Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
@@ -119,6 +123,7 @@ struct TcPassArgs {
   unsigned* masks;
   long long mask_wr;
   unsigned long long* chgP;
+  int partial;  // as in PassArgs (not together with masks)
 };
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
@@ -206,6 +211,10 @@ cudaError_t launch_convert_f64_to_f32(const double* src, long long ld_src, float
                                       cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float* src, long long ld_src, double* dst, int m, int n,
                                       cudaStream_t s);
+// Number of entries of D (m x n, leading dimension ld, FP32 if f32 else FP64) that are not NaN,
+// into *count (device).
+cudaError_t launch_count_observed(const void* D, long long ld, int m, int n, bool f32, unsigned long long* count,
+                                  cudaStream_t s);
 // hi = bf16_rn(d), lo = bf16_rn(d - hi) into rows of ld_dst elements; lo may be null.
 cudaError_t launch_convert_f32_to_bf16x2(const float* src, long long ld_src, void* hi, void* lo, long long ld_dst,
                                          int m, int n, cudaStream_t s);

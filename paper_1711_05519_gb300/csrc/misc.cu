@@ -43,6 +43,21 @@ __global__ void convert_f32_bf16x2(const float* __restrict__ src, long long ld, 
   }
 }
 
+// Entries of D that are not NaN (partial observation: NaN marks an unobserved entry).
+template <typename T>
+__global__ void count_observed(const T* __restrict__ D, long long ld, int m, int n, unsigned long long* count) {
+  const long long total = (long long)m * n;
+  unsigned long long c = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const T d = D[(e / n) * ld + e % n];
+    c += (d == d) ? 1ull : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(count, c);
+}
+
 // Exclusive scan of m row counts into m+1 offsets, one block of 1024 threads.
 __global__ void __launch_bounds__(1024) scan_rows(const unsigned long long* __restrict__ cnt,
                                                   unsigned long long* __restrict__ off, int m) {
@@ -72,6 +87,17 @@ __global__ void __launch_bounds__(1024) scan_rows(const unsigned long long* __re
 
 cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s) {
   scan_rows<<<1, 1024, 0, s>>>(cnt, off, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_observed(const void* D, long long ld, int m, int n, bool f32, unsigned long long* count,
+                                  cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (f32)
+    count_observed<float><<<1024, 256, 0, s>>>(static_cast<const float*>(D), ld, m, n, count);
+  else
+    count_observed<double><<<1024, 256, 0, s>>>(static_cast<const double*>(D), ld, m, n, count);
   return cudaGetLastError();
 }
 

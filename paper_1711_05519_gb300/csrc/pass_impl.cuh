@@ -173,6 +173,10 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   __syncthreads();
 
   const T zeta = static_cast<T>(a.st->zeta);
+  // partial observation: a NaN entry of D is unobserved (Z = L there, outside the support and
+  // the residual); an observed entry outside the support gets Z = L + (D - L) / p
+  const bool po = a.partial != 0;
+  const T invp = static_cast<T>(a.st->inv_p);
   const bool vec = a.vec != 0;
   const bool use_lo = DM == 1 && a.Dlo != nullptr && a.st->use_lo != 0;
   // residual: the TM x VW terms of one sub-chunk are summed in T, the sub-chunk sums in
@@ -233,11 +237,12 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
         for (int c = 0; c < VW; ++c) {
           const T l = rebuild<T, R>(w, v[c]);
           const T rr = d[t][c] - l;
-          const bool s = fabs(rr) > zeta;
-          rsc = s ? rsc : fma(rr, rr, rsc);
+          const bool s = fabs(rr) > zeta;  // false for NaN
+          const bool keep_l = s || (po && !(d[t][c] == d[t][c]));
+          rsc = keep_l ? rsc : fma(rr, rr, rsc);
           nnz += s ? 1u : 0u;
           sb |= (s ? 1u : 0u) << (t * VW + c);
-          const T z = s ? l : d[t][c];
+          const T z = keep_l ? l : (po ? fma(rr, invp, l) : d[t][c]);
 #pragma unroll
           for (int k = 0; k < R; ++k) {
             y1[t][k] = fma(z, vt[c][k], y1[t][k]);

@@ -133,6 +133,10 @@ struct TcArgs {
   unsigned long long* chgP;
 };
 
+// Variants of the epilogue: the plain pass; with the support bitmask of the learned schedule;
+// with partially observed D (NaN entries unobserved).
+enum { MODE_PLAIN = 0, MODE_MASK = 1, MODE_PARTIAL = 2 };
+
 __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) {
   atomicCAS(a.status, 0, (int)kErrTimeout);
   *abort_flag = 1;
@@ -171,13 +175,17 @@ __device__ __forceinline__ void tmem_ld_y(uint32_t taddr, uint32_t (&v)[NY]) {
 // lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
 // DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
 // 32 KB and Z is written over it (where: zhi_off / zlo_off).  RK: operand image layout (8 or 16).
-// MASK: also write the support as a bitmask (word 2 ct + h of row i holds columns
+// MODE_MASK: also write the support as a bitmask (word 2 ct + h of row i holds columns
 // 64 ct + 32 h .. + 31) and count the entries whose membership differs from the previous
 // pass's bitmask (the learned schedule's support-change statistic).
-template <int DM, int RK, bool MASK>
+// MODE_PARTIAL: a NaN entry of D is unobserved: it is outside the support and the residual,
+// and Z = L there; an observed entry outside the support gets Z = L + (D - L) / p (the step of
+// the partially observed iteration, DevState.inv_p = 1 / p).
+template <int DM, int RK, int MODE>
 __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constant__ CUtensorMap dmap,
                                                             const __grid_constant__ CUtensorMap dmap_lo, TcArgs a) {
   using C = Cfg<RK>;
+  constexpr bool MASK = MODE == MODE_MASK, PO = MODE == MODE_PARTIAL;
   constexpr int NSTAGE = C::NSTAGE, STAGE_BYTES = C::STAGE_BYTES, OFF_W = C::OFF_W, OFF_U = C::OFF_U;
   constexpr int OFF_BAR = C::OFF_BAR;
   constexpr int VOP_BYTES = C::VOP_BYTES, VTOP_BYTES = C::VTOP_BYTES, UTOP_BYTES = C::UTOP_BYTES;
@@ -389,6 +397,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const int q = warp & 3, h = (e >> 2) & 1;
     const int rowl = 32 * q + lane;
     const float zeta = static_cast<float>(a.st->zeta);
+    const float invp = PO ? static_cast<float>(a.st->inv_p) : 1.f;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     // residual: each tile's 32 squared terms of this thread are summed in a chain of their
     // own and only the tile sums (~40 per pass) are added up, so no FP32 chain is longer than
@@ -482,13 +491,21 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       for (int c = 0; c < 32; c += 2) {
         const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
         const float2 r2 = __ffma2_rn(l2, m1, make_float2(z[c], z[c + 1]));  // D - L, exactly rounded
-        const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;
-        rq = s0 ? rq : fmaf(r2.x, r2.x, rq);
-        rq = s1 ? rq : fmaf(r2.y, r2.y, rq);
+        const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;  // false for NaN
+        if (PO) {
+          const bool k0 = s0 || !(z[c] == z[c]), k1 = s1 || !(z[c + 1] == z[c + 1]);  // Z = L
+          rq = k0 ? rq : fmaf(r2.x, r2.x, rq);
+          rq = k1 ? rq : fmaf(r2.y, r2.y, rq);
+          z[c] = k0 ? l2.x : fmaf(r2.x, invp, l2.x);
+          z[c + 1] = k1 ? l2.y : fmaf(r2.y, invp, l2.y);
+        } else {
+          rq = s0 ? rq : fmaf(r2.x, r2.x, rq);
+          rq = s1 ? rq : fmaf(r2.y, r2.y, rq);
+          z[c] = s0 ? l2.x : z[c];
+          z[c + 1] = s1 ? l2.y : z[c + 1];
+        }
         nnz += (s0 ? 1u : 0u) + (s1 ? 1u : 0u);
         if (MASK) bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
-        z[c] = s0 ? l2.x : z[c];
-        z[c + 1] = s1 ? l2.y : z[c + 1];
       }
       res += rq;
       if (MASK) {
@@ -637,18 +654,28 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
 
 static_assert(Cfg<8>::MAX_CT >= 20 && Cfg<16>::MAX_CT >= 10, "column tiles per CTA (tc_max_col_tiles)");
 
-template <int DM, int RK, bool MASK>
+template <int DM, int RK, int MODE>
 cudaError_t set_tc_smem() {
-  return cudaFuncSetAttribute(fused_pass_tc<DM, RK, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(fused_pass_tc<DM, RK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Cfg<RK>::SMEM_BYTES);
 }
 
 template <int DM, int RK>
-cudaError_t launch_tc(const CUtensorMap& dmap, const CUtensorMap& lo, const TcArgs& a, cudaStream_t s) {
+cudaError_t set_tc_smem_modes() {
+  cudaError_t e = set_tc_smem<DM, RK, MODE_PLAIN>();
+  if (e == cudaSuccess) e = set_tc_smem<DM, RK, MODE_MASK>();
+  if (e == cudaSuccess) e = set_tc_smem<DM, RK, MODE_PARTIAL>();
+  return e;
+}
+
+template <int DM, int RK>
+cudaError_t launch_tc(const CUtensorMap& dmap, const CUtensorMap& lo, const TcArgs& a, int partial, cudaStream_t s) {
   if (a.masks)
-    fused_pass_tc<DM, RK, true><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+    fused_pass_tc<DM, RK, MODE_MASK><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+  else if (partial)
+    fused_pass_tc<DM, RK, MODE_PARTIAL><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
   else
-    fused_pass_tc<DM, RK, false><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+    fused_pass_tc<DM, RK, MODE_PLAIN><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
   return cudaGetLastError();
 }
 
@@ -662,14 +689,10 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
                                  cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_tc_smem<0, 8, false>();
-    if (e == cudaSuccess) e = set_tc_smem<1, 8, false>();
-    if (e == cudaSuccess) e = set_tc_smem<0, 16, false>();
-    if (e == cudaSuccess) e = set_tc_smem<1, 16, false>();
-    if (e == cudaSuccess) e = set_tc_smem<0, 8, true>();
-    if (e == cudaSuccess) e = set_tc_smem<1, 8, true>();
-    if (e == cudaSuccess) e = set_tc_smem<0, 16, true>();
-    if (e == cudaSuccess) e = set_tc_smem<1, 16, true>();
+    cudaError_t e = set_tc_smem_modes<0, 8>();
+    if (e == cudaSuccess) e = set_tc_smem_modes<1, 8>();
+    if (e == cudaSuccess) e = set_tc_smem_modes<0, 16>();
+    if (e == cudaSuccess) e = set_tc_smem_modes<1, 16>();
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -698,10 +721,11 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
   a.chgP = p.chgP;
-  if (a.masks && (!a.chgP || a.mask_wr < 2ll * a.TC)) return cudaErrorInvalidValue;
+  if (a.masks && (!a.chgP || a.mask_wr < 2ll * a.TC || p.partial)) return cudaErrorInvalidValue;
   const CUtensorMap& lo = dm ? *dmap_lo : *dmap;
-  if (p.R <= 8) return dm == 0 ? launch_tc<0, 8>(*dmap, lo, a, s) : launch_tc<1, 8>(*dmap, lo, a, s);
-  return dm == 0 ? launch_tc<0, 16>(*dmap, lo, a, s) : launch_tc<1, 16>(*dmap, lo, a, s);
+  const int po = p.partial;
+  if (p.R <= 8) return dm == 0 ? launch_tc<0, 8>(*dmap, lo, a, po, s) : launch_tc<1, 8>(*dmap, lo, a, po, s);
+  return dm == 0 ? launch_tc<0, 16>(*dmap, lo, a, po, s) : launch_tc<1, 16>(*dmap, lo, a, po, s);
 }
 
 }  // namespace rpca

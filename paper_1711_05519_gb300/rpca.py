@@ -22,6 +22,7 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16_split": 3}
 ZETA = {"paper": 0, "simple": 1, "external": 2, "learned": 3}
 SCHEDULE_PARAMS = 1313
 PASS_KIND = {"auto": 0, "simt": 1, "tensor": 2}
+OBSERVED = {"all": 0, "nan": 1}
 STATE_READS_LO = 1
 
 
@@ -46,6 +47,7 @@ class Params(ctypes.Structure):
         ("init_tol", ctypes.c_double),
         ("pass_kind", ctypes.c_int),
         ("split_switch", ctypes.c_double),
+        ("observed", ctypes.c_int),
     ]
 
 
@@ -146,7 +148,7 @@ class Solver:
     def __init__(self, beta: float, gamma: float, tol: float, precision: str = "fp32", trim: bool = True,
                  zeta_mode: str = "paper", max_iter: int = 100, beta_init: float = 0.0, mu_trim: float = 0.0,
                  init_max_passes: int = 0, init_tol: float = 0.0, pass_kind: str = "auto",
-                 split_switch: float = 0.0, stream=None):
+                 split_switch: float = 0.0, observed: str = "all", stream=None):
         L = lib()
         p = Params()
         L.rpca_params_default(ctypes.byref(p))
@@ -157,6 +159,7 @@ class Solver:
         p.init_max_passes, p.init_tol = init_max_passes, init_tol
         p.pass_kind = PASS_KIND[pass_kind]
         p.split_switch = split_switch
+        p.observed = OBSERVED[observed]
         self.params = p
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._ctx = ctypes.c_void_p()
