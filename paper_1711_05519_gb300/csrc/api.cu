@@ -74,7 +74,7 @@ struct rpca_ctx {
   int depth = 0;
   bool theta_set = false;
   unsigned* masks = nullptr;
-  long long mask_wr = 0;
+  long long mask_wr = 0, mask_words = 0;  // words per row (SIMT layout), words per buffer
   unsigned long long* chgP = nullptr;
   unsigned long long* obs_count = nullptr;  // partial observation: observed entries of D
   // tensor-core pass
@@ -231,6 +231,7 @@ int run_pass(rpca_ctx* c, int R, bool init) {
   const bool track = learned(c) && !init;
   a.masks = track ? c->masks : nullptr;
   a.mask_wr = c->mask_wr;
+  a.mask_words = c->mask_words;
   a.chgP = track ? c->chgP : nullptr;
   a.partial = c->p.observed == RPCA_OBS_NAN ? 1 : 0;
   prof_mark(c, true, true);
@@ -258,7 +259,7 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.ch_max = c->y2_ch;
     t.ct_max = c->y2_ct;
     t.masks = a.masks;
-    t.mask_wr = a.mask_wr;
+    t.mask_wr = c->mask_words;
     t.chgP = a.chgP;
     t.partial = a.partial;
     CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
@@ -586,12 +587,13 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     }
   }
   if (learned(c)) {
-    // words per row: the tensor-core pass uses 2 per 64-column tile, the SIMT pass VW per
-    // sub-chunk of 32 VW columns (VW = 4 in FP32, 2 in FP64)
-    const long long wr_tc = 2 * ((n + 63) / 64), wr_simt = (c->prec == PREC_F32) ? 4 * ((n + 127) / 128) : wr_tc;
-    c->mask_wr = wr_tc > wr_simt ? wr_tc : wr_simt;
-    CK(cudaMalloc((void**)&c->masks, sizeof(unsigned) * 2 * (size_t)m * c->mask_wr));
-    CK(cudaMemsetAsync(c->masks, 0, sizeof(unsigned) * 2 * (size_t)m * c->mask_wr, c->stream));
+    // SIMT pass: rows of VW words per sub-chunk of 32 VW columns (VW = 4 in FP32, 2 in FP64);
+    // tensor-core pass: 256 words per 128 x 64 tile, tile-major
+    const long long wr_simt = (c->prec == PREC_F32) ? 4 * ((n + 127) / 128) : 2 * ((n + 63) / 64);
+    c->mask_wr = wr_simt;
+    c->mask_words = std::max(wr_simt * m, 256ll * ((m + 127) / 128) * ((n + 63) / 64));
+    CK(cudaMalloc((void**)&c->masks, sizeof(unsigned) * 2 * (size_t)c->mask_words));
+    CK(cudaMemsetAsync(c->masks, 0, sizeof(unsigned) * 2 * (size_t)c->mask_words, c->stream));
     if ((st = dalloc(&c->chgP, ncta))) return st;
   }
   c->ws_m = m;

@@ -86,9 +86,10 @@ struct PassArgs {
   int dm;
   const void* Dlo;
   // support bitmasks (null unless the learned schedule needs the support change): two
-  // buffers of m x mask_wr words; pass k writes buffer k % 2 and compares with the other
+  // buffers of m x mask_wr words (SIMT pass, row-major); pass k writes buffer k % 2 and
+  // compares with the other
   unsigned* masks;
-  long long mask_wr;
+  long long mask_wr, mask_words;  // words per row, words per buffer
   unsigned long long* chgP;  // per CTA: entries whose support membership changed
   // partial observation: NaN entries of D are unobserved; the pass then takes
   // Z = L + (D - L - S) / p on observed entries and Z = L elsewhere (DevState.inv_p = 1 / p)
@@ -119,7 +120,8 @@ struct TcPassArgs {
   // kTcY2Chunk), ct_max >= column tiles per CTA
   float* Y2c;
   int ch_max, ct_max;
-  // support bitmasks as in PassArgs (null: not tracked)
+  // support bitmasks as in PassArgs (null: not tracked), here two buffers of mask_wr words
+  // each (>= TR TC 256, tile-major, see pass_tc.cu)
   unsigned* masks;
   long long mask_wr;
   unsigned long long* chgP;

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256, 1) fused_pass_kernel(PassArgs a) {
   // support bitmasks (learned schedule): word (i, chunk, c) holds, in bit l, the entry of row
   // i at column chunk * SCW + l * VW + c; pass k writes buffer k % 2 and compares with the other
   const bool track = a.masks != nullptr;
-  const long long mask_sz = a.mask_wr * (long long)m;
+  const long long mask_sz = a.mask_words;
   unsigned* mask_new = track ? a.masks + ((a.st->k & 1) ? mask_sz : 0) : nullptr;
   const unsigned* mask_old = track ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
 

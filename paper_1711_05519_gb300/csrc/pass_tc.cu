@@ -175,9 +175,10 @@ __device__ __forceinline__ void tmem_ld_y(uint32_t taddr, uint32_t (&v)[NY]) {
 // lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
 // DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
 // 32 KB and Z is written over it (where: zhi_off / zlo_off).  RK: operand image layout (8 or 16).
-// MODE_MASK: also write the support as a bitmask (word 2 ct + h of row i holds columns
-// 64 ct + 32 h .. + 31) and count the entries whose membership differs from the previous
-// pass's bitmask (the learned schedule's support-change statistic).
+// MODE_MASK: also write the support as a bitmask and count the entries whose membership
+// differs from the previous pass's bitmask (the learned schedule's support-change
+// statistic).  Layout, tile-major so that a warp's 32 rows are 32 consecutive words: word
+// ((rt TC + ct) 2 + h) 128 + row-in-tile holds columns 64 ct + 32 h .. + 31 of that row.
 // MODE_PARTIAL: a NaN entry of D is unobserved: it is outside the support and the residual,
 // and Z = L there; an observed entry outside the support gets Z = L + (D - L) / p (the step of
 // the partially observed iteration, DevState.inv_p = 1 / p).
@@ -405,8 +406,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // up to ~1e-4 relative); the totals over threads are taken in FP64
     float res = 0.f;
     unsigned nnz = 0, chg = 0;
-    // support bitmasks of this pass (k even: buffer 0) and of the previous one
-    const long long mask_sz = a.mask_wr * (long long)a.m;
+    // support bitmasks of this pass (k even: buffer 0) and of the previous one, mask_wr words
+    // each (at least TR TC 256)
+    const long long mask_sz = a.mask_wr;
     unsigned* mask_new = MASK ? a.masks + ((a.st->k & 1) ? mask_sz : 0) : nullptr;
     const unsigned* mask_old = MASK ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
     for (int t = grp; t < ntiles && !abort_flag; t += 2) {
@@ -509,13 +511,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       }
       res += rq;
       if (MASK) {
-        const int row = (rt0 + rtl) * BM + rowl;
-        if (row < a.m) {
-          const long long w = (long long)row * a.mask_wr + 2 * (ct0 + ctl) + h;
-          const unsigned old = mask_old[w];
-          mask_new[w] = bits;
-          chg += __popc(bits ^ old);
-        }
+        // rows past m hold no support (their D reads as zero and L as zero)
+        const long long w = (((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl;
+        const unsigned old = mask_old[w];
+        mask_new[w] = bits;
+        chg += __popc(bits ^ old);
       }
       // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
       // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
@@ -721,7 +721,7 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
   a.chgP = p.chgP;
-  if (a.masks && (!a.chgP || a.mask_wr < 2ll * a.TC || p.partial)) return cudaErrorInvalidValue;
+  if (a.masks && (!a.chgP || a.mask_wr < 256ll * a.TR * a.TC || p.partial)) return cudaErrorInvalidValue;
   const CUtensorMap& lo = dm ? *dmap_lo : *dmap;
   const int po = p.partial;
   if (p.R <= 8) return dm == 0 ? launch_tc<0, 8>(*dmap, lo, a, po, s) : launch_tc<1, 8>(*dmap, lo, a, po, s);

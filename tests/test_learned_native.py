@@ -47,10 +47,14 @@ def test_schedule_kernels_match_fp64_reference():
     assert np.allclose(zeta.cpu().numpy(), ref.detach().numpy(), rtol=2e-6, atol=0)
     gref = th64.grad.numpy()
     assert np.linalg.norm(grad.double().cpu().numpy() - gref) < 2e-5 * np.linalg.norm(gref)
-    # the saturated sample contributes nothing through the clamp
-    only_last = torch.zeros_like(zb)
-    only_last[-1] = 1.0
-    assert float(PL.schedule_backward(th, feats, plain, only_last).abs().max()) == 0.0
+    # a saturated output contributes nothing through the clamp, and the threshold is the
+    # paper's times 4
+    sat = th.clone()
+    sat[1312] = 50.0
+    zs, gs = PL.schedule_forward(sat, feats, plain)
+    assert torch.equal(gs.cpu(), torch.full((n,), float(np.float32(np.log(4.0)))))
+    assert np.allclose(zs.cpu().numpy(), 4.0 * plain.cpu().numpy(), rtol=1e-6)
+    assert float(PL.schedule_backward(sat, feats, plain, zb).abs().max()) == 0.0
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -100,7 +104,7 @@ def test_learned_iteration_applies_the_network_on_the_device():
         assert f[4] == pytest.approx((k + 1) / 9, rel=1e-6)
         assert f[5] == pytest.approx(np.log(st["zeta"] / st["sigma1"]), rel=1e-5, abs=1e-6)
         assert f[3] == pytest.approx(st["support_changes"] / (600 * 560), rel=1e-6, abs=1e-9)
-    assert stats[0]["support_changes"] == 0 and stats[2]["support_changes"] > 0
+    assert stats[0]["support_changes"] == 0 and max(st["support_changes"] for st in stats[1:]) > 0
 
 
 def test_support_change_count_of_the_pass():
@@ -112,13 +116,15 @@ def test_support_change_count_of_the_pass():
     with PL._solver(x, 0.0, 8) as s:
         s.set_schedule(th, 8)
         s.init(x["D"], 4)
-        prev = None
+        prev, seen = None, 0
         for k in range(6):
             idx = set(s.sparse()[0].cpu().numpy().tolist())
             _, st = s.iterate(1)
             if prev is not None:
                 assert abs(st[0]["support_changes"] - len(idx ^ prev)) <= 4
+                seen = max(seen, len(idx ^ prev))
             prev = idx
+    assert seen > 100  # the supports did move between these iterations
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
