@@ -66,7 +66,8 @@ typedef enum {
  * LEARNED (not in the paper): zeta_{k+1} = zeta^plain_{k+1} exp(clamp(g(s_k), -log 4, log 4)),
  *   zeta^plain the PAPER rule and g a 6 -> 32 -> 32 -> 1 tanh network (FP32) on the statistics
  *   s_k = [log sigma_1, log(sigma_{r+1}/sigma_1), log err_k, fraction of the entries whose
- *   support membership changed since pass k - 1 (0 at k = 0), (k + 1) / K, log(zeta_k/sigma_1)],
+ *   support membership changed since pass k - 1 (0 at k = 0), (k + 1) / K, log(zeta_k/sigma_1)]
+ *   (FP32, arguments of the logarithms floored at 1e-37),
  *   evaluated on the device inside the iteration; parameters and K from rpca_set_schedule.
  *   The passes then also keep the support of the last two passes as bitmasks (2 m n / 8 bytes). */
 typedef enum {

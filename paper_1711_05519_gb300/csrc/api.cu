@@ -746,10 +746,14 @@ int rpca_get_pass_operands(rpca_ctx* c, void* W, void* V, void* Ut, void* Vt, in
   *width = c->Rr;
   const size_t rm = (size_t)c->m * c->Rr * c->tsize, rn = (size_t)c->n * c->Rr * c->tsize;
   CK(cudaMemcpyAsync(W, c->Wc, rm, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(Ut, c->Utc, rm, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemcpyAsync(V, c->Vc, rn, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(Vt, c->Vtc, rn, cudaMemcpyDeviceToDevice, c->stream));
-  return RPCA_OK;
+  // the pass reads the trimmed factors; their orthonormal bases come from a small kernel
+  CK(cudaMemsetAsync(Ut, 0, rm, c->stream));
+  CK(cudaMemsetAsync(Vt, 0, rn, c->stream));
+  SmallArgs b = small_args(c, SM_BASES, c->Rr);
+  b.out_ut = Ut;
+  b.out_vt = Vt;
+  return run_small(c, b);
 }
 
 int rpca_get_lowrank(rpca_ctx* c, double* U, double* sigma, double* V) {

@@ -159,7 +159,7 @@ cudaError_t launch_extract_write(int prec, int R, const ExtractArgs& a, cudaStre
 // CholeskyQR, the small SVD, the factor update, Trim and the pass-precision copies.
 // Gram partials: kSmallSlots slots of 16 x 16 doubles per block.
 constexpr int kSmallSlots = 8;
-enum SmallMode { SM_UPDATE = 0, SM_PREPARE = 1, SM_RR = 2, SM_RAND = 3 };
+enum SmallMode { SM_UPDATE = 0, SM_PREPARE = 1, SM_RR = 2, SM_RAND = 3, SM_BASES = 4 };
 
 struct SmallArgs {
   int mode;
@@ -201,6 +201,9 @@ struct SmallArgs {
   int img_rk[2];
   int img_init;
   int img_iter;
+  // SM_BASES: outputs U~ (m x Rit), V~ (n x Rit) in the working precision
+  void* out_ut;
+  void* out_vt;
 };
 cudaError_t launch_small(const SmallArgs& a, int grid, cudaStream_t s);
 // Runs the bounded-wait self-test kernels (small.cu) on the current device and returns the

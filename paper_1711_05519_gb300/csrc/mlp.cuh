@@ -25,18 +25,20 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * IN, OFF_W2 = OFF_B1 + H, OFF_B2 
               OFF_B3 = OFF_W3 + H, NPARAM = OFF_B3 + 1;
 constexpr float kLog4 = 1.38629436111989061883f;
 
-// Statistics of one iteration (see above), computed in double and rounded to FP32.  Zero
-// singular values, residuals or support changes are floored at 1e-300 before the logarithm.
+// Statistics of one iteration (see above): the ratios are formed in double, rounded to FP32
+// and floored at 1e-37 (a zero singular value or residual), and the logarithms taken in FP32
+// (double-precision logarithms are long-latency on this part, and the network reads FP32).
+__device__ __forceinline__ float log_floor(double x) { return logf(fmaxf((float)x, 1e-37f)); }
+
 __device__ __forceinline__ void features(double sigma1, double sigma_r1, double err, double change, int k, int depth,
                                          double zeta, float (&s)[IN]) {
-  const double tiny = 1e-300;
-  const double s1 = fmax(sigma1, tiny);
-  s[0] = (float)log(s1);
-  s[1] = (float)log(fmax(sigma_r1, tiny) / s1);
-  s[2] = (float)log(fmax(err, tiny));
+  const double s1 = fmax(sigma1, 1e-300);
+  s[0] = log_floor(s1);
+  s[1] = log_floor(sigma_r1 / s1);
+  s[2] = log_floor(err);
   s[3] = (float)change;
-  s[4] = (float)((double)(k + 1) / (double)(depth > 0 ? depth : 1));
-  s[5] = (float)log(fmax(zeta, tiny) / s1);
+  s[4] = (float)(k + 1) / (float)(depth > 0 ? depth : 1);
+  s[5] = log_floor(zeta / s1);
 }
 
 // Network output g(s) before the clamp, the same in all 32 lanes of the calling warp (all

@@ -413,6 +413,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const unsigned* mask_old = MASK ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
     for (int t = grp; t < ntiles && !abort_flag; t += 2) {
       const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
+      // support word of this thread's row and columns in the previous pass, loaded here so that
+      // its latency passes while the tile is waited for (used after Z is handed on)
+      long long mw = 0;
+      unsigned mold = 0;
+      if (MASK) {
+        mw = (((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl;
+        mold = mask_old[mw];
+      }
       if (rtl % G2 == 0 && rtl > 0) {
         // read chunk c - 1 of column tile ctl's Y2 accumulator (hi + lo column halves) out to
         // its slot before this tile's products restart the accumulator
@@ -510,13 +518,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         if (MASK) bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
       }
       res += rq;
-      if (MASK) {
-        // rows past m hold no support (their D reads as zero and L as zero)
-        const long long w = (((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl;
-        const unsigned old = mask_old[w];
-        mask_new[w] = bits;
-        chg += __popc(bits ^ old);
-      }
       // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
       // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
       uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
@@ -543,6 +544,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_ZFULL + s]);
+      if (MASK) {  // rows past m hold no support (their D reads as zero and L as zero)
+        mask_new[mw] = bits;
+        chg += __popc(bits ^ mold);
+      }
       if (ctl == nct - 1 && h == 0) {
         // drain Y1 of this row tile
         if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {

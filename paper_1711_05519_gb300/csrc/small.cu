@@ -7,28 +7,27 @@
 // 2r x 2r core M_k and its SVD) are computed redundantly, in the same order, by every
 // block, so the only cross-block traffic is the per-block Gram partials.
 //
-// All of it runs in the working precision (double in FP64 mode, float in FP32 mode); sums
-// run as pairwise trees, and Cholesky factorisations scale the Gram matrix to unit
-// diagonal first.  The Q factor of the projected products is never formed: with
+// The per-row work runs in the working precision (double in FP64 mode, float in FP32 mode);
+// the small steps of the iteration (Gram sums, Cholesky factors, the 2r x 2r SVD, sigma_1)
+// run in double in every mode.  Sums run as pairwise trees, and Cholesky factorisations
+// scale the Gram matrix to unit diagonal first.  The Q factor of the projected products is never formed: with
 // (I - U~U~^T) Z V~ = W1 = Q1 R1 and Q1 = W1 T1 (T1 upper, T1 = R1^{-1} on the non-zero
 // pivots), Eq. (9) becomes U_{k+1} = U~ U_M[:r, :r] + W1 (T1 U_M[r:, :r]).
 //
 // Modes:
-//   SM_UPDATE : after a fused pass of Algorithm 1.  err_k (Eq. (11)) from the per-CTA
-//               totals; stop if err_k < tol (with bf16 split storage of D, only on a
-//               pass that read hi + lo; the switch to hi + lo is made here too).  Otherwise
-//                 A: Y1 = Z V~, Y2 = Z^T U~ (sums of the pass partials); C = U~^T Y1
-//                 B: W1 = Y1 - U~ C, W2 = Y2 - V~ C^T and their Gram matrices
-//                 C: R1, R2 (Cholesky), M = [[C, R2^T], [R1, 0]] and its SVD, zeta_{k+1}
-//                    (Algorithm 1), the new factors (Eq. (9)), Trim (Algorithm 2) and the
-//                    Gram matrices of the trimmed factors
-//                 D: orthonormal bases U~, V~ of the trimmed factors (the footnote to
-//                    Eq. (5) asks for a QR) and the copies read by the next pass.
-//   SM_PREPARE: Trim + D from the factors held (U, sigma, V).
+//   SM_UPDATE : after a fused pass of Algorithm 1 (see mode_update): err_k (Eq. (11)) and the
+//               stop test; the orthonormal bases U~, V~ of the trimmed factors the pass read;
+//               Y1 = Z V~, Y2 = Z^T U~, the QR of their projections (Section 2.1) by Cholesky of
+//               Gram matrices, M = [[C, R2^T], [R1, 0]] and its SVD, zeta_{k+1} (Algorithm 1),
+//               the new factors (Eq. (9)), Trim (Algorithm 2) and the hand-over to the next pass.
+//               One grid barrier (two in FP64 working precision).
+//   SM_PREPARE: Trim and hand-over from the factors held (U, sigma, V).
 //   SM_RR     : one step of block subspace iteration for Algorithm 3 (sigma_1(D), then the
 //               top-r SVD of D - S_{-1}): Rayleigh-Ritz B = U~^T (Z V~), SVD(B), the Ritz
-//               residuals, and the next bases orth(Z V~), orth(Z^T U~) by CholeskyQR2.
+//               residuals, and the next bases orth(Z V~), orth(Z^T U~) by CholeskyQR2; after
+//               the last step, Trim and the hand-over to the first pass of Algorithm 1.
 //   SM_RAND   : random orthonormal starting bases for SM_RR.
+//   SM_BASES  : the orthonormal bases U~, V~ of the next pass, for a caller.
 // Where the next pass is the tensor-core one, the step that writes the pass copies also
 // writes that pass's operand images (tc_images.cuh) for the rows it owns.
 //
@@ -76,7 +75,35 @@ struct Smem {
   T sv[2][MW];             // sigma_c, 1/sigma_c
   int pairs[32 * 32];      // Jacobi round-robin partner of each lane in each round
   int ok;
+  // double-precision small steps of the iteration (every mode): Gram sums, the trimmed
+  // factors' T factors, the Cholesky factors of the projected products, the core M and its
+  // SVD
+  double dbuf[ST];
+  double Gd[6][GSLOT];     // reduced Gram matrices
+  double Cd[GSLOT];        // U~^T Y1
+  double Tt[2][GSLOT];     // T factors of the trimmed factors (U~ = A~ Tt[0], V~ = B~ Tt[1])
+  double Rt[2][GSLOT];     // their R factors (unused beyond the factorisation)
+  double Rd[2][GSLOT];     // R1, R2
+  double Td[2][GSLOT];     // T1, T2
+  double Md[NM * NM];
+  double UMd[NM * NM];
+  double VMd[NM * NM];
+  double sigd[NM];
 };
+
+// 1 / sqrt(x) for x > 0 in double precision: the single-precision estimate refined by two
+// Newton-Raphson steps y <- y (3 - x y^2) / 2 (each roughly doubles the correct bits).  Double
+// square roots and divisions are long-latency on this part; this takes a few fused
+// multiply-adds.  Arguments outside the single-precision range take the library routine.
+__device__ __forceinline__ double rsqrt_d(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+__device__ __forceinline__ float rsqrt_d(float x) { return 1.0f / sqrtf(x); }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -242,17 +269,93 @@ __device__ __noinline__ void reduce_slots(const void* part, int slot0, int ns, i
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Gram sums in double precision (the iteration's small steps): per-thread shares over the
+// staged rows (row stride WM) of X^T Y, the block's partial into a double slot, and the sum
+// over blocks of double slots.  Summation orders depend only on the grid size.
+template <typename T, int WM>
+__device__ __forceinline__ double gram_acc_d(const T* X, int wx, const T* Y, int wy, int nrows, double acc) {
+  const int P = wx * wy, t = threadIdx.x, nl = ST / P, l = t / P;
+  if (l < nl) {
+    const int p = t % P, a = p / wy, b = p % wy;
+    for (int i = l; i < nrows; i += nl) acc = fma((double)X[i * WM + a], (double)Y[i * WM + b], acc);
+  }
+  return acc;
+}
+
+template <typename S>
+__device__ __noinline__ void tree_combine_d(int cnt, int nparts, S& sh) {
+  const int t = threadIdx.x, q = t / cnt, j = t % cnt;
+  int h = 1;
+  while (h < nparts) h <<= 1;
+  for (h >>= 1; h > 0; h >>= 1) {
+    if (q < h && q + h < nparts) sh.dbuf[q * cnt + j] += sh.dbuf[(q + h) * cnt + j];
+    __syncthreads();
+  }
+}
+
+template <typename S>
+__device__ __noinline__ void gram_store_d(double acc, int P, void* part, int slot, S& sh) {
+  const int t = threadIdx.x;
+  sh.dbuf[t] = acc;
+  __syncthreads();
+  tree_combine_d(P, ST / P, sh);
+  if (t < P) slot_ptr<double>(part, slot, blockIdx.x)[t] = sh.dbuf[t];
+  __syncthreads();
+}
+
+template <typename S>
+__device__ __noinline__ void reduce_slots_d(const void* part, int slot0, int ns, int P, double* G, S& sh) {
+  const int t = threadIdx.x, nb = gridDim.x, total = ns * P;
+  const double* pb = static_cast<const double*>(part);
+  for (int j0 = 0; j0 < total; j0 += ST) {
+    const int cnt = min(ST, total - j0);
+    const int nch = min(32, ST / cnt);
+    const int c = t / cnt;
+    double s = 0.0;
+    if (c < nch) {
+      const int j = j0 + t % cnt;
+      const double* base = pb + (size_t)(slot0 + j / P) * nb * GSLOT + (j % P);
+      for (int b0 = c; b0 < nb; b0 += 16 * nch) {
+        double v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int b = b0 + u * nch;
+          v[u] = (b < nb) ? base[(size_t)b * GSLOT] : 0.0;
+        }
+        s += tree_sum<double, 16>(v);
+      }
+    }
+    sh.dbuf[t] = s;
+    __syncthreads();
+    tree_combine_d(cnt, nch, sh);
+    if (t < cnt) {
+      const int j = j0 + t;
+      G[(j / P) * GSLOT + (j % P)] = sh.dbuf[t];
+    }
+    __syncthreads();
+  }
+}
+
 // R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix (w <= WM),
 // by one warp in the working precision, in registers: lane l holds column l.  G is scaled to
 // unit diagonal first, G^ = D^-1/2 G D^-1/2; a pivot of G^ at or below 1e-6 (float) or 1e-14
 // (double), a direction lost to rounding, gives a zero row of R and a zero column of T.  Then
 // R = R^ D^1/2 and T = D^-1/2 R^-1, column l of R^-1 by back substitution in lane l.
+//
+// With `ref` given, a column whose squared norm G_ll is at or below eps_ref ref_l is treated as
+// zero from the start (ref: the squared norms of the columns it was projected from, so that a
+// direction below the precision of the data is dropped even when G itself is only rounding).
+// In double precision the square roots and divisions are the Newton-refined rsqrt_d.
 template <typename T, int WM>
-__device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm) {
+__device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm, const T* ref = nullptr,
+                                         T eps_ref = T(0)) {
   const int l = threadIdx.x & 31;
   const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
-  const T dl = (l < w) ? sqrt(fmax(G[l * w + l], T(0))) : T(0);
-  const T il = dl > T(0) ? T(1) / dl : T(0);
+  const T gll = (l < w) ? G[l * w + l] : T(0);
+  const bool dead = ref != nullptr && l < w && !(gll > eps_ref * ref[l]);
+  const T il = (l < w && gll > T(0) && !dead) ? rsqrt_d(gll) : T(0);
+  const T dl = gll * il;
   T a[WM];  // column l of the working matrix
 #pragma unroll
   for (int k = 0; k < WM; ++k) {
@@ -260,13 +363,15 @@ __device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm) {
     a[k] = (l < w && k < w) ? G[k * w + l] * (ik * il) : T(0);
   }
   // right-looking Cholesky: step j fixes row j of R^ (a[j] of every lane becomes R^_jl)
+  T pinv = T(0);  // this lane's 1 / R^_ll
 #pragma unroll
   for (int j = 0; j < WM; ++j) {
     if (j < w) {
       const T d = __shfl_sync(FULL, a[j], j);
       const bool good = d > tiny;
-      const T rjj = good ? sqrt(d) : T(0);
-      const T inv = good ? T(1) / rjj : T(0);
+      const T inv = good ? rsqrt_d(d) : T(0);
+      const T rjj = d * inv;
+      if (l == j) pinv = inv;
       const T rjl = (l > j) ? a[j] * inv : ((l == j) ? rjj : T(0));
       a[j] = rjl;
 #pragma unroll
@@ -282,11 +387,7 @@ __device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm) {
     if (l < w && k < w) R[k * w + l] = (k <= l) ? a[k] : T(0);
   __syncwarp();
   // 1 / R^_ii from lane i
-  T rd = T(0);
-  if (l < w) {
-    const T dii = R[l * w + l];
-    rd = dii != T(0) ? T(1) / dii : T(0);
-  }
+  const T rd = (l < w) ? pinv : T(0);
   // column l of R^-1: t_i = (delta_il - sum_{k=i+1}^{l} R^_ik t_k) / R^_ii for i = l .. 0
   T t[WM];
 #pragma unroll
@@ -569,6 +670,157 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
   __syncwarp();
 }
 
+// Double-precision sweeps of one-sided Jacobi on nearly orthogonal columns (the refinement
+// after the single-precision sweeps): the rotation angle is taken in single precision (near
+// convergence only its relative accuracy matters for the quadratic convergence of Jacobi's
+// method), the rotation itself is exactly orthogonal in double (c = 1/sqrt(1 + t^2) by
+// rsqrt_d, s = c t) and applied in double.  Pairs rotate while gamma^2 > 1e-28 alpha beta.
+template <int NM>
+__device__ void jacobi_refine_d(int N, double (&x)[NM], double (&v)[NM], int max_sweeps, const int* pairs) {
+  const int lane = threadIdx.x & 31;
+  const int L = N + (N & 1) - 1;
+  for (int sweep = 0; sweep < max_sweeps && L > 0; ++sweep) {
+    bool rot = false;
+    for (int rd = 0; rd < L; ++rd) {
+      const int q = pairs[rd * 32 + lane];
+      const bool low = lane < q;
+      // partner values are fetched element by element (twice: for the sums and for the
+      // rotation) so that only this lane's two columns stay in registers
+      double sa = 0.0, sb = 0.0, sg = 0.0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        const double xq = __shfl_sync(FULL, x[i], q);
+        const double a0 = low ? x[i] : xq, b0 = low ? xq : x[i];
+        sa = fma(a0, a0, sa);
+        sb = fma(b0, b0, sb);
+        sg = fma(a0, b0, sg);
+      }
+      bool doit = (q != lane) && sg != 0.0 && sg * sg > 1e-28 * sa * sb;
+      double c_rot = 1.0, s_rot = 0.0;
+      if (doit) {
+        const float zf = (float)(sb - sa) / (2.0f * (float)sg);
+        const float az = fabsf(zf);
+        float tf = (az > 1e18f) ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(zf, zf, 1.0f)));
+        tf = (zf < 0.0f) ? -tf : tf;
+        const double t = (double)tf;
+        c_rot = rsqrt_d(fma(t, t, 1.0));
+        s_rot = low ? -(c_rot * t) : (c_rot * t);
+        doit = tf != 0.0f;
+      }
+      // every lane takes part in the shuffles; a lane that does not rotate keeps its columns
+      const double cc = doit ? c_rot : 1.0, ss = doit ? s_rot : 0.0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        const double xq = __shfl_sync(FULL, x[i], q), vq = __shfl_sync(FULL, v[i], q);
+        x[i] = fma(cc, x[i], ss * xq);
+        v[i] = fma(cc, v[i], ss * vq);
+      }
+      rot = rot || doit;
+    }
+    if (!__any_sync(FULL, rot)) break;
+  }
+}
+
+// Double-precision part of small_svd_d on registers sized NJ >= N: V from the single-precision
+// sweeps (vf) re-orthonormalised in double (modified Gram-Schmidt), then double-precision
+// sweeps on M V; results sorted by singular value into sh.sigd, sh.UMd, sh.VMd.
+template <int NJ, typename T, int WM>
+__device__ __forceinline__ void svd_refine_sized(int N, const float* vf, Smem<T, WM>& sh) {
+  constexpr int NM = Smem<T, WM>::NM;
+  const int lane = threadIdx.x & 31;
+  double vd[NJ], y[NJ];
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) vd[i] = (double)vf[i];
+  for (int j = 0; j < N; ++j) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) s2 = fma(vd[i], vd[i], s2);
+    if (lane == j) {
+      const double inv = rsqrt_d(s2);
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) vd[i] *= inv;
+    }
+    double vj[NJ];
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) vj[i] = __shfl_sync(FULL, vd[i], j);
+    if (lane > j && lane < N) {
+      double d = 0.0;
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) d = fma(vd[i], vj[i], d);
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) vd[i] = fma(-d, vj[i], vd[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) acc = fma(sh.Md[i * NM + k], vd[k], acc);
+    y[i] = (lane < N && i < N) ? acc : 0.0;
+  }
+  jacobi_refine_d<NJ>(N, y, vd, 4, sh.pairs);
+  double s2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) s2 = fma(y[i], y[i], s2);
+  const double inv = s2 > 0.0 ? rsqrt_d(s2) : 0.0;
+  const double sg = (lane < N) ? s2 * inv : -1.0;
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) y[i] *= inv;
+  int rank = 0;
+  for (int i = 0; i < N; ++i) {
+    const double si = __shfl_sync(FULL, sg, i);
+    rank += (si > sg || (si == sg && i < lane)) ? 1 : 0;
+  }
+  if (lane < N) {
+    sh.sigd[rank] = sg;
+    for (int i = 0; i < NM; ++i) {
+      sh.UMd[rank * NM + i] = 0.0;
+      sh.VMd[rank * NM + i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) {
+      sh.UMd[rank * NM + i] = y[i];
+      sh.VMd[rank * NM + i] = vd[i];
+    }
+  }
+  __syncwarp();
+}
+
+// SVD of the N x N matrix sh.Md (N <= NM, double) by warp 0: single-precision one-sided Jacobi
+// on Md scaled to max |M_ij| = 1, then the double-precision refinement above.  On return
+// sh.sigd holds the singular values in descending order and sh.UMd / sh.VMd the matching left /
+// right singular vectors (column c at [c * NM + i]; a zero singular value gives a zero left
+// vector).
+template <typename T, int WM>
+__device__ void small_svd_d(int N, Smem<T, WM>& sh) {
+  constexpr int NM = Smem<T, WM>::NM;
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  jacobi_pairs(N, sh.pairs);
+  double mx = 0.0;
+  for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.Md[(e / N) * NM + (e % N)]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
+  const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+  float xf[NM], vf[NM];
+  if (N <= 8) {
+    jacobi_f32_sized<8, NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    svd_refine_sized<8>(N, vf, sh);
+  } else if (N <= 12) {
+    jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    svd_refine_sized<(NM < 12 ? NM : 12)>(N, vf, sh);
+  } else if (N <= 16 || NM <= 16) {
+    jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    svd_refine_sized<(NM < 16 ? NM : 16)>(N, vf, sh);
+  } else if (N <= 20) {
+    jacobi_f32_sized<20, NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    svd_refine_sized<20>(N, vf, sh);
+  } else {
+    jacobi_f32_sized<NM, NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    svd_refine_sized<NM>(N, vf, sh);
+  }
+}
+
 template <typename T, int WM>
 __device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long& nnz, Smem<T, WM>& sh,
                            unsigned long long* changes = nullptr) {
@@ -638,90 +890,126 @@ __device__ __noinline__ void write_images(const SmallArgs& a, int set, int side,
 }
 
 // ---------------------------------------------------------------------------------------
-// Trim of the factors held (Algorithm 2) and the Gram matrices of the trimmed factors
-// (slots 3, 4).  The trimmed rows go to U~, V~ (orthonormalised by finish_bases).
+// Trim (Algorithm 2) and the hand-over to the next pass.
+//
+// The pass of iteration k reads W = U_k Sigma_k, V_k and, in place of the orthonormal bases
+// U~_k, V~_k of the footnote to Eq. (5), the trimmed factors A~_k, B~_k themselves, so its
+// products are X1 = Z B~ and X2 = Z^T A~.  The update that follows takes U~ = A~ T_u and
+// V~ = B~ T_v (one CholeskyQR each, T = R^-1 from the Gram matrices of A~, B~), and
+// Y1 = Z V~ = X1 T_v, Y2 = Z^T U~ = X2 T_u.  The Gram partials of A~, B~ are written by the
+// kernel that trims (double slots 6, 7) and summed by the next kernel, so no grid barrier
+// separates the trim from the orthonormalisation.
+
+// Pass copies of row i for the next pass: W = f sigma (side 0) or V = f (side 1) and the
+// trimmed row t (A~ or B~), zero-padded to width Rit, and (tensor-core pass) their images.
 template <typename T, int WM>
-__device__ void trim_and_gram(const SmallArgs& a, Smem<T, WM>& sh) {
+__device__ __forceinline__ void hand_over_row(const SmallArgs& a, int side, int i, const T (&f)[WM], const T (&t)[WM],
+                                              const T* sig) {
+  T w[WM];
+#pragma unroll
+  for (int j = 0; j < WM; ++j) w[j] = side ? f[j] : f[j] * sig[j];
+  store_copy<T, WM>(static_cast<T*>(side ? a.Vc : a.Wc), i, a.Rit, w);
+  store_copy<T, WM>(static_cast<T*>(side ? a.Vtc : a.Utc), i, a.Rit, t);
+  if constexpr (sizeof(T) == 4) {
+    if (a.img_iter) write_images<T, WM>(a, 1, side, i, w, t);
+  }
+}
+
+// Row f of U (side 0, cap sqrt(mu r / m)) or V (side 1, cap sqrt(mu r / n)) scaled by
+// min(1, cap / ||f||) (Algorithm 2), or left as it is without trimming.
+template <typename T, int WM>
+__device__ __forceinline__ void trim_row(const T (&f)[WM], T cap, bool do_trim, T (&x)[WM]) {
+  T nrm = T(0);
+#pragma unroll
+  for (int j = 0; j < WM; ++j) nrm = fma(f[j], f[j], nrm);
+  nrm = sqrt(nrm);
+  const T sc = (do_trim && nrm > cap) ? cap / nrm : T(1);
+#pragma unroll
+  for (int j = 0; j < WM; ++j) x[j] = f[j] * sc;
+}
+
+template <typename T>
+__device__ __forceinline__ T trim_cap(const SmallArgs& a, int side) {
+  return sqrt((T)a.st->mu_trim * (T)a.r / (T)(side ? a.n : a.m));
+}
+
+// Trim and hand-over of the factors held (U, V; sigma in sh.sv[0]) over the block's rows,
+// with the Gram partials of A~, B~ into double slots 6, 7.
+template <typename T, int WM>
+__device__ void trim_hand_over(const SmallArgs& a, Smem<T, WM>& sh) {
   const int r = a.r, t = threadIdx.x;
-  const double mu = a.st->mu_trim;
   const bool do_trim = a.st->trim != 0;
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? a.n : a.m;
-    const T cap = sqrt((T)mu * (T)r / (T)rows);
+    const T cap = trim_cap<T>(a, side);
     const T* F = static_cast<const T*>(side ? a.V : a.U);
-    T* Tt = static_cast<T*>(side ? a.Vt : a.Ut);
     int lo, hi;
     block_range(rows, lo, hi);
-    T acc = T(0);
+    double acc = 0.0;
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T x[WM];
       zero_row<T, WM>(x);
       if (i < hi) {
-        load_row<T, WM>(F, i, r, x);
-        T nrm = T(0);
-#pragma unroll
-        for (int j = 0; j < WM; ++j) nrm = fma(x[j], x[j], nrm);
-        nrm = sqrt(nrm);
-        const T sc = (do_trim && nrm > cap) ? cap / nrm : T(1);
-#pragma unroll
-        for (int j = 0; j < WM; ++j) x[j] *= sc;
-        store_row<T, WM>(Tt, i, r, x);
+        T f[WM];
+        load_row<T, WM>(F, i, r, f);
+        trim_row<T, WM>(f, cap, do_trim, x);
+        hand_over_row<T, WM>(a, side, i, f, x, sh.sv[0]);
       }
       stage_row<T, WM>(sh.stage[0], t, x);
       __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      acc = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
-    gram_store(acc, r * r, a.part, 3 + side, sh);
+    gram_store_d(acc, r * r, a.part, 6 + side, sh);
   }
 }
 
-// After a barrier: U~ <- trimmed U T_u, V~ <- trimmed V T_v (one CholeskyQR), and the
-// copies read by the next pass: W = U Sigma, V, U~, V~ zero-padded
-// to width Rit.  sh.sv[0] holds sigma.
+// T_u, T_v of the trimmed factors the last pass read, from the Gram partials in double slots
+// 6, 7 (every block sums them in the same order; one warp factors each), into sh.Tt and, in
+// the working precision and zero-padded, sh.tm.
 template <typename T, int WM>
-__device__ void finish_bases(const SmallArgs& a, Smem<T, WM>& sh) {
-  const int r = a.r, t = threadIdx.x, Rc = a.Rit;
-  reduce_slots(a.part, 3, 2, r * r, &sh.G[0][0], sh);
-  factor_pair<T, WM>(r, 0, 1, sh);
-  for (int side = 0; side < 2; ++side) {
-    const int rows = side ? a.n : a.m;
-    const T* F = static_cast<const T*>(side ? a.V : a.U);
-    T* Tt = static_cast<T*>(side ? a.Vt : a.Ut);
-    T* d0 = static_cast<T*>(side ? a.Vc : a.Wc);
-    T* d1 = static_cast<T*>(side ? a.Vtc : a.Utc);
-    int lo, hi;
-    block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
-      T x[WM], q[WM], f[WM];
-      load_row<T, WM>(Tt, i, r, x);
-      load_row<T, WM>(F, i, r, f);
-      row_times<T, WM>(x, sh.tm[side], q);
-      store_row<T, WM>(Tt, i, r, q);
-      if (!side) {
-#pragma unroll
-        for (int j = 0; j < WM; ++j) f[j] *= sh.sv[0][j];
-      }
-      store_copy<T, WM>(d0, i, Rc, f);
-      store_copy<T, WM>(d1, i, Rc, q);
-      if constexpr (sizeof(T) == 4) {
-        if (a.img_iter) write_images<T, WM>(a, 1, side, i, f, q);
-      }
-    }
+__device__ void trimmed_t_factors(const SmallArgs& a, Smem<T, WM>& sh) {
+  const int r = a.r, warp = threadIdx.x >> 5;
+  reduce_slots_d(a.part, 6, 2, r * r, &sh.Gd[4][0], sh);
+  if (warp == 0) factor_warp<double, WM>(sh.Gd[4], r, sh.Rt[0], sh.Tt[0]);
+  if (warp == 1) factor_warp<double, WM>(sh.Gd[5], r, sh.Rt[1], sh.Tt[1]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * WM * WM; e += ST) {
+    const int s2 = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
+    sh.tm[s2][q * WM + c] = (q < r && c < r) ? (T)sh.Tt[s2][q * r + c] : T(0);
   }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------------
+// One update of Algorithm 1 after the fused pass.  Phases (FP32 working precision):
+//   start: err_k, the stop test, T_u and T_v (above)
+//   A    : rows of Y1 = X1 T_v, U~ = A~ T_u, Y2 = X2 T_u, V~ = B~ T_v; double Gram partials
+//          of C = U~^T Y1, Y1^T Y1, U~^T U~, D2 = V~^T Y2, Y2^T Y2, V~^T V~
+//   -- grid barrier --
+//   serial (every block, same order, double): with W1 = Y1 - U~ C and W2 = Y2 - V~ C^T,
+//          W1^T W1 = Y1^T Y1 - 2 C^T C + C^T (U~^T U~) C and
+//          W2^T W2 = Y2^T Y2 - D2^T C^T - C D2 + C (V~^T V~) C^T, exact identities of the sums
+//          taken; R1, R2 by Cholesky (the QR of Section 2.1, with the Q factors implicit);
+//          M = [[C, R2^T], [R1, 0]], its SVD, zeta_{k+1} (Algorithm 1)
+//   B    : new factors by Eq. (9), U_{k+1} = U~ U_M[:r, :r] + W1 (T1 U_M[r:, :r]), Trim and
+//          the hand-over to the next pass.
+// In FP64 working precision the Gram identities would lose the small singular values of
+// W1 (its Gram is formed from sums of the size of ||Y1||^2), so W1, W2 are formed first and
+// their Gram matrices summed after a second grid barrier.
 template <typename T, int WM>
 __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   constexpr int NM = Smem<T, WM>::NM;
+  constexpr bool F64 = sizeof(T) == 8;
   DevState* st = a.st;
-  const int m = a.m, n = a.n, r = a.r, t = threadIdx.x;
+  const int m = a.m, n = a.n, r = a.r, t = threadIdx.x, warp = t >> 5;
   T* Ut = static_cast<T*>(a.Ut);
   T* Vt = static_cast<T*>(a.Vt);
   T* Y1 = static_cast<T*>(a.Y1);
   T* Y2 = static_cast<T*>(a.Y2);
+  const T* At = static_cast<const T*>(a.Utc);  // A~ and B~ as the pass read them (width Rit)
+  const T* Bt = static_cast<const T*>(a.Vtc);
   double res2;
   unsigned long long nnz, changes;
   cta_totals(a, res2, nnz, sh, &changes);
@@ -750,144 +1038,181 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   }
   // bf16 split storage of D: while the passes read only the hi part, err_k measures against
   // bf16(D) and cannot end the run; the next pass reads hi + lo once err_k is below the switch
-  // level (use_lo is written below, after grid barriers every CTA passes after this read)
+  // level (use_lo is written below, after a grid barrier every CTA passes after this read)
   const bool hi_only = st->split_switch > 0 && !st->use_lo;
   if ((err < st->tol && !hi_only) || k >= st->max_iter) {
     if (blockIdx.x == 0 && t == 0) st->done = 1;
     return;
   }
+  trimmed_t_factors<T, WM>(a, sh);
 
-  // A: own rows of Y1 = Z V~ and Y2 = Z^T U~; partial of C = U~^T Y1 (slot 0)
-  {
-    int lo, hi;
-    block_range(m, lo, hi);
-    T acc = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
-      T y[WM], u[WM];
-      zero_row<T, WM>(y);
-      zero_row<T, WM>(u);
-      if (i < hi) {
-        reduce_row<T, WM>(static_cast<const T*>(a.P1), a.n_p1, (size_t)m * a.R, i, a.R, r, y);
-        load_row<T, WM>(Ut, i, r, u);
-        store_row<T, WM>(Y1, i, r, y);
-      }
-      stage_row<T, WM>(sh.stage[0], t, u);
-      stage_row<T, WM>(sh.stage[1], t, y);
-      __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[1], r, min(ST, hi - c0), acc);
-      __syncthreads();
-    }
-    gram_store(acc, r * r, a.part, 0, sh);
-    block_range(n, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
-      T y[WM];
-      reduce_row<T, WM>(static_cast<const T*>(a.P2), a.n_p2, (size_t)n * a.R, i, a.R, r, y);
-      store_row<T, WM>(Y2, i, r, y);
-    }
-  }
-  if (!grid_barrier(st, sh)) return;
-
-  // B: W1 = Y1 - U~ C, W2 = Y2 - V~ C^T (in place) and their Gram matrices (slots 1, 2)
-  reduce_slots(a.part, 0, 1, r * r, sh.C, sh);
-  for (int e = t; e < WM * WM; e += ST) {
-    const int q = e / WM, c = e % WM;
-    sh.cm[e] = (q < r && c < r) ? sh.C[q * r + c] : T(0);
-  }
-  __syncthreads();
+  // A: own rows of Y1, U~ (side 0) and Y2, V~ (side 1), and their Gram partials
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
-    T* Y = side ? Y2 : Y1;
-    const T* B = side ? Vt : Ut;
+    const T* Pp = static_cast<const T*>(side ? a.P2 : a.P1);
+    const int nsl = side ? a.n_p2 : a.n_p1;
+    const T* F = side ? Bt : At;
+    T* Yo = side ? Y2 : Y1;
+    T* Bo = side ? Vt : Ut;
     int lo, hi;
     block_range(rows, lo, hi);
-    T acc = T(0);
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
-      T y[WM];
+      T y[WM], b[WM];
       zero_row<T, WM>(y);
+      zero_row<T, WM>(b);
       if (i < hi) {
-        T b[WM];
-        load_row<T, WM>(Y, i, r, y);
-        load_row<T, WM>(B, i, r, b);
-#pragma unroll
-        for (int c = 0; c < WM; ++c) {
-          T s = y[c];
-#pragma unroll
-          for (int q = 0; q < WM; ++q) s = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], s);
-          y[c] = s;
-        }
-        store_row<T, WM>(Y, i, r, y);
+        T x[WM], f[WM];
+        reduce_row<T, WM>(Pp, nsl, (size_t)rows * a.R, i, a.R, r, x);
+        load_row<T, WM>(F, i, a.Rit, f);
+        row_times<T, WM>(x, sh.tm[1 - side], y);  // X1 T_v, X2 T_u
+        row_times<T, WM>(f, sh.tm[side], b);      // A~ T_u, B~ T_v
+        store_row<T, WM>(Yo, i, r, y);
+        store_row<T, WM>(Bo, i, r, b);
       }
-      stage_row<T, WM>(sh.stage[0], t, y);
+      stage_row<T, WM>(sh.stage[0], t, b);
+      stage_row<T, WM>(sh.stage[1], t, y);
       __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      const int nr = min(ST, hi - c0);
+      g0 = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[1], r, nr, g0);  // U~^T Y1 / V~^T Y2
+      if (!F64) {
+        g1 = gram_acc_d<T, WM>(sh.stage[1], r, sh.stage[1], r, nr, g1);  // Y^T Y
+        g2 = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, nr, g2);  // basis Gram
+      }
       __syncthreads();
     }
-    gram_store(acc, r * r, a.part, 1 + side, sh);
+    if (!F64 || side == 0) gram_store_d(g0, r * r, a.part, 3 * side, sh);
+    if (!F64) {
+      gram_store_d(g1, r * r, a.part, 3 * side + 1, sh);
+      gram_store_d(g2, r * r, a.part, 3 * side + 2, sh);
+    }
   }
   if (!grid_barrier(st, sh)) return;
 
-  // C: R1, R2; M = [[C, R2^T], [R1, 0]]; SVD; new factors (Eq. (9)); Trim
-  reduce_slots(a.part, 1, 2, r * r, &sh.G[0][0], sh);
-  factor_pair<T, WM>(r, 0, 1, sh);
+  if (!F64) {
+    // Gd[0] = C, Gd[1] = Y1^T Y1, Gd[2] = U~^T U~, Gd[3] = D2, Gd[4] = Y2^T Y2, Gd[5] = V~^T V~
+    reduce_slots_d(a.part, 0, 6, r * r, &sh.Gd[0][0], sh);
+    double* G1 = sh.Md;   // scratch until M is formed
+    double* G2 = sh.UMd;
+    for (int e = t; e < r * r; e += ST) {
+      const int i = e / r, j = e % r;
+      const double* C = sh.Gd[0];
+      const double* GU = sh.Gd[2];
+      const double* D2 = sh.Gd[3];
+      const double* GV = sh.Gd[5];
+      double cc = 0.0, cuc = 0.0, cd = 0.0, dc = 0.0, cvc = 0.0;
+      for (int q = 0; q < r; ++q) {
+        cc = fma(C[q * r + i], C[q * r + j], cc);
+        cd = fma(C[i * r + q], D2[q * r + j], cd);   // (C D2)_ij
+        dc = fma(C[j * r + q], D2[q * r + i], dc);   // (C D2)_ji
+        double u = 0.0, v = 0.0;
+        for (int p = 0; p < r; ++p) {
+          u = fma(GU[q * r + p], C[p * r + j], u);   // (U~^T U~ C)_qj
+          v = fma(GV[q * r + p], C[j * r + p], v);   // (V~^T V~ C^T)_qj
+        }
+        cuc = fma(C[q * r + i], u, cuc);
+        cvc = fma(C[i * r + q], v, cvc);
+      }
+      G1[e] = sh.Gd[1][e] - 2.0 * cc + cuc;
+      G2[e] = sh.Gd[4][e] - cd - dc + cvc;
+    }
+    if (t < MW) {
+      sh.dbuf[t] = (t < r) ? sh.Gd[1][t * r + t] : 0.0;
+      sh.dbuf[MW + t] = (t < r) ? sh.Gd[4][t * r + t] : 0.0;
+    }
+    __syncthreads();
+    // a direction of W1 below 1e-6 of the norm of its column of Y1 is below the precision of
+    // the single-precision products it comes from: it is dropped (zero row of R1)
+    if (warp == 0) factor_warp<double, WM>(G1, r, sh.Rd[0], sh.Td[0], sh.dbuf, 1e-12);
+    if (warp == 1) factor_warp<double, WM>(G2, r, sh.Rd[1], sh.Td[1], sh.dbuf + MW, 1e-12);
+    __syncthreads();
+  } else {
+    // C, then W1 = Y1 - U~ C and W2 = Y2 - V~ C^T in place and their Gram partials
+    reduce_slots_d(a.part, 0, 1, r * r, &sh.Gd[0][0], sh);
+    for (int e = t; e < WM * WM; e += ST) {
+      const int q = e / WM, c = e % WM;
+      sh.cm[e] = (q < r && c < r) ? (T)sh.Gd[0][q * r + c] : T(0);
+    }
+    __syncthreads();
+    for (int side = 0; side < 2; ++side) {
+      const int rows = side ? n : m;
+      T* Y = side ? Y2 : Y1;
+      const T* B = side ? Vt : Ut;
+      int lo, hi;
+      block_range(rows, lo, hi);
+      double acc = 0.0;
+      for (int c0 = lo; c0 < hi; c0 += ST) {
+        const int i = c0 + t;
+        T y[WM];
+        zero_row<T, WM>(y);
+        if (i < hi) {
+          T b[WM];
+          load_row<T, WM>(Y, i, r, y);
+          load_row<T, WM>(B, i, r, b);
+#pragma unroll
+          for (int c = 0; c < WM; ++c) {
+            T sacc = y[c];
+#pragma unroll
+            for (int q = 0; q < WM; ++q) sacc = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], sacc);
+            y[c] = sacc;
+          }
+          store_row<T, WM>(Y, i, r, y);
+        }
+        stage_row<T, WM>(sh.stage[0], t, y);
+        __syncthreads();
+        acc = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+        __syncthreads();
+      }
+      gram_store_d(acc, r * r, a.part, 1 + side, sh);
+    }
+    if (!grid_barrier(st, sh)) return;
+    reduce_slots_d(a.part, 1, 2, r * r, &sh.Gd[1][0], sh);
+    if (warp == 0) factor_warp<double, WM>(sh.Gd[1], r, sh.Rd[0], sh.Td[0]);
+    if (warp == 1) factor_warp<double, WM>(sh.Gd[2], r, sh.Rd[1], sh.Td[1]);
+    __syncthreads();
+  }
+
+  // M = [[C, R2^T], [R1, 0]] and its SVD (double)
   const int N = 2 * r;
   for (int e = t; e < NM * NM; e += ST) {
     const int row = e / NM, col = e % NM;
-    T v = T(0);
+    double v = 0.0;
     if (row < r && col < r)
-      v = sh.C[row * r + col];
+      v = sh.Gd[0][row * r + col];
     else if (row < r && col >= r && col < N)
-      v = sh.Rf[1][(col - r) * r + row];  // R2^T
+      v = sh.Rd[1][(col - r) * r + row];  // R2^T
     else if (row >= r && row < N && col < r)
-      v = sh.Rf[0][(row - r) * r + col];  // R1
-    sh.M[e] = v;
+      v = sh.Rd[0][(row - r) * r + col];  // R1
+    sh.Md[e] = v;
   }
   __syncthreads();
-  small_svd<T, WM>(N, sh);
+  small_svd_d<T, WM>(N, sh);
   __syncthreads();
-  // update matrices: side 0 acts on [U~ W1], side 1 on [V~ W2]; rows q < r take the top
-  // block of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2)
+  // update matrices: side 0 acts on [U~ W1], side 1 on [V~ W2]; rows q < r take the top block
+  // of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2); C for W1 = Y1 - U~ C
   for (int e = t; e < 2 * 2 * WM * WM; e += ST) {
     const int side = e / (2 * WM * WM), rem = e % (2 * WM * WM), row = rem / WM, c = rem % WM;
-    const T* Y = side ? sh.VM : sh.UM;
-    T v = T(0);
+    const double* Y = side ? sh.VMd : sh.UMd;
+    double v = 0.0;
     if (c < r) {
       if (row < r) {
         v = Y[c * NM + row];
       } else if (row < 2 * r) {
         const int q = row - r;
-        for (int kk = q; kk < r; ++kk) v = fma(sh.Tf[side][q * r + kk], Y[c * NM + r + kk], v);
+        for (int kk = q; kk < r; ++kk) v = fma(sh.Td[side][q * r + kk], Y[c * NM + r + kk], v);
       }
     }
-    sh.mat[side][rem] = v;
+    sh.mat[side][rem] = (T)v;
   }
-  if (t < MW) sh.sv[0][t] = (t < r) ? (T)sh.sig[t] : T(0);
+  for (int e = t; e < WM * WM; e += ST) {
+    const int q = e / WM, c = e % WM;
+    sh.cm[e] = (q < r && c < r) ? (T)sh.Gd[0][q * r + c] : T(0);
+  }
+  if (t < MW) sh.sv[0][t] = (t < r) ? (T)sh.sigd[t] : T(0);
   __syncthreads();
-  const double s1 = (double)sh.sig[0], sr1 = (double)sh.sig[r];
-  for (int side = 0; side < 2; ++side) {
-    const int rows = side ? n : m;
-    const T* B = side ? Vt : Ut;
-    const T* W = side ? Y2 : Y1;
-    T* F = static_cast<T*>(side ? a.V : a.U);
-    const T* A = sh.mat[side];
-    int lo, hi;
-    block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
-      T b[WM], w[WM], f[WM];
-      load_row<T, WM>(B, i, r, b);
-      load_row<T, WM>(W, i, r, w);
-#pragma unroll
-      for (int c = 0; c < WM; ++c) {
-        T s = T(0);
-#pragma unroll
-        for (int q = 0; q < WM; ++q) s = fma(b[q], A[q * WM + c], fma(w[q], A[(r + q) * WM + c], s));
-        f[c] = s;
-      }
-      store_row<T, WM>(F, i, r, f);
-    }
-  }
-  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[t];
+  const double s1 = sh.sigd[0], sr1 = sh.sigd[r];
+  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sigd[t];
   if (blockIdx.x == 0 && t >= ST - 32) {  // a warp with no rows when m, n <= 224 * grid
     const int lane = t & 31;
     const int k1 = k + 1;
@@ -917,27 +1242,88 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     if (lane == 0) {
       st->zeta = zeta_new;
       a.stats[k].zeta_next_plain = plain;
-      for (int i = 0; i < N; ++i) st->sigma[i] = (double)sh.sig[i];
+      for (int i = 0; i < N; ++i) st->sigma[i] = sh.sigd[i];
       a.stats[k].sigma1 = s1;
       a.stats[k].sigma_r1 = sr1;
       if (hi_only && (err < st->split_switch || err < st->tol)) st->use_lo = 1;
       st->k = k1;
     }
   }
-  __syncthreads();
-  trim_and_gram<T, WM>(a, sh);
-  if (!grid_barrier(st, sh)) return;
-  // D: orthonormal bases of the trimmed factors and the pass copies
-  finish_bases<T, WM>(a, sh);
+
+  // B: new factors (Eq. (9)), Trim (Algorithm 2), hand-over; Gram partials of A~, B~
+  const bool do_trim = st->trim != 0;
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? n : m;
+    const T* B = side ? Vt : Ut;
+    const T* Y = side ? Y2 : Y1;
+    T* F = static_cast<T*>(side ? a.V : a.U);
+    const T* A = sh.mat[side];
+    const T cap = trim_cap<T>(a, side);
+    int lo, hi;
+    block_range(rows, lo, hi);
+    double acc = 0.0;
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T x[WM];
+      zero_row<T, WM>(x);
+      if (i < hi) {
+        T b[WM], w[WM], f[WM];
+        load_row<T, WM>(B, i, r, b);
+        load_row<T, WM>(Y, i, r, w);
+        if (!F64) {  // W1 = Y1 - U~ C, W2 = Y2 - V~ C^T (formed in place before in FP64)
+#pragma unroll
+          for (int c = 0; c < WM; ++c) {
+            T sacc = w[c];
+#pragma unroll
+            for (int q = 0; q < WM; ++q) sacc = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], sacc);
+            w[c] = sacc;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < WM; ++c) {
+          T sacc = T(0);
+#pragma unroll
+          for (int q = 0; q < WM; ++q) sacc = fma(b[q], A[q * WM + c], fma(w[q], A[(r + q) * WM + c], sacc));
+          f[c] = sacc;
+        }
+        store_row<T, WM>(F, i, r, f);
+        trim_row<T, WM>(f, cap, do_trim, x);
+        hand_over_row<T, WM>(a, side, i, f, x, sh.sv[0]);
+      }
+      stage_row<T, WM>(sh.stage[0], t, x);
+      __syncthreads();
+      acc = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      __syncthreads();
+    }
+    gram_store_d(acc, r * r, a.part, 6 + side, sh);
+  }
 }
 
 template <typename T, int WM>
 __device__ void mode_prepare(const SmallArgs& a, Smem<T, WM>& sh) {
   if (threadIdx.x < MW) sh.sv[0][threadIdx.x] = (threadIdx.x < a.r) ? static_cast<const T*>(a.sig)[threadIdx.x] : T(0);
   __syncthreads();
-  trim_and_gram<T, WM>(a, sh);
-  if (!grid_barrier(a.st, sh)) return;
-  finish_bases<T, WM>(a, sh);
+  trim_hand_over<T, WM>(a, sh);
+}
+
+// The orthonormal bases U~ = A~ T_u and V~ = B~ T_v of the pass that comes next, into out_ut
+// (m x Rit) and out_vt (n x Rit), zero-padded.
+template <typename T, int WM>
+__device__ void mode_bases(const SmallArgs& a, Smem<T, WM>& sh) {
+  trimmed_t_factors<T, WM>(a, sh);
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? a.n : a.m;
+    const T* F = static_cast<const T*>(side ? a.Vtc : a.Utc);
+    T* O = static_cast<T*>(side ? a.out_vt : a.out_ut);
+    int lo, hi;
+    block_range(rows, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += ST) {
+      T f[WM], b[WM];
+      load_row<T, WM>(F, i, a.Rit, f);
+      row_times<T, WM>(f, sh.tm[side], b);
+      store_copy<T, WM>(O, i, a.Rit, b);
+    }
+  }
 }
 
 __device__ float gauss(unsigned long long seed, unsigned long long i) {
@@ -1196,9 +1582,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
     }
   }
   if (conv && phase == 1) {
-    trim_and_gram<T, WM>(a, sh);
-    if (!grid_barrier(st, sh)) return;
-    finish_bases<T, WM>(a, sh);
+    trim_hand_over<T, WM>(a, sh);
     return;
   }
   orth_second_pass<T, WM>(a, w, 3, sh);
@@ -1218,6 +1602,7 @@ __global__ void __launch_bounds__(ST, 1) small_kernel(SmallArgs a) {
   if (MODE == SM_PREPARE) mode_prepare<T, WM>(a, sh);
   if (MODE == SM_RR) mode_rr<T, WM>(a, sh);
   if (MODE == SM_RAND) mode_rand<T, WM>(a, sh);
+  if (MODE == SM_BASES) mode_bases<T, WM>(a, sh);
 }
 
 template <typename T, int WM, int MODE>
@@ -1232,6 +1617,7 @@ void set_smem() {
   set_smem_mode<T, WM, SM_PREPARE>();
   set_smem_mode<T, WM, SM_RR>();
   set_smem_mode<T, WM, SM_RAND>();
+  set_smem_mode<T, WM, SM_BASES>();
 }
 
 template <typename T, int WM, int MODE>
@@ -1253,6 +1639,8 @@ cudaError_t launch_one(const SmallArgs& a, int grid, cudaStream_t s) {
       return launch_mode<T, WM, SM_RR>(a, grid, s);
     case SM_RAND:
       return launch_mode<T, WM, SM_RAND>(a, grid, s);
+    case SM_BASES:
+      return launch_mode<T, WM, SM_BASES>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }

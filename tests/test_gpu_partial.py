@@ -45,7 +45,9 @@ def test_partial_observation_matches_oracle(prec, tol, ltol, kind):
     ref = OP.accaltproj_partial(Dh, obs, r, p["beta"], p["gamma"], 0.0, p["mu"], beta_init=p["beta_init"], max_iter=k)
     L = (U * sig) @ V.T
     assert rel_fro(L, ref["L"]) < ltol
-    assert np.allclose([x["err"] for x in stats], ref["history"]["err"], rtol=1e-6 if prec == "fp64" else 1e-3)
+    # err_k carries the absolute error of L relative to ||D|| (1e-6 in FP32)
+    assert np.allclose([x["err"] for x in stats], ref["history"]["err"], rtol=1e-6 if prec == "fp64" else 1e-3,
+                       atol=1e-12 if prec == "fp64" else 2e-6)
     assert obs.reshape(-1)[idx].all()
     diff, ok = support_mismatch(idx, Dh, ref["L"], ref["zeta"], band_abs_rel_D=0.0 if prec == "fp64" else 1e-6)
     assert ok, diff[:10]
