@@ -80,7 +80,11 @@ struct rpca_ctx {
   // tensor-core pass
   bool tc_iter = false, tc_init = false;
   CUtensorMap dmap, dmap_lo;
-  int tcA = 0, tcB = 0, TR = 0, TC = 0;
+  int TR = 0, TC = 0;
+  TcPlan plan;                 // tile partition of the tensor-core pass
+  int4* d_rect = nullptr;      // its tables on the device
+  int2* d_ids = nullptr;
+  int* d_p1nsl = nullptr;
   float* Y2c = nullptr;  // Y2 chunk slots of the tensor-core pass
   int y2_ch = 0, y2_ct = 0;
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
@@ -121,7 +125,8 @@ void free_workspace(rpca_ctx* c) {
                    (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
                    &c->Down, &c->Dhl, (void**)&c->wop[0], (void**)&c->vop[0], (void**)&c->vtop[0],
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
-                   (void**)&c->utop[1], (void**)&c->Y2c, (void**)&c->masks, (void**)&c->chgP};
+                   (void**)&c->utop[1], (void**)&c->Y2c, (void**)&c->masks, (void**)&c->chgP,
+                   (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -196,7 +201,7 @@ bool use_tc(const rpca_ctx* c, int R) { return (R == c->Rr) ? c->tc_iter : (R ==
 bool learned(const rpca_ctx* c) { return c->p.zeta_mode == RPCA_ZETA_LEARNED; }
 
 Grid pass_grid(const rpca_ctx* c, int R) {
-  if (use_tc(c, R)) return Grid{c->tcB, c->tcA, c->tcA * c->tcB};
+  if (use_tc(c, R)) return Grid{c->plan.Bmax, c->plan.A, c->plan.ncta};
   const PassGeom g = pass_geometry(c->prec, R);
   const int gx = (int)((c->n + g.BW - 1) / g.BW), gy = (int)((c->m + g.BH - 1) / g.BH);
   return Grid{gx, gy, gx * gy};
@@ -240,8 +245,9 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.m = (int)c->m;
     t.n = (int)c->n;
     t.R = R;
-    t.A = c->tcA;
-    t.B = c->tcB;
+    t.ncta = c->plan.ncta;
+    t.rect = c->d_rect;
+    t.ids = c->d_ids;
     t.TR = c->TR;
     t.TC = c->TC;
     const int set = init ? 0 : 1;
@@ -278,28 +284,81 @@ int run_small(rpca_ctx* c, const SmallArgs& a) {
 }
 
 
-// A x B CTA grid of the tensor-core pass: every CTA gets at least one 128-row and one
-// 64-column tile and at most 20 column tiles (tensor-memory budget); minimises the
-// largest block of tiles.
-bool tc_partition(int TR, int TC, int nsm, int max_ct, int* A, int* B) {
-  long best = -1;
-  int bA = 0, bB = 0;
-  for (int a = 1; a <= TR && a <= nsm; ++a) {
-    int b = nsm / a;
-    if (b > TC) b = TC;
-    if (b < 1) continue;
-    if ((TC + b - 1) / b > max_ct) continue;
-    const long mx = (long)((TR + a - 1) / a) * ((TC + b - 1) / b);
-    if (best < 0 || mx < best || (mx == best && a * b > bA * bB)) {
-      best = mx;
-      bA = a;
-      bB = b;
+// Tile partition of the tensor-core pass.  The TR x TC tiles (128 x 64) are cut into row
+// groups of different heights; group g of h_g row tiles splits all TC column tiles among its
+// own B_g CTAs (ranges of nearly equal width, at most max_ct column tiles each: the
+// tensor-memory budget).  The plan takes the smallest largest-CTA tile count T for which the
+// groups fit on nsm CTAs (one per SM), and among those the one with the fewest partial
+// products (every CTA writes an m-slice of Y1 for its rows and every group an n-slice of Y2).
+// Dynamic programming over (row tiles, CTAs).
+bool tc_plan(int TR, int TC, int nsm, int max_ct, TcPlan* out) {
+  if (TR < 1 || TC < 1 || nsm < 1) return false;
+  const long long tiles = (long long)TR * TC;
+  for (long long T = (tiles + nsm - 1) / nsm; T <= tiles; ++T) {
+    std::vector<std::pair<int, int>> opts;  // (group height, CTAs)
+    for (int h = 1; h <= TR; ++h) {
+      const long long w = std::min<long long>(std::min<long long>(T / h, max_ct), TC);
+      if (w < 1) break;
+      opts.push_back({h, (int)((TC + w - 1) / w)});
     }
+    const double INF = 1e300;
+    std::vector<double> best((size_t)(TR + 1) * (nsm + 1), INF);
+    std::vector<int> pick((size_t)(TR + 1) * (nsm + 1), -1);
+    auto at = [&](int rows, int c) { return (size_t)rows * (nsm + 1) + c; };
+    best[at(0, 0)] = 0.0;
+    for (int rows = 1; rows <= TR; ++rows)
+      for (int o = 0; o < (int)opts.size(); ++o) {
+        const int h = opts[o].first, B = opts[o].second;
+        if (h > rows) break;
+        for (int c = B; c <= nsm; ++c) {
+          const double prev = best[at(rows - h, c - B)];
+          if (prev >= INF) continue;
+          const double v = prev + (double)h * 128.0 * B + (double)TC * 64.0;
+          if (v < best[at(rows, c)]) {
+            best[at(rows, c)] = v;
+            pick[at(rows, c)] = o;
+          }
+        }
+      }
+    int cbest = -1;
+    for (int c = 1; c <= nsm; ++c)
+      if (best[at(TR, c)] < INF && (cbest < 0 || best[at(TR, c)] < best[at(TR, cbest)])) cbest = c;
+    if (cbest < 0) continue;
+    // unwind: groups from the bottom row tile up
+    std::vector<std::pair<int, int>> groups;
+    for (int rows = TR, c = cbest; rows > 0;) {
+      const auto g = opts[pick[at(rows, c)]];
+      groups.push_back(g);
+      rows -= g.first;
+      c -= g.second;
+    }
+    std::reverse(groups.begin(), groups.end());
+    out->rect.clear();
+    out->ids.clear();
+    out->p1_nsl.assign(TR, 0);
+    out->A = (int)groups.size();
+    out->Bmax = 0;
+    out->ct_max = 0;
+    out->ch_max = 0;
+    int rt = 0;
+    for (int gi = 0; gi < (int)groups.size(); ++gi) {
+      const int h = groups[gi].first, B = groups[gi].second;
+      for (int b = 0; b < B; ++b) {
+        const int c0 = (int)((long long)b * TC / B), c1 = (int)((long long)(b + 1) * TC / B);
+        out->rect.push_back(make_int4(rt, rt + h, c0, c1));
+        out->ids.push_back(make_int2(gi, b));
+        out->ct_max = std::max(out->ct_max, c1 - c0);
+      }
+      for (int q = rt; q < rt + h; ++q) out->p1_nsl[q] = B;
+      out->Bmax = std::max(out->Bmax, B);
+      out->ch_max = std::max(out->ch_max, (h + kTcY2Chunk - 1) / kTcY2Chunk);
+      rt += h;
+    }
+    out->ncta = (int)out->rect.size();
+    out->T = (int)T;
+    return out->ct_max <= max_ct;
   }
-  if (best < 0) return false;
-  *A = bA;
-  *B = bB;
-  return true;
+  return false;
 }
 
 // Tensor map of an m x n row-major matrix with rows of `ld` elements, in boxes of 128 rows x
@@ -344,6 +403,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.prec = c->prec;
   a.n_p1 = g.n_p1;
   a.n_p2 = g.n_p2;
+  a.p1_nsl = use_tc(c, R) ? c->d_p1nsl : nullptr;
   a.n_cta = g.n_cta;
   a.P1 = c->P1;
   a.P2 = c->P2;
@@ -518,7 +578,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     int max_ct = 1 << 30;
     if (it) max_ct = std::min(max_ct, tc_max_col_tiles(c->Rr));
     if (in) max_ct = std::min(max_ct, tc_max_col_tiles(c->Rb));
-    if (nsm > 0 && (it || in) && tc_partition(c->TR, c->TC, nsm, max_ct, &c->tcA, &c->tcB)) {
+    if (nsm > 0 && (it || in) && ((reuse && c->plan.ncta > 0) || tc_plan(c->TR, c->TC, nsm, max_ct, &c->plan))) {
       c->tc_iter = it;
       c->tc_init = in;
     }
@@ -539,7 +599,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   for (int R : {c->Rr, c->Rb}) {
     const PassGeom pg = pass_geometry(c->prec, R);
     const Grid gs{(int)((n + pg.BW - 1) / pg.BW), (int)((m + pg.BH - 1) / pg.BH), 0};
-    const Grid gt{c->tcB, c->tcA, c->tcA * c->tcB};
+    const Grid gt{c->plan.Bmax, c->plan.A, c->plan.ncta};
     for (const Grid& g : {gs, gt}) {
       p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
       p2 = p2 > (size_t)g.n_p2 * n * R ? p2 : (size_t)g.n_p2 * n * R;
@@ -569,10 +629,16 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   CK(cudaMalloc(&c->P2, p2 * c->tsize));
   if (c->TR > 0) {
     if (c->tc_iter || c->tc_init) {
-      const int rpc = (c->TR + c->tcA - 1) / c->tcA;
-      c->y2_ch = (rpc + kTcY2Chunk - 1) / kTcY2Chunk;
-      c->y2_ct = (c->TC + c->tcB - 1) / c->tcB;
-      CK(cudaMalloc((void**)&c->Y2c, (size_t)c->tcA * c->tcB * c->y2_ch * c->y2_ct * 128 * 16 * sizeof(float)));
+      c->y2_ch = c->plan.ch_max;
+      c->y2_ct = c->plan.ct_max;
+      CK(cudaMalloc((void**)&c->Y2c, (size_t)c->plan.ncta * c->y2_ch * c->y2_ct * 128 * 16 * sizeof(float)));
+      const int nc = c->plan.ncta;
+      CK(cudaMalloc((void**)&c->d_rect, sizeof(int4) * nc));
+      CK(cudaMalloc((void**)&c->d_ids, sizeof(int2) * nc));
+      CK(cudaMalloc((void**)&c->d_p1nsl, sizeof(int) * c->TR));
+      CK(cudaMemcpy(c->d_rect, c->plan.rect.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->d_p1nsl, c->plan.p1_nsl.data(), sizeof(int) * c->TR, cudaMemcpyHostToDevice));
     }
     // zero-filled: rows past m, n are never written and must read as zero
     for (int set = 0; set < 2; ++set) {

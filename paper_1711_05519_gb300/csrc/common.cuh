@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace rpca {
 
 // Ranks with a compiled fused pass.  A rank r is run with the smallest entry >= r and
@@ -102,7 +104,9 @@ cudaError_t launch_fused_pass(int prec, int R, const PassArgs& a, cudaStream_t s
 // Tensor-core fused pass (FP32 or bf16-stored D, compiled rank R <= 16); see pass_tc.cu.
 struct TcPassArgs {
   int m, n, R;
-  int A, B;      // CTA grid: A row groups x B column groups
+  int ncta;      // CTAs of the tile partition (TcPlan, below)
+  const int4* rect;  // [ncta] tile rectangle of each CTA (device)
+  const int2* ids;   // [ncta] row group and index within the group (device)
   int TR, TC;    // 128-row and 64-column tile counts
   // operand images (tc_images.cuh) in the layout of tc_image_rank(R): per row tile W and
   // U~, per column tile V and V~
@@ -112,11 +116,11 @@ struct TcPassArgs {
   const uint8_t* utop;
   const DevState* st;
   int* status;
-  float* P1;     // [B][m][R]
-  float* P2;     // [A][n][R]
-  double* resP;  // [A*B]
+  float* P1;     // [Bmax][m][R]: slice = index of the CTA within its row group
+  float* P2;     // [A][n][R]: slice = row group
+  double* resP;  // [ncta]
   unsigned long long* nnzP;
-  // Y2 chunk slots: [A*B][ch_max][ct_max][128][RK] FP32, ch_max >= ceil(row tiles per CTA /
+  // Y2 chunk slots: [ncta][ch_max][ct_max][128][RK] FP32, ch_max >= ceil(row tiles per CTA /
   // kTcY2Chunk), ct_max >= column tiles per CTA
   float* Y2c;
   int ch_max, ct_max;
@@ -129,6 +133,16 @@ struct TcPassArgs {
 };
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
+// Tile partition of the tensor-core pass (api.cu, tc_plan): per CTA its rectangle of tiles
+// {first row tile, end row tile, first column tile, end column tile} and its ids {row group
+// (the n-slice of Y2 it writes), index in the group (the m-slice of Y1 it writes)}; per row
+// tile the number of Y1 slices its rows have.
+struct TcPlan {
+  int ncta = 0, A = 0, Bmax = 0, ct_max = 0, ch_max = 0, T = 0;
+  std::vector<int4> rect;
+  std::vector<int2> ids;
+  std::vector<int> p1_nsl;
+};
 bool tc_pass_supported(int R);
 // image layout (8 or 16) of the tensor-core pass for compiled rank R, and the most column
 // tiles one CTA of that pass may own (its Y2 accumulators stay in tensor memory)
@@ -169,6 +183,7 @@ struct SmallArgs {
   int b;        // width of the subspace-iteration bases in init (RR / RAND modes)
   int prec;
   int n_p1, n_p2, n_cta;  // partial slices and CTA count of the pass that ran
+  const int* p1_nsl;      // tensor-core pass: Y1 slices of each 128-row tile (null: n_p1 everywhere)
   const void* P1;
   const void* P2;
   const double* resP;

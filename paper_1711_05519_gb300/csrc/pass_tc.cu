@@ -115,7 +115,9 @@ constexpr uint32_t kErrTimeout = 6;
 
 struct TcArgs {
   int m, n, R;
-  int A, B, TR, TC;
+  int ncta, TR, TC;
+  const int4* rect;
+  const int2* ids;
   const uint8_t* wop;
   const uint8_t* vop;
   const uint8_t* vtop;
@@ -203,9 +205,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x;
-  const int ai = cta / a.B, bi = cta % a.B;
-  const int rt0 = (int)((long long)ai * a.TR / a.A), rt1 = (int)((long long)(ai + 1) * a.TR / a.A);
-  const int ct0 = (int)((long long)bi * a.TC / a.B), ct1 = (int)((long long)(bi + 1) * a.TC / a.B);
+  // this CTA's rectangle of tiles and its slices of the partial products (host plan)
+  const int4 rc = a.rect[cta];
+  const int2 id = a.ids[cta];
+  const int ai = id.x, bi = id.y;
+  const int rt0 = rc.x, rt1 = rc.y, ct0 = rc.z, ct1 = rc.w;
   const int nrt = rt1 - rt0, nct = ct1 - ct0;
   const int ntiles = nrt * nct;
   // the host's partition keeps a CTA's column tiles within the tensor-memory and barrier
@@ -676,11 +680,11 @@ cudaError_t set_tc_smem_modes() {
 template <int DM, int RK>
 cudaError_t launch_tc(const CUtensorMap& dmap, const CUtensorMap& lo, const TcArgs& a, int partial, cudaStream_t s) {
   if (a.masks)
-    fused_pass_tc<DM, RK, MODE_MASK><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+    fused_pass_tc<DM, RK, MODE_MASK><<<a.ncta, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
   else if (partial)
-    fused_pass_tc<DM, RK, MODE_PARTIAL><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+    fused_pass_tc<DM, RK, MODE_PARTIAL><<<a.ncta, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
   else
-    fused_pass_tc<DM, RK, MODE_PLAIN><<<a.A * a.B, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
+    fused_pass_tc<DM, RK, MODE_PLAIN><<<a.ncta, THREADS, Cfg<RK>::SMEM_BYTES, s>>>(dmap, lo, a);
   return cudaGetLastError();
 }
 
@@ -706,8 +710,9 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.m = p.m;
   a.n = p.n;
   a.R = p.R;
-  a.A = p.A;
-  a.B = p.B;
+  a.ncta = p.ncta;
+  a.rect = p.rect;
+  a.ids = p.ids;
   a.TR = p.TR;
   a.TC = p.TC;
   a.wop = p.wop;

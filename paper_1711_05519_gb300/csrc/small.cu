@@ -698,7 +698,12 @@ __device__ void jacobi_refine_d(int N, double (&x)[NM], double (&v)[NM], int max
       bool doit = (q != lane) && sg != 0.0 && sg * sg > 1e-28 * sa * sb;
       double c_rot = 1.0, s_rot = 0.0;
       if (doit) {
-        const float zf = (float)(sb - sa) / (2.0f * (float)sg);
+        // (sb - sa) / (2 sg) in single precision, both terms first scaled by the same power of
+        // two so that neither underflows (columns of tiny norm have tiny sums)
+        const double num = sb - sa, den = 2.0 * sg;
+        int e;
+        frexp(fmax(fabs(num), fabs(den)), &e);
+        const float zf = (float)ldexp(num, -e) / (float)ldexp(den, -e);
         const float az = fabsf(zf);
         float tf = (az > 1e18f) ? 0.5f / az : 1.0f / (az + sqrtf(fmaf(zf, zf, 1.0f)));
         tf = (zf < 0.0f) ? -tf : tf;
@@ -1050,7 +1055,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* Pp = static_cast<const T*>(side ? a.P2 : a.P1);
-    const int nsl = side ? a.n_p2 : a.n_p1;
+    const int nsl_all = side ? a.n_p2 : a.n_p1;
     const T* F = side ? Bt : At;
     T* Yo = side ? Y2 : Y1;
     T* Bo = side ? Vt : Ut;
@@ -1064,6 +1069,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       zero_row<T, WM>(b);
       if (i < hi) {
         T x[WM], f[WM];
+        const int nsl = (!side && a.p1_nsl) ? a.p1_nsl[i >> 7] : nsl_all;
         reduce_row<T, WM>(Pp, nsl, (size_t)rows * a.R, i, a.R, r, x);
         load_row<T, WM>(F, i, a.Rit, f);
         row_times<T, WM>(x, sh.tm[1 - side], y);  // X1 T_v, X2 T_u
@@ -1462,7 +1468,8 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
       zero_row<T, WM>(y);
       zero_row<T, WM>(u);
       if (i < hi) {
-        reduce_row<T, WM>(static_cast<const T*>(side ? a.P2 : a.P1), side ? a.n_p2 : a.n_p1, (size_t)rows * a.R, i,
+        reduce_row<T, WM>(static_cast<const T*>(side ? a.P2 : a.P1),
+                          side ? a.n_p2 : (a.p1_nsl ? a.p1_nsl[i >> 7] : a.n_p1), (size_t)rows * a.R, i,
                           a.R, w, y);
         store_row<T, WM>(side ? Y2 : Y1, i, w, y);
         if (!side) load_row<T, WM>(Ut, i, w, u);

@@ -267,3 +267,26 @@ def test_bounded_waits_report_timeout_and_leave_the_context_usable():
     inst = synth.planted_instance(200, 180, 3, 0.1, 1.0, 2)
     g = _gpu_run(inst, "fp32", 1e-5)
     assert g["code"] == P.OK
+
+
+@pytest.mark.parametrize("prec,ltol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("m,n,r,seed", [(300, 260, 4, 51), (420, 400, 6, 52)])
+def test_rank_deficient_projection_keeps_the_solve_valid(prec, ltol, m, n, r, seed):
+    """alpha = 0: D = L* is exactly of rank r, the initialisation finds its column space, and
+    (I - U~U~^T) Z V~ vanishes up to rounding, so the QR of Section 2.1 meets a zero R1 (a
+    direction lost to rounding; the library drops it as a zero row of R1).  The iteration
+    (tol 0, six steps) must stay at L* and agree with the oracle, whose QR completes the
+    basis in its own way (only L is compared)."""
+    inst = synth.planted_instance(m, n, r, 0.0, 1.0, seed)
+    p = inst.params()
+    D = torch.from_numpy(inst.D).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
+    with _solver(p, prec, 0.0, max_iter=6) as s:
+        s.init(D, r)
+        code, stats = s.run()
+        U, sig, V = (t.cpu().numpy() for t in s.lowrank())
+    assert code == P.NOT_CONVERGED and stats[-1]["k"] == 6
+    assert all(np.isfinite([x["err"] for x in stats])) and np.isfinite(U).all() and np.isfinite(V).all()
+    L = (U * sig) @ V.T
+    assert rel_fro(L, inst.L) < ltol
+    ref = _oracle_same_k(D.double().cpu().numpy(), inst, 6)
+    assert rel_fro(L, ref["L"]) < ltol
