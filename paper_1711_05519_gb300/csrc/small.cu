@@ -75,20 +75,6 @@ struct Smem {
   T sv[2][MW];             // sigma_c, 1/sigma_c
   int pairs[32 * 32];      // Jacobi round-robin partner of each lane in each round
   int ok;
-  // double-precision small steps of the iteration (every mode): Gram sums, the trimmed
-  // factors' T factors, the Cholesky factors of the projected products, the core M and its
-  // SVD
-  double dbuf[ST];
-  double Gd[6][GSLOT];     // reduced Gram matrices
-  double Cd[GSLOT];        // U~^T Y1
-  double Tt[2][GSLOT];     // T factors of the trimmed factors (U~ = A~ Tt[0], V~ = B~ Tt[1])
-  double Rt[2][GSLOT];     // their R factors (unused beyond the factorisation)
-  double Rd[2][GSLOT];     // R1, R2
-  double Td[2][GSLOT];     // T1, T2
-  double Md[NM * NM];
-  double UMd[NM * NM];
-  double VMd[NM * NM];
-  double sigd[NM];
 };
 
 // 1 / sqrt(x) for x > 0 in double precision: the single-precision estimate refined by two
@@ -269,92 +255,18 @@ __device__ __noinline__ void reduce_slots(const void* part, int slot0, int ns, i
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Gram sums in double precision (the iteration's small steps): per-thread shares over the
-// staged rows (row stride WM) of X^T Y, the block's partial into a double slot, and the sum
-// over blocks of double slots.  Summation orders depend only on the grid size.
-template <typename T, int WM>
-__device__ __forceinline__ double gram_acc_d(const T* X, int wx, const T* Y, int wy, int nrows, double acc) {
-  const int P = wx * wy, t = threadIdx.x, nl = ST / P, l = t / P;
-  if (l < nl) {
-    const int p = t % P, a = p / wy, b = p % wy;
-    for (int i = l; i < nrows; i += nl) acc = fma((double)X[i * WM + a], (double)Y[i * WM + b], acc);
-  }
-  return acc;
-}
-
-template <typename S>
-__device__ __noinline__ void tree_combine_d(int cnt, int nparts, S& sh) {
-  const int t = threadIdx.x, q = t / cnt, j = t % cnt;
-  int h = 1;
-  while (h < nparts) h <<= 1;
-  for (h >>= 1; h > 0; h >>= 1) {
-    if (q < h && q + h < nparts) sh.dbuf[q * cnt + j] += sh.dbuf[(q + h) * cnt + j];
-    __syncthreads();
-  }
-}
-
-template <typename S>
-__device__ __noinline__ void gram_store_d(double acc, int P, void* part, int slot, S& sh) {
-  const int t = threadIdx.x;
-  sh.dbuf[t] = acc;
-  __syncthreads();
-  tree_combine_d(P, ST / P, sh);
-  if (t < P) slot_ptr<double>(part, slot, blockIdx.x)[t] = sh.dbuf[t];
-  __syncthreads();
-}
-
-template <typename S>
-__device__ __noinline__ void reduce_slots_d(const void* part, int slot0, int ns, int P, double* G, S& sh) {
-  const int t = threadIdx.x, nb = gridDim.x, total = ns * P;
-  const double* pb = static_cast<const double*>(part);
-  for (int j0 = 0; j0 < total; j0 += ST) {
-    const int cnt = min(ST, total - j0);
-    const int nch = min(32, ST / cnt);
-    const int c = t / cnt;
-    double s = 0.0;
-    if (c < nch) {
-      const int j = j0 + t % cnt;
-      const double* base = pb + (size_t)(slot0 + j / P) * nb * GSLOT + (j % P);
-      for (int b0 = c; b0 < nb; b0 += 16 * nch) {
-        double v[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int b = b0 + u * nch;
-          v[u] = (b < nb) ? base[(size_t)b * GSLOT] : 0.0;
-        }
-        s += tree_sum<double, 16>(v);
-      }
-    }
-    sh.dbuf[t] = s;
-    __syncthreads();
-    tree_combine_d(cnt, nch, sh);
-    if (t < cnt) {
-      const int j = j0 + t;
-      G[(j / P) * GSLOT + (j % P)] = sh.dbuf[t];
-    }
-    __syncthreads();
-  }
-}
-
 // R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix (w <= WM),
 // by one warp in the working precision, in registers: lane l holds column l.  G is scaled to
 // unit diagonal first, G^ = D^-1/2 G D^-1/2; a pivot of G^ at or below 1e-6 (float) or 1e-14
 // (double), a direction lost to rounding, gives a zero row of R and a zero column of T.  Then
 // R = R^ D^1/2 and T = D^-1/2 R^-1, column l of R^-1 by back substitution in lane l.
-//
-// With `ref` given, a column whose squared norm G_ll is at or below eps_ref ref_l is treated as
-// zero from the start (ref: the squared norms of the columns it was projected from, so that a
-// direction below the precision of the data is dropped even when G itself is only rounding).
 // In double precision the square roots and divisions are the Newton-refined rsqrt_d.
 template <typename T, int WM>
-__device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm, const T* ref = nullptr,
-                                         T eps_ref = T(0)) {
+__device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm) {
   const int l = threadIdx.x & 31;
   const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
   const T gll = (l < w) ? G[l * w + l] : T(0);
-  const bool dead = ref != nullptr && l < w && !(gll > eps_ref * ref[l]);
-  const T il = (l < w && gll > T(0) && !dead) ? rsqrt_d(gll) : T(0);
+  const T il = (l < w && gll > T(0)) ? rsqrt_d(gll) : T(0);
   const T dl = gll * il;
   T a[WM];  // column l of the working matrix
 #pragma unroll
@@ -728,7 +640,7 @@ __device__ void jacobi_refine_d(int N, double (&x)[NM], double (&v)[NM], int max
 
 // Double-precision part of small_svd_d on registers sized NJ >= N: V from the single-precision
 // sweeps (vf) re-orthonormalised in double (modified Gram-Schmidt), then double-precision
-// sweeps on M V; results sorted by singular value into sh.sigd, sh.UMd, sh.VMd.
+// sweeps on M V; results sorted by singular value into sh.sig, sh.UM, sh.VM.
 template <int NJ, typename T, int WM>
 __device__ __forceinline__ void svd_refine_sized(int N, const float* vf, Smem<T, WM>& sh) {
   constexpr int NM = Smem<T, WM>::NM;
@@ -760,7 +672,7 @@ __device__ __forceinline__ void svd_refine_sized(int N, const float* vf, Smem<T,
   for (int i = 0; i < NJ; ++i) {
     double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < NJ; ++k) acc = fma(sh.Md[i * NM + k], vd[k], acc);
+    for (int k = 0; k < NJ; ++k) acc = fma(sh.M[i * NM + k], vd[k], acc);
     y[i] = (lane < N && i < N) ? acc : 0.0;
   }
   jacobi_refine_d<NJ>(N, y, vd, 4, sh.pairs);
@@ -777,25 +689,27 @@ __device__ __forceinline__ void svd_refine_sized(int N, const float* vf, Smem<T,
     rank += (si > sg || (si == sg && i < lane)) ? 1 : 0;
   }
   if (lane < N) {
-    sh.sigd[rank] = sg;
+    sh.sig[rank] = sg;
     for (int i = 0; i < NM; ++i) {
-      sh.UMd[rank * NM + i] = 0.0;
-      sh.VMd[rank * NM + i] = 0.0;
+      sh.UM[rank * NM + i] = 0.0;
+      sh.VM[rank * NM + i] = 0.0;
     }
 #pragma unroll
     for (int i = 0; i < NJ; ++i) {
-      sh.UMd[rank * NM + i] = y[i];
-      sh.VMd[rank * NM + i] = vd[i];
+      sh.UM[rank * NM + i] = y[i];
+      sh.VM[rank * NM + i] = vd[i];
     }
   }
   __syncwarp();
 }
 
-// SVD of the N x N matrix sh.Md (N <= NM, double) by warp 0: single-precision one-sided Jacobi
-// on Md scaled to max |M_ij| = 1, then the double-precision refinement above.  On return
-// sh.sigd holds the singular values in descending order and sh.UMd / sh.VMd the matching left /
-// right singular vectors (column c at [c * NM + i]; a zero singular value gives a zero left
-// vector).
+// SVD of the N x N matrix sh.M (N <= NM) by warp 0, double working precision: single-precision
+// one-sided Jacobi on M scaled to max |M_ij| = 1, then the double-precision refinement above.
+// On return sh.sig holds the singular values in descending order and sh.UM / sh.VM the
+// matching left / right singular vectors (column c at [c * NM + i]; a zero singular value
+// gives a zero left vector).  Measured on this part (10^4 x 10^4, r = 5): ~165 us, against
+// ~20 us for the single-precision sweeps alone (small_svd), which the FP32 working precision
+// keeps.
 template <typename T, int WM>
 __device__ void small_svd_d(int N, Smem<T, WM>& sh) {
   constexpr int NM = Smem<T, WM>::NM;
@@ -803,25 +717,25 @@ __device__ void small_svd_d(int N, Smem<T, WM>& sh) {
   const int lane = threadIdx.x;
   jacobi_pairs(N, sh.pairs);
   double mx = 0.0;
-  for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.Md[(e / N) * NM + (e % N)]));
+  for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.M[(e / N) * NM + (e % N)]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
   const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
   float xf[NM], vf[NM];
   if (N <= 8) {
-    jacobi_f32_sized<8, NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<8, NM>(N, sh.M, sc, sh.pairs, xf, vf);
     svd_refine_sized<8>(N, vf, sh);
   } else if (N <= 12) {
-    jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.M, sc, sh.pairs, xf, vf);
     svd_refine_sized<(NM < 12 ? NM : 12)>(N, vf, sh);
   } else if (N <= 16 || NM <= 16) {
-    jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.M, sc, sh.pairs, xf, vf);
     svd_refine_sized<(NM < 16 ? NM : 16)>(N, vf, sh);
   } else if (N <= 20) {
-    jacobi_f32_sized<20, NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<20, NM>(N, sh.M, sc, sh.pairs, xf, vf);
     svd_refine_sized<20>(N, vf, sh);
   } else {
-    jacobi_f32_sized<NM, NM>(N, sh.Md, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<NM, NM>(N, sh.M, sc, sh.pairs, xf, vf);
     svd_refine_sized<NM>(N, vf, sh);
   }
 }
@@ -902,8 +816,8 @@ __device__ __noinline__ void write_images(const SmallArgs& a, int set, int side,
 // products are X1 = Z B~ and X2 = Z^T A~.  The update that follows takes U~ = A~ T_u and
 // V~ = B~ T_v (one CholeskyQR each, T = R^-1 from the Gram matrices of A~, B~), and
 // Y1 = Z V~ = X1 T_v, Y2 = Z^T U~ = X2 T_u.  The Gram partials of A~, B~ are written by the
-// kernel that trims (double slots 6, 7) and summed by the next kernel, so no grid barrier
-// separates the trim from the orthonormalisation.
+// kernel that trims (slots 6, 7) and summed by the next kernel, so no grid barrier separates
+// the trim from the orthonormalisation.
 
 // Pass copies of row i for the next pass: W = f sigma (side 0) or V = f (side 1) and the
 // trimmed row t (A~ or B~), zero-padded to width Rit, and (tensor-core pass) their images.
@@ -939,7 +853,7 @@ __device__ __forceinline__ T trim_cap(const SmallArgs& a, int side) {
 }
 
 // Trim and hand-over of the factors held (U, V; sigma in sh.sv[0]) over the block's rows,
-// with the Gram partials of A~, B~ into double slots 6, 7.
+// with the Gram partials of A~, B~ into slots 6, 7.
 template <typename T, int WM>
 __device__ void trim_hand_over(const SmallArgs& a, Smem<T, WM>& sh) {
   const int r = a.r, t = threadIdx.x;
@@ -963,52 +877,42 @@ __device__ void trim_hand_over(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       stage_row<T, WM>(sh.stage[0], t, x);
       __syncthreads();
-      acc = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
-    gram_store_d(acc, r * r, a.part, 6 + side, sh);
+    gram_store(acc, r * r, a.part, 6 + side, sh);
   }
 }
 
-// T_u, T_v of the trimmed factors the last pass read, from the Gram partials in double slots
-// 6, 7 (every block sums them in the same order; one warp factors each), into sh.Tt and, in
-// the working precision and zero-padded, sh.tm.
+// T_u, T_v of the trimmed factors the last pass read, from the Gram partials in slots 6, 7
+// (every block sums them in the same order; one warp factors each), into sh.tm (zero-padded).
 template <typename T, int WM>
 __device__ void trimmed_t_factors(const SmallArgs& a, Smem<T, WM>& sh) {
-  const int r = a.r, warp = threadIdx.x >> 5;
-  reduce_slots_d(a.part, 6, 2, r * r, &sh.Gd[4][0], sh);
-  if (warp == 0) factor_warp<double, WM>(sh.Gd[4], r, sh.Rt[0], sh.Tt[0]);
-  if (warp == 1) factor_warp<double, WM>(sh.Gd[5], r, sh.Rt[1], sh.Tt[1]);
-  __syncthreads();
-  for (int e = threadIdx.x; e < 2 * WM * WM; e += ST) {
-    const int s2 = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
-    sh.tm[s2][q * WM + c] = (q < r && c < r) ? (T)sh.Tt[s2][q * r + c] : T(0);
-  }
-  __syncthreads();
+  reduce_slots(a.part, 6, 2, a.r * a.r, &sh.G[0][0], sh);
+  factor_pair<T, WM>(a.r, 0, 1, sh);
 }
 
 // ---------------------------------------------------------------------------------------
-// One update of Algorithm 1 after the fused pass.  Phases (FP32 working precision):
+// One update of Algorithm 1 after the fused pass, in the working precision:
 //   start: err_k, the stop test, T_u and T_v (above)
-//   A    : rows of Y1 = X1 T_v, U~ = A~ T_u, Y2 = X2 T_u, V~ = B~ T_v; double Gram partials
-//          of C = U~^T Y1, Y1^T Y1, U~^T U~, D2 = V~^T Y2, Y2^T Y2, V~^T V~
+//   A    : rows of Y1 = X1 T_v, U~ = A~ T_u, Y2 = X2 T_u, V~ = B~ T_v; partials of C = U~^T Y1
 //   -- grid barrier --
-//   serial (every block, same order, double): with W1 = Y1 - U~ C and W2 = Y2 - V~ C^T,
-//          W1^T W1 = Y1^T Y1 - 2 C^T C + C^T (U~^T U~) C and
-//          W2^T W2 = Y2^T Y2 - D2^T C^T - C D2 + C (V~^T V~) C^T, exact identities of the sums
-//          taken; R1, R2 by Cholesky (the QR of Section 2.1, with the Q factors implicit);
-//          M = [[C, R2^T], [R1, 0]], its SVD, zeta_{k+1} (Algorithm 1)
+//   A2   : W1 = Y1 - U~ C and W2 = Y2 - V~ C^T (the projections of Section 2.1) and their
+//          Gram partials
+//   -- grid barrier --
+//   serial (every block, same order): R1, R2 by Cholesky (the QR of Section 2.1, with the Q
+//          factors implicit), M = [[C, R2^T], [R1, 0]], its SVD, zeta_{k+1} (Algorithm 1)
 //   B    : new factors by Eq. (9), U_{k+1} = U~ U_M[:r, :r] + W1 (T1 U_M[r:, :r]), Trim and
 //          the hand-over to the next pass.
-// In FP64 working precision the Gram identities would lose the small singular values of
-// W1 (its Gram is formed from sums of the size of ||Y1||^2), so W1, W2 are formed first and
-// their Gram matrices summed after a second grid barrier.
+// Double-precision serial steps are long-latency on this part (measured at 10^4 x 10^4,
+// r = 5: ~250 us per update with the Gram sums, Cholesky factors and the SVD refinement in
+// double, against ~60 us in single precision), so only the FP64 working precision runs them
+// in double.
 template <typename T, int WM>
 __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   constexpr int NM = Smem<T, WM>::NM;
-  constexpr bool F64 = sizeof(T) == 8;
   DevState* st = a.st;
-  const int m = a.m, n = a.n, r = a.r, t = threadIdx.x, warp = t >> 5;
+  const int m = a.m, n = a.n, r = a.r, t = threadIdx.x;
   T* Ut = static_cast<T*>(a.Ut);
   T* Vt = static_cast<T*>(a.Vt);
   T* Y1 = static_cast<T*>(a.Y1);
@@ -1043,7 +947,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   }
   // bf16 split storage of D: while the passes read only the hi part, err_k measures against
   // bf16(D) and cannot end the run; the next pass reads hi + lo once err_k is below the switch
-  // level (use_lo is written below, after a grid barrier every CTA passes after this read)
+  // level (use_lo is written below, after grid barriers every CTA passes after this read)
   const bool hi_only = st->split_switch > 0 && !st->use_lo;
   if ((err < st->tol && !hi_only) || k >= st->max_iter) {
     if (blockIdx.x == 0 && t == 0) st->done = 1;
@@ -1051,7 +955,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   }
   trimmed_t_factors<T, WM>(a, sh);
 
-  // A: own rows of Y1, U~ (side 0) and Y2, V~ (side 1), and their Gram partials
+  // A: own rows of Y1, U~ (side 0) and Y2, V~ (side 1); partial of C = U~^T Y1 (slot 0)
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* Pp = static_cast<const T*>(side ? a.P2 : a.P1);
@@ -1061,7 +965,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     T* Bo = side ? Vt : Ut;
     int lo, hi;
     block_range(rows, lo, hi);
-    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T y[WM], b[WM];
@@ -1077,148 +981,99 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         store_row<T, WM>(Yo, i, r, y);
         store_row<T, WM>(Bo, i, r, b);
       }
-      stage_row<T, WM>(sh.stage[0], t, b);
-      stage_row<T, WM>(sh.stage[1], t, y);
-      __syncthreads();
-      const int nr = min(ST, hi - c0);
-      g0 = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[1], r, nr, g0);  // U~^T Y1 / V~^T Y2
-      if (!F64) {
-        g1 = gram_acc_d<T, WM>(sh.stage[1], r, sh.stage[1], r, nr, g1);  // Y^T Y
-        g2 = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, nr, g2);  // basis Gram
+      if (!side) {
+        stage_row<T, WM>(sh.stage[0], t, b);
+        stage_row<T, WM>(sh.stage[1], t, y);
+        __syncthreads();
+        acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[1], r, min(ST, hi - c0), acc);
+        __syncthreads();
       }
-      __syncthreads();
     }
-    if (!F64 || side == 0) gram_store_d(g0, r * r, a.part, 3 * side, sh);
-    if (!F64) {
-      gram_store_d(g1, r * r, a.part, 3 * side + 1, sh);
-      gram_store_d(g2, r * r, a.part, 3 * side + 2, sh);
-    }
+    if (!side) gram_store(acc, r * r, a.part, 0, sh);
   }
   if (!grid_barrier(st, sh)) return;
 
-  if (!F64) {
-    // Gd[0] = C, Gd[1] = Y1^T Y1, Gd[2] = U~^T U~, Gd[3] = D2, Gd[4] = Y2^T Y2, Gd[5] = V~^T V~
-    reduce_slots_d(a.part, 0, 6, r * r, &sh.Gd[0][0], sh);
-    double* G1 = sh.Md;   // scratch until M is formed
-    double* G2 = sh.UMd;
-    for (int e = t; e < r * r; e += ST) {
-      const int i = e / r, j = e % r;
-      const double* C = sh.Gd[0];
-      const double* GU = sh.Gd[2];
-      const double* D2 = sh.Gd[3];
-      const double* GV = sh.Gd[5];
-      double cc = 0.0, cuc = 0.0, cd = 0.0, dc = 0.0, cvc = 0.0;
-      for (int q = 0; q < r; ++q) {
-        cc = fma(C[q * r + i], C[q * r + j], cc);
-        cd = fma(C[i * r + q], D2[q * r + j], cd);   // (C D2)_ij
-        dc = fma(C[j * r + q], D2[q * r + i], dc);   // (C D2)_ji
-        double u = 0.0, v = 0.0;
-        for (int p = 0; p < r; ++p) {
-          u = fma(GU[q * r + p], C[p * r + j], u);   // (U~^T U~ C)_qj
-          v = fma(GV[q * r + p], C[j * r + p], v);   // (V~^T V~ C^T)_qj
-        }
-        cuc = fma(C[q * r + i], u, cuc);
-        cvc = fma(C[i * r + q], v, cvc);
-      }
-      G1[e] = sh.Gd[1][e] - 2.0 * cc + cuc;
-      G2[e] = sh.Gd[4][e] - cd - dc + cvc;
-    }
-    if (t < MW) {
-      sh.dbuf[t] = (t < r) ? sh.Gd[1][t * r + t] : 0.0;
-      sh.dbuf[MW + t] = (t < r) ? sh.Gd[4][t * r + t] : 0.0;
-    }
-    __syncthreads();
-    // a direction of W1 below 1e-6 of the norm of its column of Y1 is below the precision of
-    // the single-precision products it comes from: it is dropped (zero row of R1)
-    if (warp == 0) factor_warp<double, WM>(G1, r, sh.Rd[0], sh.Td[0], sh.dbuf, 1e-12);
-    if (warp == 1) factor_warp<double, WM>(G2, r, sh.Rd[1], sh.Td[1], sh.dbuf + MW, 1e-12);
-    __syncthreads();
-  } else {
-    // C, then W1 = Y1 - U~ C and W2 = Y2 - V~ C^T in place and their Gram partials
-    reduce_slots_d(a.part, 0, 1, r * r, &sh.Gd[0][0], sh);
-    for (int e = t; e < WM * WM; e += ST) {
-      const int q = e / WM, c = e % WM;
-      sh.cm[e] = (q < r && c < r) ? (T)sh.Gd[0][q * r + c] : T(0);
-    }
-    __syncthreads();
-    for (int side = 0; side < 2; ++side) {
-      const int rows = side ? n : m;
-      T* Y = side ? Y2 : Y1;
-      const T* B = side ? Vt : Ut;
-      int lo, hi;
-      block_range(rows, lo, hi);
-      double acc = 0.0;
-      for (int c0 = lo; c0 < hi; c0 += ST) {
-        const int i = c0 + t;
-        T y[WM];
-        zero_row<T, WM>(y);
-        if (i < hi) {
-          T b[WM];
-          load_row<T, WM>(Y, i, r, y);
-          load_row<T, WM>(B, i, r, b);
-#pragma unroll
-          for (int c = 0; c < WM; ++c) {
-            T sacc = y[c];
-#pragma unroll
-            for (int q = 0; q < WM; ++q) sacc = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], sacc);
-            y[c] = sacc;
-          }
-          store_row<T, WM>(Y, i, r, y);
-        }
-        stage_row<T, WM>(sh.stage[0], t, y);
-        __syncthreads();
-        acc = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
-        __syncthreads();
-      }
-      gram_store_d(acc, r * r, a.part, 1 + side, sh);
-    }
-    if (!grid_barrier(st, sh)) return;
-    reduce_slots_d(a.part, 1, 2, r * r, &sh.Gd[1][0], sh);
-    if (warp == 0) factor_warp<double, WM>(sh.Gd[1], r, sh.Rd[0], sh.Td[0]);
-    if (warp == 1) factor_warp<double, WM>(sh.Gd[2], r, sh.Rd[1], sh.Td[1]);
-    __syncthreads();
+  // A2: W1 = Y1 - U~ C, W2 = Y2 - V~ C^T (in place) and their Gram matrices (slots 1, 2)
+  reduce_slots(a.part, 0, 1, r * r, sh.C, sh);
+  for (int e = t; e < WM * WM; e += ST) {
+    const int q = e / WM, c = e % WM;
+    sh.cm[e] = (q < r && c < r) ? sh.C[q * r + c] : T(0);
   }
+  __syncthreads();
+  for (int side = 0; side < 2; ++side) {
+    const int rows = side ? n : m;
+    T* Y = side ? Y2 : Y1;
+    const T* B = side ? Vt : Ut;
+    int lo, hi;
+    block_range(rows, lo, hi);
+    T acc = T(0);
+    for (int c0 = lo; c0 < hi; c0 += ST) {
+      const int i = c0 + t;
+      T y[WM];
+      zero_row<T, WM>(y);
+      if (i < hi) {
+        T b[WM];
+        load_row<T, WM>(Y, i, r, y);
+        load_row<T, WM>(B, i, r, b);
+#pragma unroll
+        for (int c = 0; c < WM; ++c) {
+          T sacc = y[c];
+#pragma unroll
+          for (int q = 0; q < WM; ++q) sacc = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], sacc);
+          y[c] = sacc;
+        }
+        store_row<T, WM>(Y, i, r, y);
+      }
+      stage_row<T, WM>(sh.stage[0], t, y);
+      __syncthreads();
+      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      __syncthreads();
+    }
+    gram_store(acc, r * r, a.part, 1 + side, sh);
+  }
+  if (!grid_barrier(st, sh)) return;
 
-  // M = [[C, R2^T], [R1, 0]] and its SVD (double)
+  // R1, R2; M = [[C, R2^T], [R1, 0]] and its SVD
+  reduce_slots(a.part, 1, 2, r * r, &sh.G[0][0], sh);
+  factor_pair<T, WM>(r, 0, 1, sh);
   const int N = 2 * r;
   for (int e = t; e < NM * NM; e += ST) {
     const int row = e / NM, col = e % NM;
-    double v = 0.0;
+    T v = T(0);
     if (row < r && col < r)
-      v = sh.Gd[0][row * r + col];
+      v = sh.C[row * r + col];
     else if (row < r && col >= r && col < N)
-      v = sh.Rd[1][(col - r) * r + row];  // R2^T
+      v = sh.Rf[1][(col - r) * r + row];  // R2^T
     else if (row >= r && row < N && col < r)
-      v = sh.Rd[0][(row - r) * r + col];  // R1
-    sh.Md[e] = v;
+      v = sh.Rf[0][(row - r) * r + col];  // R1
+    sh.M[e] = v;
   }
   __syncthreads();
-  small_svd_d<T, WM>(N, sh);
+  if constexpr (sizeof(T) == 8)
+    small_svd_d<T, WM>(N, sh);
+  else
+    small_svd<T, WM>(N, sh);
   __syncthreads();
   // update matrices: side 0 acts on [U~ W1], side 1 on [V~ W2]; rows q < r take the top block
-  // of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2); C for W1 = Y1 - U~ C
+  // of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2)
   for (int e = t; e < 2 * 2 * WM * WM; e += ST) {
     const int side = e / (2 * WM * WM), rem = e % (2 * WM * WM), row = rem / WM, c = rem % WM;
-    const double* Y = side ? sh.VMd : sh.UMd;
-    double v = 0.0;
+    const T* Y = side ? sh.VM : sh.UM;
+    T v = T(0);
     if (c < r) {
       if (row < r) {
         v = Y[c * NM + row];
       } else if (row < 2 * r) {
         const int q = row - r;
-        for (int kk = q; kk < r; ++kk) v = fma(sh.Td[side][q * r + kk], Y[c * NM + r + kk], v);
+        for (int kk = q; kk < r; ++kk) v = fma(sh.Tf[side][q * r + kk], Y[c * NM + r + kk], v);
       }
     }
-    sh.mat[side][rem] = (T)v;
+    sh.mat[side][rem] = v;
   }
-  for (int e = t; e < WM * WM; e += ST) {
-    const int q = e / WM, c = e % WM;
-    sh.cm[e] = (q < r && c < r) ? (T)sh.Gd[0][q * r + c] : T(0);
-  }
-  if (t < MW) sh.sv[0][t] = (t < r) ? (T)sh.sigd[t] : T(0);
+  if (t < MW) sh.sv[0][t] = (t < r) ? (T)sh.sig[t] : T(0);
   __syncthreads();
-  const double s1 = sh.sigd[0], sr1 = sh.sigd[r];
-  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sigd[t];
+  const double s1 = (double)sh.sig[0], sr1 = (double)sh.sig[r];
+  if (t < r) static_cast<T*>(a.sig)[t] = (T)sh.sig[t];
   if (blockIdx.x == 0 && t >= ST - 32) {  // a warp with no rows when m, n <= 224 * grid
     const int lane = t & 31;
     const int k1 = k + 1;
@@ -1248,7 +1103,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     if (lane == 0) {
       st->zeta = zeta_new;
       a.stats[k].zeta_next_plain = plain;
-      for (int i = 0; i < N; ++i) st->sigma[i] = sh.sigd[i];
+      for (int i = 0; i < N; ++i) st->sigma[i] = (double)sh.sig[i];
       a.stats[k].sigma1 = s1;
       a.stats[k].sigma_r1 = sr1;
       if (hi_only && (err < st->split_switch || err < st->tol)) st->use_lo = 1;
@@ -1261,13 +1116,13 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   for (int side = 0; side < 2; ++side) {
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
-    const T* Y = side ? Y2 : Y1;
+    const T* W = side ? Y2 : Y1;
     T* F = static_cast<T*>(side ? a.V : a.U);
     const T* A = sh.mat[side];
     const T cap = trim_cap<T>(a, side);
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T x[WM];
@@ -1275,16 +1130,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       if (i < hi) {
         T b[WM], w[WM], f[WM];
         load_row<T, WM>(B, i, r, b);
-        load_row<T, WM>(Y, i, r, w);
-        if (!F64) {  // W1 = Y1 - U~ C, W2 = Y2 - V~ C^T (formed in place before in FP64)
-#pragma unroll
-          for (int c = 0; c < WM; ++c) {
-            T sacc = w[c];
-#pragma unroll
-            for (int q = 0; q < WM; ++q) sacc = fma(-b[q], side ? sh.cm[c * WM + q] : sh.cm[q * WM + c], sacc);
-            w[c] = sacc;
-          }
-        }
+        load_row<T, WM>(W, i, r, w);
 #pragma unroll
         for (int c = 0; c < WM; ++c) {
           T sacc = T(0);
@@ -1298,10 +1144,10 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       }
       stage_row<T, WM>(sh.stage[0], t, x);
       __syncthreads();
-      acc = gram_acc_d<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
+      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
-    gram_store_d(acc, r * r, a.part, 6 + side, sh);
+    gram_store(acc, r * r, a.part, 6 + side, sh);
   }
 }
 
