@@ -83,10 +83,8 @@ struct rpca_ctx {
   int TR = 0, TC = 0;
   TcPlan plan;                 // tile partition of the tensor-core pass
   int4* d_rect = nullptr;      // its tables on the device
-  int2* d_ids = nullptr;
+  int4* d_ids = nullptr;
   int* d_p1nsl = nullptr;
-  float* Y2c = nullptr;  // Y2 chunk slots of the tensor-core pass
-  int y2_ch = 0, y2_ct = 0;
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
   uint8_t *wop[2] = {nullptr, nullptr}, *vop[2] = {nullptr, nullptr}, *vtop[2] = {nullptr, nullptr},
           *utop[2] = {nullptr, nullptr};
@@ -125,7 +123,7 @@ void free_workspace(rpca_ctx* c) {
                    (void**)&c->nnzP, (void**)&c->st, (void**)&c->stats, (void**)&c->rowcnt, (void**)&c->rowoff,
                    &c->Down, &c->Dhl, (void**)&c->wop[0], (void**)&c->vop[0], (void**)&c->vtop[0],
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
-                   (void**)&c->utop[1], (void**)&c->Y2c, (void**)&c->masks, (void**)&c->chgP,
+                   (void**)&c->utop[1], (void**)&c->masks, (void**)&c->chgP,
                    (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
@@ -201,7 +199,7 @@ bool use_tc(const rpca_ctx* c, int R) { return (R == c->Rr) ? c->tc_iter : (R ==
 bool learned(const rpca_ctx* c) { return c->p.zeta_mode == RPCA_ZETA_LEARNED; }
 
 Grid pass_grid(const rpca_ctx* c, int R) {
-  if (use_tc(c, R)) return Grid{c->plan.Bmax, c->plan.A, c->plan.ncta};
+  if (use_tc(c, R)) return Grid{c->plan.Bmax, c->plan.S2, c->plan.ncta};
   const PassGeom g = pass_geometry(c->prec, R);
   const int gx = (int)((c->n + g.BW - 1) / g.BW), gy = (int)((c->m + g.BH - 1) / g.BH);
   return Grid{gx, gy, gx * gy};
@@ -261,9 +259,6 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.P2 = static_cast<float*>(c->P2);
     t.resP = c->resP;
     t.nnzP = c->nnzP;
-    t.Y2c = c->Y2c;
-    t.ch_max = c->y2_ch;
-    t.ct_max = c->y2_ct;
     t.masks = a.masks;
     t.mask_wr = c->mask_words;
     t.chgP = a.chgP;
@@ -339,19 +334,19 @@ bool tc_plan(int TR, int TC, int nsm, int max_ct, TcPlan* out) {
     out->A = (int)groups.size();
     out->Bmax = 0;
     out->ct_max = 0;
-    out->ch_max = 0;
+    out->S2 = 0;
     int rt = 0;
     for (int gi = 0; gi < (int)groups.size(); ++gi) {
-      const int h = groups[gi].first, B = groups[gi].second;
+      const int h = groups[gi].first, B = groups[gi].second, nch = (h + kTcY2Chunk - 1) / kTcY2Chunk;
       for (int b = 0; b < B; ++b) {
         const int c0 = (int)((long long)b * TC / B), c1 = (int)((long long)(b + 1) * TC / B);
         out->rect.push_back(make_int4(rt, rt + h, c0, c1));
-        out->ids.push_back(make_int2(gi, b));
+        out->ids.push_back(make_int4(gi, b, out->S2, nch));
         out->ct_max = std::max(out->ct_max, c1 - c0);
       }
       for (int q = rt; q < rt + h; ++q) out->p1_nsl[q] = B;
       out->Bmax = std::max(out->Bmax, B);
-      out->ch_max = std::max(out->ch_max, (h + kTcY2Chunk - 1) / kTcY2Chunk);
+      out->S2 += 2 * nch;
       rt += h;
     }
     out->ncta = (int)out->rect.size();
@@ -599,7 +594,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   for (int R : {c->Rr, c->Rb}) {
     const PassGeom pg = pass_geometry(c->prec, R);
     const Grid gs{(int)((n + pg.BW - 1) / pg.BW), (int)((m + pg.BH - 1) / pg.BH), 0};
-    const Grid gt{c->plan.Bmax, c->plan.A, c->plan.ncta};
+    const Grid gt{c->plan.Bmax, c->plan.S2, c->plan.ncta};
     for (const Grid& g : {gs, gt}) {
       p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
       p2 = p2 > (size_t)g.n_p2 * n * R ? p2 : (size_t)g.n_p2 * n * R;
@@ -629,15 +624,12 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   CK(cudaMalloc(&c->P2, p2 * c->tsize));
   if (c->TR > 0) {
     if (c->tc_iter || c->tc_init) {
-      c->y2_ch = c->plan.ch_max;
-      c->y2_ct = c->plan.ct_max;
-      CK(cudaMalloc((void**)&c->Y2c, (size_t)c->plan.ncta * c->y2_ch * c->y2_ct * 128 * 16 * sizeof(float)));
       const int nc = c->plan.ncta;
       CK(cudaMalloc((void**)&c->d_rect, sizeof(int4) * nc));
-      CK(cudaMalloc((void**)&c->d_ids, sizeof(int2) * nc));
+      CK(cudaMalloc((void**)&c->d_ids, sizeof(int4) * nc));
       CK(cudaMalloc((void**)&c->d_p1nsl, sizeof(int) * c->TR));
       CK(cudaMemcpy(c->d_rect, c->plan.rect.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_p1nsl, c->plan.p1_nsl.data(), sizeof(int) * c->TR, cudaMemcpyHostToDevice));
     }
     // zero-filled: rows past m, n are never written and must read as zero

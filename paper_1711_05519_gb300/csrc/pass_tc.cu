@@ -86,8 +86,6 @@ struct Cfg {
   static_assert((D_BYTES + VOP_BYTES) % 1024 == 0, "1024-byte aligned images");
   static_assert(SMEM_BYTES <= 232448, "shared memory");
   static_assert(NSTAGE <= 8, "barrier slots");
-  // the Y2 drain uses the idle stages as [column tile][128][RK] FP32 scratch
-  static_assert(MAX_CT * BM * RK * 4 <= NSTAGE * STAGE_BYTES, "Y2 drain scratch");
   static_assert(CT_BARS >= (RK == 8 ? 20 : 10), "Y2 chunk barriers for tc_max_col_tiles");
 };
 
@@ -117,7 +115,7 @@ struct TcArgs {
   int m, n, R;
   int ncta, TR, TC;
   const int4* rect;
-  const int2* ids;
+  const int4* ids;
   const uint8_t* wop;
   const uint8_t* vop;
   const uint8_t* vtop;
@@ -128,8 +126,6 @@ struct TcArgs {
   float* P2;
   double* resP;
   unsigned long long* nnzP;
-  float* Y2c;
-  int ch_max, ct_max;
   unsigned* masks;
   long long mask_wr;
   unsigned long long* chgP;
@@ -144,8 +140,8 @@ __device__ __forceinline__ void fail(const TcArgs& a, volatile int* abort_flag) 
   *abort_flag = 1;
 }
 
-// Z layout in a stage (descriptor units of 16 bytes for the Y1 k-steps of 16 columns, and the
-// Y2 accumulator rows of column jl's hi and lo parts).  DM = 0: box h (16 KB) holds
+// Z layout in a stage (descriptor units of 16 bytes for the Y1 k-steps of 16 columns), and
+// which column and which part (Z_hi or Z_lo) a row of the Y2 accumulator holds.  DM = 0: box h (16 KB) holds
 // [Z_hi | Z_lo] of columns 32h .. 32h+31; DM = 1: Z_hi in the first 16 KB, Z_lo in the second.
 template <int DM>
 __device__ __forceinline__ uint64_t zhi_off(int k) {
@@ -156,12 +152,12 @@ __device__ __forceinline__ uint64_t zlo_off(int k) {
   return DM == 0 ? zhi_off<0>(k) + 4 : (uint64_t)(((Z_BYTES / 2) >> 4) + 2 * k);
 }
 template <int DM>
-__device__ __forceinline__ int y2_hi_row(int jl) {
-  return DM == 0 ? (jl >> 5) * 64 + (jl & 31) : jl;
+__device__ __forceinline__ int y2_row_col(int row) {
+  return DM == 0 ? (row >> 6) * 32 + (row & 31) : (row & 63);
 }
 template <int DM>
-__device__ __forceinline__ int y2_lo_row(int jl) {
-  return DM == 0 ? y2_hi_row<0>(jl) + 32 : 64 + jl;
+__device__ __forceinline__ int y2_row_part(int row) {
+  return DM == 0 ? ((row >> 5) & 1) : (row >> 6);
 }
 
 // NY consecutive accumulator columns of this warp's 32 lanes.
@@ -207,14 +203,14 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   const int cta = blockIdx.x;
   // this CTA's rectangle of tiles and its slices of the partial products (host plan)
   const int4 rc = a.rect[cta];
-  const int2 id = a.ids[cta];
-  const int ai = id.x, bi = id.y;
+  const int4 id = a.ids[cta];
+  const int bi = id.y, p2base = id.z;  // Y1 slice; first Y2 slice of the row group
   const int rt0 = rc.x, rt1 = rc.y, ct0 = rc.z, ct1 = rc.w;
   const int nrt = rt1 - rt0, nct = ct1 - ct0;
   const int ntiles = nrt * nct;
   // the host's partition keeps a CTA's column tiles within the tensor-memory and barrier
   // budget and its row tiles within the chunk slots; refuse a launch that does not
-  if (nct > C::MAX_CT || nct > CT_BARS || nct > a.ct_max || (nrt + G2 - 1) / G2 > a.ch_max) {
+  if (nct > C::MAX_CT || nct > CT_BARS) {
     if (tid == 0) atomicCAS(a.status, 0, 1);
     return;
   }
@@ -426,8 +422,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         mold = mask_old[mw];
       }
       if (rtl % G2 == 0 && rtl > 0) {
-        // read chunk c - 1 of column tile ctl's Y2 accumulator (hi + lo column halves) out to
-        // its slot before this tile's products restart the accumulator
+        // read chunk c - 1 of column tile ctl's Y2 accumulator out (hi + lo column halves, this
+        // warp's half of the components) to its Y2 slices, before this tile's products restart
+        // the accumulator: the Z_hi and Z_lo rows of a column go to slices p2base + 2 (c - 1)
+        // and + 1, which the update adds up
         const int c = rtl / G2;
         if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
           fail(a, &abort_flag);
@@ -440,16 +438,16 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
-        float* slot = a.Y2c + ((((size_t)cta * a.ch_max + (c - 1)) * a.ct_max + ctl) * BM + rowl) * RK + h * (RK / 2);
-        float sv[RK / 2];  // k = h RK/2 + j (register indices fixed at compile time)
+        const int col = (ct0 + ctl) * BN + y2_row_col<DM>(rowl);
+        if (col < a.n) {
+          float* dst = a.P2 + ((size_t)(p2base + 2 * (c - 1) + y2_row_part<DM>(rowl)) * a.n + col) * a.R;
 #pragma unroll
-        for (int j = 0; j < RK / 2; ++j) {
-          const uint32_t x = h ? yv[RK / 2 + j] : yv[j], y = h ? yv[RK + RK / 2 + j] : yv[RK + j];
-          sv[j] = __uint_as_float(x) + __uint_as_float(y);
+          for (int j = 0; j < RK / 2; ++j) {  // k = h RK/2 + j (register indices fixed at compile time)
+            const int k = h * (RK / 2) + j;
+            const uint32_t x = h ? yv[RK / 2 + j] : yv[j], y = h ? yv[RK + RK / 2 + j] : yv[RK + j];
+            if (k < a.R) dst[k] = __uint_as_float(x) + __uint_as_float(y);
+          }
         }
-#pragma unroll
-        for (int j = 0; j < RK / 2; j += 4)
-          *reinterpret_cast<float4*>(slot + j) = make_float4(sv[j], sv[j + 1], sv[j + 2], sv[j + 3]);
       }
       if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
         fail(a, &abort_flag);
@@ -574,59 +572,32 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         if (lane == 0) mbar_arrive(&bar[B_Y1EMPTY + yb]);
       }
     }
-    // drain Y2: each warp takes the column tiles ctl = g, g + 4, ...; lane quarter q holds
-    // accumulator rows 32q .. 32q+31 (the Z_hi and Z_lo parts of the tile's columns, placed as
-    // y2_hi_row / y2_lo_row give).  The last
-    // chunk is in tensor memory, the earlier ones in their slots (written by any epilogue warp:
-    // the barrier below orders those stores before the reads)
-    asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
+    // drain Y2: the last chunk of every column tile is still in tensor memory; each warp takes
+    // the column tiles ctl = g, g + 4, ...  (lane quarter q: accumulator rows 32q .. 32q+31) and
+    // writes them to the last Y2 slices of the row group, as the chunk read-outs above do
     const int nch = (nrt + G2 - 1) / G2;
     if (ntiles > 0 && !abort_flag) {
-      // the Y2 products are complete (YFIN) and so are the Y1 products (Y1DRAIN): only then
-      // may the stages be reused as scratch
-      if (!mbar_wait(&bar[B_YFIN], 0) || !mbar_wait(&bar[B_Y1DRAIN], 0)) {
+      if (!mbar_wait(&bar[B_YFIN], 0)) {
         fail(a, &abort_flag);
       } else {
         tc_fence_after();
-        float* scratch = reinterpret_cast<float*>(sm + OFF_STAGE);  // [nct][128][RK], stages are idle now
+        const int col0 = y2_row_col<DM>(rowl);
+        const int slice = p2base + 2 * (nch - 1) + y2_row_part<DM>(rowl);
         for (int ctl = gq; ctl < nct; ctl += EPI_WARPS / 4) {
           uint32_t yv[NY];
           tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
           tmem_wait_ld();
-          float acc[RK];
+          const int col = (ct0 + ctl) * BN + col0;
+          if (col < a.n) {
+            float* dst = a.P2 + ((size_t)slice * a.n + col) * a.R;
 #pragma unroll
-          for (int k = 0; k < RK; ++k) acc[k] = 0.f;
-          for (int c = 0; c + 1 < nch; ++c) {
-            const float4* slot = reinterpret_cast<const float4*>(
-                a.Y2c + ((((size_t)cta * a.ch_max + c) * a.ct_max + ctl) * BM + rowl) * RK);
-#pragma unroll
-            for (int k4 = 0; k4 < RK / 4; ++k4) {
-              const float4 v = slot[k4];
-              acc[4 * k4] += v.x;
-              acc[4 * k4 + 1] += v.y;
-              acc[4 * k4 + 2] += v.z;
-              acc[4 * k4 + 3] += v.w;
-            }
+            for (int k = 0; k < RK; ++k)
+              if (k < a.R) dst[k] = __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]);
           }
-#pragma unroll
-          for (int k = 0; k < RK; ++k)
-            scratch[((size_t)ctl * BM + rowl) * RK + k] = acc[k] + (__uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]));
         }
       }
     }
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
-    if (ntiles > 0 && !abort_flag) {
-      const float* scratch = reinterpret_cast<const float*>(sm + OFF_STAGE);
-      const int et = tid - 128;
-      for (int e = et; e < nct * 64; e += EPI_THREADS) {
-        const int ctl = e / 64, jl = e % 64;
-        const int col = (ct0 + ctl) * BN + jl;
-        if (col < a.n)
-          for (int k = 0; k < a.R; ++k)
-            a.P2[((size_t)ai * a.n + col) * a.R + k] = scratch[((size_t)ctl * BM + y2_hi_row<DM>(jl)) * RK + k] +
-                                                       scratch[((size_t)ctl * BM + y2_lo_row<DM>(jl)) * RK + k];
-      }
-    }
     // CTA totals of the residual and the support size
     double rd = (double)res;
     unsigned long long nz = nnz, cz = chg;
@@ -725,9 +696,6 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.P2 = p.P2;
   a.resP = p.resP;
   a.nnzP = p.nnzP;
-  a.Y2c = p.Y2c;
-  a.ch_max = p.ch_max;
-  a.ct_max = p.ct_max;
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
   a.chgP = p.chgP;

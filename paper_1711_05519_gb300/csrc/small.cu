@@ -864,7 +864,7 @@ __device__ void trim_hand_over(const SmallArgs& a, Smem<T, WM>& sh) {
     const T* F = static_cast<const T*>(side ? a.V : a.U);
     int lo, hi;
     block_range(rows, lo, hi);
-    double acc = 0.0;
+    T acc = T(0);
     for (int c0 = lo; c0 < hi; c0 += ST) {
       const int i = c0 + t;
       T x[WM];
@@ -880,7 +880,7 @@ __device__ void trim_hand_over(const SmallArgs& a, Smem<T, WM>& sh) {
       acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
-    gram_store(acc, r * r, a.part, 6 + side, sh);
+    gram_store<T>(acc, r * r, a.part, 6 + side, sh);
   }
 }
 
@@ -989,7 +989,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         __syncthreads();
       }
     }
-    if (!side) gram_store(acc, r * r, a.part, 0, sh);
+    if (!side) gram_store<T>(acc, r * r, a.part, 0, sh);
   }
   if (!grid_barrier(st, sh)) return;
 
@@ -1029,7 +1029,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
-    gram_store(acc, r * r, a.part, 1 + side, sh);
+    gram_store<T>(acc, r * r, a.part, 1 + side, sh);
   }
   if (!grid_barrier(st, sh)) return;
 
@@ -1147,7 +1147,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
       __syncthreads();
     }
-    gram_store(acc, r * r, a.part, 6 + side, sh);
+    gram_store<T>(acc, r * r, a.part, 6 + side, sh);
   }
 }
 
