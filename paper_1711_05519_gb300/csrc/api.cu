@@ -337,16 +337,16 @@ bool tc_plan(int TR, int TC, int nsm, int max_ct, TcPlan* out) {
     out->S2 = 0;
     int rt = 0;
     for (int gi = 0; gi < (int)groups.size(); ++gi) {
-      const int h = groups[gi].first, B = groups[gi].second, nch = (h + kTcY2Chunk - 1) / kTcY2Chunk;
+      const int h = groups[gi].first, B = groups[gi].second;
       for (int b = 0; b < B; ++b) {
         const int c0 = (int)((long long)b * TC / B), c1 = (int)((long long)(b + 1) * TC / B);
         out->rect.push_back(make_int4(rt, rt + h, c0, c1));
-        out->ids.push_back(make_int4(gi, b, out->S2, nch));
+        out->ids.push_back(make_int4(gi, b, 2 * gi, 0));
         out->ct_max = std::max(out->ct_max, c1 - c0);
       }
       for (int q = rt; q < rt + h; ++q) out->p1_nsl[q] = B;
       out->Bmax = std::max(out->Bmax, B);
-      out->S2 += 2 * nch;
+      out->S2 += 2;
       rt += h;
     }
     out->ncta = (int)out->rect.size();

@@ -107,7 +107,7 @@ struct TcPassArgs {
   int ncta;      // CTAs of the tile partition (TcPlan, below)
   const int4* rect;  // [ncta] tile rectangle of each CTA (device)
   const int4* ids;   // [ncta] {row group, index within the group, first Y2 slice of the group,
-                     //  Y2 chunks of the group} (device)
+                     //  unused} (device)
   int TR, TC;    // 128-row and 64-column tile counts
   // operand images (tc_images.cuh) in the layout of tc_image_rank(R): per row tile W and
   // U~, per column tile V and V~
@@ -118,8 +118,8 @@ struct TcPassArgs {
   const DevState* st;
   int* status;
   float* P1;     // [Bmax][m][R]: slice = index of the CTA within its row group
-  float* P2;     // [S2][n][R]: per row group, per chunk of kTcY2Chunk row tiles, the Z_hi and
-                 // the Z_lo part of Z^T U~ over the chunk's rows (TcPlan::p2_base)
+  float* P2;     // [S2 = 2 A][n][R]: per row group, the Z_hi and the Z_lo part of Z^T U~ over
+                 // the group's rows (slices 2 a and 2 a + 1)
   double* resP;  // [ncta]
   unsigned long long* nnzP;
   // support bitmasks as in PassArgs (null: not tracked), here two buffers of mask_wr words
@@ -132,10 +132,9 @@ struct TcPassArgs {
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
 // Tile partition of the tensor-core pass (api.cu, tc_plan): per CTA its rectangle of tiles
-// {first row tile, end row tile, first column tile, end column tile} and its ids {row group,
-// index in the group (the m-slice of Y1 it writes), the group's first n-slice of Y2, the
-// group's Y2 chunks}; per row tile the number of Y1 slices its rows have.  Group g of h_g row
-// tiles owns the 2 ceil(h_g / kTcY2Chunk) Y2 slices from its p2_base on; S2 slices in all.
+// {first row tile, end row tile, first column tile, end column tile} and its ids {row group a,
+// index in the group (the m-slice of Y1 it writes), 2 a (its group's first n-slice of Y2),
+// 0}; per row tile the number of Y1 slices its rows have.  S2 = 2 A Y2 slices in all.
 struct TcPlan {
   int ncta = 0, A = 0, Bmax = 0, ct_max = 0, S2 = 0, T = 0;
   std::vector<int4> rect;

@@ -5,11 +5,12 @@
 // the residual sum over unthresholded entries (Eq. (11)) and Z = D - S_k; accumulate
 // Y1 = Z V~ and Y2 = Z^T U~ (Section 2.1).  D is read once from HBM.
 //
-// Work decomposition.  D is cut into 128 x 64 tiles.  The CTA grid is A x B (one CTA per
-// SM); CTA (a, b) owns a contiguous block of row tiles and column tiles and walks it row
-// tile by row tile.  Y1 for the current row tile and Y2 for every column tile of the CTA
-// stay in tensor memory, so each CTA writes one Y1 partial per row (slice b) and one Y2
-// partial per column (slice a).
+// Work decomposition.  D is cut into 128 x 64 tiles, and the tiles into row groups of
+// different heights (one CTA per SM; the host's plan balances the tile counts): CTA (a, b)
+// owns row group a's row tiles and the b-th range of column tiles, and walks them row tile by
+// row tile.  Y1 for the current row tile and Y2 for every column tile of the CTA stay in
+// tensor memory, so each CTA writes one Y1 partial per row (slice b) and, per column, the
+// Z_hi and Z_lo parts of one Y2 partial (slices 2a, 2a + 1), added up chunk by chunk.
 //
 // Per tile (RK = 8 for R <= 8, RK = 16 for R <= 16: the operand image layout, tc_images.cuh):
 //   TMA (warp 0)     : D tile (two 128 x 32 FP32 boxes, or one 128 x 64 bf16 box per part,
@@ -102,12 +103,13 @@ enum {
   B_Y1EMPTY = 34,  // [2]
   B_YFIN = 36,
   B_DRAIN = 37,
+  B_Y2ACC = 38,    // [CT_BARS]: a chunk of column tile ctl has been added into the Y2 partial
   B_LDRAIN = 70,
   B_Y1DRAIN = 71,
   B_Y2DONE = 72,   // [CT_BARS]: the MMAs of a non-final Y2 chunk of column tile ctl completed
   B_Y2FREE = 92    // [CT_BARS]: that chunk has been read out of tensor memory
 };
-static_assert(B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
+static_assert(B_Y2FREE + CT_BARS <= NBAR && B_Y2ACC + CT_BARS <= B_LDRAIN, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -204,12 +206,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   // this CTA's rectangle of tiles and its slices of the partial products (host plan)
   const int4 rc = a.rect[cta];
   const int4 id = a.ids[cta];
-  const int bi = id.y, p2base = id.z;  // Y1 slice; first Y2 slice of the row group
+  const int bi = id.y, p2base = id.z;  // Y1 slice; Y2 slices of the row group (Z_hi, Z_lo parts)
   const int rt0 = rc.x, rt1 = rc.y, ct0 = rc.z, ct1 = rc.w;
   const int nrt = rt1 - rt0, nct = ct1 - ct0;
   const int ntiles = nrt * nct;
   // the host's partition keeps a CTA's column tiles within the tensor-memory and barrier
-  // budget and its row tiles within the chunk slots; refuse a launch that does not
+  // budget; refuse a launch that does not
   if (nct > C::MAX_CT || nct > CT_BARS) {
     if (tid == 0) atomicCAS(a.status, 0, 1);
     return;
@@ -237,6 +239,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     for (int i = 0; i < CT_BARS; ++i) {
       mbar_init(&bar[B_Y2DONE + i], 1);
       mbar_init(&bar[B_Y2FREE + i], EPI_WARPS / 2);
+      mbar_init(&bar[B_Y2ACC + i], EPI_WARPS / 2);
     }
     fence_mbar_init();
   }
@@ -422,10 +425,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         mold = mask_old[mw];
       }
       if (rtl % G2 == 0 && rtl > 0) {
-        // read chunk c - 1 of column tile ctl's Y2 accumulator out (hi + lo column halves, this
-        // warp's half of the components) to its Y2 slices, before this tile's products restart
-        // the accumulator: the Z_hi and Z_lo rows of a column go to slices p2base + 2 (c - 1)
-        // and + 1, which the update adds up
+        // chunk c - 1 of column tile ctl's Y2 accumulator is complete: read it out (hi + lo
+        // column halves, this warp's half of the components) before this tile's products
+        // restart the accumulator, and add it into the group's Y2 partial (slice p2base for the
+        // Z_hi rows, p2base + 1 for the Z_lo rows).  Each (slice, column) belongs to this CTA
+        // alone; the adds of consecutive chunks, possibly by the other group, are ordered by
+        // B_Y2ACC (release by the warps that added chunk c - 2, acquire here).
         const int c = rtl / G2;
         if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
           fail(a, &abort_flag);
@@ -438,16 +443,22 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
+        if (c >= 2 && !mbar_wait(&bar[B_Y2ACC + ctl], (c - 2) & 1)) {
+          fail(a, &abort_flag);
+          break;
+        }
         const int col = (ct0 + ctl) * BN + y2_row_col<DM>(rowl);
         if (col < a.n) {
-          float* dst = a.P2 + ((size_t)(p2base + 2 * (c - 1) + y2_row_part<DM>(rowl)) * a.n + col) * a.R;
+          float* dst = a.P2 + ((size_t)(p2base + y2_row_part<DM>(rowl)) * a.n + col) * a.R;
 #pragma unroll
           for (int j = 0; j < RK / 2; ++j) {  // k = h RK/2 + j (register indices fixed at compile time)
             const int k = h * (RK / 2) + j;
             const uint32_t x = h ? yv[RK / 2 + j] : yv[j], y = h ? yv[RK + RK / 2 + j] : yv[RK + j];
-            if (k < a.R) dst[k] = __uint_as_float(x) + __uint_as_float(y);
+            if (k < a.R) dst[k] = (c >= 2 ? dst[k] : 0.f) + (__uint_as_float(x) + __uint_as_float(y));
           }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[B_Y2ACC + ctl]);
       }
       if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
         fail(a, &abort_flag);
@@ -574,7 +585,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     }
     // drain Y2: the last chunk of every column tile is still in tensor memory; each warp takes
     // the column tiles ctl = g, g + 4, ...  (lane quarter q: accumulator rows 32q .. 32q+31) and
-    // writes them to the last Y2 slices of the row group, as the chunk read-outs above do
+    // adds them into the group's Y2 partial, after the read-outs above have added the earlier
+    // chunks
     const int nch = (nrt + G2 - 1) / G2;
     if (ntiles > 0 && !abort_flag) {
       if (!mbar_wait(&bar[B_YFIN], 0)) {
@@ -582,17 +594,21 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       } else {
         tc_fence_after();
         const int col0 = y2_row_col<DM>(rowl);
-        const int slice = p2base + 2 * (nch - 1) + y2_row_part<DM>(rowl);
+        const int slice = p2base + y2_row_part<DM>(rowl);
         for (int ctl = gq; ctl < nct; ctl += EPI_WARPS / 4) {
           uint32_t yv[NY];
           tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
           tmem_wait_ld();
+          if (nch >= 2 && !mbar_wait(&bar[B_Y2ACC + ctl], (nch - 2) & 1)) {
+            fail(a, &abort_flag);
+            break;
+          }
           const int col = (ct0 + ctl) * BN + col0;
           if (col < a.n) {
             float* dst = a.P2 + ((size_t)slice * a.n + col) * a.R;
 #pragma unroll
             for (int k = 0; k < RK; ++k)
-              if (k < a.R) dst[k] = __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]);
+              if (k < a.R) dst[k] = (nch >= 2 ? dst[k] : 0.f) + (__uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]));
           }
         }
       }

@@ -442,11 +442,27 @@ __device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_swee
       const U sa = sa0 + sa1, sb = sb0 + sb1, sg = sg0 + sg1;
       bool doit = (q != lane) && sg != U(0) && sg * sg > tol2 * sa * sb;
       if (doit) {
-        const U z = (sb - sa) / (U(2) * sg);
-        const U az = fabs(z);
-        U tt = (az > big) ? U(0.5) / az : U(1) / (az + sqrt(fma(z, z, U(1))));
-        tt = (z < U(0)) ? -tt : tt;
-        const U c = U(1) / sqrt(fma(tt, tt, U(1)));
+        U tt, c;
+        if constexpr (sizeof(U) == 4) {
+          // t = tan(theta) of the rotation with tan(2 theta) = 2 gamma / (beta - alpha), the
+          // smaller root: t = sign(d) 2 gamma / (|d| + sqrt(d^2 + 4 gamma^2)), d = beta - alpha
+          // (one square root and one division); c = 1 / sqrt(1 + t^2) from the hardware
+          // estimate and one Newton step y <- y (3 - x y^2) / 2.  The operands are column sums of
+          // a matrix scaled to max |M_ij| = 1, so d^2 + 4 gamma^2 cannot overflow.
+          const float d = sb - sa, g2 = 2.f * sg;
+          const float h = sqrtf(fmaf(d, d, g2 * g2));
+          tt = g2 / (fabsf(d) + h);
+          tt = (d < 0.f) ? -tt : tt;
+          const float x1 = fmaf(tt, tt, 1.f);
+          const float y0 = rsqrtf(x1);
+          c = y0 * fmaf(-0.5f * x1 * y0, y0, 1.5f);
+        } else {
+          const U z = (sb - sa) / (U(2) * sg);
+          const U az = fabs(z);
+          tt = (az > big) ? U(0.5) / az : U(1) / (az + sqrt(fma(z, z, U(1))));
+          tt = (z < U(0)) ? -tt : tt;
+          c = U(1) / sqrt(fma(tt, tt, U(1)));
+        }
         const U sn = low ? -(c * tt) : (c * tt);  // low: c x - s xq; high: c x + s xq
         doit = tt != U(0);
         if (doit) {
@@ -505,6 +521,8 @@ __device__ void small_svd(int N, Smem<T, WM>& sh) {
   // (the padding entries are zero and would only add exact zeros)
   if (N <= 8)
     jacobi_f32_sized<8, NM>(N, sh.M, sc, sh.pairs, xf, vf);
+  else if (N <= 10)
+    jacobi_f32_sized<(NM < 10 ? NM : 10), NM>(N, sh.M, sc, sh.pairs, xf, vf);
   else if (N <= 12)
     jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.M, sc, sh.pairs, xf, vf);
   else if (N <= 16 || NM <= 16)
@@ -764,15 +782,16 @@ __device__ __forceinline__ void reduce_row(const T* __restrict__ Pp, int nsl, si
                                            T (&y)[WM]) {
   zero_row<T, WM>(y);
   const T* p = Pp + i * R;
+  constexpr int UNR = (WM * sizeof(T) <= 32) ? 8 : 4;  // slices whose loads are issued together
   int q = 0;
-  for (; q + 4 <= nsl; q += 4) {
-    T v[4][WM];
+  for (; q + UNR <= nsl; q += UNR) {
+    T v[UNR][WM];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < UNR; ++u)
 #pragma unroll
       for (int j = 0; j < WM; ++j) v[u][j] = (j < w) ? p[(size_t)(q + u) * stride + j] : T(0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < UNR; ++u)
 #pragma unroll
       for (int j = 0; j < WM; ++j) y[j] += v[u][j];
   }
@@ -893,6 +912,42 @@ __device__ void trimmed_t_factors(const SmallArgs& a, Smem<T, WM>& sh) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Half-block steps of the update: the m-side rows (side 0) and the n-side rows (side 1) are
+// processed at once, side s by threads s HT .. s HT + HT - 1 with its own named barrier
+// (1 + s) and its own staging rows, so neither side waits for the other.
+constexpr int HT = ST / 2;
+
+__device__ __forceinline__ void half_sync(int side) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + side), "r"(HT) : "memory");
+}
+
+// Entries p = tl and p = tl + HT (p < w^2) of X^T Y over nrows staged rows (row stride WM),
+// each added by one thread in row order into acc[0], acc[1] (no cross-thread combination).
+template <typename T, int WM>
+__device__ __forceinline__ void gram_rows_h(const T* X, const T* Y, int w, int nrows, int tl, T (&acc)[2]) {
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int p = tl + e * HT;
+    if (p < w * w) {
+      const int ca = p / w, cb = p % w;
+      T s = acc[e];
+      for (int i = 0; i < nrows; ++i) s = fma(X[i * WM + ca], Y[i * WM + cb], s);
+      acc[e] = s;
+    }
+  }
+}
+
+// This block's partial of the Gram matrix (entries as in gram_rows_h) into slot `slot`.
+template <typename T>
+__device__ __forceinline__ void gram_put_h(const T (&acc)[2], int w, void* part, int slot, int tl) {
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int p = tl + e * HT;
+    if (p < w * w) slot_ptr<T>(part, slot, blockIdx.x)[p] = acc[e];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // One update of Algorithm 1 after the fused pass, in the working precision:
 //   start: err_k, the stop test, T_u and T_v (above)
 //   A    : rows of Y1 = X1 T_v, U~ = A~ T_u, Y2 = X2 T_u, V~ = B~ T_v; partials of C = U~^T Y1
@@ -955,41 +1010,45 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   }
   trimmed_t_factors<T, WM>(a, sh);
 
-  // A: own rows of Y1, U~ (side 0) and Y2, V~ (side 1); partial of C = U~^T Y1 (slot 0)
-  for (int side = 0; side < 2; ++side) {
+  // A: own rows of Y1, U~ (side 0) and Y2, V~ (side 1), both sides at once; partial of
+  // C = U~^T Y1 (slot 0)
+  {
+    const int side = t / HT, tl = t % HT;
     const int rows = side ? n : m;
     const T* Pp = static_cast<const T*>(side ? a.P2 : a.P1);
     const int nsl_all = side ? a.n_p2 : a.n_p1;
     const T* F = side ? Bt : At;
     T* Yo = side ? Y2 : Y1;
     T* Bo = side ? Vt : Ut;
+    T* sb = sh.stage[0];            // side 0: rows of U~ ...
+    T* sy = sh.stage[0] + HT * WM;  // ... and of Y1
     int lo, hi;
     block_range(rows, lo, hi);
-    T acc = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
+    T acc[2] = {T(0), T(0)};
+    for (int c0 = lo; c0 < hi; c0 += HT) {
+      const int i = c0 + tl;
       T y[WM], b[WM];
       zero_row<T, WM>(y);
       zero_row<T, WM>(b);
       if (i < hi) {
         T x[WM], f[WM];
+        load_row<T, WM>(F, i, a.Rit, f);
         const int nsl = (!side && a.p1_nsl) ? a.p1_nsl[i >> 7] : nsl_all;
         reduce_row<T, WM>(Pp, nsl, (size_t)rows * a.R, i, a.R, r, x);
-        load_row<T, WM>(F, i, a.Rit, f);
         row_times<T, WM>(x, sh.tm[1 - side], y);  // X1 T_v, X2 T_u
         row_times<T, WM>(f, sh.tm[side], b);      // A~ T_u, B~ T_v
         store_row<T, WM>(Yo, i, r, y);
         store_row<T, WM>(Bo, i, r, b);
       }
       if (!side) {
-        stage_row<T, WM>(sh.stage[0], t, b);
-        stage_row<T, WM>(sh.stage[1], t, y);
-        __syncthreads();
-        acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[1], r, min(ST, hi - c0), acc);
-        __syncthreads();
+        stage_row<T, WM>(sb, tl, b);
+        stage_row<T, WM>(sy, tl, y);
+        half_sync(0);
+        gram_rows_h<T, WM>(sb, sy, r, min(HT, hi - c0), tl, acc);
+        half_sync(0);
       }
     }
-    if (!side) gram_store<T>(acc, r * r, a.part, 0, sh);
+    if (!side) gram_put_h<T>(acc, r, a.part, 0, tl);
   }
   if (!grid_barrier(st, sh)) return;
 
@@ -1000,15 +1059,17 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     sh.cm[e] = (q < r && c < r) ? sh.C[q * r + c] : T(0);
   }
   __syncthreads();
-  for (int side = 0; side < 2; ++side) {
+  {
+    const int side = t / HT, tl = t % HT;
     const int rows = side ? n : m;
     T* Y = side ? Y2 : Y1;
     const T* B = side ? Vt : Ut;
+    T* sw = sh.stage[side];
     int lo, hi;
     block_range(rows, lo, hi);
-    T acc = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
+    T acc[2] = {T(0), T(0)};
+    for (int c0 = lo; c0 < hi; c0 += HT) {
+      const int i = c0 + tl;
       T y[WM];
       zero_row<T, WM>(y);
       if (i < hi) {
@@ -1024,12 +1085,12 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         }
         store_row<T, WM>(Y, i, r, y);
       }
-      stage_row<T, WM>(sh.stage[0], t, y);
-      __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
-      __syncthreads();
+      stage_row<T, WM>(sw, tl, y);
+      half_sync(side);
+      gram_rows_h<T, WM>(sw, sw, r, min(HT, hi - c0), tl, acc);
+      half_sync(side);
     }
-    gram_store<T>(acc, r * r, a.part, 1 + side, sh);
+    gram_put_h<T>(acc, r, a.part, 1 + side, tl);
   }
   if (!grid_barrier(st, sh)) return;
 
@@ -1111,20 +1172,23 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     }
   }
 
-  // B: new factors (Eq. (9)), Trim (Algorithm 2), hand-over; Gram partials of A~, B~
-  const bool do_trim = st->trim != 0;
-  for (int side = 0; side < 2; ++side) {
+  // B: new factors (Eq. (9)), Trim (Algorithm 2), hand-over; Gram partials of A~, B~ (both
+  // sides at once)
+  {
+    const bool do_trim = st->trim != 0;
+    const int side = t / HT, tl = t % HT;
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
     const T* W = side ? Y2 : Y1;
     T* F = static_cast<T*>(side ? a.V : a.U);
     const T* A = sh.mat[side];
     const T cap = trim_cap<T>(a, side);
+    T* sx = sh.stage[side];
     int lo, hi;
     block_range(rows, lo, hi);
-    T acc = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
+    T acc[2] = {T(0), T(0)};
+    for (int c0 = lo; c0 < hi; c0 += HT) {
+      const int i = c0 + tl;
       T x[WM];
       zero_row<T, WM>(x);
       if (i < hi) {
@@ -1142,12 +1206,12 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         trim_row<T, WM>(f, cap, do_trim, x);
         hand_over_row<T, WM>(a, side, i, f, x, sh.sv[0]);
       }
-      stage_row<T, WM>(sh.stage[0], t, x);
-      __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
-      __syncthreads();
+      stage_row<T, WM>(sx, tl, x);
+      half_sync(side);
+      gram_rows_h<T, WM>(sx, sx, r, min(HT, hi - c0), tl, acc);
+      half_sync(side);
     }
-    gram_store<T>(acc, r * r, a.part, 6 + side, sh);
+    gram_put_h<T>(acc, r, a.part, 6 + side, tl);
   }
 }
 
