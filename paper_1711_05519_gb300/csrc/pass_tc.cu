@@ -103,13 +103,12 @@ enum {
   B_Y1EMPTY = 34,  // [2]
   B_YFIN = 36,
   B_DRAIN = 37,
-  B_Y2ACC = 38,    // [CT_BARS]: a chunk of column tile ctl has been added into the Y2 partial
   B_LDRAIN = 70,
   B_Y1DRAIN = 71,
   B_Y2DONE = 72,   // [CT_BARS]: the MMAs of a non-final Y2 chunk of column tile ctl completed
   B_Y2FREE = 92    // [CT_BARS]: that chunk has been read out of tensor memory
 };
-static_assert(B_Y2FREE + CT_BARS <= NBAR && B_Y2ACC + CT_BARS <= B_LDRAIN, "barrier slots");
+static_assert(B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
@@ -239,7 +238,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     for (int i = 0; i < CT_BARS; ++i) {
       mbar_init(&bar[B_Y2DONE + i], 1);
       mbar_init(&bar[B_Y2FREE + i], EPI_WARPS / 2);
-      mbar_init(&bar[B_Y2ACC + i], EPI_WARPS / 2);
     }
     fence_mbar_init();
   }
@@ -400,6 +398,17 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const int e = warp - 4, grp = e >> 3, gq = e >> 2;
     const int q = warp & 3, h = (e >> 2) & 1;
     const int rowl = 32 * q + lane;
+    {
+      // zero this CTA's columns of the group's two Y2 slices before the first add (the adds
+      // come at least kTcY2Chunk row tiles later, after the barrier below)
+      const int et = tid - 128, ncol = nct * BN;
+      for (int e2 = et; e2 < 2 * ncol * a.R; e2 += EPI_THREADS) {
+        const int part = e2 / (ncol * a.R), rem = e2 % (ncol * a.R);
+        const int col = ct0 * BN + rem / a.R;
+        if (col < a.n) a.P2[((size_t)(p2base + part) * a.n + col) * a.R + rem % a.R] = 0.f;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS) : "memory");
+    }
     const float zeta = static_cast<float>(a.st->zeta);
     const float invp = PO ? static_cast<float>(a.st->inv_p) : 1.f;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
@@ -428,9 +437,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         // chunk c - 1 of column tile ctl's Y2 accumulator is complete: read it out (hi + lo
         // column halves, this warp's half of the components) before this tile's products
         // restart the accumulator, and add it into the group's Y2 partial (slice p2base for the
-        // Z_hi rows, p2base + 1 for the Z_lo rows).  Each (slice, column) belongs to this CTA
-        // alone; the adds of consecutive chunks, possibly by the other group, are ordered by
-        // B_Y2ACC (release by the warps that added chunk c - 2, acquire here).
+        // Z_hi rows, p2base + 1 for the Z_lo rows; each (slice, column) belongs to this CTA
+        // alone, zeroed before the first tile) with fire-and-forget atomic adds, so no warp
+        // waits for the partial's previous value.  Consecutive chunks of a column tile are read
+        // out at least kTcY2Chunk row tiles apart.
         const int c = rtl / G2;
         if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
           fail(a, &abort_flag);
@@ -443,10 +453,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
-        if (c >= 2 && !mbar_wait(&bar[B_Y2ACC + ctl], (c - 2) & 1)) {
-          fail(a, &abort_flag);
-          break;
-        }
         const int col = (ct0 + ctl) * BN + y2_row_col<DM>(rowl);
         if (col < a.n) {
           float* dst = a.P2 + ((size_t)(p2base + y2_row_part<DM>(rowl)) * a.n + col) * a.R;
@@ -454,11 +460,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           for (int j = 0; j < RK / 2; ++j) {  // k = h RK/2 + j (register indices fixed at compile time)
             const int k = h * (RK / 2) + j;
             const uint32_t x = h ? yv[RK / 2 + j] : yv[j], y = h ? yv[RK + RK / 2 + j] : yv[RK + j];
-            if (k < a.R) dst[k] = (c >= 2 ? dst[k] : 0.f) + (__uint_as_float(x) + __uint_as_float(y));
+            if (k < a.R) atomicAdd(dst + k, __uint_as_float(x) + __uint_as_float(y));
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bar[B_Y2ACC + ctl]);
       }
       if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
         fail(a, &abort_flag);
@@ -585,9 +589,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     }
     // drain Y2: the last chunk of every column tile is still in tensor memory; each warp takes
     // the column tiles ctl = g, g + 4, ...  (lane quarter q: accumulator rows 32q .. 32q+31) and
-    // adds them into the group's Y2 partial, after the read-outs above have added the earlier
-    // chunks
-    const int nch = (nrt + G2 - 1) / G2;
+    // adds them into the group's Y2 partial as the read-outs above do
     if (ntiles > 0 && !abort_flag) {
       if (!mbar_wait(&bar[B_YFIN], 0)) {
         fail(a, &abort_flag);
@@ -599,16 +601,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           uint32_t yv[NY];
           tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
           tmem_wait_ld();
-          if (nch >= 2 && !mbar_wait(&bar[B_Y2ACC + ctl], (nch - 2) & 1)) {
-            fail(a, &abort_flag);
-            break;
-          }
           const int col = (ct0 + ctl) * BN + col0;
           if (col < a.n) {
             float* dst = a.P2 + ((size_t)slice * a.n + col) * a.R;
 #pragma unroll
             for (int k = 0; k < RK; ++k)
-              if (k < a.R) dst[k] = (nch >= 2 ? dst[k] : 0.f) + (__uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]));
+              if (k < a.R) atomicAdd(dst + k, __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]));
           }
         }
       }

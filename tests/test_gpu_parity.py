@@ -255,8 +255,11 @@ def test_resume_from_factor_checkpoint(prec):
         L1 = [t.cpu().numpy() for t in s.lowrank()]
     assert code0 == code1 == P.OK
     assert st1[0]["k"] == ck and st1[-1]["k"] == st0[-1]["k"]
-    # same iterates up to rounding (Trim and the bases are recomputed from the checkpoint)
-    assert [x["err"] for x in st1] == pytest.approx([x["err"] for x in st0[ck:]], rel=1e-3)
+    # same iterates up to rounding (Trim and the bases are recomputed from the checkpoint); in
+    # single precision the two runs' iterates differ by ~1e-7 relative, which moves err_k by
+    # up to ~1e-8 absolute
+    assert [x["err"] for x in st1] == pytest.approx([x["err"] for x in st0[ck:]], rel=1e-3,
+                                                    abs=0.0 if prec == "fp64" else 1e-7)
     A, B = [(U * s) @ V.T for U, s, V in (L0, L1)]
     assert rel_fro(B, A) < (1e-9 if prec == "fp64" else 1e-5)
 
