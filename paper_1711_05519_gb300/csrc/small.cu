@@ -449,10 +449,18 @@ __device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_swee
           // (one square root and one division); c = 1 / sqrt(1 + t^2) from the hardware
           // estimate and one Newton step y <- y (3 - x y^2) / 2.  The operands are column sums of
           // a matrix scaled to max |M_ij| = 1, so d^2 + 4 gamma^2 cannot overflow.
+          // t only has to zero gamma to a few ulps (the next sweep takes what is left), so the
+          // square root and the division are the fast hardware approximations; c is refined
+          // so that c^2 + s^2 = c^2 (1 + t^2) = 1 to rounding and the rotations stay orthogonal.
           const float d = sb - sa, g2 = 2.f * sg;
-          const float h = sqrtf(fmaf(d, d, g2 * g2));
-          tt = g2 / (fabsf(d) + h);
-          tt = (d < 0.f) ? -tt : tt;
+          const float e2 = fmaf(d, d, g2 * g2);
+          if (e2 > 1e-36f) {  // else both columns are below 1e-18: left as they are
+            const float h = e2 * rsqrtf(e2);
+            tt = __fdividef(g2, fabsf(d) + h);
+            tt = (d < 0.f) ? -tt : tt;
+          } else {
+            tt = 0.f;
+          }
           const float x1 = fmaf(tt, tt, 1.f);
           const float y0 = rsqrtf(x1);
           c = y0 * fmaf(-0.5f * x1 * y0, y0, 1.5f);
