@@ -85,6 +85,7 @@ struct rpca_ctx {
   int4* d_rect = nullptr;      // its tables on the device
   int4* d_ids = nullptr;
   int* d_p1nsl = nullptr;
+  float* tfac = nullptr;  // T_u, T_v from the tensor-core pass for the update (TcPassArgs)
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
   uint8_t *wop[2] = {nullptr, nullptr}, *vop[2] = {nullptr, nullptr}, *vtop[2] = {nullptr, nullptr},
           *utop[2] = {nullptr, nullptr};
@@ -124,7 +125,7 @@ void free_workspace(rpca_ctx* c) {
                    &c->Down, &c->Dhl, (void**)&c->wop[0], (void**)&c->vop[0], (void**)&c->vtop[0],
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
                    (void**)&c->utop[1], (void**)&c->masks, (void**)&c->chgP,
-                   (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl};
+                   (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl, (void**)&c->tfac};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -263,6 +264,11 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.mask_wr = c->mask_words;
     t.chgP = a.chgP;
     t.partial = a.partial;
+    t.tgram = static_cast<const float*>(c->part);
+    t.tnb = c->small_grid;
+    t.tw = c->r;
+    t.tcta = c->plan.min_cta;
+    t.tfac = init ? nullptr : c->tfac;
     CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
   } else {
     CK(launch_fused_pass(c->prec, R, a, c->stream));
@@ -350,6 +356,11 @@ bool tc_plan(int TR, int TC, int nsm, int max_ct, TcPlan* out) {
       rt += h;
     }
     out->ncta = (int)out->rect.size();
+    out->min_cta = 0;
+    for (int i = 1; i < out->ncta; ++i) {
+      const int4 a = out->rect[i], b = out->rect[out->min_cta];
+      if ((a.y - a.x) * (a.w - a.z) < (b.y - b.x) * (b.w - b.z)) out->min_cta = i;
+    }
     out->T = (int)T;
     return out->ct_max <= max_ct;
   }
@@ -399,6 +410,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.n_p1 = g.n_p1;
   a.n_p2 = g.n_p2;
   a.p1_nsl = use_tc(c, R) ? c->d_p1nsl : nullptr;
+  a.tfac = (mode == SM_UPDATE && c->tc_iter) ? c->tfac : nullptr;
   a.n_cta = g.n_cta;
   a.P1 = c->P1;
   a.P2 = c->P2;
@@ -628,6 +640,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       CK(cudaMalloc((void**)&c->d_rect, sizeof(int4) * nc));
       CK(cudaMalloc((void**)&c->d_ids, sizeof(int4) * nc));
       CK(cudaMalloc((void**)&c->d_p1nsl, sizeof(int) * c->TR));
+      CK(cudaMalloc((void**)&c->tfac, sizeof(float) * 1024));
       CK(cudaMemcpy(c->d_rect, c->plan.rect.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_p1nsl, c->plan.p1_nsl.data(), sizeof(int) * c->TR, cudaMemcpyHostToDevice));

@@ -128,6 +128,13 @@ struct TcPassArgs {
   long long mask_wr;
   unsigned long long* chgP;
   int partial;  // as in PassArgs (not together with masks)
+  // T factors for the update that follows (null: not computed), by CTA tcta: the Gram
+  // partials of the trimmed factors (the small kernel's slots 6, 7: [slot][tnb blocks][256]
+  // FP32, tw x tw) and the output [1024]: T_u, T_v (row-major, leading dimension tw) at 0 and
+  // 256, the reduced Gram matrices (scratch) from 512
+  const float* tgram;
+  int tnb, tw, tcta;
+  float* tfac;
 };
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
@@ -140,6 +147,7 @@ struct TcPlan {
   std::vector<int4> rect;
   std::vector<int4> ids;
   std::vector<int> p1_nsl;
+  int min_cta = 0;  // a CTA with the fewest tiles
 };
 bool tc_pass_supported(int R);
 // image layout (8 or 16) of the tensor-core pass for compiled rank R, and the most column
@@ -182,6 +190,8 @@ struct SmallArgs {
   int prec;
   int n_p1, n_p2, n_cta;  // partial slices and CTA count of the pass that ran
   const int* p1_nsl;      // tensor-core pass: Y1 slices of each 128-row tile (null: n_p1 everywhere)
+  const float* tfac;      // SM_UPDATE after a tensor-core pass: T_u, T_v computed by that pass
+                          // (TcPassArgs::tfac); null: the update computes them
   const void* P1;
   const void* P2;
   const double* resP;

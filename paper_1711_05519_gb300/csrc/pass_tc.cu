@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "factor.cuh"
 #include "tc_images.cuh"
 #include "tc_util.cuh"
 
@@ -129,6 +130,9 @@ struct TcArgs {
   unsigned long long* nnzP;
   unsigned* masks;
   long long mask_wr;
+  const float* tgram;
+  int tnb, tw, tcta;
+  float* tfac;
   unsigned long long* chgP;
 };
 
@@ -398,6 +402,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const int e = warp - 4, grp = e >> 3, gq = e >> 2;
     const int q = warp & 3, h = (e >> 2) & 1;
     const int rowl = 32 * q + lane;
+    const bool tcta = cta == a.tcta && a.tfac != nullptr;
     {
       // zero this CTA's columns of the group's two Y2 slices before the first add (the adds
       // come at least kTcY2Chunk row tiles later, after the barrier below)
@@ -407,7 +412,32 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         const int col = ct0 * BN + rem / a.R;
         if (col < a.n) a.P2[((size_t)(p2base + part) * a.n + col) * a.R + rem % a.R] = 0.f;
       }
+      if (tcta) {
+        // T factors for the update that follows, in the CTA with the fewest tiles while the
+        // first tile is on its way: T_u and T_v (U~ = A~ T_u, V~ = B~ T_v, the orthonormal
+        // bases of Section 2.1 by CholeskyQR) of the trimmed factors A~, B~ this pass reads,
+        // from the Gram partials that the kernel which trimmed them left (per block of that
+        // kernel).  Sums: warp e takes entries e, e + 16, ... of the two Gram matrices, each
+        // lane the blocks lane, lane + 32, ... in order, then a fixed shuffle tree.
+        const int w = a.tw, nb = a.tnb, ne = 2 * w * w;
+        for (int q0 = e; q0 < ne; q0 += EPI_WARPS) {
+          const int sd = q0 / (w * w), pe = q0 % (w * w);
+          const float* src = a.tgram + (size_t)(6 + sd) * nb * 256 + pe;
+          float v = 0.f;
+          for (int b = lane; b < nb; b += 32) v += src[(size_t)b * 256];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) a.tfac[512 + q0] = v;  // the reduced Gram matrices, scratch
+        }
+      }
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS) : "memory");
+      if (tcta && e < 2) {
+        const int w = a.tw;
+        float g[RK];
+#pragma unroll
+        for (int k = 0; k < RK; ++k) g[k] = (lane < w && k < w) ? a.tfac[512 + e * w * w + k * w + lane] : 0.f;
+        fac::chol_cols<float, RK>(g, w, nullptr, a.tfac + e * 256);
+      }
     }
     const float zeta = static_cast<float>(a.st->zeta);
     const float invp = PO ? static_cast<float>(a.st->inv_p) : 1.f;
@@ -712,6 +742,11 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.nnzP = p.nnzP;
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
+  a.tgram = p.tgram;
+  a.tnb = p.tnb;
+  a.tw = p.tw;
+  a.tcta = p.tcta;
+  a.tfac = p.tfac;
   a.chgP = p.chgP;
   if (a.masks && (!a.chgP || a.mask_wr < 256ll * a.TR * a.TC || p.partial)) return cudaErrorInvalidValue;
   const CUtensorMap& lo = dm ? *dmap_lo : *dmap;

@@ -39,6 +39,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "factor.cuh"
 #include "mlp.cuh"
 #include "tc_images.cuh"
 #include "tc_util.cuh"
@@ -46,6 +47,8 @@
 namespace rpca {
 
 namespace {
+
+using fac::rsqrt_d;
 
 constexpr int ST = 256;             // threads per block
 constexpr int MW = 16;              // max width of the tall-skinny arrays
@@ -76,20 +79,6 @@ struct Smem {
   int pairs[32 * 32];      // Jacobi round-robin partner of each lane in each round
   int ok;
 };
-
-// 1 / sqrt(x) for x > 0 in double precision: the single-precision estimate refined by two
-// Newton-Raphson steps y <- y (3 - x y^2) / 2 (each roughly doubles the correct bits).  Double
-// square roots and divisions are long-latency on this part; this takes a few fused
-// multiply-adds.  Arguments outside the single-precision range take the library routine.
-__device__ __forceinline__ double rsqrt_d(double x) {
-  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  double h = 0.5 * x;
-  y = y * fma(-h * y, y, 1.5);
-  y = y * fma(-h * y, y, 1.5);
-  return y;
-}
-__device__ __forceinline__ float rsqrt_d(float x) { return 1.0f / sqrtf(x); }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -255,73 +244,16 @@ __device__ __noinline__ void reduce_slots(const void* part, int slot0, int ns, i
   }
 }
 
-// R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix (w <= WM),
-// by one warp in the working precision, in registers: lane l holds column l.  G is scaled to
-// unit diagonal first, G^ = D^-1/2 G D^-1/2; a pivot of G^ at or below 1e-6 (float) or 1e-14
-// (double), a direction lost to rounding, gives a zero row of R and a zero column of T.  Then
-// R = R^ D^1/2 and T = D^-1/2 R^-1, column l of R^-1 by back substitution in lane l.
-// In double precision the square roots and divisions are the Newton-refined rsqrt_d.
+// R (upper, R^T R = G) and T (X T = Q for X = Q R, upper) of a w x w Gram matrix G (w <= WM,
+// row-major, leading dimension w) by one warp (fac::chol_cols).  A real call: the update runs
+// it several times per launch from one copy of its code.
 template <typename T, int WM>
 __device__ __noinline__ void factor_warp(const T* G, int w, T* R, T* Tm) {
   const int l = threadIdx.x & 31;
-  const T tiny = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
-  const T gll = (l < w) ? G[l * w + l] : T(0);
-  const T il = (l < w && gll > T(0)) ? rsqrt_d(gll) : T(0);
-  const T dl = gll * il;
-  T a[WM];  // column l of the working matrix
+  T g[WM];
 #pragma unroll
-  for (int k = 0; k < WM; ++k) {
-    const T ik = __shfl_sync(FULL, il, k);
-    a[k] = (l < w && k < w) ? G[k * w + l] * (ik * il) : T(0);
-  }
-  // right-looking Cholesky: step j fixes row j of R^ (a[j] of every lane becomes R^_jl)
-  T pinv = T(0);  // this lane's 1 / R^_ll
-#pragma unroll
-  for (int j = 0; j < WM; ++j) {
-    if (j < w) {
-      const T d = __shfl_sync(FULL, a[j], j);
-      const bool good = d > tiny;
-      const T inv = good ? rsqrt_d(d) : T(0);
-      const T rjj = d * inv;
-      if (l == j) pinv = inv;
-      const T rjl = (l > j) ? a[j] * inv : ((l == j) ? rjj : T(0));
-      a[j] = rjl;
-#pragma unroll
-      for (int k = j + 1; k < WM; ++k) {
-        const T rjk = __shfl_sync(FULL, rjl, k);
-        a[k] = fma(-rjk, rjl, a[k]);
-      }
-    }
-  }
-  // R^ to shared memory (for the back substitutions), rows k <= l of column l
-#pragma unroll
-  for (int k = 0; k < WM; ++k)
-    if (l < w && k < w) R[k * w + l] = (k <= l) ? a[k] : T(0);
-  __syncwarp();
-  // 1 / R^_ii from lane i
-  const T rd = (l < w) ? pinv : T(0);
-  // column l of R^-1: t_i = (delta_il - sum_{k=i+1}^{l} R^_ik t_k) / R^_ii for i = l .. 0
-  T t[WM];
-#pragma unroll
-  for (int i = WM - 1; i >= 0; --i) {
-    const T ri = __shfl_sync(FULL, rd, i);
-    T sacc = (i == l) ? T(1) : T(0);
-#pragma unroll
-    for (int k = i + 1; k < WM; ++k)
-      if (k <= l && k < w) sacc = fma(-R[i * w + k], t[k], sacc);
-    t[i] = (i <= l && i < w) ? sacc * ri : T(0);
-  }
-  __syncwarp();
-  // T = D^-1/2 R^-1 (row i scaled by 1 / d_i), R = R^ D^1/2 (column l scaled by d_l)
-#pragma unroll
-  for (int i = 0; i < WM; ++i) {
-    const T ii = __shfl_sync(FULL, il, i);
-    if (l < w && i < w) {
-      Tm[i * w + l] = t[i] * ii;
-      R[i * w + l] = (i <= l) ? a[i] * dl : T(0);
-    }
-  }
-  __syncwarp();
+  for (int k = 0; k < WM; ++k) g[k] = (l < w && k < w) ? G[k * w + l] : T(0);
+  fac::chol_cols<T, WM>(g, w, R, Tm);
 }
 
 template <typename T, int WM>
@@ -957,7 +889,8 @@ __device__ __forceinline__ void gram_put_h(const T (&acc)[2], int w, void* part,
 
 // ---------------------------------------------------------------------------------------
 // One update of Algorithm 1 after the fused pass, in the working precision:
-//   start: err_k, the stop test, T_u and T_v (above)
+//   start: err_k, the stop test, T_u and T_v (above; after a tensor-core pass, which computes
+//          them beside its tiles, only loaded)
 //   A    : rows of Y1 = X1 T_v, U~ = A~ T_u, Y2 = X2 T_u, V~ = B~ T_v; partials of C = U~^T Y1
 //   -- grid barrier --
 //   A2   : W1 = Y1 - U~ C and W2 = Y2 - V~ C^T (the projections of Section 2.1) and their
@@ -1016,7 +949,15 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     if (blockIdx.x == 0 && t == 0) st->done = 1;
     return;
   }
-  trimmed_t_factors<T, WM>(a, sh);
+  if (a.tfac) {
+    for (int e = t; e < 2 * WM * WM; e += ST) {
+      const int s2 = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
+      sh.tm[s2][q * WM + c] = (q < r && c < r) ? (T)a.tfac[s2 * 256 + q * r + c] : T(0);
+    }
+    __syncthreads();
+  } else {
+    trimmed_t_factors<T, WM>(a, sh);
+  }
 
   // A: own rows of Y1, U~ (side 0) and Y2, V~ (side 1), both sides at once; partial of
   // C = U~^T Y1 (slot 0)
