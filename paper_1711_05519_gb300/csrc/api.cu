@@ -410,6 +410,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.n_p1 = g.n_p1;
   a.n_p2 = g.n_p2;
   a.p1_nsl = use_tc(c, R) ? c->d_p1nsl : nullptr;
+  a.R2 = use_tc(c, R) ? tc_image_rank(R) : R;
   a.tfac = (mode == SM_UPDATE && c->tc_iter) ? c->tfac : nullptr;
   a.n_cta = g.n_cta;
   a.P1 = c->P1;
@@ -608,8 +609,9 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     const Grid gs{(int)((n + pg.BW - 1) / pg.BW), (int)((m + pg.BH - 1) / pg.BH), 0};
     const Grid gt{c->plan.Bmax, c->plan.S2, c->plan.ncta};
     for (const Grid& g : {gs, gt}) {
+      const size_t R2 = (&g == &gt) ? (size_t)tc_image_rank(R) : (size_t)R;  // tensor-core rows padded
       p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
-      p2 = p2 > (size_t)g.n_p2 * n * R ? p2 : (size_t)g.n_p2 * n * R;
+      p2 = p2 > (size_t)g.n_p2 * n * R2 ? p2 : (size_t)g.n_p2 * n * R2;
     }
     ncta = ncta > (size_t)gs.n_p1 * gs.n_p2 ? ncta : (size_t)gs.n_p1 * gs.n_p2;
     ncta = ncta > (size_t)gt.n_cta ? ncta : (size_t)gt.n_cta;

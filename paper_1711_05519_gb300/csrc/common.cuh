@@ -118,8 +118,9 @@ struct TcPassArgs {
   const DevState* st;
   int* status;
   float* P1;     // [Bmax][m][R]: slice = index of the CTA within its row group
-  float* P2;     // [S2 = 2 A][n][R]: per row group, the Z_hi and the Z_lo part of Z^T U~ over
-                 // the group's rows (slices 2 a and 2 a + 1)
+  float* P2;     // [S2 = 2 A][n][RK]: per row group, the Z_hi and the Z_lo part of Z^T U~ over
+                 // the group's rows (slices 2 a and 2 a + 1), rows padded to the image rank RK
+                 // (tc_image_rank(R); the padding columns hold zeros)
   double* resP;  // [ncta]
   unsigned long long* nnzP;
   // support bitmasks as in PassArgs (null: not tracked), here two buffers of mask_wr words
@@ -190,6 +191,8 @@ struct SmallArgs {
   int prec;
   int n_p1, n_p2, n_cta;  // partial slices and CTA count of the pass that ran
   const int* p1_nsl;      // tensor-core pass: Y1 slices of each 128-row tile (null: n_p1 everywhere)
+  int R2;                 // row width of the Y2 partial slices (R; the image rank after a
+                          // tensor-core pass)
   const float* tfac;      // SM_UPDATE after a tensor-core pass: T_u, T_v computed by that pass
                           // (TcPassArgs::tfac); null: the update computes them
   const void* P1;

@@ -407,10 +407,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       // zero this CTA's columns of the group's two Y2 slices before the first add (the adds
       // come at least kTcY2Chunk row tiles later, after the barrier below)
       const int et = tid - 128, ncol = nct * BN;
-      for (int e2 = et; e2 < 2 * ncol * a.R; e2 += EPI_THREADS) {
-        const int part = e2 / (ncol * a.R), rem = e2 % (ncol * a.R);
-        const int col = ct0 * BN + rem / a.R;
-        if (col < a.n) a.P2[((size_t)(p2base + part) * a.n + col) * a.R + rem % a.R] = 0.f;
+      for (int e2 = et; e2 < 2 * ncol * (RK / 4); e2 += EPI_THREADS) {
+        const int part = e2 / (ncol * (RK / 4)), rem = e2 % (ncol * (RK / 4));
+        const int col = ct0 * BN + rem / (RK / 4);
+        if (col < a.n)
+          reinterpret_cast<float4*>(a.P2 + ((size_t)(p2base + part) * a.n + col) * RK)[rem % (RK / 4)] =
+              make_float4(0.f, 0.f, 0.f, 0.f);
       }
       if (tcta) {
         // T factors for the update that follows, in the CTA with the fewest tiles while the
@@ -468,8 +470,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         // column halves, this warp's half of the components) before this tile's products
         // restart the accumulator, and add it into the group's Y2 partial (slice p2base for the
         // Z_hi rows, p2base + 1 for the Z_lo rows; each (slice, column) belongs to this CTA
-        // alone, zeroed before the first tile) with fire-and-forget atomic adds, so no warp
-        // waits for the partial's previous value.  Consecutive chunks of a column tile are read
+        // alone, zeroed before the first tile) with fire-and-forget vector atomic adds, so no
+        // warp waits for the partial's previous value.  Consecutive chunks of a column tile are read
         // out at least kTcY2Chunk row tiles apart.
         const int c = rtl / G2;
         if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
@@ -485,12 +487,18 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
         const int col = (ct0 + ctl) * BN + y2_row_col<DM>(rowl);
         if (col < a.n) {
-          float* dst = a.P2 + ((size_t)(p2base + y2_row_part<DM>(rowl)) * a.n + col) * a.R;
+          // components k = h RK/2 + j (register indices fixed at compile time), 4 per vector add
+          float4* dst = reinterpret_cast<float4*>(a.P2 + ((size_t)(p2base + y2_row_part<DM>(rowl)) * a.n + col) * RK +
+                                                  h * (RK / 2));
 #pragma unroll
-          for (int j = 0; j < RK / 2; ++j) {  // k = h RK/2 + j (register indices fixed at compile time)
-            const int k = h * (RK / 2) + j;
-            const uint32_t x = h ? yv[RK / 2 + j] : yv[j], y = h ? yv[RK + RK / 2 + j] : yv[RK + j];
-            if (k < a.R) atomicAdd(dst + k, __uint_as_float(x) + __uint_as_float(y));
+          for (int j = 0; j < RK / 2; j += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t x = h ? yv[RK / 2 + j + u] : yv[j + u], y = h ? yv[RK + RK / 2 + j + u] : yv[RK + j + u];
+              v[u] = __uint_as_float(x) + __uint_as_float(y);
+            }
+            atomicAdd(dst + j / 4, make_float4(v[0], v[1], v[2], v[3]));
           }
         }
       }
@@ -633,10 +641,13 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           tmem_wait_ld();
           const int col = (ct0 + ctl) * BN + col0;
           if (col < a.n) {
-            float* dst = a.P2 + ((size_t)slice * a.n + col) * a.R;
+            float4* dst = reinterpret_cast<float4*>(a.P2 + ((size_t)slice * a.n + col) * RK);
 #pragma unroll
-            for (int k = 0; k < RK; ++k)
-              if (k < a.R) atomicAdd(dst + k, __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]));
+            for (int k = 0; k < RK; k += 4)
+              atomicAdd(dst + k / 4, make_float4(__uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]),
+                                                 __uint_as_float(yv[k + 1]) + __uint_as_float(yv[RK + k + 1]),
+                                                 __uint_as_float(yv[k + 2]) + __uint_as_float(yv[RK + k + 2]),
+                                                 __uint_as_float(yv[k + 3]) + __uint_as_float(yv[RK + k + 3])));
           }
         }
       }

@@ -983,7 +983,8 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         T x[WM], f[WM];
         load_row<T, WM>(F, i, a.Rit, f);
         const int nsl = (!side && a.p1_nsl) ? a.p1_nsl[i >> 7] : nsl_all;
-        reduce_row<T, WM>(Pp, nsl, (size_t)rows * a.R, i, a.R, r, x);
+        const int Rw = side ? a.R2 : a.R;  // row width of the partial slices
+        reduce_row<T, WM>(Pp, nsl, (size_t)rows * Rw, i, Rw, r, x);
         row_times<T, WM>(x, sh.tm[1 - side], y);  // X1 T_v, X2 T_u
         row_times<T, WM>(f, sh.tm[side], b);      // A~ T_u, B~ T_v
         store_row<T, WM>(Yo, i, r, y);
@@ -1328,8 +1329,8 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
       zero_row<T, WM>(u);
       if (i < hi) {
         reduce_row<T, WM>(static_cast<const T*>(side ? a.P2 : a.P1),
-                          side ? a.n_p2 : (a.p1_nsl ? a.p1_nsl[i >> 7] : a.n_p1), (size_t)rows * a.R, i,
-                          a.R, w, y);
+                          side ? a.n_p2 : (a.p1_nsl ? a.p1_nsl[i >> 7] : a.n_p1),
+                          (size_t)rows * (side ? a.R2 : a.R), i, side ? a.R2 : a.R, w, y);
         store_row<T, WM>(side ? Y2 : Y1, i, w, y);
         if (!side) load_row<T, WM>(Ut, i, w, u);
       }
