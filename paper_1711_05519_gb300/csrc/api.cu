@@ -65,7 +65,7 @@ struct rpca_ctx {
   unsigned long long* nnzP = nullptr;
   DevState* st = nullptr;
   DevStats* stats = nullptr;
-  int* h_flags = nullptr;  // pinned: done, k, status, conv
+  int* h_flags = nullptr;  // pinned: k, done, status, conv, use_lo, emit, emit_k, pad
   unsigned long long *rowcnt = nullptr, *rowoff = nullptr;
   bool ready = false;
   // learned threshold schedule: network parameters (mlp.cuh), unrolled depth, support
@@ -86,6 +86,7 @@ struct rpca_ctx {
   int4* d_ids = nullptr;
   int* d_p1nsl = nullptr;
   float* tfac = nullptr;  // T_u, T_v from the tensor-core pass for the update (TcPassArgs)
+  unsigned* swords = nullptr;  // support words of the last pass predicted to be final (TcPassArgs)
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
   uint8_t *wop[2] = {nullptr, nullptr}, *vop[2] = {nullptr, nullptr}, *vtop[2] = {nullptr, nullptr},
           *utop[2] = {nullptr, nullptr};
@@ -125,7 +126,8 @@ void free_workspace(rpca_ctx* c) {
                    &c->Down, &c->Dhl, (void**)&c->wop[0], (void**)&c->vop[0], (void**)&c->vtop[0],
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
                    (void**)&c->utop[1], (void**)&c->masks, (void**)&c->chgP,
-                   (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl, (void**)&c->tfac};
+                   (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl, (void**)&c->tfac,
+                   (void**)&c->swords};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -264,6 +266,9 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.mask_wr = c->mask_words;
     t.chgP = a.chgP;
     t.partial = a.partial;
+    t.swords = (!init && !c->dmode) ? c->swords : nullptr;
+    t.nw = 2 * c->TC;
+    t.emit_k = &c->st->emit_k;
     t.tgram = static_cast<const float*>(c->part);
     t.tnb = c->small_grid;
     t.tw = c->r;
@@ -411,6 +416,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.n_p2 = g.n_p2;
   a.p1_nsl = use_tc(c, R) ? c->d_p1nsl : nullptr;
   a.R2 = use_tc(c, R) ? tc_image_rank(R) : R;
+  a.emit_ok = (c->swords && c->tc_iter && !c->dmode) ? 1 : 0;
   a.tfac = (mode == SM_UPDATE && c->tc_iter) ? c->tfac : nullptr;
   a.n_cta = g.n_cta;
   a.P1 = c->P1;
@@ -454,12 +460,13 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
 
 int read_flags(rpca_ctx* c) {
   prof_break(c);
-  CK(cudaMemcpyAsync(c->h_flags, &c->st->k, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_flags, &c->st->k, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return RPCA_OK;
 }
-// DevState layout: k, done, status, conv are consecutive ints.
+// DevState layout: k, done, status, conv, use_lo, emit, emit_k are consecutive ints.
 inline int flag_k(const rpca_ctx* c) { return c->h_flags[0]; }
+inline int flag_emit_k(const rpca_ctx* c) { return c->h_flags[6]; }
 inline int flag_done(const rpca_ctx* c) { return c->h_flags[1]; }
 inline int flag_status(const rpca_ctx* c) { return c->h_flags[2]; }
 inline int flag_conv(const rpca_ctx* c) { return c->h_flags[3]; }
@@ -608,11 +615,10 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
     const PassGeom pg = pass_geometry(c->prec, R);
     const Grid gs{(int)((n + pg.BW - 1) / pg.BW), (int)((m + pg.BH - 1) / pg.BH), 0};
     const Grid gt{c->plan.Bmax, c->plan.S2, c->plan.ncta};
-    for (const Grid& g : {gs, gt}) {
-      const size_t R2 = (&g == &gt) ? (size_t)tc_image_rank(R) : (size_t)R;  // tensor-core rows padded
-      p1 = p1 > (size_t)g.n_p1 * m * R ? p1 : (size_t)g.n_p1 * m * R;
-      p2 = p2 > (size_t)g.n_p2 * n * R2 ? p2 : (size_t)g.n_p2 * n * R2;
-    }
+    // partial slices: SIMT pass [n_p][rows][R]; tensor-core pass Y1 [Bmax][m][R] and Y2
+    // [S2][n][RK] (rows padded to the image rank)
+    p1 = std::max(p1, std::max((size_t)gs.n_p1 * m * R, (size_t)gt.n_p1 * m * R));
+    p2 = std::max(p2, std::max((size_t)gs.n_p2 * n * R, (size_t)gt.n_p2 * n * (size_t)tc_image_rank(R)));
     ncta = ncta > (size_t)gs.n_p1 * gs.n_p2 ? ncta : (size_t)gs.n_p1 * gs.n_p2;
     ncta = ncta > (size_t)gt.n_cta ? ncta : (size_t)gt.n_cta;
   }
@@ -643,6 +649,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       CK(cudaMalloc((void**)&c->d_ids, sizeof(int4) * nc));
       CK(cudaMalloc((void**)&c->d_p1nsl, sizeof(int) * c->TR));
       CK(cudaMalloc((void**)&c->tfac, sizeof(float) * 1024));
+      if (c->tc_iter && !c->dmode) CK(cudaMalloc((void**)&c->swords, sizeof(unsigned) * (size_t)m * 2 * c->TC));
       CK(cudaMemcpy(c->d_rect, c->plan.rect.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_p1nsl, c->plan.p1_nsl.data(), sizeof(int) * c->TR, cudaMemcpyHostToDevice));
@@ -701,6 +708,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   h.zeta = INFINITY;
   h.split_switch = c->split ? (c->p.split_switch > 0 ? c->p.split_switch : 1e-2) : 0.0;
   h.inv_p = inv_p;
+  h.emit_k = -1;
   CK(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
 
   // Algorithm 3.  Phase A: sigma_1(D) with L = 0 and no threshold; phase B: top-r SVD of
@@ -878,6 +886,8 @@ int rpca_set_lowrank(rpca_ctx* c, const double* U, const double* sigma, const do
   CK(cudaMemcpyAsync(&c->st->zeta, &zeta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(&c->st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(&c->st->use_lo, &use_lo, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  const int no_emit[2] = {0, -1};  // emit, emit_k: no support words for this iterate yet
+  CK(cudaMemcpyAsync(&c->st->emit, no_emit, sizeof(no_emit), cudaMemcpyHostToDevice, c->stream));
   // Trim (Algorithm 2), orthonormal bases and the copies (and images) read by the next pass
   int st = run_small(c, small_args(c, SM_PREPARE, c->Rr));
   if (st) return st;
@@ -899,6 +909,7 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
     CK(cudaMalloc((void**)&c->rowoff, sizeof(unsigned long long) * (c->m + 1)));
   }
   ExtractArgs a;
+  memset(&a, 0, sizeof(a));
   a.D = c->D;
   a.ld = c->ld;
   a.m = (int)c->m;
@@ -911,9 +922,17 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
   a.idx = (long long*)idx;
   a.val = val;
   a.vec = c->vec;
+  // S_k from the support words when the last pass wrote them for the iterate held (FP32 D,
+  // tensor-core pass): D is then read only at the support; else two passes over D
+  int st;
+  if ((st = read_flags(c))) return st;
+  const bool from_words = c->swords != nullptr && flag_emit_k(c) == flag_k(c);
   prof_break(c);
   prof_mark(c, false, true);
-  CK(launch_extract_count(c->prec, c->Rr, a, c->stream));
+  if (from_words)
+    CK(launch_words_rowcnt(c->swords, 2 * c->TC, (int)c->m, c->rowcnt, c->stream));
+  else
+    CK(launch_extract_count(c->prec, c->Rr, a, c->stream));
   prof_mark(c, false, false);
   prof_mark(c, false, true);
   CK(launch_scan_rows(c->rowcnt, c->rowoff, (int)c->m, c->stream));
@@ -928,7 +947,10 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
     return RPCA_ERR_CAPACITY;
   }
   prof_mark(c, false, true);
-  CK(launch_extract_write(c->prec, c->Rr, a, c->stream));
+  if (from_words)
+    CK(launch_extract_words_f32(c->Rr, a, c->swords, 2 * c->TC, c->stream));
+  else
+    CK(launch_extract_write(c->prec, c->Rr, a, c->stream));
   prof_mark(c, false, false);
   CK(cudaStreamSynchronize(c->stream));
   prof_collect(c, 0);

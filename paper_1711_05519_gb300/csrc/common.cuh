@@ -32,6 +32,8 @@ struct DevState {
   int status;            // 0 or an rpca_status code raised on the device
   int conv;              // initialisation finished (both subspace iterations converged)
   int use_lo;            // bf16 split storage of D: the passes also read the lo part
+  int emit;              // the next tensor-core pass writes its support words (predicted last)
+  int emit_k;            // k of the last pass that wrote them (-1: none)
   int pad1;
   double split_switch;   // bf16 split storage: set use_lo once err_k falls below this
   double inv_p;          // partial observation: m n / |observed entries| (1 otherwise)
@@ -129,6 +131,12 @@ struct TcPassArgs {
   long long mask_wr;
   unsigned long long* chgP;
   int partial;  // as in PassArgs (not together with masks)
+  // support words of S_k (FP32 D only; null: never): when DevState.emit is set the pass
+  // writes, per row and 32 columns, the bit mask of |D_ij - L_ij| > zeta_k (row-major,
+  // nw = 2 TC words per row, word j = columns 32 j .. 32 j + 31) and *emit_k = k
+  unsigned* swords;
+  int nw;
+  int* emit_k;
   // T factors for the update that follows (null: not computed), by CTA tcta: the Gram
   // partials of the trimmed factors (the small kernel's slots 6, 7: [slot][tnb blocks][256]
   // FP32, tw x tw) and the output [1024]: T_u, T_v (row-major, leading dimension tw) at 0 and
@@ -191,6 +199,7 @@ struct SmallArgs {
   int prec;
   int n_p1, n_p2, n_cta;  // partial slices and CTA count of the pass that ran
   const int* p1_nsl;      // tensor-core pass: Y1 slices of each 128-row tile (null: n_p1 everywhere)
+  int emit_ok;            // SM_UPDATE: the iteration's pass can write the support words
   int R2;                 // row width of the Y2 partial slices (R; the image rank after a
                           // tensor-core pass)
   const float* tfac;      // SM_UPDATE after a tensor-core pass: T_u, T_v computed by that pass
@@ -238,6 +247,10 @@ cudaError_t run_wait_selftest(int* mbar_status, int* grid_status);
 int small_grid_size(int device);
 
 cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s);
+// Support of S_k from the support words of the tensor-core pass (TcPassArgs::swords): per-row
+// counts, then (after the scan) the ordered write of indices and values S_ij = D_ij - L_ij.
+cudaError_t launch_words_rowcnt(const unsigned* words, int nw, int m, unsigned long long* rowcnt, cudaStream_t s);
+cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, int nw, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double* src, long long ld_src, float* dst, int m, int n,
                                       cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float* src, long long ld_src, double* dst, int m, int n,

@@ -83,7 +83,26 @@ __global__ void __launch_bounds__(1024) scan_rows(const unsigned long long* __re
   if (t == 1023) off[m] = part[1023];
 }
 
+// Row counts of the support words: one warp per row.
+__global__ void __launch_bounds__(256) words_rowcnt(const unsigned* __restrict__ words, int nw, int m,
+                                                    unsigned long long* __restrict__ rowcnt) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= m) return;
+  const unsigned* w = words + (size_t)row * nw;
+  unsigned c = 0;
+  for (int j = lane; j < nw; j += 32) c += __popc(w[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) rowcnt[row] = c;
+}
+
 }  // namespace
+
+cudaError_t launch_words_rowcnt(const unsigned* words, int nw, int m, unsigned long long* rowcnt, cudaStream_t s) {
+  words_rowcnt<<<(m + 7) / 8, 256, 0, s>>>(words, nw, m, rowcnt);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s) {
   scan_rows<<<1, 1024, 0, s>>>(cnt, off, m);

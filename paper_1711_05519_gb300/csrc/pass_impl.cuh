@@ -390,6 +390,58 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
   if (!WRITE && lane == 0) a.rowcnt[row] = cnt;
 }
 
+// The ordered write from the support words of the tensor-core pass (the bit of column j of
+// row i is set iff |D_ij - L_ij| > zeta_k in that pass): one warp per row, lane l the word
+// j0 + l; the values S_ij = D_ij - L_ij are rebuilt only at the support, so D is read only
+// where a 32-byte sector holds a support entry.  Offsets: the row's start (rowoff) plus an
+// exclusive scan of the words' bit counts.
+template <int R>
+__global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const unsigned* __restrict__ words, int nw) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= a.m) return;
+  const float* __restrict__ D = static_cast<const float*>(a.D);
+  const float* __restrict__ W = static_cast<const float*>(a.W);
+  const float* __restrict__ V = static_cast<const float*>(a.V);
+  float w[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) w[k] = W[(long long)row * R + k];
+  const unsigned long long base = a.rowoff[row];
+  unsigned carry = 0;
+  for (int j0 = 0; j0 < nw; j0 += 32) {
+    const int j = j0 + lane;
+    unsigned wd = (j < nw) ? words[(size_t)row * nw + j] : 0u;
+    const unsigned c = __popc(wd);
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    unsigned long long pos = base + carry + (incl - c);
+    while (wd) {
+      const int b = __ffs(wd) - 1;
+      wd &= wd - 1u;
+      const int col = 32 * j + b;
+      if (col >= a.n) break;  // never set: columns past n read as zero in the pass
+      float v[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = V[(long long)col * R + k];
+      const float rr = D[(long long)row * a.ld + col] - rebuild<float, R>(w, v);
+      a.idx[pos] = (long long)row * a.n + col;
+      a.val[pos] = static_cast<double>(rr);
+      ++pos;
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+template <int R>
+cudaError_t launch_extract_words_t(const ExtractArgs& a, const unsigned* words, int nw, cudaStream_t s) {
+  extract_words_kernel<R><<<(a.m + 7) / 8, 256, 0, s>>>(a, words, nw);
+  return cudaGetLastError();
+}
+
 template <typename T, int R>
 cudaError_t launch_extract_count_t(const ExtractArgs& a, cudaStream_t s) {
   extract_kernel<T, R, false><<<(a.m + 7) / 8, 256, 0, s>>>(a);

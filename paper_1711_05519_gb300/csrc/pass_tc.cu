@@ -113,6 +113,11 @@ static_assert(B_Y2FREE + CT_BARS <= NBAR, "barrier slots");
 
 constexpr uint32_t kErrTimeout = 6;
 
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
+
 struct TcArgs {
   int m, n, R;
   int ncta, TR, TC;
@@ -130,6 +135,9 @@ struct TcArgs {
   unsigned long long* nnzP;
   unsigned* masks;
   long long mask_wr;
+  unsigned* swords;
+  int nw;
+  int* emit_k;
   const float* tgram;
   int tnb, tw, tcta;
   float* tfac;
@@ -403,6 +411,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const int q = warp & 3, h = (e >> 2) & 1;
     const int rowl = 32 * q + lane;
     const bool tcta = cta == a.tcta && a.tfac != nullptr;
+    // this pass writes the support words of S_k when the update before it predicted that it is
+    // the last one (FP32 D only)
+    const bool emit = DM == 0 && a.swords != nullptr && a.st->emit != 0;
+    if (emit && cta == 0 && tid == 128) *a.emit_k = a.st->k;
     {
       // zero this CTA's columns of the group's two Y2 slices before the first add (the adds
       // come at least kTcY2Chunk row tiles later, after the barrier below)
@@ -455,176 +467,192 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const long long mask_sz = a.mask_wr;
     unsigned* mask_new = MASK ? a.masks + ((a.st->k & 1) ? mask_sz : 0) : nullptr;
     const unsigned* mask_old = MASK ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
-    for (int t = grp; t < ntiles && !abort_flag; t += 2) {
-      const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
-      // support word of this thread's row and columns in the previous pass, loaded here so that
-      // its latency passes while the tile is waited for (used after Z is handed on)
-      long long mw = 0;
-      unsigned mold = 0;
-      if (MASK) {
-        mw = (((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl;
-        mold = mask_old[mw];
-      }
-      if (rtl % G2 == 0 && rtl > 0) {
-        // chunk c - 1 of column tile ctl's Y2 accumulator is complete: read it out (hi + lo
-        // column halves, this warp's half of the components) before this tile's products
-        // restart the accumulator, and add it into the group's Y2 partial (slice p2base for the
-        // Z_hi rows, p2base + 1 for the Z_lo rows; each (slice, column) belongs to this CTA
-        // alone, zeroed before the first tile) with fire-and-forget vector atomic adds, so no
-        // warp waits for the partial's previous value.  Consecutive chunks of a column tile are read
-        // out at least kTcY2Chunk row tiles apart.
-        const int c = rtl / G2;
-        if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
+    // the tile loop in two copies, without and with the support words, so that the plain
+    // passes keep their registers
+    auto tile_loop = [&](auto emit_c) {
+      constexpr bool EMIT = decltype(emit_c)::value;
+      for (int t = grp; t < ntiles && !abort_flag; t += 2) {
+        const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
+        // support word of this thread's row and columns in the previous pass, loaded here so that
+        // its latency passes while the tile is waited for (used after Z is handed on)
+        long long mw = 0;
+        unsigned mold = 0;
+        if (MASK) {
+          mw = (((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl;
+          mold = mask_old[mw];
+        }
+        if (rtl % G2 == 0 && rtl > 0) {
+          // chunk c - 1 of column tile ctl's Y2 accumulator is complete: read it out (hi + lo
+          // column halves, this warp's half of the components) before this tile's products
+          // restart the accumulator, and add it into the group's Y2 partial (slice p2base for the
+          // Z_hi rows, p2base + 1 for the Z_lo rows; each (slice, column) belongs to this CTA
+          // alone, zeroed before the first tile) with fire-and-forget vector atomic adds, so no
+          // warp waits for the partial's previous value.  Consecutive chunks of a column tile are read
+          // out at least kTcY2Chunk row tiles apart.
+          const int c = rtl / G2;
+          if (!mbar_wait(&bar[B_Y2DONE + ctl], (c - 1) & 1)) {
+            fail(a, &abort_flag);
+            break;
+          }
+          tc_fence_after();
+          uint32_t yv[NY];
+          tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
+          const int col = (ct0 + ctl) * BN + y2_row_col<DM>(rowl);
+          if (col < a.n) {
+            // components k = h RK/2 + j (register indices fixed at compile time), 4 per vector add
+            float4* dst = reinterpret_cast<float4*>(a.P2 + ((size_t)(p2base + y2_row_part<DM>(rowl)) * a.n + col) * RK +
+                                                    h * (RK / 2));
+  #pragma unroll
+            for (int j = 0; j < RK / 2; j += 4) {
+              float v[4];
+  #pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const uint32_t x = h ? yv[RK / 2 + j + u] : yv[j + u], y = h ? yv[RK + RK / 2 + j + u] : yv[RK + j + u];
+                v[u] = __uint_as_float(x) + __uint_as_float(y);
+              }
+              atomicAdd(dst + j / 4, make_float4(v[0], v[1], v[2], v[3]));
+            }
+          }
+        }
+        if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
           fail(a, &abort_flag);
           break;
         }
         tc_fence_after();
-        uint32_t yv[NY];
-        tmem_ld_y<NY>(tmem + lane_base + TM_Y2 + ctl * NY, yv);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bar[B_Y2FREE + ctl]);
-        const int col = (ct0 + ctl) * BN + y2_row_col<DM>(rowl);
-        if (col < a.n) {
-          // components k = h RK/2 + j (register indices fixed at compile time), 4 per vector add
-          float4* dst = reinterpret_cast<float4*>(a.P2 + ((size_t)(p2base + y2_row_part<DM>(rowl)) * a.n + col) * RK +
-                                                  h * (RK / 2));
-#pragma unroll
-          for (int j = 0; j < RK / 2; j += 4) {
-            float v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t x = h ? yv[RK / 2 + j + u] : yv[j + u], y = h ? yv[RK + RK / 2 + j + u] : yv[RK + j + u];
-              v[u] = __uint_as_float(x) + __uint_as_float(y);
-            }
-            atomicAdd(dst + j / 4, make_float4(v[0], v[1], v[2], v[3]));
+        uint32_t lv[32];
+        tmem_ld32(tmem + lane_base + lb * BN + 32 * h, lv);
+        uint8_t* stg = sm + OFF_STAGE + s * STAGE_BYTES;
+        float z[32];
+        if (DM == 0) {
+          const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
+  #pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
+            z[4 * c + 0] = d4.x;
+            z[4 * c + 1] = d4.y;
+            z[4 * c + 2] = d4.z;
+            z[4 * c + 3] = d4.w;
           }
-        }
-      }
-      if (!mbar_wait(&bar[B_LFULL + lb], (t >> 1) & 1) || !mbar_wait(&bar[B_FULL + s], (t / NSTAGE) & 1)) {
-        fail(a, &abort_flag);
-        break;
-      }
-      tc_fence_after();
-      uint32_t lv[32];
-      tmem_ld32(tmem + lane_base + lb * BN + 32 * h, lv);
-      uint8_t* stg = sm + OFF_STAGE + s * STAGE_BYTES;
-      float z[32];
-      if (DM == 0) {
-        const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 d4 = *reinterpret_cast<const float4*>(drow + ((c ^ (rowl & 7)) << 4));
-          z[4 * c + 0] = d4.x;
-          z[4 * c + 1] = d4.y;
-          z[4 * c + 2] = d4.z;
-          z[4 * c + 3] = d4.w;
-        }
-      } else {
-        // columns 32h .. 32h+31 of the bf16 row = 16-byte chunks 4h .. 4h+3 (8 values each)
-        const uint8_t* hrow = stg + rowl * 128;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int off = (((4 * h + c) ^ (rowl & 7)) & 7) << 4;
-          const uint4 hv = *reinterpret_cast<const uint4*>(hrow + off);
-          const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            z[8 * c + 2 * e2] = __uint_as_float(hw[e2] << 16);
-            z[8 * c + 2 * e2 + 1] = __uint_as_float(hw[e2] & 0xffff0000u);
-          }
-          if (use_lo) {
-            const uint4 lv4 = *reinterpret_cast<const uint4*>(hrow + D_BYTES / 2 + off);
-            const uint32_t lw[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
-#pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-              z[8 * c + 2 * e2] += __uint_as_float(lw[e2] << 16);
-              z[8 * c + 2 * e2 + 1] += __uint_as_float(lw[e2] & 0xffff0000u);
-            }
-          }
-        }
-      }
-      tmem_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
-      const float2 m1 = make_float2(-1.f, -1.f);
-      float rq = 0.f;
-      uint32_t bits = 0;
-#pragma unroll
-      for (int c = 0; c < 32; c += 2) {
-        const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
-        const float2 r2 = __ffma2_rn(l2, m1, make_float2(z[c], z[c + 1]));  // D - L, exactly rounded
-        const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;  // false for NaN
-        if (PO) {
-          const bool k0 = s0 || !(z[c] == z[c]), k1 = s1 || !(z[c + 1] == z[c + 1]);  // Z = L
-          rq = k0 ? rq : fmaf(r2.x, r2.x, rq);
-          rq = k1 ? rq : fmaf(r2.y, r2.y, rq);
-          z[c] = k0 ? l2.x : fmaf(r2.x, invp, l2.x);
-          z[c + 1] = k1 ? l2.y : fmaf(r2.y, invp, l2.y);
         } else {
-          rq = s0 ? rq : fmaf(r2.x, r2.x, rq);
-          rq = s1 ? rq : fmaf(r2.y, r2.y, rq);
-          z[c] = s0 ? l2.x : z[c];
-          z[c + 1] = s1 ? l2.y : z[c + 1];
+          // columns 32h .. 32h+31 of the bf16 row = 16-byte chunks 4h .. 4h+3 (8 values each)
+          const uint8_t* hrow = stg + rowl * 128;
+  #pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int off = (((4 * h + c) ^ (rowl & 7)) & 7) << 4;
+            const uint4 hv = *reinterpret_cast<const uint4*>(hrow + off);
+            const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+  #pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+              z[8 * c + 2 * e2] = __uint_as_float(hw[e2] << 16);
+              z[8 * c + 2 * e2 + 1] = __uint_as_float(hw[e2] & 0xffff0000u);
+            }
+            if (use_lo) {
+              const uint4 lv4 = *reinterpret_cast<const uint4*>(hrow + D_BYTES / 2 + off);
+              const uint32_t lw[4] = {lv4.x, lv4.y, lv4.z, lv4.w};
+  #pragma unroll
+              for (int e2 = 0; e2 < 4; ++e2) {
+                z[8 * c + 2 * e2] += __uint_as_float(lw[e2] << 16);
+                z[8 * c + 2 * e2 + 1] += __uint_as_float(lw[e2] & 0xffff0000u);
+              }
+            }
+          }
         }
-        nnz += (s0 ? 1u : 0u) + (s1 ? 1u : 0u);
-        if (MASK) bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
-      }
-      res += rq;
-      // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
-      // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
-      uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
-      uint8_t* zlo = DM == 0 ? zhi : stg + Z_BYTES / 2;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          const float2 zz = make_float2(z[8 * c + 2 * e2], z[8 * c + 2 * e2 + 1]);
-          const __nv_bfloat162 hi = __floats2bfloat162_rn(zz.x, zz.y);
-          const float2 hf = __bfloat1622float2(hi);
-          const float2 lf = __ffma2_rn(hf, make_float2(-1.f, -1.f), zz);  // z - hi, exact
-          const __nv_bfloat162 lo = __floats2bfloat162_rn(lf.x, lf.y);
-          hw[e2] = *reinterpret_cast<const uint32_t*>(&hi);
-          lw[e2] = *reinterpret_cast<const uint32_t*>(&lo);
-        }
-        const int chi = DM == 0 ? c : 4 * h + c, clo = DM == 0 ? 4 + c : 4 * h + c;
-        *reinterpret_cast<uint4*>(zhi + rowl * 128 + (((chi ^ (rowl & 7)) & 7) << 4)) =
-            make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(zlo + rowl * 128 + (((clo ^ (rowl & 7)) & 7) << 4)) =
-            make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar[B_ZFULL + s]);
-      if (MASK) {  // rows past m hold no support (their D reads as zero and L as zero)
-        mask_new[mw] = bits;
-        chg += __popc(bits ^ mold);
-      }
-      if (ctl == nct - 1 && h == 0) {
-        // drain Y1 of this row tile
-        if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {
-          fail(a, &abort_flag);
-          break;
-        }
-        tc_fence_after();
-        uint32_t yv[NY];
-        tmem_ld_y<NY>(tmem + lane_base + TM_Y1 + yb * NY, yv);
         tmem_wait_ld();
-        const int row = (rt0 + rtl) * BM + rowl;
-        if (row < a.m) {
-#pragma unroll
-          for (int k = 0; k < RK; ++k)
-            if (k < a.R)
-              a.P1[((size_t)bi * a.m + row) * a.R + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]);
-        }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bar[B_Y1EMPTY + yb]);
+        if (lane == 0) mbar_arrive(&bar[B_LEMPTY + lb]);
+        const float2 m1 = make_float2(-1.f, -1.f);
+        float rq = 0.f;
+        uint32_t bits = 0;
+  #pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+          const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
+          const float2 r2 = __ffma2_rn(l2, m1, make_float2(z[c], z[c + 1]));  // D - L, exactly rounded
+          const bool s0 = fabsf(r2.x) > zeta, s1 = fabsf(r2.y) > zeta;  // false for NaN
+          if (PO) {
+            const bool k0 = s0 || !(z[c] == z[c]), k1 = s1 || !(z[c + 1] == z[c + 1]);  // Z = L
+            rq = k0 ? rq : fmaf(r2.x, r2.x, rq);
+            rq = k1 ? rq : fmaf(r2.y, r2.y, rq);
+            z[c] = k0 ? l2.x : fmaf(r2.x, invp, l2.x);
+            z[c + 1] = k1 ? l2.y : fmaf(r2.y, invp, l2.y);
+          } else {
+            rq = s0 ? rq : fmaf(r2.x, r2.x, rq);
+            rq = s1 ? rq : fmaf(r2.y, r2.y, rq);
+            z[c] = s0 ? l2.x : z[c];
+            z[c + 1] = s1 ? l2.y : z[c + 1];
+          }
+          if (MASK || EMIT)
+            bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
+          else
+            nnz += (s0 ? 1u : 0u) + (s1 ? 1u : 0u);
+        }
+        if (MASK || EMIT) nnz += __popc(bits);
+        res += rq;
+        // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
+        // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
+        uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
+        uint8_t* zlo = DM == 0 ? zhi : stg + Z_BYTES / 2;
+  #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t hw[4], lw[4];
+  #pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            const float2 zz = make_float2(z[8 * c + 2 * e2], z[8 * c + 2 * e2 + 1]);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(zz.x, zz.y);
+            const float2 hf = __bfloat1622float2(hi);
+            const float2 lf = __ffma2_rn(hf, make_float2(-1.f, -1.f), zz);  // z - hi, exact
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(lf.x, lf.y);
+            hw[e2] = *reinterpret_cast<const uint32_t*>(&hi);
+            lw[e2] = *reinterpret_cast<const uint32_t*>(&lo);
+          }
+          const int chi = DM == 0 ? c : 4 * h + c, clo = DM == 0 ? 4 + c : 4 * h + c;
+          *reinterpret_cast<uint4*>(zhi + rowl * 128 + (((chi ^ (rowl & 7)) & 7) << 4)) =
+              make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(zlo + rowl * 128 + (((clo ^ (rowl & 7)) & 7) << 4)) =
+              make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[B_ZFULL + s]);
+        if (MASK) {  // rows past m hold no support (their D reads as zero and L as zero)
+          mask_new[mw] = bits;
+          chg += __popc(bits ^ mold);
+        }
+        if (EMIT) {  // support words of S_k (columns past n hold no support either)
+          const int row = (rt0 + rtl) * BM + rowl;
+          if (row < a.m) a.swords[(size_t)row * a.nw + 2 * (ct0 + ctl) + h] = bits;
+        }
+        if (ctl == nct - 1 && h == 0) {
+          // drain Y1 of this row tile
+          if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {
+            fail(a, &abort_flag);
+            break;
+          }
+          tc_fence_after();
+          uint32_t yv[NY];
+          tmem_ld_y<NY>(tmem + lane_base + TM_Y1 + yb * NY, yv);
+          tmem_wait_ld();
+          const int row = (rt0 + rtl) * BM + rowl;
+          if (row < a.m) {
+  #pragma unroll
+            for (int k = 0; k < RK; ++k)
+              if (k < a.R)
+                a.P1[((size_t)bi * a.m + row) * a.R + k] = __uint_as_float(yv[k]) + __uint_as_float(yv[RK + k]);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar[B_Y1EMPTY + yb]);
+        }
       }
-    }
+    };
+    if (emit)
+      tile_loop(BoolC<true>{});
+    else
+      tile_loop(BoolC<false>{});
     // drain Y2: the last chunk of every column tile is still in tensor memory; each warp takes
     // the column tiles ctl = g, g + 4, ...  (lane quarter q: accumulator rows 32q .. 32q+31) and
     // adds them into the group's Y2 partial as the read-outs above do
@@ -753,6 +781,9 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.nnzP = p.nnzP;
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
+  a.swords = p.swords;
+  a.nw = p.nw;
+  a.emit_k = p.emit_k;
   a.tgram = p.tgram;
   a.tnb = p.tnb;
   a.tw = p.tw;

@@ -279,16 +279,23 @@ class Solver:
                                       ctypes.c_void_p(V.data_ptr()), int(k), float(zeta), int(flags)),
                "rpca_set_lowrank")
 
-    def sparse(self):
-        """supp(S_k) as ascending linear indices i*n + j, and the values S_ij."""
+    def sparse(self, cap: int | None = None):
+        """supp(S_k) as ascending linear indices i*n + j, and the values S_ij.  With `cap` (for
+        example the support count of the last iteration's statistics) one call fills buffers
+        of that size; without it, or if the support is larger, a first call sizes them."""
         nnz = ctypes.c_int64(0)
-        code = lib().rpca_get_sparse(self._ctx, None, None, 0, ctypes.byref(nnz))
-        _check(code, "rpca_get_sparse", allow=(OK, CAPACITY))
+        if cap is None:
+            code = lib().rpca_get_sparse(self._ctx, None, None, 0, ctypes.byref(nnz))
+            _check(code, "rpca_get_sparse", allow=(OK, CAPACITY))
+            cap = nnz.value
         dev = self._D.device
-        idx = torch.empty(max(nnz.value, 1), dtype=torch.int64, device=dev)
-        val = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
-        _check(lib().rpca_get_sparse(self._ctx, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
-                                     nnz.value, ctypes.byref(nnz)), "rpca_get_sparse")
+        idx = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        val = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+        code = lib().rpca_get_sparse(self._ctx, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(val.data_ptr()),
+                                     cap, ctypes.byref(nnz))
+        if code == CAPACITY:
+            return self.sparse(None)
+        _check(code, "rpca_get_sparse")
         return idx[: nnz.value], val[: nnz.value]
 
 
