@@ -189,7 +189,12 @@ int rpca_get_lowrank(rpca_ctx* ctx, double* U, double* sigma, double* V);
 /* Writes supp(S_k) = {(i,j) : |D_ij - L_k,ij| > zeta_k} (Eq. (10)) as linear indices
  * i*n + j in ascending order with the values S_ij = D_ij - L_k,ij, into caller-owned
  * device buffers idx (int64) and val (double).  If cap < nnz returns RPCA_ERR_CAPACITY
- * and writes only *nnz (host).  Takes three passes over D; synchronises the stream. */
+ * and writes only *nnz (host).  When the last fused pass computed S_k itself (a converged
+ * FP32 solve on the tensor-core pass: the update before that pass predicts it to be the last
+ * and the pass writes its support as bit masks), the support is read from those masks and
+ * D only where S_k is nonzero; otherwise two passes over D count and write it.  The
+ * support is then the pass's own (its count equals the iteration statistics' nnz).
+ * Synchronises the stream. */
 int rpca_get_sparse(rpca_ctx* ctx, int64_t* idx, double* val, int64_t cap, int64_t* nnz);
 
 /* Bit of the checkpoint flags: the passes of a BF16_SPLIT solve read hi + lo. */
