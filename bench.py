@@ -748,6 +748,7 @@ def main():
         e2 = torch.cuda.Event(enable_timing=True)
         idx, val = solver.sparse(cap=stats[-1]["nnz"])
         e2.record(stream)
+        e2.synchronize()
         sparse_ms.append(e1.elapsed_time(e2))
         assert idx.numel() == stats[-1]["nnz"] or code != P.OK
         return code, stats, prof0, prof1
