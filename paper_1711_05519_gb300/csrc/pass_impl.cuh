@@ -391,12 +391,15 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
 }
 
 // The ordered write from the support words of the tensor-core pass (the bit of column j of
-// row i is set iff |D_ij - L_ij| > zeta_k in that pass): one warp per row, lane l the word
-// j0 + l; the values S_ij = D_ij - L_ij are rebuilt only at the support, so D is read only
-// where a 32-byte sector holds a support entry.  Offsets: the row's start (rowoff) plus an
-// exclusive scan of the words' bit counts.
+// row i is set iff |D_ij - L_ij| > zeta_k in that pass): one warp per row, 32 words at a time.
+// The warp scans the words' bit counts, then takes the chunk's support entries in order, lane
+// l the entries l, l + 32, ... (up to UNR per lane at once, so their loads are in flight
+// together): the source word by a binary search over the scan, the column by the rank of the
+// bit, and S_ij = D_ij - L_ij rebuilt only there.  Consecutive lanes write consecutive
+// positions (rowoff[i] onwards).
 template <int R>
 __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const unsigned* __restrict__ words, int nw) {
+  constexpr int UNR = 4;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= a.m) return;
@@ -407,10 +410,10 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
 #pragma unroll
   for (int k = 0; k < R; ++k) w[k] = W[(long long)row * R + k];
   const unsigned long long base = a.rowoff[row];
-  unsigned carry = 0;
+  unsigned long long carry = 0;
   for (int j0 = 0; j0 < nw; j0 += 32) {
     const int j = j0 + lane;
-    unsigned wd = (j < nw) ? words[(size_t)row * nw + j] : 0u;
+    const unsigned wd = (j < nw) ? words[(size_t)row * nw + j] : 0u;
     const unsigned c = __popc(wd);
     unsigned incl = c;
 #pragma unroll
@@ -418,21 +421,42 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
       const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += v;
     }
-    unsigned long long pos = base + carry + (incl - c);
-    while (wd) {
-      const int b = __ffs(wd) - 1;
-      wd &= wd - 1u;
-      const int col = 32 * j + b;
-      if (col >= a.n) break;  // never set: columns past n read as zero in the pass
-      float v[R];
+    const unsigned excl = incl - c;
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    for (unsigned e0 = 0; e0 < total; e0 += 32 * UNR) {
+      int col[UNR];
+      float d[UNR], v[UNR][R];
 #pragma unroll
-      for (int k = 0; k < R; ++k) v[k] = V[(long long)col * R + k];
-      const float rr = D[(long long)row * a.ld + col] - rebuild<float, R>(w, v);
-      a.idx[pos] = (long long)row * a.n + col;
-      a.val[pos] = static_cast<double>(rr);
-      ++pos;
+      for (int u = 0; u < UNR; ++u) {
+        const unsigned e = e0 + 32u * u + lane;
+        // source lane: the number of lanes whose inclusive count is <= e
+        int src = 0;
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1) {
+          const unsigned t = __shfl_sync(0xffffffffu, incl, src + b - 1);
+          if (t <= e) src += b;
+        }
+        unsigned ws = __shfl_sync(0xffffffffu, wd, src & 31);
+        const unsigned es = __shfl_sync(0xffffffffu, excl, src & 31);
+        col[u] = -1;
+        if (e < total) {
+          for (unsigned q = es; q < e; ++q) ws &= ws - 1u;  // drop the lower set bits
+          col[u] = 32 * (j0 + src) + (__ffs(ws) - 1);
+          d[u] = D[(long long)row * a.ld + col[u]];
+#pragma unroll
+          for (int k = 0; k < R; ++k) v[u][k] = V[(long long)col[u] * R + k];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        if (col[u] >= 0) {
+          const unsigned long long pos = base + carry + e0 + 32u * u + lane;
+          a.idx[pos] = (long long)row * a.n + col[u];
+          a.val[pos] = static_cast<double>(d[u] - rebuild<float, R>(w, v[u]));
+        }
+      }
     }
-    carry += __shfl_sync(0xffffffffu, incl, 31);
+    carry += total;
   }
 }
 

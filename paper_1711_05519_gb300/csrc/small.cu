@@ -117,6 +117,39 @@ __device__ bool grid_barrier(DevState* st, S& sh) {
   return sh.ok != 0;
 }
 
+// The same barrier, with `idle` run by every thread but thread 0 while thread 0 waits for the
+// other blocks (work that needs nothing from them).
+template <typename S, typename F>
+__device__ bool grid_barrier(DevState* st, S& sh, F idle) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &st->bar_gen;
+    volatile int* status = &st->status;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer();
+      while (*gen == g && *status == 0) {
+        if (globaltimer() - t0 > 1000000000ull) {
+          atomicCAS(&st->status, 0, kErrTimeout);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    sh.ok = (*status == 0);
+  } else {
+    idle();
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
 __device__ __forceinline__ void block_range(int rows, int& lo, int& hi) {
   const int chunk = (rows + gridDim.x - 1) / gridDim.x;
   lo = min(rows, (int)blockIdx.x * chunk);
@@ -423,7 +456,7 @@ __device__ void jacobi_lanes(int N, U (&x)[NM], U (&v)[NM], U tol2, int max_swee
 // registers sized NJ; results returned zero-padded to NM.
 template <int NJ, int NM, typename T>
 __device__ __forceinline__ void jacobi_f32_sized(int N, const T* M, T sc, const int* pairs, float (&x)[NM],
-                                                 float (&v)[NM]) {
+                                                 float (&v)[NM], int max_sweeps = 12) {
   const int lane = threadIdx.x & 31;
   float xj[NJ], vj[NJ];
 #pragma unroll
@@ -431,7 +464,7 @@ __device__ __forceinline__ void jacobi_f32_sized(int N, const T* M, T sc, const 
     xj[i] = (lane < N && i < N) ? (float)(M[i * NM + lane] * sc) : 0.f;
     vj[i] = (lane < N && i == lane) ? 1.f : 0.f;
   }
-  jacobi_lanes<float, NJ>(N, xj, vj, 1e-11f, 12, pairs);
+  jacobi_lanes<float, NJ>(N, xj, vj, 1e-11f, max_sweeps, pairs);
 #pragma unroll
   for (int i = 0; i < NM; ++i) {
     x[i] = i < NJ ? xj[i < NJ ? i : 0] : 0.f;
@@ -439,36 +472,151 @@ __device__ __forceinline__ void jacobi_f32_sized(int N, const T* M, T sc, const 
   }
 }
 
-// SVD of the N x N matrix in sh.M (N <= NM), by warp 0 (other threads return at once).
+// One-sided Jacobi with two lanes per column (N <= 16): lanes 2j and 2j + 1 hold rows
+// 0 .. NH-1 and NH .. 2NH-1 of column j of X (x) and of V (v).  The sums alpha, beta, gamma
+// of a pair are formed by halves and added across the two lanes (the same additions in both
+// columns' lanes, so both take the same rotation); each lane exchanges and rotates NH entries
+// instead of N.  Rotation as in jacobi_lanes (single precision).
+template <int NH>
+__device__ void jacobi_two_lane(int N, float (&x)[NH], float (&v)[NH], float tol2, int max_sweeps,
+                                const int* pairs) {
+  const int lane = threadIdx.x & 31, j = lane >> 1, hf = lane & 1;
+  const int L = N + (N & 1) - 1;
+  for (int sweep = 0; sweep < max_sweeps && L > 0; ++sweep) {
+    bool rot = false;
+    for (int rd = 0; rd < L; ++rd) {
+      const int q = (j < 16) ? pairs[rd * 32 + j] : j;
+      const bool low = j < q;
+      const int pl = 2 * q + hf;
+      float xq[NH], vq[NH];
+#pragma unroll
+      for (int i = 0; i < NH; ++i) xq[i] = __shfl_sync(FULL, x[i], pl);
+#pragma unroll
+      for (int i = 0; i < NH; ++i) vq[i] = __shfl_sync(FULL, v[i], pl);
+      float sa = 0.f, sb = 0.f, sg = 0.f;
+#pragma unroll
+      for (int i = 0; i < NH; ++i) {
+        const float a = low ? x[i] : xq[i], b = low ? xq[i] : x[i];
+        sa = fmaf(a, a, sa);
+        sb = fmaf(b, b, sb);
+        sg = fmaf(a, b, sg);
+      }
+      sa += __shfl_xor_sync(FULL, sa, 1);
+      sb += __shfl_xor_sync(FULL, sb, 1);
+      sg += __shfl_xor_sync(FULL, sg, 1);
+      bool doit = (q != j) && j < N && sg != 0.f && sg * sg > tol2 * sa * sb;
+      if (doit) {
+        const float d = sb - sa, g2 = 2.f * sg;
+        const float e2 = fmaf(d, d, g2 * g2);
+        float tt = 0.f;
+        if (e2 > 1e-36f) {
+          const float h = e2 * rsqrtf(e2);
+          tt = __fdividef(g2, fabsf(d) + h);
+          tt = (d < 0.f) ? -tt : tt;
+        }
+        const float x1 = fmaf(tt, tt, 1.f);
+        const float y0 = rsqrtf(x1);
+        const float c = y0 * fmaf(-0.5f * x1 * y0, y0, 1.5f);
+        const float sn = low ? -(c * tt) : (c * tt);
+        doit = tt != 0.f;
+        if (doit) {
+#pragma unroll
+          for (int i = 0; i < NH; ++i) {
+            x[i] = fmaf(c, x[i], sn * xq[i]);
+            v[i] = fmaf(c, v[i], sn * vq[i]);
+          }
+        }
+      }
+      rot = rot || doit;
+    }
+    if (!__any_sync(FULL, rot)) break;
+  }
+}
+
+// small_svd for N <= 2 NH <= 16 in single precision on the two-lane layout; same outputs.
+template <int NH, typename T, int WM>
+__device__ __forceinline__ void small_svd_two_lane(int N, T mx, T sc, int max_sweeps, Smem<T, WM>& sh) {
+  constexpr int NM = Smem<T, WM>::NM;
+  const int lane = threadIdx.x & 31, j = lane >> 1, hf = lane & 1;
+  float x[NH], v[NH];
+#pragma unroll
+  for (int i = 0; i < NH; ++i) {
+    const int row = hf * NH + i;
+    x[i] = (j < N && row < N) ? (float)(sh.M[row * NM + j] * sc) : 0.f;
+    v[i] = (j < N && row == j) ? 1.f : 0.f;
+  }
+  jacobi_two_lane<NH>(N, x, v, 1e-11f, max_sweeps, sh.pairs);
+  float s2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NH; ++i) s2 = fmaf(x[i], x[i], s2);
+  s2 += __shfl_xor_sync(FULL, s2, 1);
+  const float sf = sqrtf(s2);
+  const float inv = sf > 0.f ? 1.f / sf : 0.f;
+  const T sg = (j < N) ? (T)(sf * (float)mx) : T(-1);
+  int rank = 0;
+  for (int i = 0; i < N; ++i) {
+    const T si = __shfl_sync(FULL, sg, 2 * i);
+    rank += (si > sg || (si == sg && i < j)) ? 1 : 0;
+  }
+  if (j < N) {
+    if (hf == 0) sh.sig[rank] = sg;
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      const int row = hf * NH + i;
+      if (row < NM) {
+        sh.UM[rank * NM + row] = (row < N) ? (T)(x[i] * inv) : T(0);
+        sh.VM[rank * NM + row] = (row < N) ? (T)v[i] : T(0);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// SVD of the N x N matrix in sh.M (N <= NM), by the one warp that calls it.
 // On return sh.sig holds the singular values in descending order and sh.UM / sh.VM the
 // matching left / right singular vectors (a zero singular value gives a zero left vector).
 // Single-precision one-sided Jacobi on M scaled to max |M_ij| = 1 keeps the small singular
 // values to high relative accuracy; in FP64 mode V is then re-orthonormalised in double
 // and double-precision sweeps on M V polish the result.
 template <typename T, int WM>
-__device__ void small_svd(int N, Smem<T, WM>& sh) {
+__device__ __noinline__ void small_svd(int N, Smem<T, WM>& sh, int max_sweeps = 12) {
   constexpr int NM = Smem<T, WM>::NM;
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   jacobi_pairs(N, sh.pairs);
   T mx = T(0);
   for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.M[(e / N) * NM + (e % N)]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
   const T sc = mx > T(0) ? T(1) / mx : T(1);
+  if constexpr (sizeof(T) == 4) {
+    // two lanes per column up to N = 16 (half the exchanges and products per round)
+    if (N <= 8) {
+      small_svd_two_lane<4, T, WM>(N, mx, sc, max_sweeps, sh);
+      return;
+    } else if (N <= 10) {
+      small_svd_two_lane<5, T, WM>(N, mx, sc, max_sweeps, sh);
+      return;
+    } else if (N <= 12) {
+      small_svd_two_lane<6, T, WM>(N, mx, sc, max_sweeps, sh);
+      return;
+    } else if (N <= 16) {
+      small_svd_two_lane<8, T, WM>(N, mx, sc, max_sweeps, sh);
+      return;
+    }
+  }
   float xf[NM], vf[NM];
   // rotate until every pair of columns is orthogonal to ~3e-6, on registers sized to N
   // (the padding entries are zero and would only add exact zeros)
   if (N <= 8)
-    jacobi_f32_sized<8, NM>(N, sh.M, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<8, NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   else if (N <= 10)
-    jacobi_f32_sized<(NM < 10 ? NM : 10), NM>(N, sh.M, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<(NM < 10 ? NM : 10), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   else if (N <= 12)
-    jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.M, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   else if (N <= 16 || NM <= 16)
-    jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.M, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   else
-    jacobi_f32_sized<NM, NM>(N, sh.M, sc, sh.pairs, xf, vf);
+    jacobi_f32_sized<NM, NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   T sg;
   T y[NM], vd[NM];
   if (sizeof(T) == 8) {
@@ -1042,7 +1190,29 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     }
     gram_put_h<T>(acc, r, a.part, 1 + side, tl);
   }
-  if (!grid_barrier(st, sh)) return;
+  // while thread 0 waits at the barrier, warps 1 and 2 run the Cholesky factorisation and one
+  // Jacobi sweep on stand-in matrices: the code of these one-warp serial steps is executed
+  // once per launch and would otherwise be fetched while the whole grid waits for it (measured:
+  // the first factorisation of a launch ~6 us, a second one ~1.6 us); their scratch (G[2], the
+  // factors, M, the singular vectors) is rewritten after the barrier
+  auto warm = [&]() {
+    if constexpr (sizeof(T) == 4) {
+      const int wp = t >> 5, lane = t & 31, N2 = 2 * r;
+      if (wp == 1) {
+        for (int e = lane; e < r * r; e += 32) sh.G[2][e] = (e / r == e % r) ? T(2) : T(1);
+        __syncwarp();
+        factor_warp<T, WM>(sh.G[2], r, sh.Rf[0], sh.Tf[0]);
+      } else if (wp == 2) {
+        for (int e = lane; e < NM * NM; e += 32) {
+          const int i = e / NM, j = e % NM;
+          sh.M[e] = (i < N2 && j < N2) ? T(1) / T(i + j + 1) : T(0);
+        }
+        __syncwarp();
+        small_svd<T, WM>(N2, sh, 1);
+      }
+    }
+  };
+  if (!grid_barrier(st, sh, warm)) return;
 
   // R1, R2; M = [[C, R2^T], [R1, 0]] and its SVD
   reduce_slots(a.part, 1, 2, r * r, &sh.G[0][0], sh);
@@ -1062,7 +1232,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   __syncthreads();
   if constexpr (sizeof(T) == 8)
     small_svd_d<T, WM>(N, sh);
-  else
+  else if (t < 32)
     small_svd<T, WM>(N, sh);
   __syncthreads();
   // update matrices: side 0 acts on [U~ W1], side 1 on [V~ W2]; rows q < r take the top block
