@@ -49,6 +49,7 @@ SEED = 0
 TOL = 1e-5
 PROFILE_JSON = os.path.join(ROOT, "profiles", "fused_pass_traffic.json")
 KERNEL_SOURCES = ["paper_1711_05519_gb300/csrc/pass_tc.cu", "paper_1711_05519_gb300/csrc/tc_util.cuh",
+                  "paper_1711_05519_gb300/csrc/factor.cuh",
                   "paper_1711_05519_gb300/csrc/tc_images.cuh"]
 
 

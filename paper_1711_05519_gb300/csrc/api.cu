@@ -87,6 +87,9 @@ struct rpca_ctx {
   int* d_p1nsl = nullptr;
   float* tfac = nullptr;  // T_u, T_v from the tensor-core pass for the update (TcPassArgs)
   unsigned* swords = nullptr;  // support words of the last pass predicted to be final (TcPassArgs)
+  float* svals = nullptr;      // their values ([m][2 TC][kSlotVals])
+  long long last_nnz = -1;     // support count of the pass at iterate last_nnz_k (host copy)
+  int last_nnz_k = -1;
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
   uint8_t *wop[2] = {nullptr, nullptr}, *vop[2] = {nullptr, nullptr}, *vtop[2] = {nullptr, nullptr},
           *utop[2] = {nullptr, nullptr};
@@ -127,7 +130,7 @@ void free_workspace(rpca_ctx* c) {
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
                    (void**)&c->utop[1], (void**)&c->masks, (void**)&c->chgP,
                    (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl, (void**)&c->tfac,
-                   (void**)&c->swords};
+                   (void**)&c->swords, (void**)&c->svals};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -267,6 +270,7 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.chgP = a.chgP;
     t.partial = a.partial;
     t.swords = (!init && !c->dmode) ? c->swords : nullptr;
+    t.svals = c->svals;
     t.nw = 2 * c->TC;
     t.emit_k = &c->st->emit_k;
     t.tgram = static_cast<const float*>(c->part);
@@ -649,7 +653,10 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       CK(cudaMalloc((void**)&c->d_ids, sizeof(int4) * nc));
       CK(cudaMalloc((void**)&c->d_p1nsl, sizeof(int) * c->TR));
       CK(cudaMalloc((void**)&c->tfac, sizeof(float) * 1024));
-      if (c->tc_iter && !c->dmode) CK(cudaMalloc((void**)&c->swords, sizeof(unsigned) * (size_t)m * 2 * c->TC));
+      if (c->tc_iter && !c->dmode) {
+        CK(cudaMalloc((void**)&c->swords, sizeof(unsigned) * (size_t)m * 2 * c->TC));
+        CK(cudaMalloc((void**)&c->svals, sizeof(float) * (size_t)m * 2 * c->TC * kSlotVals));
+      }
       CK(cudaMemcpy(c->d_rect, c->plan.rect.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_p1nsl, c->plan.p1_nsl.data(), sizeof(int) * c->TR, cudaMemcpyHostToDevice));
@@ -754,6 +761,10 @@ int rpca_get_pass_kind(rpca_ctx* c, int* iteration_kind, int* init_kind) {
 int rpca_set_zeta(rpca_ctx* c, double zeta) {
   if (!c || !c->ready || !(zeta >= 0)) return RPCA_ERR_INVALID_ARG;
   CK(cudaMemcpyAsync(&c->st->zeta, &zeta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // the support words, if any, were taken with the former threshold
+  const int none = -1;
+  CK(cudaMemcpyAsync(&c->st->emit_k, &none, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  c->h_flags[6] = -1;
   return RPCA_OK;
 }
 
@@ -806,6 +817,8 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     DevStats last;
     CK(cudaMemcpyAsync(&last, c->stats + k1, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->last_nnz = last.nnz;  // the support the pass at iterate k1 counted
+    c->last_nnz_k = k1;
     return (last.err < c->p.tol) ? RPCA_OK : RPCA_ERR_NOT_CONVERGED;
   }
   return RPCA_ERR_NOT_CONVERGED;
@@ -922,36 +935,46 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
   a.idx = (long long*)idx;
   a.val = val;
   a.vec = c->vec;
-  // S_k from the support words when the last pass wrote them for the iterate held (FP32 D,
-  // tensor-core pass): D is then read only at the support; else two passes over D
-  int st;
-  if ((st = read_flags(c))) return st;
-  const bool from_words = c->swords != nullptr && flag_emit_k(c) == flag_k(c);
-  prof_break(c);
-  prof_mark(c, false, true);
-  if (from_words)
-    CK(launch_words_rowcnt(c->swords, 2 * c->TC, (int)c->m, c->rowcnt, c->stream));
-  else
-    CK(launch_extract_count(c->prec, c->Rr, a, c->stream));
-  prof_mark(c, false, false);
-  prof_mark(c, false, true);
-  CK(launch_scan_rows(c->rowcnt, c->rowoff, (int)c->m, c->stream));
-  prof_mark(c, false, false);
+  // S_k from the support words and values when the last pass wrote them for the iterate held
+  // (FP32 D, tensor-core pass; the host's copy of the state flags is current after
+  // rpca_iterate, rpca_init and rpca_set_lowrank): their count is the one that pass reported,
+  // so no count has to come back first.  Otherwise two passes over D.
+  const bool from_words = c->swords != nullptr && flag_emit_k(c) == flag_k(c) && c->last_nnz_k == flag_k(c);
   unsigned long long total = 0;
-  CK(cudaMemcpyAsync(&total, c->rowoff + c->m, sizeof(total), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  *nnz = (int64_t)total;
-  prof_break(c);
-  if ((int64_t)total > cap) {
-    prof_collect(c, 0);
-    return RPCA_ERR_CAPACITY;
-  }
-  prof_mark(c, false, true);
-  if (from_words)
-    CK(launch_extract_words_f32(c->Rr, a, c->swords, 2 * c->TC, c->stream));
-  else
+  if (from_words) {
+    total = (unsigned long long)c->last_nnz;
+    *nnz = (int64_t)total;
+    if ((int64_t)total > cap) return RPCA_ERR_CAPACITY;
+    prof_break(c);
+    prof_mark(c, false, true);
+    CK(launch_words_rowcnt(c->swords, 2 * c->TC, (int)c->m, c->rowcnt, c->stream));
+    prof_mark(c, false, false);
+    prof_mark(c, false, true);
+    CK(launch_scan_rows(c->rowcnt, c->rowoff, (int)c->m, c->stream));
+    prof_mark(c, false, false);
+    prof_mark(c, false, true);
+    if (total > 0) CK(launch_extract_words_f32(c->Rr, a, c->swords, c->svals, 2 * c->TC, c->stream));
+    prof_mark(c, false, false);
+  } else {
+    prof_break(c);
+    prof_mark(c, false, true);
+    CK(launch_extract_count(c->prec, c->Rr, a, c->stream));
+    prof_mark(c, false, false);
+    prof_mark(c, false, true);
+    CK(launch_scan_rows(c->rowcnt, c->rowoff, (int)c->m, c->stream));
+    prof_mark(c, false, false);
+    CK(cudaMemcpyAsync(&total, c->rowoff + c->m, sizeof(total), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *nnz = (int64_t)total;
+    prof_break(c);
+    if ((int64_t)total > cap) {
+      prof_collect(c, 0);
+      return RPCA_ERR_CAPACITY;
+    }
+    prof_mark(c, false, true);
     CK(launch_extract_write(c->prec, c->Rr, a, c->stream));
-  prof_mark(c, false, false);
+    prof_mark(c, false, false);
+  }
   CK(cudaStreamSynchronize(c->stream));
   prof_collect(c, 0);
   return RPCA_OK;

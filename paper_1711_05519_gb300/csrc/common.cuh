@@ -135,6 +135,8 @@ struct TcPassArgs {
   // writes, per row and 32 columns, the bit mask of |D_ij - L_ij| > zeta_k (row-major,
   // nw = 2 TC words per row, word j = columns 32 j .. 32 j + 31) and *emit_k = k
   unsigned* swords;
+  float* svals;  // with the words: per word its first kSlotVals values S_ij in column order
+                 // (zero-filled; a word with more set bits leaves the rest to the reader)
   int nw;
   int* emit_k;
   // T factors for the update that follows (null: not computed), by CTA tcta: the Gram
@@ -147,6 +149,8 @@ struct TcPassArgs {
 };
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
+// values of S_k kept per 32-column support word (one 32-byte sector)
+constexpr int kSlotVals = 8;
 // Tile partition of the tensor-core pass (api.cu, tc_plan): per CTA its rectangle of tiles
 // {first row tile, end row tile, first column tile, end column tile} and its ids {row group a,
 // index in the group (the m-slice of Y1 it writes), 2 a (its group's first n-slice of Y2),
@@ -250,7 +254,8 @@ cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* 
 // Support of S_k from the support words of the tensor-core pass (TcPassArgs::swords): per-row
 // counts, then (after the scan) the ordered write of indices and values S_ij = D_ij - L_ij.
 cudaError_t launch_words_rowcnt(const unsigned* words, int nw, int m, unsigned long long* rowcnt, cudaStream_t s);
-cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, int nw, cudaStream_t s);
+cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, const float* vals, int nw,
+                                     cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double* src, long long ld_src, float* dst, int m, int n,
                                       cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float* src, long long ld_src, double* dst, int m, int n,

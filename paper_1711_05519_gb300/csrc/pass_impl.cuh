@@ -391,14 +391,16 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
 }
 
 // The ordered write from the support words of the tensor-core pass (the bit of column j of
-// row i is set iff |D_ij - L_ij| > zeta_k in that pass): one warp per row, 32 words at a time.
-// The warp scans the words' bit counts, then takes the chunk's support entries in order, lane
-// l the entries l, l + 32, ... (up to UNR per lane at once, so their loads are in flight
-// together): the source word by a binary search over the scan, the column by the rank of the
-// bit, and S_ij = D_ij - L_ij rebuilt only there.  Consecutive lanes write consecutive
-// positions (rowoff[i] onwards).
+// row i is set iff |D_ij - L_ij| > zeta_k in that pass) and the values that pass kept: one
+// warp per row, 32 words at a time.  The warp scans the words' bit counts, then takes the
+// chunk's support entries in order, lane l the entries l, l + 32, ... (up to UNR per lane at
+// once, so their loads are in flight together): the source word by a binary search over the
+// scan, the column by the rank of the bit, the value S_ij = D_ij - L_ij from the word's slot
+// (or, for a word with more set bits than its slot holds, rebuilt from D and the factors).
+// Consecutive lanes write consecutive positions (rowoff[i] onwards).
 template <int R>
-__global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const unsigned* __restrict__ words, int nw) {
+__global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const unsigned* __restrict__ words,
+                                                            const float* __restrict__ vals, int nw) {
   constexpr int UNR = 4;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -425,6 +427,7 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
     const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
     for (unsigned e0 = 0; e0 < total; e0 += 32 * UNR) {
       int col[UNR];
+      bool slot[UNR];
       float d[UNR], v[UNR][R];
 #pragma unroll
       for (int u = 0; u < UNR; ++u) {
@@ -439,12 +442,19 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
         unsigned ws = __shfl_sync(0xffffffffu, wd, src & 31);
         const unsigned es = __shfl_sync(0xffffffffu, excl, src & 31);
         col[u] = -1;
+        slot[u] = false;
         if (e < total) {
-          for (unsigned q = es; q < e; ++q) ws &= ws - 1u;  // drop the lower set bits
+          const unsigned q0 = e - es;  // rank of the entry in its word
+          slot[u] = __popc(ws) <= (unsigned)kSlotVals;
+          for (unsigned q = 0; q < q0; ++q) ws &= ws - 1u;  // drop the lower set bits
           col[u] = 32 * (j0 + src) + (__ffs(ws) - 1);
-          d[u] = D[(long long)row * a.ld + col[u]];
+          if (slot[u]) {
+            d[u] = vals[((size_t)row * nw + j0 + src) * kSlotVals + q0];
+          } else {  // more support entries in the word than its slot holds: rebuild
+            d[u] = D[(long long)row * a.ld + col[u]];
 #pragma unroll
-          for (int k = 0; k < R; ++k) v[u][k] = V[(long long)col[u] * R + k];
+            for (int k = 0; k < R; ++k) v[u][k] = V[(long long)col[u] * R + k];
+          }
         }
       }
 #pragma unroll
@@ -452,7 +462,7 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
         if (col[u] >= 0) {
           const unsigned long long pos = base + carry + e0 + 32u * u + lane;
           a.idx[pos] = (long long)row * a.n + col[u];
-          a.val[pos] = static_cast<double>(d[u] - rebuild<float, R>(w, v[u]));
+          a.val[pos] = static_cast<double>(slot[u] ? d[u] : d[u] - rebuild<float, R>(w, v[u]));
         }
       }
     }
@@ -461,8 +471,9 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
 }
 
 template <int R>
-cudaError_t launch_extract_words_t(const ExtractArgs& a, const unsigned* words, int nw, cudaStream_t s) {
-  extract_words_kernel<R><<<(a.m + 7) / 8, 256, 0, s>>>(a, words, nw);
+cudaError_t launch_extract_words_t(const ExtractArgs& a, const unsigned* words, const float* vals, int nw,
+                                   cudaStream_t s) {
+  extract_words_kernel<R><<<(a.m + 7) / 8, 256, 0, s>>>(a, words, vals, nw);
   return cudaGetLastError();
 }
 

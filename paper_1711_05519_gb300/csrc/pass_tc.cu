@@ -136,6 +136,7 @@ struct TcArgs {
   unsigned* masks;
   long long mask_wr;
   unsigned* swords;
+  float* svals;
   int nw;
   int* emit_k;
   const float* tgram;
@@ -568,6 +569,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         const float2 m1 = make_float2(-1.f, -1.f);
         float rq = 0.f;
         uint32_t bits = 0;
+        // support values of this thread's word, in column order, into its slot (EMIT)
+        const int erow = (rt0 + rtl) * BM + rowl;
+        float* vslot = EMIT ? a.svals + ((size_t)erow * a.nw + 2 * (ct0 + ctl) + h) * kSlotVals : nullptr;
+        int ecnt = 0;
   #pragma unroll
         for (int c = 0; c < 32; c += 2) {
           const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
@@ -584,6 +589,16 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
             rq = s1 ? rq : fmaf(r2.y, r2.y, rq);
             z[c] = s0 ? l2.x : z[c];
             z[c + 1] = s1 ? l2.y : z[c + 1];
+          }
+          if (EMIT) {
+            if (s0) {
+              if (ecnt < kSlotVals) vslot[ecnt] = r2.x;
+              ++ecnt;
+            }
+            if (s1) {
+              if (ecnt < kSlotVals) vslot[ecnt] = r2.y;
+              ++ecnt;
+            }
           }
           if (MASK || EMIT)
             bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
@@ -622,9 +637,11 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           mask_new[mw] = bits;
           chg += __popc(bits ^ mold);
         }
-        if (EMIT) {  // support words of S_k (columns past n hold no support either)
-          const int row = (rt0 + rtl) * BM + rowl;
-          if (row < a.m) a.swords[(size_t)row * a.nw + 2 * (ct0 + ctl) + h] = bits;
+        if (EMIT && erow < a.m) {  // support words of S_k (columns past n hold no support either)
+          a.swords[(size_t)erow * a.nw + 2 * (ct0 + ctl) + h] = bits;
+#pragma unroll
+          for (int i = 0; i < kSlotVals; ++i)  // the rest of the slot: whole sectors written
+            if (i >= ecnt) vslot[i] = 0.f;
         }
         if (ctl == nct - 1 && h == 0) {
           // drain Y1 of this row tile
@@ -782,6 +799,7 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
   a.swords = p.swords;
+  a.svals = p.svals;
   a.nw = p.nw;
   a.emit_k = p.emit_k;
   a.tgram = p.tgram;

@@ -1190,25 +1190,19 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     }
     gram_put_h<T>(acc, r, a.part, 1 + side, tl);
   }
-  // while thread 0 waits at the barrier, warps 1 and 2 run the Cholesky factorisation and one
-  // Jacobi sweep on stand-in matrices: the code of these one-warp serial steps is executed
-  // once per launch and would otherwise be fetched while the whole grid waits for it (measured:
-  // the first factorisation of a launch ~6 us, a second one ~1.6 us); their scratch (G[2], the
-  // factors, M, the singular vectors) is rewritten after the barrier
+  // while thread 0 waits at the barrier, warp 1 runs the Cholesky factorisation on a stand-in
+  // matrix: the code of this one-warp serial step is executed once per launch and would
+  // otherwise be fetched while the whole grid waits for it (measured: the first factorisation
+  // of a launch ~6 us, a second one ~1.6-2 us); its scratch (G[2], the factors) is rewritten
+  // after the barrier.  (The same for one Jacobi sweep of the SVD cost more than it saved: its
+  // cold run outlasts the barrier.)
   auto warm = [&]() {
     if constexpr (sizeof(T) == 4) {
-      const int wp = t >> 5, lane = t & 31, N2 = 2 * r;
+      const int wp = t >> 5, lane = t & 31;
       if (wp == 1) {
         for (int e = lane; e < r * r; e += 32) sh.G[2][e] = (e / r == e % r) ? T(2) : T(1);
         __syncwarp();
         factor_warp<T, WM>(sh.G[2], r, sh.Rf[0], sh.Tf[0]);
-      } else if (wp == 2) {
-        for (int e = lane; e < NM * NM; e += 32) {
-          const int i = e / NM, j = e % NM;
-          sh.M[e] = (i < N2 && j < N2) ? T(1) / T(i + j + 1) : T(0);
-        }
-        __syncwarp();
-        small_svd<T, WM>(N2, sh, 1);
       }
     }
   };
