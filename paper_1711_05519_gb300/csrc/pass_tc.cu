@@ -569,10 +569,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         const float2 m1 = make_float2(-1.f, -1.f);
         float rq = 0.f;
         uint32_t bits = 0;
-        // support values of this thread's word, in column order, into its slot (EMIT)
-        const int erow = (rt0 + rtl) * BM + rowl;
-        float* vslot = EMIT ? a.svals + ((size_t)erow * a.nw + 2 * (ct0 + ctl) + h) * kSlotVals : nullptr;
-        int ecnt = 0;
   #pragma unroll
         for (int c = 0; c < 32; c += 2) {
           const float2 l2 = make_float2(__uint_as_float(lv[c]), __uint_as_float(lv[c + 1]));
@@ -590,16 +586,6 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
             z[c] = s0 ? l2.x : z[c];
             z[c + 1] = s1 ? l2.y : z[c + 1];
           }
-          if (EMIT) {
-            if (s0) {
-              if (ecnt < kSlotVals) vslot[ecnt] = r2.x;
-              ++ecnt;
-            }
-            if (s1) {
-              if (ecnt < kSlotVals) vslot[ecnt] = r2.y;
-              ++ecnt;
-            }
-          }
           if (MASK || EMIT)
             bits |= ((s0 ? 1u : 0u) << c) | ((s1 ? 1u : 0u) << (c + 1));
           else
@@ -607,6 +593,26 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         }
         if (MASK || EMIT) nnz += __popc(bits);
         res += rq;
+        const int erow = (rt0 + rtl) * BM + rowl;
+        if (EMIT && erow < a.m) {
+          // the support values of this thread's word, in column order, into its slot: S = D - L
+          // with D still in the stage (Z overwrites it below) and L in z at the support
+          float* vslot = a.svals + ((size_t)erow * a.nw + 2 * (ct0 + ctl) + h) * kSlotVals;
+          const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
+          int ecnt = 0;
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            if ((bits >> c) & 1u) {
+              const float dv = *reinterpret_cast<const float*>(drow + (((c >> 2) ^ (rowl & 7)) << 4) + 4 * (c & 3));
+              if (ecnt < kSlotVals) vslot[ecnt] = dv - z[c];
+              ++ecnt;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kSlotVals; ++i)  // the rest of the slot: whole sectors written
+            if (i >= ecnt) vslot[i] = 0.f;
+          a.swords[(size_t)erow * a.nw + 2 * (ct0 + ctl) + h] = bits;
+        }
         // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
         // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
         uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
@@ -637,12 +643,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
           mask_new[mw] = bits;
           chg += __popc(bits ^ mold);
         }
-        if (EMIT && erow < a.m) {  // support words of S_k (columns past n hold no support either)
-          a.swords[(size_t)erow * a.nw + 2 * (ct0 + ctl) + h] = bits;
-#pragma unroll
-          for (int i = 0; i < kSlotVals; ++i)  // the rest of the slot: whole sectors written
-            if (i >= ecnt) vslot[i] = 0.f;
-        }
+
         if (ctl == nct - 1 && h == 0) {
           // drain Y1 of this row tile
           if (!mbar_wait(&bar[B_Y1FULL + yb], (rtl >> 1) & 1)) {
@@ -666,8 +667,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         }
       }
     };
-    if (emit)
-      tile_loop(BoolC<true>{});
+    if (DM == 0 && emit)
+      tile_loop(BoolC<DM == 0>{});
     else
       tile_loop(BoolC<false>{});
     // drain Y2: the last chunk of every column tile is still in tensor memory; each warp takes
