@@ -229,6 +229,43 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     return;
   }
 
+  // producer (thread 0): copies of tile t into stage t % NSTAGE, and the W and U~ images of
+  // its 128-row block when t starts one; false if a wait gave up
+  int issued = 0, w_issued = 0;
+  auto issue = [&](int t) -> bool {
+    const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE;
+    const int rt = rt0 + rtl, ct = ct0 + ctl;
+    if (ctl == 0) {
+      const int wb = rtl & 1;
+      if (rtl >= 2 && !mbar_wait(&bar[B_WEMPTY + wb], ((rtl - 2) >> 1) & 1)) {
+        fail(a, &abort_flag);
+        return false;
+      }
+      mbar_arrive_expect_tx(&bar[B_WFULL + wb], WOP_BYTES + UTOP_BYTES);
+      bulk_load(sm + OFF_W + wb * WOP_BYTES, a.wop + (size_t)rt * WOP_BYTES, WOP_BYTES, &bar[B_WFULL + wb]);
+      bulk_load(sm + OFF_U + wb * UTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES, &bar[B_WFULL + wb]);
+      w_issued = rtl + 1;
+    }
+    if (t >= NSTAGE && !mbar_wait(&bar[B_EMPTY + s], ((t - NSTAGE) / NSTAGE) & 1)) {
+      fail(a, &abort_flag);
+      return false;
+    }
+    uint8_t* st = sm + OFF_STAGE + s * STAGE_BYTES;
+    if (DM == 0) {
+      mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES);
+      tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
+      tma_load_2d(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s]);
+    } else {
+      mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES - (use_lo ? 0 : D_BYTES / 2));
+      tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
+      if (use_lo) tma_load_2d(st + D_BYTES / 2, &dmap_lo, ct * BN, rt * BM, &bar[B_FULL + s]);
+    }
+    bulk_load(st + D_BYTES, a.vop + (size_t)ct * VOP_BYTES, VOP_BYTES, &bar[B_FULL + s]);
+    bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
+    issued = t + 1;
+    return true;
+  };
+
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < NSTAGE; ++s) {
@@ -253,6 +290,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
       mbar_init(&bar[B_Y2FREE + i], EPI_WARPS / 2);
     }
     fence_mbar_init();
+    // the first tiles' copies go out at once, while the tensor memory is being allocated: the
+    // stages are free and no wait is needed for tiles of the first two row blocks
+    const int first = min(min(NSTAGE, ntiles), 2 * nct);
+    for (int t = 0; t < first; ++t) issue(t);
   }
   if (warp == 1) {
     tmem_alloc(&tmem_base, TMEM_COLS);
@@ -265,39 +306,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
 
   if (ntiles > 0 && warp == 0 && lane == 0) {
     // ------------------------------------------------------------------ producer
-    int issued = 0, w_issued = 0;
-    for (int t = 0; t < ntiles && !abort_flag; ++t) {
-      const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE;
-      const int rt = rt0 + rtl, ct = ct0 + ctl;
-      if (ctl == 0) {
-        const int wb = rtl & 1;
-        if (rtl >= 2 && !mbar_wait(&bar[B_WEMPTY + wb], ((rtl - 2) >> 1) & 1)) {
-          fail(a, &abort_flag);
-          break;
-        }
-        mbar_arrive_expect_tx(&bar[B_WFULL + wb], WOP_BYTES + UTOP_BYTES);
-        bulk_load(sm + OFF_W + wb * WOP_BYTES, a.wop + (size_t)rt * WOP_BYTES, WOP_BYTES, &bar[B_WFULL + wb]);
-        bulk_load(sm + OFF_U + wb * UTOP_BYTES, a.utop + (size_t)rt * UTOP_BYTES, UTOP_BYTES, &bar[B_WFULL + wb]);
-        w_issued = rtl + 1;
-      }
-      if (t >= NSTAGE && !mbar_wait(&bar[B_EMPTY + s], ((t - NSTAGE) / NSTAGE) & 1)) {
-        fail(a, &abort_flag);
-        break;
-      }
-      uint8_t* st = sm + OFF_STAGE + s * STAGE_BYTES;
-      if (DM == 0) {
-        mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES);
-        tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
-        tma_load_2d(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s]);
-      } else {
-        mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES - (use_lo ? 0 : D_BYTES / 2));
-        tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
-        if (use_lo) tma_load_2d(st + D_BYTES / 2, &dmap_lo, ct * BN, rt * BM, &bar[B_FULL + s]);
-      }
-      bulk_load(st + D_BYTES, a.vop + (size_t)ct * VOP_BYTES, VOP_BYTES, &bar[B_FULL + s]);
-      bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
-      issued = t + 1;
-    }
+    for (int t = issued; t < ntiles && !abort_flag; ++t)
+      if (!issue(t)) break;
     // wait (bounded) for this thread's copies still in flight before the CTA may exit: the
     // last NSTAGE stage loads and the last two W / U~ image loads (after an abort some of them
     // may never have been consumed)
