@@ -132,11 +132,13 @@ struct TcPassArgs {
   unsigned long long* chgP;
   int partial;  // as in PassArgs (not together with masks)
   // support words of S_k (FP32 D only; null: never): when DevState.emit is set the pass
-  // writes, per row and 32 columns, the bit mask of |D_ij - L_ij| > zeta_k (row-major,
-  // nw = 2 TC words per row, word j = columns 32 j .. 32 j + 31) and *emit_k = k
+  // writes, per row and 32 columns, the bit mask of |D_ij - L_ij| > zeta_k ([word][row]
+  // layout: word j (columns 32 j .. 32 j + 31) of row i at j m + i; nw = 2 TC words per row)
+  // and *emit_k = k
   unsigned* swords;
   float* svals;  // with the words: per word its first kSlotVals values S_ij in column order
-                 // (zero-filled; a word with more set bits leaves the rest to the reader)
+                 // at (j m + i) kSlotVals (zero-filled; a word with more set bits leaves the
+                 // rest to the reader)
   int nw;
   int* emit_k;
   // T factors for the update that follows (null: not computed), by CTA tcta: the Gram

@@ -89,9 +89,8 @@ __global__ void __launch_bounds__(256) words_rowcnt(const unsigned* __restrict__
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= m) return;
-  const unsigned* w = words + (size_t)row * nw;
   unsigned c = 0;
-  for (int j = lane; j < nw; j += 32) c += __popc(w[j]);
+  for (int j = lane; j < nw; j += 32) c += __popc(words[(size_t)j * m + row]);  // [word][row] layout
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if (lane == 0) rowcnt[row] = c;

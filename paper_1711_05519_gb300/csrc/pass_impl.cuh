@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
   unsigned long long carry = 0;
   for (int j0 = 0; j0 < nw; j0 += 32) {
     const int j = j0 + lane;
-    const unsigned wd = (j < nw) ? words[(size_t)row * nw + j] : 0u;
+    const unsigned wd = (j < nw) ? words[(size_t)j * a.m + row] : 0u;  // [word][row] layout
     const unsigned c = __popc(wd);
     unsigned incl = c;
 #pragma unroll
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
           for (unsigned q = 0; q < q0; ++q) ws &= ws - 1u;  // drop the lower set bits
           col[u] = 32 * (j0 + src) + (__ffs(ws) - 1);
           if (slot[u]) {
-            d[u] = vals[((size_t)row * nw + j0 + src) * kSlotVals + q0];
+            d[u] = vals[((size_t)(j0 + src) * a.m + row) * kSlotVals + q0];
           } else {  // more support entries in the word than its slot holds: rebuild
             d[u] = D[(long long)row * a.ld + col[u]];
 #pragma unroll

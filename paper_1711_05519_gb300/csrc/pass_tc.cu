@@ -605,23 +605,38 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         res += rq;
         const int erow = (rt0 + rtl) * BM + rowl;
         if (EMIT && erow < a.m) {
-          // the support values of this thread's word, in column order, into its slot: S = D - L
-          // with D still in the stage (Z overwrites it below) and L in z at the support
-          float* vslot = a.svals + ((size_t)erow * a.nw + 2 * (ct0 + ctl) + h) * kSlotVals;
-          const uint8_t* drow = stg + h * (D_BYTES / 2) + rowl * 128;
+          // the word's support bits and its first kSlotVals values S = D - L in column order:
+          // D is still in the stage (this thread's 128-byte row segment, which only it reads
+          // and which its Z overwrites below) and L is in z at the support; the values are
+          // packed to the front of that segment (an entry never moves up, so no unread D is
+          // overwritten) and written as two 16-byte stores.  Layout [word][row]: the lanes of
+          // a warp (consecutive rows) write consecutive slots.
+          uint8_t* seg = stg + h * (D_BYTES / 2) + rowl * 128;
+          const int sw = rowl & 7;
           int ecnt = 0;
 #pragma unroll
           for (int c = 0; c < 32; ++c) {
             if ((bits >> c) & 1u) {
-              const float dv = *reinterpret_cast<const float*>(drow + (((c >> 2) ^ (rowl & 7)) << 4) + 4 * (c & 3));
-              if (ecnt < kSlotVals) vslot[ecnt] = dv - z[c];
+              const float sv = *reinterpret_cast<const float*>(seg + (((c >> 2) ^ sw) << 4) + 4 * (c & 3)) - z[c];
+              if (ecnt < kSlotVals) *reinterpret_cast<float*>(seg + (((ecnt >> 2) ^ sw) << 4) + 4 * (ecnt & 3)) = sv;
               ++ecnt;
             }
           }
-#pragma unroll
-          for (int i = 0; i < kSlotVals; ++i)  // the rest of the slot: whole sectors written
-            if (i >= ecnt) vslot[i] = 0.f;
-          a.swords[(size_t)erow * a.nw + 2 * (ct0 + ctl) + h] = bits;
+          float4 v0 = *reinterpret_cast<const float4*>(seg + ((0 ^ sw) << 4));
+          float4 v1 = *reinterpret_cast<const float4*>(seg + ((1 ^ sw) << 4));
+          v0.x = ecnt > 0 ? v0.x : 0.f;
+          v0.y = ecnt > 1 ? v0.y : 0.f;
+          v0.z = ecnt > 2 ? v0.z : 0.f;
+          v0.w = ecnt > 3 ? v0.w : 0.f;
+          v1.x = ecnt > 4 ? v1.x : 0.f;
+          v1.y = ecnt > 5 ? v1.y : 0.f;
+          v1.z = ecnt > 6 ? v1.z : 0.f;
+          v1.w = ecnt > 7 ? v1.w : 0.f;
+          const size_t widx = (size_t)(2 * (ct0 + ctl) + h) * a.m + erow;
+          float4* dst = reinterpret_cast<float4*>(a.svals + widx * kSlotVals);
+          dst[0] = v0;
+          dst[1] = v1;
+          a.swords[widx] = bits;
         }
         // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
         // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles

@@ -1283,10 +1283,10 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
       a.stats[k].sigma_r1 = sr1;
       if (hi_only && (err < st->split_switch || err < st->tol)) st->use_lo = 1;
       // the next pass writes the support words if it is likely the last one: err_{k+1}
-      // predicted from the contraction of the last two passes below 4 tol, or k + 1 the cap
+      // predicted from the contraction of the last two passes below 2 tol, or k + 1 the cap
       const double prev = k > 0 ? a.stats[k - 1].err : 0.0;
       const double pred = (prev > err) ? err * (err / prev) : err;
-      st->emit = (a.emit_ok && (k1 >= st->max_iter || pred < 4.0 * st->tol)) ? 1 : 0;
+      st->emit = (a.emit_ok && (k1 >= st->max_iter || pred < 2.0 * st->tol)) ? 1 : 0;
       st->k = k1;
     }
   }
