@@ -400,7 +400,9 @@ def profile_case(n: int) -> int:
         for _ in range(3):
             s.init(D, RANK)
             code, stats = s.run()
-    print(json.dumps({"profile_case": n, "iterations": stats[-1]["k"], "err": stats[-1]["err"], "status": code}))
+            idx, _ = s.sparse(cap=stats[-1]["nnz"])
+    print(json.dumps({"profile_case": n, "iterations": stats[-1]["k"], "err": stats[-1]["err"], "status": code,
+                      "nnz": int(idx.numel())}))
     return 0 if code == P.OK else 1
 
 
