@@ -87,7 +87,7 @@ struct rpca_ctx {
   int* d_p1nsl = nullptr;
   float* tfac = nullptr;  // T_u, T_v from the tensor-core pass for the update (TcPassArgs)
   unsigned* swords = nullptr;  // support words of the last pass predicted to be final (TcPassArgs)
-  float* svals = nullptr;      // their values ([m][2 TC][kSlotVals])
+  unsigned* wcc = nullptr;     // support counts per row and chunk of support words
   long long last_nnz = -1;     // support count of the pass at iterate last_nnz_k (host copy)
   int last_nnz_k = -1;
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
@@ -130,7 +130,7 @@ void free_workspace(rpca_ctx* c) {
                    (void**)&c->utop[0], (void**)&c->wop[1], (void**)&c->vop[1], (void**)&c->vtop[1],
                    (void**)&c->utop[1], (void**)&c->masks, (void**)&c->chgP,
                    (void**)&c->d_rect, (void**)&c->d_ids, (void**)&c->d_p1nsl, (void**)&c->tfac,
-                   (void**)&c->swords, (void**)&c->svals};
+                   (void**)&c->swords, (void**)&c->wcc};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -270,7 +270,6 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.chgP = a.chgP;
     t.partial = a.partial;
     t.swords = (!init && !c->dmode) ? c->swords : nullptr;
-    t.svals = c->svals;
     t.nw = 2 * c->TC;
     t.emit_k = &c->st->emit_k;
     t.tgram = static_cast<const float*>(c->part);
@@ -655,7 +654,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
       CK(cudaMalloc((void**)&c->tfac, sizeof(float) * 1024));
       if (c->tc_iter && !c->dmode) {
         CK(cudaMalloc((void**)&c->swords, sizeof(unsigned) * (size_t)m * 2 * c->TC));
-        CK(cudaMalloc((void**)&c->svals, sizeof(float) * (size_t)m * 2 * c->TC * kSlotVals));
+        CK(cudaMalloc((void**)&c->wcc, sizeof(unsigned) * (size_t)m * ((2 * c->TC + kWordChunk - 1) / kWordChunk)));
       }
       CK(cudaMemcpy(c->d_rect, c->plan.rect.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->d_ids, c->plan.ids.data(), sizeof(int4) * nc, cudaMemcpyHostToDevice));
@@ -935,7 +934,7 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
   a.idx = (long long*)idx;
   a.val = val;
   a.vec = c->vec;
-  // S_k from the support words and values when the last pass wrote them for the iterate held
+  // S_k from the support words when the last pass wrote them for the iterate held
   // (FP32 D, tensor-core pass; the host's copy of the state flags is current after
   // rpca_iterate, rpca_init and rpca_set_lowrank): their count is the one that pass reported,
   // so no count has to come back first.  Otherwise two passes over D.
@@ -947,13 +946,14 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
     if ((int64_t)total > cap) return RPCA_ERR_CAPACITY;
     prof_break(c);
     prof_mark(c, false, true);
-    CK(launch_words_rowcnt(c->swords, 2 * c->TC, (int)c->m, c->rowcnt, c->stream));
+    CK(cudaMemsetAsync(c->rowcnt, 0, sizeof(unsigned long long) * c->m, c->stream));
+    CK(launch_words_count(c->swords, 2 * c->TC, (int)c->m, c->wcc, c->rowcnt, c->stream));
     prof_mark(c, false, false);
     prof_mark(c, false, true);
     CK(launch_scan_rows(c->rowcnt, c->rowoff, (int)c->m, c->stream));
     prof_mark(c, false, false);
     prof_mark(c, false, true);
-    if (total > 0) CK(launch_extract_words_f32(c->Rr, a, c->swords, c->svals, 2 * c->TC, c->stream));
+    if (total > 0) CK(launch_extract_words_f32(c->Rr, a, c->swords, c->wcc, 2 * c->TC, c->stream));
     prof_mark(c, false, false);
   } else {
     prof_break(c);

@@ -136,9 +136,6 @@ struct TcPassArgs {
   // layout: word j (columns 32 j .. 32 j + 31) of row i at j m + i; nw = 2 TC words per row)
   // and *emit_k = k
   unsigned* swords;
-  float* svals;  // with the words: per word its first kSlotVals values S_ij in column order
-                 // at (j m + i) kSlotVals (zero-filled; a word with more set bits leaves the
-                 // rest to the reader)
   int nw;
   int* emit_k;
   // T factors for the update that follows (null: not computed), by CTA tcta: the Gram
@@ -151,8 +148,6 @@ struct TcPassArgs {
 };
 // row tiles per Y2 accumulation chunk of the tensor-core pass
 constexpr int kTcY2Chunk = 4;
-// values of S_k kept per 32-column support word (one 32-byte sector)
-constexpr int kSlotVals = 8;
 // Tile partition of the tensor-core pass (api.cu, tc_plan): per CTA its rectangle of tiles
 // {first row tile, end row tile, first column tile, end column tile} and its ids {row group a,
 // index in the group (the m-slice of Y1 it writes), 2 a (its group's first n-slice of Y2),
@@ -253,10 +248,13 @@ cudaError_t run_wait_selftest(int* mbar_status, int* grid_status);
 int small_grid_size(int device);
 
 cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* off, int m, cudaStream_t s);
-// Support of S_k from the support words of the tensor-core pass (TcPassArgs::swords): per-row
-// counts, then (after the scan) the ordered write of indices and values S_ij = D_ij - L_ij.
-cudaError_t launch_words_rowcnt(const unsigned* words, int nw, int m, unsigned long long* rowcnt, cudaStream_t s);
-cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, const float* vals, int nw,
+// Support of S_k from the support words of the tensor-core pass (TcPassArgs::swords): counts
+// per row and per chunk of 32 words (cc[chunk][row]; rowcnt must be zero before), then (after
+// the scan of rowcnt) the ordered write of indices and values S_ij = D_ij - L_ij.
+constexpr int kWordChunk = 32;
+cudaError_t launch_words_count(const unsigned* words, int nw, int m, unsigned* cc, unsigned long long* rowcnt,
+                               cudaStream_t s);
+cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, const unsigned* cc, int nw,
                                      cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double* src, long long ld_src, float* dst, int m, int n,
                                       cudaStream_t s);

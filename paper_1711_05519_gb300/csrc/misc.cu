@@ -83,23 +83,29 @@ __global__ void __launch_bounds__(1024) scan_rows(const unsigned long long* __re
   if (t == 1023) off[m] = part[1023];
 }
 
-// Row counts of the support words: one warp per row.
-__global__ void __launch_bounds__(256) words_rowcnt(const unsigned* __restrict__ words, int nw, int m,
-                                                    unsigned long long* __restrict__ rowcnt) {
+// Support counts per row and per chunk of kWordChunk words ([word][row] layout): one warp per
+// 32 rows and one chunk, lane l the row r0 + l (coalesced), cc[chunk][row] and rowcnt[row] +=.
+__global__ void __launch_bounds__(256) words_count(const unsigned* __restrict__ words, int nw, int m,
+                                                   unsigned* __restrict__ cc, unsigned long long* __restrict__ rowcnt) {
   const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= m) return;
+  const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int nrb = (m + 31) / 32;
+  const int rb = wid % nrb, ch = wid / nrb;
+  const int row = rb * 32 + lane, j0 = ch * kWordChunk;
+  if (j0 >= nw || row >= m) return;
+  const int j1 = min(nw, j0 + kWordChunk);
   unsigned c = 0;
-  for (int j = lane; j < nw; j += 32) c += __popc(words[(size_t)j * m + row]);  // [word][row] layout
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) rowcnt[row] = c;
+#pragma unroll 8
+  for (int j = j0; j < j1; ++j) c += __popc(words[(size_t)j * m + row]);
+  cc[(size_t)ch * m + row] = c;
+  if (c) atomicAdd(rowcnt + row, (unsigned long long)c);
 }
-
 }  // namespace
 
-cudaError_t launch_words_rowcnt(const unsigned* words, int nw, int m, unsigned long long* rowcnt, cudaStream_t s) {
-  words_rowcnt<<<(m + 7) / 8, 256, 0, s>>>(words, nw, m, rowcnt);
+cudaError_t launch_words_count(const unsigned* words, int nw, int m, unsigned* cc, unsigned long long* rowcnt,
+                               cudaStream_t s) {
+  const long long warps = (long long)((m + 31) / 32) * ((nw + kWordChunk - 1) / kWordChunk);
+  words_count<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(words, nw, m, cc, rowcnt);
   return cudaGetLastError();
 }
 

@@ -32,8 +32,8 @@ cudaError_t launch_extract_write_f32(int R, const ExtractArgs& a, cudaStream_t s
 
 #define RPCA_CASE(RR) \
   case RR:            \
-    return launch_extract_words_t<RR>(a, words, vals, nw, s);
-cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, const float* vals, int nw,
+    return launch_extract_words_t<RR>(a, words, cc, nw, s);
+cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, const unsigned* cc, int nw,
                                      cudaStream_t s) {
   switch (R) { RPCA_FOR_EACH_R(RPCA_CASE) }
   return cudaErrorInvalidValue;

@@ -391,89 +391,87 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
 }
 
 // The ordered write from the support words of the tensor-core pass (the bit of column j of
-// row i is set iff |D_ij - L_ij| > zeta_k in that pass) and the values that pass kept: one
-// warp per row, 32 words at a time.  The warp scans the words' bit counts, then takes the
-// chunk's support entries in order, lane l the entries l, l + 32, ... (up to UNR per lane at
-// once, so their loads are in flight together): the source word by a binary search over the
-// scan, the column by the rank of the bit, the value S_ij = D_ij - L_ij from the word's slot
-// (or, for a word with more set bits than its slot holds, rebuilt from D and the factors).
-// Consecutive lanes write consecutive positions (rowoff[i] onwards).
+// row i is set iff |D_ij - L_ij| > zeta_k in that pass; [word][row] layout): one warp per row
+// and chunk of kWordChunk words, so that the rows' chunks run independently.  The chunk's
+// first position is the row's offset (rowoff) plus the counts of the row's earlier chunks
+// (cc); the warp scans its words' bit counts and takes the chunk's entries in order, lane l
+// the entries l, l + 32, ... (UNR per lane at once, so that their loads are in flight
+// together): the word by a binary search over the scan, the column by the rank of the bit,
+// and S_ij = D_ij - L_ij rebuilt there (D is read only where a 32-byte sector holds a support
+// entry).  Consecutive lanes write consecutive positions.
 template <int R>
 __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const unsigned* __restrict__ words,
-                                                            const float* __restrict__ vals, int nw) {
+                                                            const unsigned* __restrict__ cc, int nw) {
   constexpr int UNR = 4;
   const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int nch = (nw + kWordChunk - 1) / kWordChunk;
+  const long long wid = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int row = (int)(wid / nch), ch = (int)(wid % nch);
   if (row >= a.m) return;
   const float* __restrict__ D = static_cast<const float*>(a.D);
   const float* __restrict__ W = static_cast<const float*>(a.W);
   const float* __restrict__ V = static_cast<const float*>(a.V);
+  unsigned earlier = 0;  // support entries in the row's earlier chunks
+  for (int c = lane; c < ch; c += 32) earlier += cc[(size_t)c * a.m + row];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) earlier += __shfl_xor_sync(0xffffffffu, earlier, o);
+  const unsigned long long base = a.rowoff[row] + earlier;
+  const int j0 = ch * kWordChunk;
+  const int j = j0 + lane;
+  const unsigned wd = (j < nw) ? words[(size_t)j * a.m + row] : 0u;
+  const unsigned c = __popc(wd);
+  unsigned incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned excl = incl - c;
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
   float w[R];
 #pragma unroll
   for (int k = 0; k < R; ++k) w[k] = W[(long long)row * R + k];
-  const unsigned long long base = a.rowoff[row];
-  unsigned long long carry = 0;
-  for (int j0 = 0; j0 < nw; j0 += 32) {
-    const int j = j0 + lane;
-    const unsigned wd = (j < nw) ? words[(size_t)j * a.m + row] : 0u;  // [word][row] layout
-    const unsigned c = __popc(wd);
-    unsigned incl = c;
+  for (unsigned e0 = 0; e0 < total; e0 += 32 * UNR) {
+    int col[UNR];
+    float d[UNR], v[UNR][R];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const unsigned excl = incl - c;
-    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    for (unsigned e0 = 0; e0 < total; e0 += 32 * UNR) {
-      int col[UNR];
-      bool slot[UNR];
-      float d[UNR], v[UNR][R];
+    for (int u = 0; u < UNR; ++u) {
+      const unsigned e = e0 + 32u * u + lane;
+      // source lane: the number of lanes whose inclusive count is <= e
+      int src = 0;
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const unsigned e = e0 + 32u * u + lane;
-        // source lane: the number of lanes whose inclusive count is <= e
-        int src = 0;
-#pragma unroll
-        for (int b = 16; b > 0; b >>= 1) {
-          const unsigned t = __shfl_sync(0xffffffffu, incl, src + b - 1);
-          if (t <= e) src += b;
-        }
-        unsigned ws = __shfl_sync(0xffffffffu, wd, src & 31);
-        const unsigned es = __shfl_sync(0xffffffffu, excl, src & 31);
-        col[u] = -1;
-        slot[u] = false;
-        if (e < total) {
-          const unsigned q0 = e - es;  // rank of the entry in its word
-          slot[u] = __popc(ws) <= (unsigned)kSlotVals;
-          for (unsigned q = 0; q < q0; ++q) ws &= ws - 1u;  // drop the lower set bits
-          col[u] = 32 * (j0 + src) + (__ffs(ws) - 1);
-          if (slot[u]) {
-            d[u] = vals[((size_t)(j0 + src) * a.m + row) * kSlotVals + q0];
-          } else {  // more support entries in the word than its slot holds: rebuild
-            d[u] = D[(long long)row * a.ld + col[u]];
-#pragma unroll
-            for (int k = 0; k < R; ++k) v[u][k] = V[(long long)col[u] * R + k];
-          }
-        }
+      for (int b = 16; b > 0; b >>= 1) {
+        const unsigned t = __shfl_sync(0xffffffffu, incl, src + b - 1);
+        if (t <= e) src += b;
       }
+      unsigned ws = __shfl_sync(0xffffffffu, wd, src & 31);
+      const unsigned es = __shfl_sync(0xffffffffu, excl, src & 31);
+      col[u] = -1;
+      if (e < total) {
+        for (unsigned q = es; q < e; ++q) ws &= ws - 1u;  // drop the lower set bits
+        col[u] = 32 * (j0 + src) + (__ffs(ws) - 1);
+        d[u] = D[(long long)row * a.ld + col[u]];
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        if (col[u] >= 0) {
-          const unsigned long long pos = base + carry + e0 + 32u * u + lane;
-          a.idx[pos] = (long long)row * a.n + col[u];
-          a.val[pos] = static_cast<double>(slot[u] ? d[u] : d[u] - rebuild<float, R>(w, v[u]));
-        }
+        for (int k = 0; k < R; ++k) v[u][k] = V[(long long)col[u] * R + k];
       }
     }
-    carry += total;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      if (col[u] >= 0) {
+        const unsigned long long pos = base + e0 + 32u * u + lane;
+        a.idx[pos] = (long long)row * a.n + col[u];
+        a.val[pos] = static_cast<double>(d[u] - rebuild<float, R>(w, v[u]));
+      }
+    }
   }
 }
 
 template <int R>
-cudaError_t launch_extract_words_t(const ExtractArgs& a, const unsigned* words, const float* vals, int nw,
+cudaError_t launch_extract_words_t(const ExtractArgs& a, const unsigned* words, const unsigned* cc, int nw,
                                    cudaStream_t s) {
-  extract_words_kernel<R><<<(a.m + 7) / 8, 256, 0, s>>>(a, words, vals, nw);
+  const long long warps = (long long)a.m * ((nw + kWordChunk - 1) / kWordChunk);
+  extract_words_kernel<R><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(a, words, cc, nw);
   return cudaGetLastError();
 }
 

@@ -136,7 +136,6 @@ struct TcArgs {
   unsigned* masks;
   long long mask_wr;
   unsigned* swords;
-  float* svals;
   int nw;
   int* emit_k;
   const float* tgram;
@@ -604,40 +603,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         if (MASK || EMIT) nnz += __popc(bits);
         res += rq;
         const int erow = (rt0 + rtl) * BM + rowl;
-        if (EMIT && erow < a.m) {
-          // the word's support bits and its first kSlotVals values S = D - L in column order:
-          // D is still in the stage (this thread's 128-byte row segment, which only it reads
-          // and which its Z overwrites below) and L is in z at the support; the values are
-          // packed to the front of that segment (an entry never moves up, so no unread D is
-          // overwritten) and written as two 16-byte stores.  Layout [word][row]: the lanes of
-          // a warp (consecutive rows) write consecutive slots.
-          uint8_t* seg = stg + h * (D_BYTES / 2) + rowl * 128;
-          const int sw = rowl & 7;
-          int ecnt = 0;
-#pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            if ((bits >> c) & 1u) {
-              const float sv = *reinterpret_cast<const float*>(seg + (((c >> 2) ^ sw) << 4) + 4 * (c & 3)) - z[c];
-              if (ecnt < kSlotVals) *reinterpret_cast<float*>(seg + (((ecnt >> 2) ^ sw) << 4) + 4 * (ecnt & 3)) = sv;
-              ++ecnt;
-            }
-          }
-          float4 v0 = *reinterpret_cast<const float4*>(seg + ((0 ^ sw) << 4));
-          float4 v1 = *reinterpret_cast<const float4*>(seg + ((1 ^ sw) << 4));
-          v0.x = ecnt > 0 ? v0.x : 0.f;
-          v0.y = ecnt > 1 ? v0.y : 0.f;
-          v0.z = ecnt > 2 ? v0.z : 0.f;
-          v0.w = ecnt > 3 ? v0.w : 0.f;
-          v1.x = ecnt > 4 ? v1.x : 0.f;
-          v1.y = ecnt > 5 ? v1.y : 0.f;
-          v1.z = ecnt > 6 ? v1.z : 0.f;
-          v1.w = ecnt > 7 ? v1.w : 0.f;
-          const size_t widx = (size_t)(2 * (ct0 + ctl) + h) * a.m + erow;
-          float4* dst = reinterpret_cast<float4*>(a.svals + widx * kSlotVals);
-          dst[0] = v0;
-          dst[1] = v1;
-          a.swords[widx] = bits;
-        }
+        // the word's support bits, [word][row] layout: the lanes of a warp (consecutive rows)
+        // write consecutive words
+        if (EMIT && erow < a.m) a.swords[(size_t)(2 * (ct0 + ctl) + h) * a.m + erow] = bits;
         // Z -> bf16 hi/lo of row rowl, columns 32h .. 32h+31: FP32 D, logical 16-byte chunks
         // 0..3 (hi) and 4..7 (lo) of box h; bf16 D, chunks 4h .. 4h+3 of the hi and lo tiles
         uint8_t* zhi = DM == 0 ? stg + h * (D_BYTES / 2) : stg;
@@ -825,7 +793,6 @@ cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dma
   a.masks = p.masks;
   a.mask_wr = p.mask_wr;
   a.swords = p.swords;
-  a.svals = p.svals;
   a.nw = p.nw;
   a.emit_k = p.emit_k;
   a.tgram = p.tgram;
