@@ -916,6 +916,42 @@ __device__ __noinline__ void write_images(const SmallArgs& a, int set, int side,
 }
 
 // ---------------------------------------------------------------------------------------
+// Half-block steps: the m-side rows (side 0) and the n-side rows (side 1) are
+// processed at once, side s by threads s HT .. s HT + HT - 1 with its own named barrier
+// (1 + s) and its own staging rows, so neither side waits for the other.
+constexpr int HT = ST / 2;
+
+__device__ __forceinline__ void half_sync(int side) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + side), "r"(HT) : "memory");
+}
+
+// Entries p = tl and p = tl + HT (p < w^2) of X^T Y over nrows staged rows (row stride WM),
+// each added by one thread in row order into acc[0], acc[1] (no cross-thread combination).
+template <typename T, int WM>
+__device__ __forceinline__ void gram_rows_h(const T* X, const T* Y, int w, int nrows, int tl, T (&acc)[2]) {
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int p = tl + e * HT;
+    if (p < w * w) {
+      const int ca = p / w, cb = p % w;
+      T s = acc[e];
+      for (int i = 0; i < nrows; ++i) s = fma(X[i * WM + ca], Y[i * WM + cb], s);
+      acc[e] = s;
+    }
+  }
+}
+
+// This block's partial of the Gram matrix (entries as in gram_rows_h) into slot `slot`.
+template <typename T>
+__device__ __forceinline__ void gram_put_h(const T (&acc)[2], int w, void* part, int slot, int tl) {
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int p = tl + e * HT;
+    if (p < w * w) slot_ptr<T>(part, slot, blockIdx.x)[p] = acc[e];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Trim (Algorithm 2) and the hand-over to the next pass.
 //
 // The pass of iteration k reads W = U_k Sigma_k, V_k and, in place of the orthonormal bases
@@ -965,30 +1001,30 @@ template <typename T, int WM>
 __device__ void trim_hand_over(const SmallArgs& a, Smem<T, WM>& sh) {
   const int r = a.r, t = threadIdx.x;
   const bool do_trim = a.st->trim != 0;
-  for (int side = 0; side < 2; ++side) {
-    const int rows = side ? a.n : a.m;
-    const T cap = trim_cap<T>(a, side);
-    const T* F = static_cast<const T*>(side ? a.V : a.U);
-    int lo, hi;
-    block_range(rows, lo, hi);
-    T acc = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
-      T x[WM];
-      zero_row<T, WM>(x);
-      if (i < hi) {
-        T f[WM];
-        load_row<T, WM>(F, i, r, f);
-        trim_row<T, WM>(f, cap, do_trim, x);
-        hand_over_row<T, WM>(a, side, i, f, x, sh.sv[0]);
-      }
-      stage_row<T, WM>(sh.stage[0], t, x);
-      __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], r, sh.stage[0], r, min(ST, hi - c0), acc);
-      __syncthreads();
+  const int side = t / HT, tl = t % HT;  // both sides at once on the two half blocks
+  const int rows = side ? a.n : a.m;
+  const T cap = trim_cap<T>(a, side);
+  const T* F = static_cast<const T*>(side ? a.V : a.U);
+  T* sx = sh.stage[side];
+  int lo, hi;
+  block_range(rows, lo, hi);
+  T acc[2] = {T(0), T(0)};
+  for (int c0 = lo; c0 < hi; c0 += HT) {
+    const int i = c0 + tl;
+    T x[WM];
+    zero_row<T, WM>(x);
+    if (i < hi) {
+      T f[WM];
+      load_row<T, WM>(F, i, r, f);
+      trim_row<T, WM>(f, cap, do_trim, x);
+      hand_over_row<T, WM>(a, side, i, f, x, sh.sv[0]);
     }
-    gram_store<T>(acc, r * r, a.part, 6 + side, sh);
+    stage_row<T, WM>(sx, tl, x);
+    half_sync(side);
+    gram_rows_h<T, WM>(sx, sx, r, min(HT, hi - c0), tl, acc);
+    half_sync(side);
   }
+  gram_put_h<T>(acc, r, a.part, 6 + side, tl);
 }
 
 // T_u, T_v of the trimmed factors the last pass read, from the Gram partials in slots 6, 7
@@ -997,42 +1033,6 @@ template <typename T, int WM>
 __device__ void trimmed_t_factors(const SmallArgs& a, Smem<T, WM>& sh) {
   reduce_slots(a.part, 6, 2, a.r * a.r, &sh.G[0][0], sh);
   factor_pair<T, WM>(a.r, 0, 1, sh);
-}
-
-// ---------------------------------------------------------------------------------------
-// Half-block steps of the update: the m-side rows (side 0) and the n-side rows (side 1) are
-// processed at once, side s by threads s HT .. s HT + HT - 1 with its own named barrier
-// (1 + s) and its own staging rows, so neither side waits for the other.
-constexpr int HT = ST / 2;
-
-__device__ __forceinline__ void half_sync(int side) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + side), "r"(HT) : "memory");
-}
-
-// Entries p = tl and p = tl + HT (p < w^2) of X^T Y over nrows staged rows (row stride WM),
-// each added by one thread in row order into acc[0], acc[1] (no cross-thread combination).
-template <typename T, int WM>
-__device__ __forceinline__ void gram_rows_h(const T* X, const T* Y, int w, int nrows, int tl, T (&acc)[2]) {
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int p = tl + e * HT;
-    if (p < w * w) {
-      const int ca = p / w, cb = p % w;
-      T s = acc[e];
-      for (int i = 0; i < nrows; ++i) s = fma(X[i * WM + ca], Y[i * WM + cb], s);
-      acc[e] = s;
-    }
-  }
-}
-
-// This block's partial of the Gram matrix (entries as in gram_rows_h) into slot `slot`.
-template <typename T>
-__device__ __forceinline__ void gram_put_h(const T (&acc)[2], int w, void* part, int slot, int tl) {
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const int p = tl + e * HT;
-    if (p < w * w) slot_ptr<T>(part, slot, blockIdx.x)[p] = acc[e];
-  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1412,7 +1412,8 @@ __device__ void orth_second_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>&
   const int t = threadIdx.x, Rc = a.Rc;
   reduce_slots(a.part, s1, 2, w * w, &sh.G[0][0], sh);
   factor_pair<T, WM>(w, 0, 1, sh);
-  for (int side = 0; side < 2; ++side) {
+  {
+    const int side = t / HT, tl = t % HT;
     const int rows = side ? a.n : a.m;
     const T* Y = static_cast<const T*>(side ? a.Y2 : a.Y1);
     T* B = static_cast<T*>(side ? a.Vt : a.Ut);
@@ -1420,7 +1421,7 @@ __device__ void orth_second_pass(const SmallArgs& a, int w, int s1, Smem<T, WM>&
     T* d1 = static_cast<T*>(side ? a.Vc : a.Wc);
     int lo, hi;
     block_range(rows, lo, hi);
-    for (int i = lo + t; i < hi; i += ST) {
+    for (int i = lo + tl; i < hi; i += HT) {
       T y[WM], q[WM], z[WM];
       load_row<T, WM>(Y, i, w, y);
       row_times<T, WM>(y, sh.tm[side], q);
@@ -1484,15 +1485,18 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   cta_totals(a, res2, nnz, sh);
   if (phase == 0 && first && blockIdx.x == 0 && t == 0) st->normD2 = res2;
 
-  // A: own rows of Y1 = Z V~, Y2 = Z^T U~; partials of B = U~^T Y1 (slot 0), Y1^T Y1
-  // (slot 1) and Y2^T Y2 (slot 2)
-  for (int side = 0; side < 2; ++side) {
+  // A: own rows of Y1 = Z V~, Y2 = Z^T U~ (both sides at once on the two half blocks);
+  // partials of B = U~^T Y1 (slot 0), Y1^T Y1 (slot 1) and Y2^T Y2 (slot 2)
+  {
+    const int side = t / HT, tl = t % HT;
     const int rows = side ? n : m;
+    T* sy = sh.stage[side];          // rows of Y1 / Y2
+    T* su = sh.stage[0] + HT * WM;   // side 0: rows of U~
     int lo, hi;
     block_range(rows, lo, hi);
-    T accB = T(0), accG = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
+    T accB[2] = {T(0), T(0)}, accG[2] = {T(0), T(0)};
+    for (int c0 = lo; c0 < hi; c0 += HT) {
+      const int i = c0 + tl;
       T y[WM], u[WM];
       zero_row<T, WM>(y);
       zero_row<T, WM>(u);
@@ -1503,16 +1507,16 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
         store_row<T, WM>(side ? Y2 : Y1, i, w, y);
         if (!side) load_row<T, WM>(Ut, i, w, u);
       }
-      stage_row<T, WM>(sh.stage[1], t, y);
-      if (!side) stage_row<T, WM>(sh.stage[0], t, u);
-      __syncthreads();
-      const int nr = min(ST, hi - c0);
-      if (!side) accB = gram_acc<T, WM>(sh.stage[0], w, sh.stage[1], w, nr, accB);
-      accG = gram_acc<T, WM>(sh.stage[1], w, sh.stage[1], w, nr, accG);
-      __syncthreads();
+      stage_row<T, WM>(sy, tl, y);
+      if (!side) stage_row<T, WM>(su, tl, u);
+      half_sync(side);
+      const int nr = min(HT, hi - c0);
+      if (!side) gram_rows_h<T, WM>(su, sy, w, nr, tl, accB);
+      gram_rows_h<T, WM>(sy, sy, w, nr, tl, accG);
+      half_sync(side);
     }
-    if (!side) gram_store(accB, w * w, a.part, 0, sh);
-    gram_store(accG, w * w, a.part, 1 + side, sh);
+    if (!side) gram_put_h<T>(accB, w, a.part, 0, tl);
+    gram_put_h<T>(accG, w, a.part, 1 + side, tl);
   }
   if (!grid_barrier(st, sh)) return;
 
@@ -1550,18 +1554,20 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   // norms, each divided by sigma_c^2, decides convergence.
   const int nr = (phase == 0) ? 1 : r;
   T res = T(0);
-  for (int side = 0; side < 2; ++side) {
+  {
+    const int side = t / HT, tl = t % HT;
     const int rows = side ? n : m;
     const T* B = side ? Vt : Ut;
     T* Y = side ? Y2 : Y1;
     T* F = static_cast<T*>(side ? a.V : a.U);
     const T* Mb = sh.mat[side];      // basis coefficients
     const T* My = sh.mat[1 - side];  // product coefficients
+    T* sq = sh.stage[side];
     int lo, hi;
     block_range(rows, lo, hi);
-    T acc = T(0);
-    for (int c0 = lo; c0 < hi; c0 += ST) {
-      const int i = c0 + t;
+    T acc[2] = {T(0), T(0)};
+    for (int c0 = lo; c0 < hi; c0 += HT) {
+      const int i = c0 + tl;
       T q[WM];
       zero_row<T, WM>(q);
       if (i < hi) {
@@ -1580,12 +1586,12 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
         row_times<T, WM>(y, sh.tm[side], q);
         store_row<T, WM>(Y, i, w, q);
       }
-      stage_row<T, WM>(sh.stage[0], t, q);
-      __syncthreads();
-      acc = gram_acc<T, WM>(sh.stage[0], w, sh.stage[0], w, min(ST, hi - c0), acc);
-      __syncthreads();
+      stage_row<T, WM>(sq, tl, q);
+      half_sync(side);
+      gram_rows_h<T, WM>(sq, sq, w, min(HT, hi - c0), tl, acc);
+      half_sync(side);
     }
-    gram_store(acc, w * w, a.part, 3 + side, sh);
+    gram_put_h<T>(acc, w, a.part, 3 + side, tl);
   }
   sh.red[t] = res;
   __syncthreads();
