@@ -278,6 +278,9 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.tcta = c->plan.min_cta;
     t.tfac = init ? nullptr : c->tfac;
     CK(launch_fused_pass_tc(&c->dmap, &c->dmap_lo, c->dmode, t, c->stream));
+    if (t.masks)  // the support changes since the previous pass, one count per CTA of the pass
+      CK(launch_count_mask_changes(c->masks, c->mask_words, 256ll * c->TR * c->TC, c->st, c->chgP, c->plan.ncta,
+                                   c->stream));
   } else {
     CK(launch_fused_pass(c->prec, R, a, c->stream));
   }

@@ -252,6 +252,9 @@ cudaError_t launch_scan_rows(const unsigned long long* cnt, unsigned long long* 
 // per row and per chunk of 32 words (cc[chunk][row]; rowcnt must be zero before), then (after
 // the scan of rowcnt) the ordered write of indices and values S_ij = D_ij - L_ij.
 constexpr int kWordChunk = 32;
+// Support changes of the learned schedule after a tensor-core pass: chgP[b] for b < nblocks.
+cudaError_t launch_count_mask_changes(const unsigned* masks, long long sz, long long nwords, const DevState* st,
+                                      unsigned long long* chgP, int nblocks, cudaStream_t s);
 cudaError_t launch_words_count(const unsigned* words, int nw, int m, unsigned* cc, unsigned long long* rowcnt,
                                cudaStream_t s);
 cudaError_t launch_extract_words_f32(int R, const ExtractArgs& a, const unsigned* words, const unsigned* cc, int nw,

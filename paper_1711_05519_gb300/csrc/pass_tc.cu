@@ -186,9 +186,10 @@ __device__ __forceinline__ void tmem_ld_y(uint32_t taddr, uint32_t (&v)[NY]) {
 // lo parts (dmap = hi, dmap_lo = lo, one 128 x 64 box each); the lo part is read only once
 // DevState.use_lo is set, and D = hi + lo (exact in FP32).  Either way the tile's D area is
 // 32 KB and Z is written over it (where: zhi_off / zlo_off).  RK: operand image layout (8 or 16).
-// MODE_MASK: also write the support as a bitmask and count the entries whose membership
-// differs from the previous pass's bitmask (the learned schedule's support-change
-// statistic).  Layout, tile-major so that a warp's 32 rows are 32 consecutive words: word
+// MODE_MASK: also write the support as a bitmask, from which count_mask_changes takes the
+// entries whose membership differs from the previous pass's (the learned schedule's
+// support-change statistic).  Layout, tile-major so that a warp's 32 rows are 32 consecutive
+// words: word
 // ((rt TC + ct) 2 + h) 128 + row-in-tile holds columns 64 ct + 32 h .. + 31 of that row.
 // MODE_PARTIAL: a NaN entry of D is unobserved: it is outside the support and the residual,
 // and Z = L there; an observed entry outside the support gets Z = L + (D - L) / p (the step of
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ double red_res[EPI_WARPS];
-  __shared__ unsigned long long red_nnz[EPI_WARPS], red_chg[EPI_WARPS];
+  __shared__ unsigned long long red_nnz[EPI_WARPS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cta = blockIdx.x;
@@ -471,26 +472,17 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     // ~40 terms (one chain over the thousands of terms a thread sees per pass biased err_k by
     // up to ~1e-4 relative); the totals over threads are taken in FP64
     float res = 0.f;
-    unsigned nnz = 0, chg = 0;
-    // support bitmasks of this pass (k even: buffer 0) and of the previous one, mask_wr words
-    // each (at least TR TC 256)
-    const long long mask_sz = a.mask_wr;
-    unsigned* mask_new = MASK ? a.masks + ((a.st->k & 1) ? mask_sz : 0) : nullptr;
-    const unsigned* mask_old = MASK ? a.masks + ((a.st->k & 1) ? 0 : mask_sz) : nullptr;
+    unsigned nnz = 0;
+    // support bitmask of this pass (k even: buffer 0, odd: buffer 1; mask_wr words each, at
+    // least TR TC 256); the entries that changed since the previous pass are counted from the
+    // two buffers by a separate kernel (count_mask_changes)
+    unsigned* mask_new = MASK ? a.masks + ((a.st->k & 1) ? a.mask_wr : 0) : nullptr;
     // the tile loop in two copies, without and with the support words, so that the plain
     // passes keep their registers
     auto tile_loop = [&](auto emit_c) {
       constexpr bool EMIT = decltype(emit_c)::value;
       for (int t = grp; t < ntiles && !abort_flag; t += 2) {
         const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE, lb = t & 1, yb = rtl & 1;
-        // support word of this thread's row and columns in the previous pass, loaded here so that
-        // its latency passes while the tile is waited for (used after Z is handed on)
-        long long mw = 0;
-        unsigned mold = 0;
-        if (MASK) {
-          mw = (((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl;
-          mold = mask_old[mw];
-        }
         if (rtl % G2 == 0 && rtl > 0) {
           // chunk c - 1 of column tile ctl's Y2 accumulator is complete: read it out (hi + lo
           // column halves, this warp's half of the components) before this tile's products
@@ -632,10 +624,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[B_ZFULL + s]);
-        if (MASK) {  // rows past m hold no support (their D reads as zero and L as zero)
-          mask_new[mw] = bits;
-          chg += __popc(bits ^ mold);
-        }
+        if (MASK)  // tile-major; rows past m hold no support (their D reads as zero, L too)
+          mask_new[(((long long)(rt0 + rtl) * a.TC + (ct0 + ctl)) * 2 + h) * BM + rowl] = bits;
 
         if (ctl == nct - 1 && h == 0) {
           // drain Y1 of this row tile
@@ -694,30 +684,26 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
     // CTA totals of the residual and the support size
     double rd = (double)res;
-    unsigned long long nz = nnz, cz = chg;
+    unsigned long long nz = nnz;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       rd += __shfl_xor_sync(0xffffffffu, rd, o);
       nz += __shfl_xor_sync(0xffffffffu, nz, o);
-      if (MASK) cz += __shfl_xor_sync(0xffffffffu, cz, o);
     }
     if (lane == 0) {
       red_res[warp - 4] = rd;
       red_nnz[warp - 4] = nz;
-      red_chg[warp - 4] = cz;
     }
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS));
     if (tid == 128) {
       double tr = 0.0;
-      unsigned long long tz = 0, tc = 0;
+      unsigned long long tz = 0;
       for (int w = 0; w < EPI_WARPS; ++w) {
         tr += red_res[w];
         tz += red_nnz[w];
-        tc += red_chg[w];
       }
       a.resP[cta] = tr;
       a.nnzP[cta] = tz;
-      if (MASK) a.chgP[cta] = tc;
     }
   }
   tc_fence_before();
