@@ -734,38 +734,32 @@ def main():
     solver = P.Solver(p["beta"], p["gamma"], TOL, precision="fp32", beta_init=p["beta_init"], mu_trim=p["mu"],
                       stream=stream)
 
-    run_ms = []
-    sparse_ms = []
+    events = []  # per step: (start, end of the iteration loop, start, end of the sparse output)
 
     def one_solve():
         solver.init(D, RANK)
-        prof0 = solver.profile()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         code, stats = solver.run()
-        e1.record(stream)
-        prof1 = solver.profile()
-        run_ms.append(e0.elapsed_time(e1))
+        ev[1].record(stream)
         U, s, V = solver.lowrank()
         # the sparse component S_k (indices and values) is part of every step
-        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2.record(stream)
+        ev[2].record(stream)
         idx, val = solver.sparse(cap=stats[-1]["nnz"])
-        e3.record(stream)
-        e3.synchronize()
-        sparse_ms.append(e2.elapsed_time(e3))
+        ev[3].record(stream)
+        events.append(ev)
         assert idx.numel() == stats[-1]["nnz"] or code != P.OK
-        return code, stats, prof0, prof1
+        return code, stats
 
     for _ in range(args.warmup):
-        code, stats, _, _ = one_solve()
+        code, stats = one_solve()
     assert code == P.OK and stats[-1]["err"] < TOL, (code, stats[-1])
     iters = stats[-1]["k"]
 
+    # per-kernel CUDA events on the solver's stream (the profile accumulates pass and other
+    # kernel times over the timed steps; it is read once, after them)
     solver.set_profiling(True)
-    run_ms.clear()
-    sparse_ms.clear()
-    iter_pass_ms, iter_pass_n = 0.0, 0
+    events.clear()
     torch.cuda.synchronize(dev)
     barrier(world)
     with ClockSampler(dev.index or 0) as clk:
@@ -773,19 +767,21 @@ def main():
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(args.steps):
-            code, stats, prof0, prof1 = one_solve()
-            iter_pass_ms += prof1["pass_ms"] - prof0["pass_ms"]
-            iter_pass_n += prof1["pass_launches"] - prof0["pass_launches"]
+            code, stats = one_solve()
         t1.record(stream)
         torch.cuda.synchronize(dev)
     barrier(world)
     prof = solver.profile()
     solver.set_profiling(False)
+    run_ms = [e[0].elapsed_time(e[1]) for e in events]
+    sparse_ms = [e[2].elapsed_time(e[3]) for e in events]
+    iter_pass_ms, iter_pass_n = prof["pass_ms"], prof["pass_launches"]
     ms_per_step = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
     clocks = clk.summary()
     gpu_launches = int(prof["pass_launches"] + prof["other_launches"])
 
-    # roofline of the dominant kernel: the fused pass of Algorithm 1 (r = 5, FP32)
+    # roofline of the dominant kernel: the fused pass (r = 5, FP32), every launch of the timed
+    # steps (the initialisation's passes read D once as well)
     it_kind, _ = solver.pass_kind()
     kernel_name = "fused_pass_tc (tcgen05 + TMA)" if it_kind == "tensor" else "fused_pass_kernel<float,5> (SIMT)"
     pass_ms = iter_pass_ms / max(iter_pass_n, 1)

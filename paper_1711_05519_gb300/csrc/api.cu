@@ -65,7 +65,7 @@ struct rpca_ctx {
   unsigned long long* nnzP = nullptr;
   DevState* st = nullptr;
   DevStats* stats = nullptr;
-  int* h_flags = nullptr;  // pinned: k, done, status, conv, use_lo, emit, emit_k, pad
+  int* h_flags = nullptr;  // pinned: k, done, status, conv, use_lo, emit, emit_k, steps_run
   unsigned long long *rowcnt = nullptr, *rowoff = nullptr;
   bool ready = false;
   // learned threshold schedule: network parameters (mlp.cuh), unrolled depth, support
@@ -470,9 +470,10 @@ int read_flags(rpca_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
   return RPCA_OK;
 }
-// DevState layout: k, done, status, conv, use_lo, emit, emit_k are consecutive ints.
+// DevState layout: k, done, status, conv, use_lo, emit, emit_k, steps_run are consecutive ints.
 inline int flag_k(const rpca_ctx* c) { return c->h_flags[0]; }
 inline int flag_emit_k(const rpca_ctx* c) { return c->h_flags[6]; }
+inline int flag_steps_run(const rpca_ctx* c) { return c->h_flags[7]; }
 inline int flag_done(const rpca_ctx* c) { return c->h_flags[1]; }
 inline int flag_status(const rpca_ctx* c) { return c->h_flags[2]; }
 inline int flag_conv(const rpca_ctx* c) { return c->h_flags[3]; }
@@ -719,6 +720,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   h.inv_p = inv_p;
   h.emit_k = -1;
   CK(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  c->h_flags[7] = 0;  // steps_run as uploaded
 
   // Algorithm 3.  Phase A: sigma_1(D) with L = 0 and no threshold; phase B: top-r SVD of
   // D - S_{-1} (the pass with L = 0 and zeta_{-1} keeps exactly D_ij where |D_ij| <= zeta).
@@ -733,16 +735,19 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   bool conv = false;
   for (int steps = 0; steps < cap && !conv;) {
     // each phase takes two steps at least (its first step is never accepted unless it is
-    // the last allowed one), so the first batch has four; later ones one each
-    int batch = (steps == 0) ? 4 : 1;
+    // the last allowed one); the first batch has five steps (most initialisations end there),
+    // later ones two (a step queued behind the convergence costs a few microseconds, a wait
+    // for the host more)
+    int batch = (steps == 0) ? 5 : 2;
     if (batch > cap - steps) batch = cap - steps;
     for (int i = 0; i < batch; ++i) {
       if ((st = run_pass(c, c->Rb, true))) return st;
       if ((st = run_small(c, small_args(c, SM_RR, c->Rb)))) return st;
     }
     steps += batch;
+    const int run0 = flag_steps_run(c);
     if ((st = read_flags(c))) return st;
-    prof_collect(c, -1);
+    prof_collect(c, flag_steps_run(c) - run0);  // the passes queued behind convergence did no work
     if (flag_status(c)) return flag_status(c);
     conv = flag_conv(c) != 0;
   }
@@ -790,15 +795,17 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     if (flag_status(c)) return flag_status(c);
     done = flag_done(c);
   }
-  if ((st = read_flags(c))) return st;
+  // the flags are current: read at the end of the last chunk (or before the loop)
   const int k1 = flag_k(c);
   int count = k1 - k0 + (flag_done(c) ? 1 : 0);
   if (count > n_iters) count = n_iters;
   if (count < 0) count = 0;
   prof_collect(c, count);
-  std::vector<DevStats> hs((size_t)(count > 0 ? count : 1));
-  if (count > 0) {
-    CK(cudaMemcpyAsync(hs.data(), c->stats + k0, sizeof(DevStats) * count, cudaMemcpyDeviceToHost, c->stream));
+  // the statistics of the passes run, and of the last pass when the run ended (one copy)
+  const int ncopy = std::max(count, flag_done(c) ? k1 - k0 + 1 : 0);
+  std::vector<DevStats> hs((size_t)(ncopy > 0 ? ncopy : 1));
+  if (ncopy > 0) {
+    CK(cudaMemcpyAsync(hs.data(), c->stats + k0, sizeof(DevStats) * ncopy, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
   if (out)
@@ -816,9 +823,7 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     }
   if (n_done) *n_done = count;
   if (flag_done(c)) {
-    DevStats last;
-    CK(cudaMemcpyAsync(&last, c->stats + k1, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    const DevStats& last = hs[(size_t)(k1 - k0)];
     c->last_nnz = last.nnz;  // the support the pass at iterate k1 counted
     c->last_nnz_k = k1;
     return (last.err < c->p.tol) ? RPCA_OK : RPCA_ERR_NOT_CONVERGED;

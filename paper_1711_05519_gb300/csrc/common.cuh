@@ -34,7 +34,7 @@ struct DevState {
   int use_lo;            // bf16 split storage of D: the passes also read the lo part
   int emit;              // the next tensor-core pass writes its support words (predicted last)
   int emit_k;            // k of the last pass that wrote them (-1: none)
-  int pad1;
+  int steps_run;         // initialisation steps that did work (profiling of the passes)
   double split_switch;   // bf16 split storage: set use_lo once err_k falls below this
   double inv_p;          // partial observation: m n / |observed entries| (1 otherwise)
   int max_iter;

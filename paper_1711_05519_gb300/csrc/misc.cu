@@ -103,24 +103,29 @@ __global__ void __launch_bounds__(256) words_count(const unsigned* __restrict__ 
 // Support changes between the learned schedule's two bitmask buffers (the one this pass
 // wrote, by the parity of k, against the other): block b counts its share of the words into
 // chgP[b] (a fixed split and a fixed-order tree, so the count per block is deterministic).
-__global__ void __launch_bounds__(256) count_mask_changes(const unsigned* __restrict__ masks, long long sz,
-                                                          long long nwords, const DevState* st,
-                                                          unsigned long long* __restrict__ chgP) {
-  __shared__ unsigned long long part[8];
+__global__ void __launch_bounds__(1024) count_mask_changes(const unsigned* __restrict__ masks, long long sz,
+                                                           long long nwords, const DevState* st,
+                                                           unsigned long long* __restrict__ chgP) {
+  __shared__ unsigned part[32];
   if (st->done) return;
-  const unsigned* cur = masks + ((st->k & 1) ? sz : 0);
-  const unsigned* prev = masks + ((st->k & 1) ? 0 : sz);
-  const long long chunk = (nwords + gridDim.x - 1) / gridDim.x;
-  const long long lo = (long long)blockIdx.x * chunk, hi = min(nwords, lo + chunk);
-  unsigned long long c = 0;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) c += __popc(cur[i] ^ prev[i]);
+  const uint4* cur = reinterpret_cast<const uint4*>(masks + ((st->k & 1) ? sz : 0));
+  const uint4* prev = reinterpret_cast<const uint4*>(masks + ((st->k & 1) ? 0 : sz));
+  const long long nv = nwords / 4;  // nwords is a multiple of 256
+  const long long chunk = (nv + gridDim.x - 1) / gridDim.x;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(nv, lo + chunk);
+  unsigned c = 0;
+#pragma unroll 4
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint4 a = cur[i], b = prev[i];
+    c += __popc(a.x ^ b.x) + __popc(a.y ^ b.y) + __popc(a.z ^ b.z) + __popc(a.w ^ b.w);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int w = 0; w < 8; ++w) t += part[w];
+    for (int w = 0; w < 32; ++w) t += part[w];
     chgP[blockIdx.x] = t;
   }
 }
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(256) count_mask_changes(const unsigned* __rest
 
 cudaError_t launch_count_mask_changes(const unsigned* masks, long long sz, long long nwords, const DevState* st,
                                       unsigned long long* chgP, int nblocks, cudaStream_t s) {
-  count_mask_changes<<<nblocks, 256, 0, s>>>(masks, sz, nwords, st, chgP);
+  count_mask_changes<<<nblocks, 1024, 0, s>>>(masks, sz, nwords, st, chgP);
   return cudaGetLastError();
 }
 

@@ -1480,6 +1480,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   // without waiting for each one (read here, before block 0 updates them at the end)
   const int phase = st->init_phase, step = st->init_step;
   const bool first = step == 0, force = step >= a.init_max - 1;
+  if (blockIdx.x == 0 && t == 0) st->steps_run += 1;  // read by the host after every batch
   double res2;
   unsigned long long nnz;
   cta_totals(a, res2, nnz, sh);
