@@ -269,7 +269,7 @@ int run_pass(rpca_ctx* c, int R, bool init) {
     t.mask_wr = c->mask_words;
     t.chgP = a.chgP;
     t.partial = a.partial;
-    t.swords = (!init && !c->dmode) ? c->swords : nullptr;
+    t.swords = (!init && !c->dmode && !track) ? c->swords : nullptr;  // not with the learned masks
     t.nw = 2 * c->TC;
     t.emit_k = &c->st->emit_k;
     t.tgram = static_cast<const float*>(c->part);
@@ -422,7 +422,7 @@ SmallArgs small_args(rpca_ctx* c, int mode, int R) {
   a.n_p2 = g.n_p2;
   a.p1_nsl = use_tc(c, R) ? c->d_p1nsl : nullptr;
   a.R2 = use_tc(c, R) ? tc_image_rank(R) : R;
-  a.emit_ok = (c->swords && c->tc_iter && !c->dmode) ? 1 : 0;
+  a.emit_ok = (c->swords && c->tc_iter && !c->dmode && !learned(c)) ? 1 : 0;
   a.tfac = (mode == SM_UPDATE && c->tc_iter) ? c->tfac : nullptr;
   a.n_cta = g.n_cta;
   a.P1 = c->P1;

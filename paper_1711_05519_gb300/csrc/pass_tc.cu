@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     const bool tcta = cta == a.tcta && a.tfac != nullptr;
     // this pass writes the support words of S_k when the update before it predicted that it is
     // the last one (FP32 D only)
-    const bool emit = DM == 0 && a.swords != nullptr && a.st->emit != 0;
+    const bool emit = DM == 0 && !MASK && a.swords != nullptr && a.st->emit != 0;
     if (emit && cta == 0 && tid == 128) *a.emit_k = a.st->k;
     {
       // zero this CTA's columns of the group's two Y2 slices before the first add (the adds
@@ -648,8 +648,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
         }
       }
     };
-    if (DM == 0 && emit)
-      tile_loop(BoolC<DM == 0>{});
+    if (DM == 0 && !MASK && emit)
+      tile_loop(BoolC<DM == 0 && !MASK>{});
     else
       tile_loop(BoolC<false>{});
     // drain Y2: the last chunk of every column tile is still in tensor memory; each warp takes
