@@ -90,6 +90,7 @@ struct rpca_ctx {
   unsigned* wcc = nullptr;     // support counts per row and chunk of support words
   long long last_nnz = -1;     // support count of the pass at iterate last_nnz_k (host copy)
   int last_nnz_k = -1;
+  int last_iters = 0;          // iterations the last solve to its end took
   // operand images: set 0 read by the initialisation's pass, set 1 by the iteration's
   uint8_t *wop[2] = {nullptr, nullptr}, *vop[2] = {nullptr, nullptr}, *vtop[2] = {nullptr, nullptr},
           *utop[2] = {nullptr, nullptr};
@@ -753,6 +754,7 @@ int rpca_init(rpca_ctx* c, const void* D, int64_t m, int64_t n, int64_t ld, int 
   }
   if (!conv) return RPCA_ERR_NOT_CONVERGED;  // not reached: the last step of each phase is accepted
   CK(cudaMemsetAsync(&c->st->done, 0, sizeof(int), c->stream));
+  c->h_flags[1] = 0;  // done, as just reset (the other flags were read after the last step)
   c->ready = true;
   return RPCA_OK;
 }
@@ -780,32 +782,42 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
   if (!c || n_iters < 0) return RPCA_ERR_INVALID_ARG;
   if (!c->ready || (learned(c) && !c->theta_set)) return RPCA_ERR_STATE;
   int st;
-  if ((st = read_flags(c))) return st;
+  // the host's copy of the state flags is current (every call that changes them on the device
+  // reads them back or sets them), so the first chunk goes out without a wait
   const int k0 = flag_k(c);
   int done = flag_done(c);
   int launched = 0;
+  const int max_stats = c->p.max_iter + 2 - k0;  // DevStats entries from k0 on
+  std::vector<DevStats> hs;
   while (!done && launched < n_iters) {
-    const int chunk = (n_iters - launched) < 8 ? (n_iters - launched) : 8;
+    // the first chunk as long as the last solve on this context took (at least 8), later ones
+    // 4; the passes queued behind convergence return at once
+    const int want = launched == 0 ? std::min(32, std::max(8, c->last_iters + 1)) : 4;
+    const int chunk = std::min(n_iters - launched, want);
     for (int i = 0; i < chunk; ++i) {
       if ((st = run_pass(c, c->Rr, false))) return st;
       if ((st = run_small(c, small_args(c, SM_UPDATE, c->Rr)))) return st;
     }
     launched += chunk;
-    if ((st = read_flags(c))) return st;
+    // the flags and the statistics of every pass launched so far, in one wait
+    const int ns = std::min(max_stats, launched + 1);
+    hs.resize((size_t)std::max(ns, 1));
+    prof_break(c);
+    CK(cudaMemcpyAsync(c->h_flags, &c->st->k, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (ns > 0) CK(cudaMemcpyAsync(hs.data(), c->stats + k0, sizeof(DevStats) * ns, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     if (flag_status(c)) return flag_status(c);
     done = flag_done(c);
   }
-  // the flags are current: read at the end of the last chunk (or before the loop)
   const int k1 = flag_k(c);
   int count = k1 - k0 + (flag_done(c) ? 1 : 0);
   if (count > n_iters) count = n_iters;
   if (count < 0) count = 0;
   prof_collect(c, count);
-  // the statistics of the passes run, and of the last pass when the run ended (one copy)
-  const int ncopy = std::max(count, flag_done(c) ? k1 - k0 + 1 : 0);
-  std::vector<DevStats> hs((size_t)(ncopy > 0 ? ncopy : 1));
-  if (ncopy > 0) {
-    CK(cudaMemcpyAsync(hs.data(), c->stats + k0, sizeof(DevStats) * ncopy, cudaMemcpyDeviceToHost, c->stream));
+  const int need = std::max(count, flag_done(c) ? k1 - k0 + 1 : 0);
+  if ((int)hs.size() < need) {  // no chunk ran (already done): the statistics held
+    hs.resize((size_t)need);
+    CK(cudaMemcpyAsync(hs.data(), c->stats + k0, sizeof(DevStats) * need, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
   if (out)
@@ -826,6 +838,7 @@ int rpca_iterate(rpca_ctx* c, int n_iters, rpca_iter_stats* out, int* n_done) {
     const DevStats& last = hs[(size_t)(k1 - k0)];
     c->last_nnz = last.nnz;  // the support the pass at iterate k1 counted
     c->last_nnz_k = k1;
+    c->last_iters = k1;
     return (last.err < c->p.tol) ? RPCA_OK : RPCA_ERR_NOT_CONVERGED;
   }
   return RPCA_ERR_NOT_CONVERGED;
