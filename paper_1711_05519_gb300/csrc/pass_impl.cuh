@@ -391,77 +391,95 @@ __global__ void __launch_bounds__(256) extract_kernel(ExtractArgs a) {
 }
 
 // The ordered write from the support words of the tensor-core pass (the bit of column j of
-// row i is set iff |D_ij - L_ij| > zeta_k in that pass; [word][row] layout): one warp per row
-// and chunk of kWordChunk words, so that the rows' chunks run independently.  The chunk's
-// first position is the row's offset (rowoff) plus the counts of the row's earlier chunks
-// (cc); the warp scans its words' bit counts and takes the chunk's entries in order, lane l
-// the entries l, l + 32, ... (UNR per lane at once, so that their loads are in flight
-// together): the word by a binary search over the scan, the column by the rank of the bit,
-// and S_ij = D_ij - L_ij rebuilt there (D is read only where a 32-byte sector holds a support
+// row i is set iff |D_ij - L_ij| > zeta_k in that pass; [word][row] layout).  One block per 32
+// rows and chunk of kWordChunk words (1024 columns): the block stages the chunk's rows of V
+// and its 32 x 32 words in shared memory (coalesced), then each warp takes 4 of the rows.  A
+// row's chunk starts at the row's offset (rowoff) plus the counts of its earlier chunks (cc);
+// the warp scans its words' bit counts and takes the chunk's entries in order, lane l the
+// entries l, l + 32, ... (UNR per lane at once, so their loads of D are in flight together):
+// the word by a binary search over the scan, the column by the rank of the bit, and
+// S_ij = D_ij - L_ij rebuilt there (D is read only where a 32-byte sector holds a support
 // entry).  Consecutive lanes write consecutive positions.
 template <int R>
 __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const unsigned* __restrict__ words,
                                                             const unsigned* __restrict__ cc, int nw) {
-  constexpr int UNR = 4;
-  const int lane = threadIdx.x & 31;
-  const int nch = (nw + kWordChunk - 1) / kWordChunk;
-  const long long wid = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int row = (int)(wid / nch), ch = (int)(wid % nch);
-  if (row >= a.m) return;
+  constexpr int UNR = 4, RB = 32, COLS = 32 * kWordChunk;
+  extern __shared__ float vs[];  // [COLS][R]: the chunk's rows of V
+  __shared__ unsigned ws[kWordChunk][RB];
+  __shared__ unsigned long long rbase[RB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nrb = (a.m + RB - 1) / RB;
+  const int rb = blockIdx.x % nrb, ch = blockIdx.x / nrb;
+  const int r0 = rb * RB, j0 = ch * kWordChunk, c0 = 32 * j0;
+  const int ncols = min(COLS, a.n - c0);
   const float* __restrict__ D = static_cast<const float*>(a.D);
   const float* __restrict__ W = static_cast<const float*>(a.W);
   const float* __restrict__ V = static_cast<const float*>(a.V);
-  unsigned earlier = 0;  // support entries in the row's earlier chunks
-  for (int c = lane; c < ch; c += 32) earlier += cc[(size_t)c * a.m + row];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) earlier += __shfl_xor_sync(0xffffffffu, earlier, o);
-  const unsigned long long base = a.rowoff[row] + earlier;
-  const int j0 = ch * kWordChunk;
-  const int j = j0 + lane;
-  const unsigned wd = (j < nw) ? words[(size_t)j * a.m + row] : 0u;
-  const unsigned c = __popc(wd);
-  unsigned incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
+  for (int e = threadIdx.x; e < ncols * R; e += blockDim.x) vs[e] = V[(long long)c0 * R + e];
+  for (int e = threadIdx.x; e < kWordChunk * RB; e += blockDim.x) {
+    const int jj = e / RB, rr = e % RB;
+    ws[jj][rr] = (j0 + jj < nw && r0 + rr < a.m) ? words[(size_t)(j0 + jj) * a.m + r0 + rr] : 0u;
   }
-  const unsigned excl = incl - c;
-  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-  if (total == 0) return;
-  float w[R];
-#pragma unroll
-  for (int k = 0; k < R; ++k) w[k] = W[(long long)row * R + k];
-  for (unsigned e0 = 0; e0 < total; e0 += 32 * UNR) {
-    int col[UNR];
-    float d[UNR], v[UNR][R];
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const unsigned e = e0 + 32u * u + lane;
-      // source lane: the number of lanes whose inclusive count is <= e
-      int src = 0;
-#pragma unroll
-      for (int b = 16; b > 0; b >>= 1) {
-        const unsigned t = __shfl_sync(0xffffffffu, incl, src + b - 1);
-        if (t <= e) src += b;
-      }
-      unsigned ws = __shfl_sync(0xffffffffu, wd, src & 31);
-      const unsigned es = __shfl_sync(0xffffffffu, excl, src & 31);
-      col[u] = -1;
-      if (e < total) {
-        for (unsigned q = es; q < e; ++q) ws &= ws - 1u;  // drop the lower set bits
-        col[u] = 32 * (j0 + src) + (__ffs(ws) - 1);
-        d[u] = D[(long long)row * a.ld + col[u]];
-#pragma unroll
-        for (int k = 0; k < R; ++k) v[u][k] = V[(long long)col[u] * R + k];
-      }
+  if (threadIdx.x < RB) {
+    const int row = r0 + threadIdx.x;
+    unsigned long long b = 0;
+    if (row < a.m) {
+      b = a.rowoff[row];
+      for (int c = 0; c < ch; ++c) b += cc[(size_t)c * a.m + row];
     }
+    rbase[threadIdx.x] = b;
+  }
+  __syncthreads();
+  for (int rr = warp; rr < RB; rr += 8) {
+    const int row = r0 + rr;
+    if (row >= a.m) break;
+    const unsigned wd = ws[lane][rr];
+    const unsigned c = __popc(wd);
+    unsigned incl = c;
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      if (col[u] >= 0) {
-        const unsigned long long pos = base + e0 + 32u * u + lane;
-        a.idx[pos] = (long long)row * a.n + col[u];
-        a.val[pos] = static_cast<double>(d[u] - rebuild<float, R>(w, v[u]));
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned excl = incl - c;
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    float w[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) w[k] = W[(long long)row * R + k];
+    const unsigned long long base = rbase[rr];
+    for (unsigned e0 = 0; e0 < total; e0 += 32 * UNR) {
+      int col[UNR];
+      float d[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const unsigned e = e0 + 32u * u + lane;
+        // source lane: the number of lanes whose inclusive count is <= e
+        int src = 0;
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1) {
+          const unsigned t = __shfl_sync(0xffffffffu, incl, src + b - 1);
+          if (t <= e) src += b;
+        }
+        unsigned wsrc = __shfl_sync(0xffffffffu, wd, src & 31);
+        const unsigned es = __shfl_sync(0xffffffffu, excl, src & 31);
+        col[u] = -1;
+        if (e < total) {
+          for (unsigned q = es; q < e; ++q) wsrc &= wsrc - 1u;  // drop the lower set bits
+          col[u] = 32 * src + (__ffs(wsrc) - 1);               // column within the chunk
+          d[u] = D[(long long)row * a.ld + c0 + col[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        if (col[u] >= 0) {
+          float v[R];
+#pragma unroll
+          for (int k = 0; k < R; ++k) v[k] = vs[col[u] * R + k];
+          const unsigned long long pos = base + e0 + 32u * u + lane;
+          a.idx[pos] = (long long)row * a.n + c0 + col[u];
+          a.val[pos] = static_cast<double>(d[u] - rebuild<float, R>(w, v));
+        }
       }
     }
   }
@@ -470,8 +488,11 @@ __global__ void __launch_bounds__(256) extract_words_kernel(ExtractArgs a, const
 template <int R>
 cudaError_t launch_extract_words_t(const ExtractArgs& a, const unsigned* words, const unsigned* cc, int nw,
                                    cudaStream_t s) {
-  const long long warps = (long long)a.m * ((nw + kWordChunk - 1) / kWordChunk);
-  extract_words_kernel<R><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(a, words, cc, nw);
+  const long long blocks = (long long)((a.m + 31) / 32) * ((nw + kWordChunk - 1) / kWordChunk);
+  const int vbytes = 32 * kWordChunk * R * (int)sizeof(float);  // up to 64 KB
+  cudaError_t e = cudaFuncSetAttribute(extract_words_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, vbytes);
+  if (e != cudaSuccess) return e;
+  extract_words_kernel<R><<<(unsigned)blocks, 256, vbytes, s>>>(a, words, cc, nw);
   return cudaGetLastError();
 }
 
