@@ -300,18 +300,21 @@ int run_small(rpca_ctx* c, const SmallArgs& a) {
 // Tile partition of the tensor-core pass.  The TR x TC tiles (128 x 64) are cut into row
 // groups of different heights; group g of h_g row tiles splits all TC column tiles among its
 // own B_g CTAs (ranges of nearly equal width, at most max_ct column tiles each: the
-// tensor-memory budget).  The plan takes the smallest largest-CTA tile count T for which the
-// groups fit on nsm CTAs (one per SM), and among those the one with the fewest partial
-// products (every CTA writes an m-slice of Y1 for its rows and every group an n-slice of Y2).
-// Dynamic programming over (row tiles, CTAs).
+// tensor-memory budget).  The plan takes the smallest largest-CTA cost (h (w + 1/2) for h row
+// tiles of w column tiles) for which the groups fit on nsm CTAs (one per SM), and among those
+// the one with the fewest partial products (every CTA writes an m-slice of Y1 for its rows and
+// every group two n-slices of Y2).  Dynamic programming over (row tiles, CTAs).
 bool tc_plan(int TR, int TC, int nsm, int max_ct, TcPlan* out) {
   if (TR < 1 || TC < 1 || nsm < 1) return false;
   const long long tiles = (long long)TR * TC;
-  for (long long T = (tiles + nsm - 1) / nsm; T <= tiles; ++T) {
+  // cost of a CTA of h row tiles and w column tiles: h (w + 1/2) tile times (each new row tile
+  // loads its W and U~ images and drains Y1: measured, a plan of one column tile per CTA ran at
+  // half the bandwidth); T2 = twice the cost bound
+  for (long long T2 = 2 * ((tiles + nsm - 1) / nsm); T2 <= 2 * tiles + 2 * TR; ++T2) {
     std::vector<std::pair<int, int>> opts;  // (group height, CTAs)
     for (int h = 1; h <= TR; ++h) {
-      const long long w = std::min<long long>(std::min<long long>(T / h, max_ct), TC);
-      if (w < 1) break;
+      const long long w = std::min<long long>(std::min<long long>((T2 - h) / (2 * h), max_ct), TC);
+      if (w < 1) continue;
       opts.push_back({h, (int)((TC + w - 1) / w)});
     }
     const double INF = 1e300;
@@ -373,7 +376,7 @@ bool tc_plan(int TR, int TC, int nsm, int max_ct, TcPlan* out) {
       const int4 a = out->rect[i], b = out->rect[out->min_cta];
       if ((a.y - a.x) * (a.w - a.z) < (b.y - b.x) * (b.w - b.z)) out->min_cta = i;
     }
-    out->T = (int)T;
+    out->T = (int)(T2 / 2);
     return out->ct_max <= max_ct;
   }
   return false;
