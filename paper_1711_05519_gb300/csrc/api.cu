@@ -1070,6 +1070,7 @@ static int solve_device(const float* D, int64_t m, int64_t n, int r, double beta
 // Serialised by a mutex; freed by rpca_solve_host_release (or with the process).
 struct HostSolveCache {
   int device = -1;
+  unsigned long long ctx_id = 0;  // CUDA context the cached objects belong to
   size_t d_elems = 0, u_elems = 0, v_elems = 0, cap = 0;
   float* dD = nullptr;
   double *dU = nullptr, *dS = nullptr, *dV = nullptr, *dval = nullptr;
@@ -1093,6 +1094,41 @@ static void host_cache_free(HostSolveCache* h) {
   if (h->s) cudaStreamDestroy(h->s);
   if (cur != h->device) cudaSetDevice(cur);
   *h = HostSolveCache();
+}
+
+// Unique id of the current CUDA context (0 if unavailable): a device reset or a context
+// teardown between calls gives a new id, and the cached objects, which belonged to the old
+// context, are then dropped without touching them (their memory went with that context).
+static unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      get_current = nullptr;
+      get_id = nullptr;
+      return 0;
+    }
+  }
+  cudaFree(nullptr);  // makes the runtime's context current
+  CUcontext cx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&cx) != CUDA_SUCCESS || !cx || get_id(cx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Host-side release of a context whose CUDA objects no longer exist (no CUDA call).
+static void forget_ctx(rpca_ctx* c) {
+  if (!c) return;
+  c->ev_free.clear();
+  c->ev_line.clear();
+  delete c;
 }
 
 // Grows a cached device array to at least `need` elements of `size` bytes.
@@ -1125,10 +1161,18 @@ int rpca_solve_host(const float* D, int64_t m, int64_t n, int r, double beta, do
   if (!g_host) g_host = new (std::nothrow) HostSolveCache();
   if (!g_host) return RPCA_ERR_CUDA;
   HostSolveCache& h = *g_host;
+  const unsigned long long cid = current_context_id();
+  if (h.device == dev && h.ctx_id != cid) {
+    // the context changed under the cache (device reset, context teardown): its objects died
+    // with the old context, so they are forgotten, not freed
+    forget_ctx(h.ctx);
+    h = HostSolveCache();
+  }
   if (h.device != dev) {
     host_cache_free(&h);
     h.device = dev;
   }
+  h.ctx_id = cid;
   if (!h.s && cudaStreamCreateWithFlags(&h.s, cudaStreamNonBlocking) != cudaSuccess) {
     host_cache_free(&h);
     return RPCA_ERR_CUDA;
