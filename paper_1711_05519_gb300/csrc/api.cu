@@ -17,6 +17,10 @@
 #include "tc_images.cuh"
 
 namespace rpca {
+unsigned long long g_attr_epoch = 1;  // see common.cuh
+}  // namespace rpca
+
+namespace rpca {
 cudaError_t launch_pass_f32(int R, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_f64(int R, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_extract_count_f32(int R, const ExtractArgs& a, cudaStream_t s);
@@ -517,6 +521,35 @@ int rpca_params_default(rpca_params* p) {
   return RPCA_OK;
 }
 
+// Unique id of the current CUDA context (0 if unavailable): a device reset or a context
+// teardown between calls gives a new id, and the cached objects, which belonged to the old
+// context, are then dropped without touching them (their memory went with that context).
+static unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      get_current = nullptr;
+      get_id = nullptr;
+      return 0;
+    }
+  }
+  cudaFree(nullptr);  // makes the runtime's context current
+  CUcontext cx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&cx) != CUDA_SUCCESS || !cx || get_id(cx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+static unsigned long long g_attr_ctx = 0;
+
 int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
   if (!out || !params) return RPCA_ERR_INVALID_ARG;
   *out = nullptr;
@@ -527,6 +560,15 @@ int rpca_create(rpca_ctx** out, const rpca_params* params, void* stream) {
       p.observed < RPCA_OBS_ALL || p.observed > RPCA_OBS_NAN ||
       (p.observed == RPCA_OBS_NAN && p.zeta_mode == RPCA_ZETA_LEARNED))
     return RPCA_ERR_INVALID_ARG;
+  {
+    // a context the kernel attributes were not set in (the first, or a new one after a device
+    // reset): the launchers set them again
+    const unsigned long long cid = current_context_id();
+    if (cid != g_attr_ctx) {
+      g_attr_ctx = cid;
+      ++g_attr_epoch;
+    }
+  }
   rpca_ctx* c = new (std::nothrow) rpca_ctx();
   if (!c) return RPCA_ERR_CUDA;
   c->p = p;
@@ -1094,33 +1136,6 @@ static void host_cache_free(HostSolveCache* h) {
   if (h->s) cudaStreamDestroy(h->s);
   if (cur != h->device) cudaSetDevice(cur);
   *h = HostSolveCache();
-}
-
-// Unique id of the current CUDA context (0 if unavailable): a device reset or a context
-// teardown between calls gives a new id, and the cached objects, which belonged to the old
-// context, are then dropped without touching them (their memory went with that context).
-static unsigned long long current_context_id() {
-  using GetCurrent = CUresult (*)(CUcontext*);
-  using GetId = CUresult (*)(CUcontext, unsigned long long*);
-  static GetCurrent get_current = nullptr;
-  static GetId get_id = nullptr;
-  if (!get_current || !get_id) {
-    cudaDriverEntryPointQueryResult q1, q2;
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q1) !=
-            cudaSuccess ||
-        cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
-            cudaSuccess ||
-        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
-      get_current = nullptr;
-      get_id = nullptr;
-      return 0;
-    }
-  }
-  cudaFree(nullptr);  // makes the runtime's context current
-  CUcontext cx = nullptr;
-  unsigned long long id = 0;
-  if (get_current(&cx) != CUDA_SUCCESS || !cx || get_id(cx, &id) != CUDA_SUCCESS) return 0;
-  return id;
 }
 
 // Host-side release of a context whose CUDA objects no longer exist (no CUDA call).

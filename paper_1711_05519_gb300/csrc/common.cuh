@@ -100,6 +100,11 @@ struct PassArgs {
   int partial;
 };
 
+// Kernel attributes (the dynamic shared-memory limits) belong to a CUDA context: each launcher
+// sets them again when this epoch changed, which rpca_create advances whenever it finds a new
+// context (after a device reset, for example).
+extern unsigned long long g_attr_epoch;
+
 // Launches the fused pass for compiled rank R (must be an RPCA_FOR_EACH_R entry).
 cudaError_t launch_fused_pass(int prec, int R, const PassArgs& a, cudaStream_t s);
 

@@ -327,12 +327,12 @@ template <typename T, int R, int DM>
 cudaError_t launch_pass_dm(const PassArgs& a, cudaStream_t s) {
   using C = PassCfg<T, R>;
   using Lay = PassLayout<T, R>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static unsigned long long attr_epoch = 0;
+  if (attr_epoch != g_attr_epoch) {
     cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<T, R, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Lay::SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_epoch = g_attr_epoch;
   }
   dim3 grid((a.n + C::BW - 1) / C::BW, (a.m + C::BH - 1) / C::BH);
   fused_pass_kernel<T, R, DM><<<grid, Lay::THREADS, Lay::SMEM, s>>>(a);

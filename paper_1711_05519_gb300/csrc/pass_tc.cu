@@ -745,14 +745,14 @@ size_t tc_pass_smem() { return Cfg<8>::SMEM_BYTES; }
 
 cudaError_t launch_fused_pass_tc(const CUtensorMap* dmap, const CUtensorMap* dmap_lo, int dm, const TcPassArgs& p,
                                  cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr_epoch = 0;
+  if (attr_epoch != g_attr_epoch) {
     cudaError_t e = set_tc_smem_modes<0, 8>();
     if (e == cudaSuccess) e = set_tc_smem_modes<1, 8>();
     if (e == cudaSuccess) e = set_tc_smem_modes<0, 16>();
     if (e == cudaSuccess) e = set_tc_smem_modes<1, 16>();
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_epoch = g_attr_epoch;
   }
   if (p.R < 1 || p.R > 16) return cudaErrorInvalidValue;
   TcArgs a;
