@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
   // before the block barrier, while the tensor memory is allocated, made the pass ~2 us slower
   // per launch, measured at 10^4 x 10^4.)
   int issued = 0, w_issued = 0;
+  // D is read once per pass: its lines go first when L2 needs room, which keeps the operand
+  // images, the partial products and the other kernels' code and data resident
+  const uint64_t dpol = l2_evict_first_policy();
   auto issue = [&](int t) -> bool {
     const int rtl = t / nct, ctl = t % nct, s = t % NSTAGE;
     const int rt = rt0 + rtl, ct = ct0 + ctl;
@@ -255,12 +258,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_pass_tc(const __grid_constan
     uint8_t* st = sm + OFF_STAGE + s * STAGE_BYTES;
     if (DM == 0) {
       mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES);
-      tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
-      tma_load_2d(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s]);
+      tma_load_2d_hint(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s], dpol);
+      tma_load_2d_hint(st + D_BYTES / 2, &dmap, ct * BN + 32, rt * BM, &bar[B_FULL + s], dpol);
     } else {
       mbar_arrive_expect_tx(&bar[B_FULL + s], STAGE_BYTES - (use_lo ? 0 : D_BYTES / 2));
-      tma_load_2d(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s]);
-      if (use_lo) tma_load_2d(st + D_BYTES / 2, &dmap_lo, ct * BN, rt * BM, &bar[B_FULL + s]);
+      tma_load_2d_hint(st, &dmap, ct * BN, rt * BM, &bar[B_FULL + s], dpol);
+      if (use_lo) tma_load_2d_hint(st + D_BYTES / 2, &dmap_lo, ct * BN, rt * BM, &bar[B_FULL + s], dpol);
     }
     bulk_load(st + D_BYTES, a.vop + (size_t)ct * VOP_BYTES, VOP_BYTES, &bar[B_FULL + s]);
     bulk_load(st + D_BYTES + VOP_BYTES, a.vtop + (size_t)ct * VTOP_BYTES, VTOP_BYTES, &bar[B_FULL + s]);
