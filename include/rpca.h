@@ -334,12 +334,15 @@ int rpca_get_sparse_noalloc(const float* D, int64_t m, int64_t n, int64_t ld, in
                             const double* sigma, const double* V, double zeta, int64_t* idx,
                             double* val, int64_t cap, int64_t* nnz, void* stream);
 
-/* Diagnostics.  With profiling on, the context records a CUDA event pair around every
- * kernel it launches on its stream.  rpca_get_profile (host outputs, any may be NULL)
- * returns, since profiling was last switched on: the summed device time and the number
- * of fused-pass launches that did work, and the same for every other launch of the
- * library (including passes that returned at once because the solve had already
- * converged).  Synchronises the stream. */
+/* Diagnostics.  on = 0 switches profiling off; on = 1 records CUDA events at the boundaries
+ * of every kernel the context launches on its stream; on = k > 1 records them only around
+ * every k-th fused-pass launch (the first, the (k+1)-th, ...), which keeps the events out of
+ * most kernel boundaries; negative on is RPCA_ERR_INVALID_ARG.  rpca_get_profile (host
+ * outputs, any may be NULL) returns, since profiling was last switched on: the summed device
+ * time and the number of the timed fused-pass launches that did work, and the summed device
+ * time of the other timed launches with the number of every other launch of the library
+ * (timed or not, including passes that returned at once because the solve had already
+ * converged), so that the two counts add up to all launches.  Synchronises the stream. */
 int rpca_set_profiling(rpca_ctx* ctx, int on);
 int rpca_get_profile(rpca_ctx* ctx, double* pass_ms, int64_t* pass_launches, double* other_ms,
                      int64_t* other_launches);

@@ -101,19 +101,23 @@ struct rpca_ctx {
   // allocation signature of the current workspace
   int64_t ws_m = -1, ws_n = -1;
   int ws_r = -1;
-  // profiling
+  // profiling: every launch (stride 1) or every stride-th fused pass only (stride > 1)
   bool prof = false;
+  int prof_stride = 1;
   std::vector<cudaEvent_t> ev_free;
-  // profiling timeline: events at kernel boundaries (a kernel's end event is the next
-  // kernel's begin event while nothing else was queued in between) and the intervals
-  // {begin index, end index, is-pass} between them
+  // profiling timeline: events at the boundaries of timed launches (a kernel's end event is
+  // the next kernel's begin event while nothing else was queued in between) and the intervals
+  // {begin index, end index, is-pass, pass ordinal in the window} between them
   struct Span {
     int b, e;
     bool pass;
+    int64_t ord;
   };
   std::vector<cudaEvent_t> ev_line;
   std::vector<Span> spans;
-  bool line_open = false;
+  bool line_open = false, cur_timed = false;
+  int64_t win_pass = 0, win_other = 0;  // launches queued since the last collection
+  int64_t pass_seq = 0;                 // pass launches since profiling was switched on
   double pass_ms = 0, other_ms = 0;
   int64_t pass_n = 0, other_n = 0;
 };
@@ -154,17 +158,27 @@ cudaEvent_t take_event(rpca_ctx* c) {
   return e;
 }
 
-// Marks the start (begin = true) or the end of one profiled launch.
+// Marks the start (begin = true) or the end of one launch.  Every launch is counted; the
+// timed ones get events at their boundaries.
 void prof_mark(rpca_ctx* c, bool pass, bool begin) {
   if (!c->prof) return;
   if (begin) {
+    const int64_t ord = pass ? c->win_pass++ : -1;
+    if (!pass) ++c->win_other;
+    c->cur_timed = c->prof_stride <= 1 || (pass && c->pass_seq % c->prof_stride == 0);
+    if (pass) ++c->pass_seq;
+    if (!c->cur_timed) {
+      c->line_open = false;
+      return;
+    }
     if (!c->line_open) {
       cudaEvent_t e = take_event(c);
       cudaEventRecord(e, c->stream);
       c->ev_line.push_back(e);
     }
-    c->spans.push_back({(int)c->ev_line.size() - 1, -1, pass});
+    c->spans.push_back({(int)c->ev_line.size() - 1, -1, pass, ord});
   } else {
+    if (!c->cur_timed) return;
     cudaEvent_t e = take_event(c);
     cudaEventRecord(e, c->stream);
     c->ev_line.push_back(e);
@@ -178,24 +192,25 @@ void prof_mark(rpca_ctx* c, bool pass, bool begin) {
 void prof_break(rpca_ctx* c) { c->line_open = false; }
 
 // Accumulates the recorded spans (the stream must be synchronised).  Only the first
-// `effective_pass` pass spans count as passes: pass launches past that count returned at
-// once on the device and are counted with the other kernels, so the pass average covers
-// only passes that did work.
+// `effective_pass` pass launches of the window count as passes: pass launches past that count
+// returned at once on the device and are counted with the other kernels, so the pass average
+// covers only passes that did work.  Launches that were not timed add to the other count.
 void prof_collect(rpca_ctx* c, int64_t effective_pass) {
-  int64_t ip = 0;
+  int64_t counted = 0;
   for (const auto& sp : c->spans) {
     if (sp.e < 0) continue;
     float t = 0.f;
     cudaEventElapsedTime(&t, c->ev_line[sp.b], c->ev_line[sp.e]);
-    if (sp.pass && (effective_pass < 0 || ip < effective_pass)) {
+    if (sp.pass && (effective_pass < 0 || sp.ord < effective_pass)) {
       c->pass_ms += t;
       ++c->pass_n;
+      ++counted;
     } else {
       c->other_ms += t;
-      ++c->other_n;
     }
-    if (sp.pass) ++ip;
   }
+  c->other_n += c->win_pass + c->win_other - counted;
+  c->win_pass = c->win_other = 0;
   for (cudaEvent_t e : c->ev_line) c->ev_free.push_back(e);
   c->ev_line.clear();
   c->spans.clear();
@@ -1049,8 +1064,11 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
 int rpca_set_profiling(rpca_ctx* c, int on) {
   if (!c) return RPCA_ERR_INVALID_ARG;
   CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+  if (on < 0) return RPCA_ERR_INVALID_ARG;
   prof_collect(c, 0);
   c->prof = on != 0;
+  c->prof_stride = on > 1 ? on : 1;
+  c->pass_seq = 0;
   c->pass_ms = c->other_ms = 0;
   c->pass_n = c->other_n = 0;
   return RPCA_OK;

@@ -217,8 +217,11 @@ class Solver:
         names = {1: "simt", 2: "tensor"}
         return names[it.value], names[ini.value]
 
-    def set_profiling(self, on: bool) -> None:
-        _check(lib().rpca_set_profiling(self._ctx, int(bool(on))), "rpca_set_profiling")
+    def set_profiling(self, on: bool, every: int = 1) -> None:
+        """Events around every launch (every = 1) or around every `every`-th fused pass only."""
+        if every < 1:
+            raise ValueError("every must be >= 1")
+        _check(lib().rpca_set_profiling(self._ctx, int(every) if on else 0), "rpca_set_profiling")
 
     def profile(self) -> dict:
         pm, om = ctypes.c_double(0), ctypes.c_double(0)
