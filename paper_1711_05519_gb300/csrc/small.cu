@@ -62,6 +62,7 @@ struct Smem {
   static constexpr int NM = 2 * WM;  // max order of the small SVD
   T red[ST];
   double dred[ST / 32];
+  unsigned long long ured[2][ST / 32];
   T G[3][GSLOT];           // reduced Gram matrices (row-major, leading dimension w)
   T Rf[2][GSLOT];          // Cholesky factors (upper)
   T Tf[2][GSLOT];          // T factors: X T has orthonormal columns (upper)
@@ -161,38 +162,42 @@ __device__ __forceinline__ T* slot_ptr(void* part, int slot, int block) {
   return static_cast<T*>(part) + ((size_t)slot * gridDim.x + block) * GSLOT;
 }
 
-// Sums over the block, the same fixed order in every block; the result in all threads.
+// Block-wide sums of v (double, summed in a fixed order: lanes by xor shuffles, then the
+// warps' partials by halving) and of z (and of z2 when it is not null) in one round of the
+// shared-memory reduction; every thread gets the totals.
 template <typename S>
-__device__ __noinline__ double block_sum_d(double v, S& sh) {
+__device__ __noinline__ void block_sum_dz(double& v, unsigned long long& z, unsigned long long* z2, S& sh) {
   const int t = threadIdx.x;
+  unsigned long long y = z2 ? *z2 : 0ull;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_xor_sync(FULL, v, o);
+    z += __shfl_xor_sync(FULL, z, o);
+    y += __shfl_xor_sync(FULL, y, o);
+  }
   __syncthreads();
-  if ((t & 31) == 0) sh.dred[t >> 5] = v;
+  if ((t & 31) == 0) {
+    sh.dred[t >> 5] = v;
+    sh.ured[0][t >> 5] = z;
+    sh.ured[1][t >> 5] = y;
+  }
   __syncthreads();
   double w[ST / 32];
+  unsigned long long sz = 0, sy = 0;
 #pragma unroll
-  for (int q = 0; q < ST / 32; ++q) w[q] = sh.dred[q];
+  for (int q = 0; q < ST / 32; ++q) {
+    w[q] = sh.dred[q];
+    sz += sh.ured[0][q];
+    sy += sh.ured[1][q];
+  }
 #pragma unroll
   for (int h = ST / 64; h > 0; h >>= 1)
 #pragma unroll
     for (int q = 0; q < h; ++q) w[q] += w[q + h];
   __syncthreads();
-  return w[0];
-}
-
-template <typename S>
-__device__ __noinline__ unsigned long long block_sum_u64(unsigned long long v, S& sh) {
-  const int t = threadIdx.x;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  __syncthreads();
-  if ((t & 31) == 0) sh.dred[t >> 5] = __longlong_as_double((long long)v);
-  __syncthreads();
-  unsigned long long s = 0;
-  for (int q = 0; q < ST / 32; ++q) s += (unsigned long long)__double_as_longlong(sh.dred[q]);
-  __syncthreads();
-  return s;
+  v = w[0];
+  z = sz;
+  if (z2) *z2 = sy;
 }
 
 // Per-thread share of X^T Y over the staged rows (row stride WM): thread t takes entry
@@ -858,9 +863,10 @@ __device__ void cta_totals(const SmallArgs& a, double& res2, unsigned long long&
     z += a.nnzP[c];
     if (changes && a.chgP) c2 += a.chgP[c];
   }
-  res2 = block_sum_d(s, sh);
-  nnz = block_sum_u64(z, sh);
-  if (changes) *changes = a.chgP ? block_sum_u64(c2, sh) : 0ull;
+  block_sum_dz(s, z, changes ? &c2 : nullptr, sh);
+  res2 = s;
+  nnz = z;
+  if (changes) *changes = a.chgP ? c2 : 0ull;
 }
 
 // Row i of Y (width w) <- fixed-order sum of the nsl pass partial slices (width R,
@@ -1063,11 +1069,24 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   T* Y2 = static_cast<T*>(a.Y2);
   const T* At = static_cast<const T*>(a.Utc);  // A~ and B~ as the pass read them (width Rit)
   const T* Bt = static_cast<const T*>(a.Vtc);
+  // the first loads go out together: the T factors the tensor-core pass computed, the state
+  // the stop test reads, and (in cta_totals) the pass's per-CTA totals
+  constexpr int NTF = (2 * WM * WM + ST - 1) / ST;
+  float tfv[NTF];
+  if (a.tfac) {
+#pragma unroll
+    for (int i = 0; i < NTF; ++i) {
+      const int e = t + i * ST, q = (e / WM) % WM, c = e % WM;
+      tfv[i] = (e < 2 * WM * WM && q < r && c < r) ? a.tfac[(e / (WM * WM)) * 256 + q * r + c] : 0.f;
+    }
+  }
+  const double normD2 = st->normD2, tol = st->tol;
+  const int k = st->k, max_iter = st->max_iter;
+  const bool hi_only = st->split_switch > 0 && !st->use_lo;
   double res2;
   unsigned long long nnz, changes;
   cta_totals(a, res2, nnz, sh, &changes);
-  const double err = sqrt(res2 / st->normD2);
-  const int k = st->k;
+  const double err = sqrt(res2 / normD2);
   if (blockIdx.x == 0 && t == 0) {
     DevStats& s = a.stats[k];
     s.err = err;
@@ -1089,18 +1108,19 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
     }
     return;
   }
-  // bf16 split storage of D: while the passes read only the hi part, err_k measures against
-  // bf16(D) and cannot end the run; the next pass reads hi + lo once err_k is below the switch
-  // level (use_lo is written below, after grid barriers every CTA passes after this read)
-  const bool hi_only = st->split_switch > 0 && !st->use_lo;
-  if ((err < st->tol && !hi_only) || k >= st->max_iter) {
+  // bf16 split storage of D: while the passes read only the hi part (hi_only), err_k measures
+  // against bf16(D) and cannot end the run; the next pass reads hi + lo once err_k is below
+  // the switch level (use_lo is written below, after grid barriers every CTA passes after the
+  // read above)
+  if ((err < tol && !hi_only) || k >= max_iter) {
     if (blockIdx.x == 0 && t == 0) st->done = 1;
     return;
   }
   if (a.tfac) {
-    for (int e = t; e < 2 * WM * WM; e += ST) {
-      const int s2 = e / (WM * WM), q = (e / WM) % WM, c = e % WM;
-      sh.tm[s2][q * WM + c] = (q < r && c < r) ? (T)a.tfac[s2 * 256 + q * r + c] : T(0);
+#pragma unroll
+    for (int i = 0; i < NTF; ++i) {
+      const int e = t + i * ST;
+      if (e < 2 * WM * WM) sh.tm[e / (WM * WM)][e % (WM * WM)] = (T)tfv[i];
     }
     __syncthreads();
   } else {
@@ -1481,10 +1501,14 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   const int phase = st->init_phase, step = st->init_step;
   const bool first = step == 0, force = step >= a.init_max - 1;
   if (blockIdx.x == 0 && t == 0) st->steps_run += 1;  // read by the host after every batch
-  double res2;
-  unsigned long long nnz;
-  cta_totals(a, res2, nnz, sh);
-  if (phase == 0 && first && blockIdx.x == 0 && t == 0) st->normD2 = res2;
+  // the pass's totals are needed once: ||D||_F^2 from the first pass of the first phase
+  // (L = 0 there); the branch is uniform over the block
+  if (phase == 0 && first && blockIdx.x == 0) {
+    double res2;
+    unsigned long long nnz;
+    cta_totals(a, res2, nnz, sh);
+    if (t == 0) st->normD2 = res2;
+  }
 
   // A: own rows of Y1 = Z V~, Y2 = Z^T U~ (both sides at once on the two half blocks);
   // partials of B = U~^T Y1 (slot 0), Y1^T Y1 (slot 1) and Y2^T Y2 (slot 2)
