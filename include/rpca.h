@@ -193,8 +193,11 @@ int rpca_get_lowrank(rpca_ctx* ctx, double* U, double* sigma, double* V);
  * FP32 solve on the tensor-core pass: the update before that pass predicts it to be the last
  * and the pass writes its support as bit masks), the support is read from those masks and
  * D only where S_k is nonzero; otherwise two passes over D count and write it.  The
- * support is then the pass's own (its count equals the iteration statistics' nnz).
- * Synchronises the stream. */
+ * support is then the pass's own (its count equals the iteration statistics' nnz), the
+ * count is known on the host and the call returns with the writes queued on the context's
+ * stream: idx and val are ready in stream order (synchronise that stream before reading them
+ * from the host or from another stream).  Otherwise the call synchronises the stream (the
+ * count decides the capacity check) and returns with the writes done. */
 int rpca_get_sparse(rpca_ctx* ctx, int64_t* idx, double* val, int64_t cap, int64_t* nnz);
 
 /* Bit of the checkpoint flags: the passes of a BF16_SPLIT solve read hi + lo. */

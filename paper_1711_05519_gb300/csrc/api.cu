@@ -1036,6 +1036,10 @@ int rpca_get_sparse(rpca_ctx* c, int64_t* idx, double* val, int64_t cap, int64_t
     prof_mark(c, false, true);
     if (total > 0) CK(launch_extract_words_f32(c->Rr, a, c->swords, c->wcc, 2 * c->TC, c->stream));
     prof_mark(c, false, false);
+    // the count was known: return with the writes queued on the stream (their profile spans
+    // are collected at the next wait)
+    prof_break(c);
+    return RPCA_OK;
   } else {
     prof_break(c);
     prof_mark(c, false, true);
