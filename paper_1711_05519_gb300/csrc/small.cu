@@ -620,6 +620,10 @@ __device__ __noinline__ void small_svd(int N, Smem<T, WM>& sh, int max_sweeps = 
     jacobi_f32_sized<(NM < 12 ? NM : 12), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   else if (N <= 16 || NM <= 16)
     jacobi_f32_sized<(NM < 16 ? NM : 16), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
+  else if (N <= 20)
+    jacobi_f32_sized<(NM < 20 ? NM : 20), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
+  else if (N <= 24)
+    jacobi_f32_sized<(NM < 24 ? NM : 24), NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   else
     jacobi_f32_sized<NM, NM>(N, sh.M, sc, sh.pairs, xf, vf, max_sweeps);
   T sg;
