@@ -582,12 +582,13 @@ __device__ __forceinline__ void small_svd_two_lane(int N, T mx, T sc, int max_sw
 // matching left / right singular vectors (a zero singular value gives a zero left vector).
 // Single-precision one-sided Jacobi on M scaled to max |M_ij| = 1 keeps the small singular
 // values to high relative accuracy; in FP64 mode V is then re-orthonormalised in double
-// and double-precision sweeps on M V polish the result.
+// and double-precision sweeps on M V polish the result.  pairs_ready: sh.pairs already holds
+// jacobi_pairs(N).
 template <typename T, int WM>
-__device__ __noinline__ void small_svd(int N, Smem<T, WM>& sh, int max_sweeps = 12) {
+__device__ __noinline__ void small_svd(int N, Smem<T, WM>& sh, int max_sweeps = 12, bool pairs_ready = false) {
   constexpr int NM = Smem<T, WM>::NM;
   const int lane = threadIdx.x & 31;
-  jacobi_pairs(N, sh.pairs);
+  if (!pairs_ready) jacobi_pairs(N, sh.pairs);
   T mx = T(0);
   for (int e = lane; e < N * N; e += 32) mx = fmax(mx, fabs(sh.M[(e / N) * NM + (e % N)]));
 #pragma unroll
@@ -1228,6 +1229,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
         __syncwarp();
         factor_warp<T, WM>(sh.G[2], r, sh.Rf[0], sh.Tf[0]);
       }
+      if (wp == 2) jacobi_pairs(2 * r, sh.pairs);  // the pairing of the SVD below
     }
   };
   if (!grid_barrier(st, sh, warm)) return;
@@ -1251,7 +1253,7 @@ __device__ void mode_update(const SmallArgs& a, Smem<T, WM>& sh) {
   if constexpr (sizeof(T) == 8)
     small_svd_d<T, WM>(N, sh);
   else if (t < 32)
-    small_svd<T, WM>(N, sh);
+    small_svd<T, WM>(N, sh, 12, true);
   __syncthreads();
   // update matrices: side 0 acts on [U~ W1], side 1 on [V~ W2]; rows q < r take the top block
   // of U_M (V_M), rows r + q the bottom block premultiplied by T1 (T2)
@@ -1547,7 +1549,13 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
     if (!side) gram_put_h<T>(accB, w, a.part, 0, tl);
     gram_put_h<T>(accG, w, a.part, 1 + side, tl);
   }
-  if (!grid_barrier(st, sh)) return;
+  // while thread 0 waits: the pairing of the SVD below (warp 2)
+  auto pairs = [&]() {
+    if constexpr (sizeof(T) == 4) {
+      if ((t >> 5) == 2) jacobi_pairs(w, sh.pairs);
+    }
+  };
+  if (!grid_barrier(st, sh, pairs)) return;
 
   // B: SVD of B (warp 0) while warps 1, 2 factor Y1^T Y1 and Y2^T Y2; Ritz vectors,
   // residuals, first CholeskyQR pass of Y1, Y2
@@ -1559,7 +1567,7 @@ __device__ void mode_rr(const SmallArgs& a, Smem<T, WM>& sh) {
   __syncthreads();
   {
     const int warp = t >> 5;
-    if (warp == 0) small_svd<T, WM>(w, sh);
+    if (warp == 0) small_svd<T, WM>(w, sh, 12, sizeof(T) == 4);
     if (warp == 1) factor_one<T, WM>(sh.G[1], w, 0, sh);
     if (warp == 2) factor_one<T, WM>(sh.G[2], w, 1, sh);
   }
