@@ -58,29 +58,46 @@ __global__ void count_observed(const T* __restrict__ D, long long ld, int m, int
   if ((threadIdx.x & 31) == 0) atomicAdd(count, c);
 }
 
-// Exclusive scan of m row counts into m+1 offsets, one block of 1024 threads.
+// Exclusive scan of m row counts into m+1 offsets, one block of 1024 threads.  Warp w owns
+// the contiguous rows [w seg, (w + 1) seg) (seg a multiple of 32): it sums them with
+// coalesced loads, the 32 warp totals are scanned by warp 0, and each warp then walks its
+// rows 32 at a time with a shuffle scan.
 __global__ void __launch_bounds__(1024) scan_rows(const unsigned long long* __restrict__ cnt,
                                                   unsigned long long* __restrict__ off, int m) {
-  __shared__ unsigned long long part[1024];
-  const int t = threadIdx.x;
-  const int chunk = (m + 1023) / 1024;
-  const int lo = min(m, t * chunk), hi = min(m, lo + chunk);
+  __shared__ unsigned long long wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int seg = ((m + 1023) / 1024) * 32;
+  const int lo = min(m, w * seg), hi = min(m, lo + seg);
   unsigned long long s = 0;
-  for (int i = lo; i < hi; ++i) s += cnt[i];
-  part[t] = s;
+  for (int i = lo + lane; i < hi; i += 32) s += cnt[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) wsum[w] = s;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
-    const unsigned long long v = (t >= o) ? part[t - o] : 0ull;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  if (w == 0) {
+    unsigned long long v = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    wsum[lane] = v;  // inclusive
   }
-  unsigned long long run = (t == 0) ? 0ull : part[t - 1];
-  for (int i = lo; i < hi; ++i) {
-    off[i] = run;
-    run += cnt[i];
+  __syncthreads();
+  unsigned long long base = (w == 0) ? 0ull : wsum[w - 1];
+  for (int i0 = lo; i0 < hi; i0 += 32) {
+    const int i = i0 + lane;
+    const unsigned long long c = (i < hi) ? cnt[i] : 0ull;
+    unsigned long long v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (i < hi) off[i] = base + v - c;
+    base += __shfl_sync(0xffffffffu, v, 31);
   }
-  if (t == 1023) off[m] = part[1023];
+  if (threadIdx.x == 0) off[m] = wsum[31];
 }
 
 // Support counts per row and per chunk of kWordChunk words ([word][row] layout): one warp per
