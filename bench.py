@@ -8,8 +8,10 @@ beta = 1.1 mu r / (2 sqrt(mn)), beta_init = 2 beta, gamma = 0.5, tol = 1e-5.
 One step = one solve to tolerance from D resident in HBM: Algorithm 3 (initialisation)
 plus Algorithm 1 until err_k < 1e-5, and the sparse output S_k (ascending linear indices and
 values, in device memory).  `value` is the time per solve (ms, lower is
-better); the per-iteration HBM bandwidth of the fused pass goes in `roofline`.  D
-(400 MB) is larger than L2 (129 MB), so no L2 flush is needed between passes.
+better); the per-iteration HBM bandwidth of the fused pass goes in `roofline`, from CUDA
+events around every fourth fused pass of the timed steps (events at every kernel boundary
+would add ~2 us to each boundary).  D (400 MB) is larger than L2 (129 MB), so no L2 flush is
+needed between passes.
 
 `e2e` times the public host-buffer entry point rpca_solve_host: the 400 MB host-to-device
 copy of D, the solve, the sparse extraction and the device-to-host copies of U, sigma, V
